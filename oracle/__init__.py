@@ -1,0 +1,301 @@
+"""TEST INFRASTRUCTURE ONLY: Python access to the FP64 CPU oracle.
+
+The oracle (``rossbi_oracle.cpp``) is a plain, slow restatement of one
+RoSSBi3D time step written from the paper.  Only ``tests/``,
+``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may import this
+package.  It imports nothing from the CUDA package; the two share only the
+seeded inputs of ``synthetic``.
+
+The initial-condition recipes below are this side's own restatement of the
+workload descriptions in ``synthetic.workloads``.
+"""
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+
+import synthetic as syn
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rossbi_oracle.cpp")
+_LIB = os.path.join(_HERE, "_build", "librossbi_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with the host C++ compiler (FP contraction off)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    tmp = f"{_LIB}.{os.getpid()}.tmp"
+    subprocess.check_call(["g++", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c++17",
+                           "-o", tmp, _SRC])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("geometry", ctypes.c_int), ("nr", ctypes.c_int), ("nth", ctypes.c_int), ("nz", ctypes.c_int),
+                ("x0", ctypes.c_double * 3), ("x1", ctypes.c_double * 3),
+                ("bc_lo", ctypes.c_int * 3), ("bc_hi", ctypes.c_int * 3),
+                ("gamma", ctypes.c_double), ("gm", ctypes.c_double), ("omega_frame", ctypes.c_double),
+                ("cfl", ctypes.c_double), ("n_dust", ctypes.c_int)]
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_L = ctypes.POINTER(ctypes.c_long)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        L.orc_create.restype = ctypes.c_void_p
+        L.orc_create.argtypes = [ctypes.POINTER(_Desc)]
+        L.orc_destroy.argtypes = [ctypes.c_void_p]
+        L.orc_nfields.argtypes = [ctypes.c_void_p]
+        L.orc_set_equilibrium.argtypes = [ctypes.c_void_p, _D]
+        L.orc_equilibrium_state.argtypes = [ctypes.c_void_p, _D]
+        L.orc_eq_prim.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, _D]
+        L.orc_coords.argtypes = [ctypes.c_void_p, ctypes.c_int, _D, _D]
+        L.orc_metric.argtypes = [ctypes.c_void_p, ctypes.c_int, _D]
+        L.orc_rhs.argtypes = [ctypes.c_void_p, _D, _D]
+        L.orc_stage.argtypes = [ctypes.c_void_p, _D, _D, _D, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+        L.orc_step.argtypes = [ctypes.c_void_p, _D, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+        L.orc_step_sampled.argtypes = [ctypes.c_void_p, _D, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                       _L, ctypes.c_long, _D]
+        L.orc_cfl_dt.restype = ctypes.c_double
+        L.orc_cfl_dt.argtypes = [ctypes.c_void_p, _D]
+        L.orc_sums.argtypes = [ctypes.c_void_p, _D, _D]
+        L.orc_counters.argtypes = [ctypes.c_void_p, _L]
+        L.orc_riemann.argtypes = [ctypes.c_double, _D, _D, ctypes.c_double, _D, _D]
+        L.orc_parabola.argtypes = [ctypes.c_double] * 8 + [_D]
+        L.orc_gas_flux.argtypes = [ctypes.c_void_p, ctypes.c_int, _D, _D, _D]
+        L.orc_dust_flux.argtypes = [ctypes.c_int, _D, _D, _D]
+        L.orc_drag.argtypes = [ctypes.c_void_p, ctypes.c_int, _D, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+        L.orc_status.argtypes = [ctypes.c_void_p]
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_D)
+
+
+def riemann(gamma, WL, WR, S=0.0):
+    """Exact Riemann solution sampled at x/t = S: ((rho, u, p), p*, u*, iters, converged, side, vacuum)."""
+    wl = np.ascontiguousarray(WL, dtype=np.float64)
+    wr = np.ascontiguousarray(WR, dtype=np.float64)
+    W = np.zeros(3)
+    star = np.zeros(5)
+    vac = lib().orc_riemann(gamma, _p(wl), _p(wr), S, _p(W), _p(star))
+    return W, star[0], star[1], int(star[2]), bool(star[3]), int(star[4]), bool(vac)
+
+
+def parabola(em, e0, ep, xm, x0, xp, fm, fp):
+    q = np.zeros(2)
+    shaped = lib().orc_parabola(em, e0, ep, xm, x0, xp, fm, fp, _p(q))
+    return q[0], q[1], bool(shaped)
+
+
+def dust_flux(ax, UL, UR):
+    ul = np.ascontiguousarray(UL, dtype=np.float64)
+    ur = np.ascontiguousarray(UR, dtype=np.float64)
+    F = np.zeros(4)
+    lib().orc_dust_flux(ax, _p(ul), _p(ur), _p(F))
+    return F
+
+
+class Oracle:
+    """One grid of the oracle; states are float64 arrays of shape (nf, nz, nth, nr)."""
+
+    def __init__(self, w: syn.Workload):
+        self.w = w
+        d = _Desc(w.geometry, w.nr, w.nth, w.nz, (ctypes.c_double * 3)(*w.x0), (ctypes.c_double * 3)(*w.x1),
+                  (ctypes.c_int * 3)(*w.bc_lo), (ctypes.c_int * 3)(*w.bc_hi),
+                  w.gamma, w.gm, w.omega_frame, w.cfl, w.n_dust)
+        self.h = ctypes.c_void_p(lib().orc_create(ctypes.byref(d)))
+        self.nf = lib().orc_nfields(self.h)
+        self.shape = (self.nf, w.nz, w.nth, w.nr)
+        self.status = 0
+        if w.disc is not None:
+            disc = np.array(w.disc, dtype=np.float64)
+            self.status |= lib().orc_set_equilibrium(self.h, _p(disc))
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.orc_destroy(self.h)
+            self.h = None
+
+    # ---- geometry / equilibrium
+    def coords(self, ax):
+        n = (self.w.nr, self.w.nth, self.w.nz)[ax]
+        c = np.zeros(n + 6)
+        f = np.zeros(n + 7)
+        lib().orc_coords(self.h, ax, _p(c), _p(f))
+        return c[3:-3], f[3:-3]
+
+    def metric(self, i):
+        m = np.zeros(8)
+        lib().orc_metric(self.h, i, _p(m))
+        return m
+
+    def volumes(self):
+        return np.array([self.metric(i)[0] for i in range(self.w.nr)])
+
+    def eq_prim(self, r, z):
+        out = np.zeros(3)
+        lib().orc_eq_prim(self.h, r, z, _p(out))
+        return out
+
+    def equilibrium_state(self):
+        E = np.zeros(self.shape)
+        lib().orc_equilibrium_state(self.h, _p(E))
+        return E
+
+    # ---- the method
+    def rhs(self, E):
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        G = np.zeros_like(E)
+        self.status |= lib().orc_rhs(self.h, _p(E), _p(G))
+        return G
+
+    def stage(self, Ein, Ebase, tau):
+        Ein = np.ascontiguousarray(Ein, dtype=np.float64)
+        Ebase = np.ascontiguousarray(Ebase, dtype=np.float64)
+        out = np.zeros_like(Ein)
+        self.status |= lib().orc_stage(self.h, _p(Ein), _p(Ebase), _p(out), tau, self.w.stokes, self.w.drag_law)
+        return out
+
+    def step(self, E, dt):
+        """One RK2 step; returns a new array."""
+        E = np.array(E, dtype=np.float64, order="C", copy=True)
+        self.status |= lib().orc_step(self.h, _p(E), dt, self.w.stokes, self.w.drag_law)
+        return E
+
+    def step_sampled(self, E, dt, cells):
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        out = np.zeros((len(cells), self.nf))
+        self.status |= lib().orc_step_sampled(self.h, _p(E), dt, self.w.stokes, self.w.drag_law,
+                                              cells.ctypes.data_as(_L), len(cells), _p(out))
+        return out
+
+    def cfl_dt(self, E):
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        return lib().orc_cfl_dt(self.h, _p(E))
+
+    def sums(self, E):
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        s = np.zeros(self.nf)
+        lib().orc_sums(self.h, _p(E), _p(s))
+        return s
+
+    def gas_flux(self, ax, UL, UR):
+        ul = np.ascontiguousarray(UL, dtype=np.float64)
+        ur = np.ascontiguousarray(UR, dtype=np.float64)
+        F = np.zeros(5)
+        lib().orc_gas_flux(self.h, ax, _p(ul), _p(ur), _p(F))
+        return F
+
+    def drag(self, i, U, tau):
+        U = np.array(U, dtype=np.float64, copy=True)
+        lib().orc_drag(self.h, i, _p(U), tau, self.w.stokes, self.w.drag_law)
+        return U
+
+    def counters(self):
+        c = np.zeros(2, dtype=np.int64)
+        lib().orc_counters(self.h, c.ctypes.data_as(_L))
+        return c
+
+    def take_status(self):
+        s = self.status | lib().orc_status(self.h)
+        self.status = 0
+        return s
+
+    # ---- runs
+    def run(self, E, steps=None, t_end=None, dts=None):
+        """Advance with the CFL step (or the given dt list); returns (E, t, dts)."""
+        t = 0.0
+        used = []
+        if dts is not None:
+            for dt in dts:
+                E = self.step(E, dt)
+                t += dt
+                used.append(dt)
+            return E, t, used
+        n = 0
+        while True:
+            if steps is not None and n >= steps:
+                break
+            dt = self.cfl_dt(E)
+            if t_end is not None:
+                if t >= t_end * (1 - 1e-14):
+                    break
+                dt = min(dt, t_end - t)
+            E = self.step(E, dt)
+            t += dt
+            used.append(dt)
+            n += 1
+        return E, t, used
+
+
+# ---------------------------------------------------------------- initial conditions (oracle side)
+def initial_state(o: Oracle) -> np.ndarray:
+    """Full conservative initial state (nf, nz, nth, nr) for the workload, built on the oracle's
+    own equilibrium; the recipe is the one stated for each workload."""
+    w = o.w
+    nf = o.nf
+    g = w.gamma
+    E = np.zeros(o.shape)
+    if w.ic == "sod":
+        xc, _ = o.coords(0)
+        left = xc < 0.5
+        rho = np.where(left, 1.0, 0.125)
+        p = np.where(left, 1.0, 0.1)
+        E[syn.F_RHO] = rho[None, None, :]
+        E[syn.F_EN] = (p / (g - 1.0))[None, None, :]
+        return E
+    E0 = o.equilibrium_state()
+    rho0 = E0[syn.F_RHO]
+    v0 = E0[syn.F_MV] / rho0
+    E[:5] = E0[:5]
+    if w.ic == "noise":
+        xi = syn.uniform_pm1(w.seed, syn.F_RHO, w.ncell).reshape(w.nz, w.nth, w.nr)
+        drho = w.noise_amp * xi * rho0
+        E[syn.F_RHO] += drho
+        E[syn.F_MV] += drho * v0
+        E[syn.F_EN] += 0.5 * drho * v0 * v0
+    elif w.ic == "vortex":
+        r, _ = o.coords(0)
+        th, _ = o.coords(1)
+        R = r[None, None, :]
+        TH = th[None, :, None]
+        up = np.zeros((1, w.nth, w.nr))
+        vp = np.zeros((1, w.nth, w.nr))
+        for (rv, thv) in w.vortices:
+            sig_r = w.vortex_width_h * math.sqrt(2.0 * w.disc[2] * rv ** w.disc[3]) / math.sqrt(w.gm / rv ** 3)
+            sig_t = w.vortex_chi * sig_r
+            omega_c = -w.vortex_amp * 1.5 * math.sqrt(w.gm / rv ** 3)
+            psi0 = omega_c / (1.0 / sig_r ** 2 + 1.0 / sig_t ** 2)
+            dth = np.mod(TH - thv + math.pi, 2.0 * math.pi) - math.pi
+            psi = psi0 * np.exp(-(R - rv) ** 2 / (2.0 * sig_r ** 2) - (rv * dth) ** 2 / (2.0 * sig_t ** 2))
+            up += -psi * rv * rv * dth / (R * sig_t ** 2)        # (1/r) dpsi/dtheta
+            vp += psi * (R - rv) / sig_r ** 2                     # -dpsi/dr
+        E[syn.F_MU] = rho0 * up
+        E[syn.F_MV] += rho0 * vp
+        E[syn.F_EN] += 0.5 * rho0 * (up * up + 2.0 * v0 * vp + vp * vp)
+        if nf > 5:
+            xi = syn.uniform_pm1(w.seed, syn.F_DRHO, w.ncell).reshape(w.nz, w.nth, w.nr)
+            rd = w.dust_ratio * rho0 * (1.0 + w.dust_noise * xi)
+            E[syn.F_DRHO] = rd
+            E[syn.F_DMU] = rd * up
+            E[syn.F_DMV] = rd * (v0 + vp)
+            E[syn.F_DMW] = 0.0
+    else:
+        raise ValueError(w.ic)
+    return E

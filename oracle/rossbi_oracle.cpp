@@ -1,0 +1,878 @@
+// RoSSBi3D hot-path oracle: TEST INFRASTRUCTURE ONLY.
+//
+// A plain, slow, FP64 CPU restatement of one time step of the RoSSBi3D method
+// (Rendon Restrepo, Barge & Vavrik, arXiv:2207.04252).  Only the test suite,
+// the smoke check and bench.py's CPU-baseline leg may load this library.  It
+// shares no code, header, table or constant with the CUDA library; the two are
+// compared on identical seeded inputs.
+//
+// Every cell is updated on its own: the six face fluxes of a cell are computed
+// from scratch for that cell (each face is therefore evaluated twice per
+// stage, once for each neighbour, with identical inputs and identical code, so
+// the scheme stays conservative).  No blocking, fusion or reordering.
+//
+// Section numbers refer to the paper.  "Toro" is E. F. Toro, Riemann Solvers
+// and Numerical Methods for Fluid Dynamics, ch. 4, which Sect. 2.6 names as the
+// source of the exact Riemann solver.
+//
+// Readings of the paper that this file takes (the paper is silent or garbled):
+//  R1  cell centre in r is the geometric mean of its face radii (log mesh).
+//  R2  MinMod rule (Sect. 2.7 names the limiter only): flat at a local extremum
+//      of E'; if a parabolic face value leaves the interval of its two
+//      neighbouring cell values, fall back to the linear minmod slope; if a
+//      reconstructed gas face state has rho<=0 or P<=0, flatten all gas fields
+//      of that cell in that direction (dust: rho_d<0 flattens the dust fields).
+//  R3  the energy flux is (E+P)u_n (App. B prints rho(E+P)u, which is not
+//      dimensionally consistent with the governing equations of Sect. 2.1).
+//  R4  the RK2 update is E + dt*G/V (Sect. 2.5 prints a*V*dt*G; the compact
+//      form V dE/dt = G of Sect. 2.2 fixes the 1/V).
+//  R5  the pressureless dust flux is the upwind flux of a pressureless gas
+//      with delta-shock speed (sqrt(rl)ul+sqrt(rr)ur)/(sqrt(rl)+sqrt(rr)).
+//  R6  rotating frame of angular speed Omega_f: Coriolis 2 Omega_f rho v e_r -
+//      2 Omega_f rho u e_theta and centrifugal rho Omega_f^2 r e_r; the stored
+//      azimuthal velocity is frame-relative.
+//  R7  semi-implicit drag: after the explicit stage update, a closed-form
+//      backward-Euler relaxation of the gas-dust relative velocity over the
+//      stage length, conserving total momentum; the gas energy changes by the
+//      work of the drag on the gas (no frictional heating).
+//  R8  equilibrium exponent uses c_iso^2 = P/rho (App. A writes c_s^2).
+//  R9  Newton on p* stops when the relative change is <= 1e-12 (the error
+//      left after that step is far below round-off); PVRS start, floored at
+//      1e-8 min(pL, pR).
+//  R10 CFL uses the frame-relative speed; a dust cell adds cfl V/(|v_d| maxA).
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#include <unordered_map>
+#include <array>
+#include <algorithm>
+
+namespace orc {
+
+using std::sqrt;
+using std::pow;
+using std::exp;
+using std::fabs;
+
+enum { GEOM_BOX = 0, GEOM_CYL = 1 };
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_EQUILIBRIUM = 2 };
+// Conservative variables in the order of App. B: (rho u, rho v, rho w, E, rho),
+// followed by the dust fluid (rho_d u_d, rho_d v_d, rho_d w_d, rho_d).
+enum { MU = 0, MV = 1, MW = 2, EN = 3, RHO = 4, DMU = 5, DMV = 6, DMW = 7, DRHO = 8 };
+enum { ST_NONPHYSICAL = 1, ST_RIEMANN = 2 };
+
+struct Desc {
+  int geometry, nr, nth, nz;
+  double x0[3], x1[3];
+  int bc_lo[3], bc_hi[3];
+  double gamma, gm, omega_frame, cfl;
+  int n_dust;
+};
+
+static const int NG = 3;  // ghost layers kept in the coordinate tables
+
+struct Oracle {
+  Desc d;
+  int n[3];
+  int nf;
+  long ncell;
+  std::vector<double> xc[3], xf[3];  // centre / lower face of cell c at [c + NG]
+  bool has_eq = false;
+  double sigma0 = 0, beta_sigma = 0, T0 = 0, beta_T = 0;
+  // equilibrium conservative gas state (5 values) at centres, r faces and z faces,
+  // over the index ranges extended by NG ghosts
+  std::vector<double> e0c, e0r, e0z;
+  std::vector<double> r0;  // balanced-scheme residual G(E0), nf x ncell
+  int status = 0;
+  long newton_iters = 0, riemann_calls = 0;
+};
+
+// ---------------------------------------------------------------- geometry
+// Sect. 2.3: logarithmic spacing in r, uniform in theta and z.  The Box option
+// (Sect. 2.11, Table of options) is uniform in x, y, z.
+static double face_coord(const Oracle& o, int ax, int c) {
+  if (o.d.geometry == GEOM_CYL && ax == 0)
+    return o.d.x0[0] * pow(o.d.x1[0] / o.d.x0[0], (double)c / o.n[0]);
+  return o.d.x0[ax] + (o.d.x1[ax] - o.d.x0[ax]) * c / o.n[ax];
+}
+static double centre_coord(const Oracle& o, int ax, int c) {
+  if (o.d.geometry == GEOM_CYL && ax == 0) return sqrt(face_coord(o, 0, c) * face_coord(o, 0, c + 1));
+  return 0.5 * (face_coord(o, ax, c) + face_coord(o, ax, c + 1));
+}
+static inline double XC(const Oracle& o, int ax, int c) { return o.xc[ax][c + NG]; }
+static inline double XF(const Oracle& o, int ax, int c) { return o.xf[ax][c + NG]; }
+
+struct Metric {
+  double V, A_lo[3], A_hi[3], maxA;
+};
+// Sect. 2.2: cell volume and face areas of the finite-volume cell.
+static Metric metric(const Oracle& o, int i) {
+  Metric m;
+  const double dy = (o.d.x1[1] - o.d.x0[1]) / o.n[1];
+  const double dz = (o.d.x1[2] - o.d.x0[2]) / o.n[2];
+  if (o.d.geometry == GEOM_CYL) {
+    const double rm = XF(o, 0, i), rp = XF(o, 0, i + 1);
+    m.V = 0.5 * (rp * rp - rm * rm) * dy * dz;
+    m.A_lo[0] = rm * dy * dz;
+    m.A_hi[0] = rp * dy * dz;
+    m.A_lo[1] = m.A_hi[1] = (rp - rm) * dz;
+    m.A_lo[2] = m.A_hi[2] = 0.5 * (rp * rp - rm * rm) * dy;
+    m.maxA = std::max(m.A_hi[0], std::max(m.A_hi[1], m.A_hi[2]));
+  } else {
+    const double dx = (o.d.x1[0] - o.d.x0[0]) / o.n[0];
+    m.V = dx * dy * dz;
+    m.A_lo[0] = m.A_hi[0] = dy * dz;
+    m.A_lo[1] = m.A_hi[1] = dx * dz;
+    m.A_lo[2] = m.A_hi[2] = dx * dy;
+    m.maxA = std::max(m.A_hi[0], std::max(m.A_hi[1], m.A_hi[2]));
+  }
+  return m;
+}
+
+// ---------------------------------------------------------------- equilibrium
+// App. A: axisymmetric, locally isothermal gas in Keplerian rotation and
+// vertical hydrostatic balance; code units GM = gm, k_B/(mu m_u) = 1.
+static void eq_prim(const Oracle& o, double r, double z, double& rho, double& vth, double& p) {
+  const double gm = o.d.gm;
+  const double cs2 = o.T0 * pow(r, o.beta_T);     // T(r) = c_iso^2
+  const double omk = sqrt(gm / (r * r * r));      // Omega_K(r)
+  const double H = sqrt(2.0 * cs2) / omk;         // H = sqrt(2/gamma) c_s / Omega_K, c_s^2 = gamma c_iso^2
+  const double R = sqrt(r * r + z * z);
+  const double g = 1.0 / R - 1.0 / r;
+  rho = o.sigma0 * pow(r, o.beta_sigma) / (sqrt(M_PI) * H) * exp(gm / cs2 * g);
+  p = cs2 * rho;
+  // d ln P0 / dr, differentiated by hand from the expressions above
+  const double dlnp = (o.beta_T + o.beta_sigma - 0.5 * (o.beta_T + 3.0)) / r +
+                      gm / cs2 * (-o.beta_T * g / r - r / (R * R * R) + 1.0 / (r * r));
+  // v_theta0^2 = -r f_star,r + (r/rho) dP/dr
+  vth = sqrt(gm * r * r / (R * R * R) + r * cs2 * dlnp);
+}
+// Conservative equilibrium state in the rotating frame (reading R6).
+static void eq_cons(const Oracle& o, double r, double z, double U[5]) {
+  double rho, vth, p;
+  eq_prim(o, r, z, rho, vth, p);
+  const double v = vth - o.d.omega_frame * r;
+  U[MU] = 0.0;
+  U[MV] = rho * v;
+  U[MW] = 0.0;
+  U[EN] = 0.5 * rho * v * v + p / (o.d.gamma - 1.0);
+  U[RHO] = rho;
+}
+static inline const double* E0C(const Oracle& o, int i, int k) {
+  return &o.e0c[((size_t)(k + NG) * (o.n[0] + 2 * NG) + (i + NG)) * 5];
+}
+static inline const double* E0R(const Oracle& o, int iface, int k) {
+  return &o.e0r[((size_t)(k + NG) * (o.n[0] + 2 * NG + 1) + (iface + NG)) * 5];
+}
+static inline const double* E0Z(const Oracle& o, int i, int kface) {
+  return &o.e0z[((size_t)(kface + NG) * (o.n[0] + 2 * NG) + (i + NG)) * 5];
+}
+
+// ---------------------------------------------------------------- state access
+struct ArrAcc {
+  const double* E;
+  long ncell;
+  double get(int f, long lin) const { return E[(size_t)f * ncell + lin]; }
+};
+
+// Deviation E' = E - E0 (Sect. 2.7) of field f at cell (i, j, k); at most one
+// index may lie outside the domain, where the ghost rule of Sect. 2.4 applies:
+// equilibrium ghosts carry E' = 0, periodic ghosts wrap, outflow ghosts copy
+// the nearest interior deviation.
+template <class Acc>
+static double dev(const Oracle& o, const Acc& E, int f, int i, int j, int k) {
+  int c[3] = {i, j, k};
+  for (int ax = 0; ax < 3; ++ax) {
+    if (c[ax] >= 0 && c[ax] < o.n[ax]) continue;
+    const int bc = c[ax] < 0 ? o.d.bc_lo[ax] : o.d.bc_hi[ax];
+    if (bc == BC_EQUILIBRIUM) return 0.0;
+    if (bc == BC_PERIODIC)
+      c[ax] = ((c[ax] % o.n[ax]) + o.n[ax]) % o.n[ax];
+    else
+      c[ax] = c[ax] < 0 ? 0 : o.n[ax] - 1;
+  }
+  const long lin = ((long)c[2] * o.n[1] + c[1]) * o.n[0] + c[0];
+  double e = E.get(f, lin);
+  if (f < 5 && o.has_eq) e -= E0C(o, c[0], c[2])[f];
+  return e;
+}
+
+// ---------------------------------------------------------------- reconstruction
+static inline bool between(double q, double a, double b) {
+  const double lo = a < b ? a : b, hi = a < b ? b : a;
+  return q >= lo && q <= hi;
+}
+// Sect. 2.7: the parabola through the three cell values of E' at the centre
+// coordinates xm < x0 < xp, evaluated at the faces fm, fp of the middle cell.
+// a and b are the paper's coefficients, with the slopes nabla E'(i) = sm and
+// nabla E'(i+1) = sp.  Returns false when the result is flat.
+static bool parabola(double em, double e0, double ep, double xm, double x0, double xp, double fm, double fp,
+                     double& qm, double& qp) {
+  const double sm = (e0 - em) / (x0 - xm);
+  const double sp = (ep - e0) / (xp - x0);
+  if (sm * sp <= 0.0) {  // R2: local extremum of E' -> flat
+    qm = qp = e0;
+    return false;
+  }
+  const double a = (sp - sm) / (xp - xm);
+  const double b = (sp * (x0 - xm) + sm * (xp - x0)) / (xp - xm);
+  const double dm = fm - x0, dp = fp - x0;
+  qm = e0 + a * dm * dm + b * dm;
+  qp = e0 + a * dp * dp + b * dp;
+  if (!between(qp, e0, ep) || !between(qm, em, e0)) {  // R2: minmod slope
+    const double s = fabs(sm) < fabs(sp) ? sm : sp;
+    qm = e0 + s * dm;
+    qp = e0 + s * dp;
+  }
+  return true;
+}
+
+static inline double pressure(double g, const double* U) {
+  return (g - 1.0) * (U[EN] - 0.5 * (U[MU] * U[MU] + U[MV] * U[MV] + U[MW] * U[MW]) / U[RHO]);
+}
+
+// Equilibrium gas state (5 values) on face `fc` (the lower face of cell fc)
+// along axis ax, for a cell with radial index i and vertical index k.
+static void eq_face(const Oracle& o, int ax, int i, int k, int fc, double e0[5]) {
+  if (!o.has_eq) {
+    for (int f = 0; f < 5; ++f) e0[f] = 0.0;
+    return;
+  }
+  const double* s = ax == 0 ? E0R(o, fc, k) : ax == 1 ? E0C(o, i, k) : E0Z(o, i, fc);
+  for (int f = 0; f < 5; ++f) e0[f] = s[f];
+}
+
+// Face deviations q- (lower face) and q+ (upper face) of cell `cell` along ax.
+template <class Acc>
+static void recon(const Oracle& o, const Acc& E, int ax, const int cell[3], double qm[9], double qp[9]) {
+  int cm[3] = {cell[0], cell[1], cell[2]}, cp[3] = {cell[0], cell[1], cell[2]};
+  cm[ax] -= 1;
+  cp[ax] += 1;
+  const int c = cell[ax];
+  const double xm = XC(o, ax, c - 1), x0 = XC(o, ax, c), xp = XC(o, ax, c + 1);
+  const double fm = XF(o, ax, c), fp = XF(o, ax, c + 1);
+  double ec[9];
+  bool gas_shaped = false, dust_shaped = false;
+  for (int f = 0; f < o.nf; ++f) {
+    const double em = dev(o, E, f, cm[0], cm[1], cm[2]);
+    ec[f] = dev(o, E, f, cell[0], cell[1], cell[2]);
+    const double ep = dev(o, E, f, cp[0], cp[1], cp[2]);
+    const bool shaped = parabola(em, ec[f], ep, xm, x0, xp, fm, fp, qm[f], qp[f]);
+    if (f < 5) gas_shaped |= shaped;
+    else dust_shaped |= shaped;
+  }
+  if (gas_shaped) {  // R2 (iii): positivity of both reconstructed gas face states
+    double e0m[5], e0p[5], Um[5], Up[5];
+    eq_face(o, ax, cell[0], cell[2], c, e0m);
+    eq_face(o, ax, cell[0], cell[2], c + 1, e0p);
+    for (int f = 0; f < 5; ++f) {
+      Um[f] = e0m[f] + qm[f];
+      Up[f] = e0p[f] + qp[f];
+    }
+    const bool ok = Um[RHO] > 0.0 && Up[RHO] > 0.0 && pressure(o.d.gamma, Um) > 0.0 && pressure(o.d.gamma, Up) > 0.0;
+    if (!ok)
+      for (int f = 0; f < 5; ++f) qm[f] = qp[f] = ec[f];
+  }
+  if (dust_shaped && (qm[DRHO] < 0.0 || qp[DRHO] < 0.0))
+    for (int f = 5; f < o.nf; ++f) qm[f] = qp[f] = ec[f];
+}
+
+// ---------------------------------------------------------------- exact Riemann solver (Toro)
+struct Side {
+  double rho, u, p, c;
+};
+// Pressure function f_K(p) of the star-region pressure and its derivative
+// (Toro ch. 4.2-4.3): rarefaction branch for p <= p_K, shock branch above.
+static void prefun(double g, const Side& K, double p, double& f, double& fd) {
+  if (p <= K.p) {  // rarefaction
+    const double prat = p / K.p;
+    f = 2.0 * K.c / (g - 1.0) * (pow(prat, (g - 1.0) / (2.0 * g)) - 1.0);
+    fd = 1.0 / (K.rho * K.c) * pow(prat, -(g + 1.0) / (2.0 * g));
+  } else {  // shock
+    const double A = 2.0 / ((g + 1.0) * K.rho);
+    const double B = (g - 1.0) / (g + 1.0) * K.p;
+    const double q = sqrt(A / (B + p));
+    f = (p - K.p) * q;
+    fd = (1.0 - 0.5 * (p - K.p) / (B + p)) * q;
+  }
+}
+
+struct RiemannResult {
+  double rho, u, p;   // state at x/t = S
+  int side;           // -1: left of the contact, +1: right, 0: vacuum
+  double pstar, ustar;
+  int iters;
+  bool converged, vacuum;
+};
+
+static void fan_left(double g, const Side& L, double S, double& rho, double& u, double& p) {
+  const double c = 2.0 / (g + 1.0) * (L.c + 0.5 * (g - 1.0) * (L.u - S));
+  u = 2.0 / (g + 1.0) * (L.c + 0.5 * (g - 1.0) * L.u + S);
+  rho = L.rho * pow(c / L.c, 2.0 / (g - 1.0));
+  p = L.p * pow(c / L.c, 2.0 * g / (g - 1.0));
+}
+static void fan_right(double g, const Side& R, double S, double& rho, double& u, double& p) {
+  const double c = 2.0 / (g + 1.0) * (R.c - 0.5 * (g - 1.0) * (R.u - S));
+  u = 2.0 / (g + 1.0) * (-R.c + 0.5 * (g - 1.0) * R.u + S);
+  rho = R.rho * pow(c / R.c, 2.0 / (g - 1.0));
+  p = R.p * pow(c / R.c, 2.0 * g / (g - 1.0));
+}
+
+// Sect. 2.6 / Toro ch. 4: exact solution of the Riemann problem between the
+// primitive states L and R, sampled at x/t = S.
+static RiemannResult riemann(double g, double rl, double ul, double pl, double rr, double ur, double pr, double S) {
+  RiemannResult out{};
+  const Side L{rl, ul, pl, sqrt(g * pl / rl)};
+  const Side R{rr, ur, pr, sqrt(g * pr / rr)};
+  if (2.0 / (g - 1.0) * (L.c + R.c) <= R.u - L.u) {  // vacuum generated (Toro 4.6)
+    out.vacuum = true;
+    out.converged = true;
+    const double sl_star = L.u + 2.0 * L.c / (g - 1.0);
+    const double sr_star = R.u - 2.0 * R.c / (g - 1.0);
+    out.pstar = 0.0;
+    out.ustar = 0.0;
+    if (S <= sl_star) {
+      out.side = -1;
+      if (S <= L.u - L.c) { out.rho = L.rho; out.u = L.u; out.p = L.p; }
+      else fan_left(g, L, S, out.rho, out.u, out.p);
+    } else if (S >= sr_star) {
+      out.side = 1;
+      if (S >= R.u + R.c) { out.rho = R.rho; out.u = R.u; out.p = R.p; }
+      else fan_right(g, R, S, out.rho, out.u, out.p);
+    } else {
+      out.side = 0;
+      out.rho = out.u = out.p = 0.0;
+    }
+    return out;
+  }
+  // Newton iteration on the star pressure (reading R9)
+  const double floor_p = 1e-8 * std::min(pl, pr);
+  double p = 0.5 * (pl + pr) - 0.125 * (ur - ul) * (rl + rr) * (L.c + R.c);  // PVRS
+  if (p < floor_p) p = floor_p;
+  double fl, fdl, fr, fdr;
+  int it = 0;
+  bool conv = false;
+  for (it = 1; it <= 100; ++it) {
+    prefun(g, L, p, fl, fdl);
+    prefun(g, R, p, fr, fdr);
+    double pn = p - (fl + fr + ur - ul) / (fdl + fdr);
+    if (pn < floor_p) pn = floor_p;
+    const double change = 2.0 * fabs(pn - p) / (pn + p);
+    p = pn;
+    if (change <= 1e-12) {
+      conv = true;
+      break;
+    }
+  }
+  prefun(g, L, p, fl, fdl);
+  prefun(g, R, p, fr, fdr);
+  const double us = 0.5 * (ul + ur) + 0.5 * (fr - fl);
+  out.pstar = p;
+  out.ustar = us;
+  out.iters = it;
+  out.converged = conv;
+  // sampling (Toro 4.5)
+  if (S <= us) {
+    out.side = -1;
+    if (p <= pl) {  // left rarefaction
+      const double shl = ul - L.c;
+      if (S <= shl) { out.rho = rl; out.u = ul; out.p = pl; }
+      else {
+        const double cml = L.c * pow(p / pl, (g - 1.0) / (2.0 * g));
+        const double stl = us - cml;
+        if (S > stl) { out.rho = rl * pow(p / pl, 1.0 / g); out.u = us; out.p = p; }
+        else fan_left(g, L, S, out.rho, out.u, out.p);
+      }
+    } else {  // left shock
+      const double pml = p / pl;
+      const double sl = ul - L.c * sqrt((g + 1.0) / (2.0 * g) * pml + (g - 1.0) / (2.0 * g));
+      if (S <= sl) { out.rho = rl; out.u = ul; out.p = pl; }
+      else {
+        const double g6 = (g - 1.0) / (g + 1.0);
+        out.rho = rl * (pml + g6) / (pml * g6 + 1.0);
+        out.u = us;
+        out.p = p;
+      }
+    }
+  } else {
+    out.side = 1;
+    if (p > pr) {  // right shock
+      const double pmr = p / pr;
+      const double sr = ur + R.c * sqrt((g + 1.0) / (2.0 * g) * pmr + (g - 1.0) / (2.0 * g));
+      if (S >= sr) { out.rho = rr; out.u = ur; out.p = pr; }
+      else {
+        const double g6 = (g - 1.0) / (g + 1.0);
+        out.rho = rr * (pmr + g6) / (pmr * g6 + 1.0);
+        out.u = us;
+        out.p = p;
+      }
+    } else {  // right rarefaction
+      const double shr = ur + R.c;
+      if (S >= shr) { out.rho = rr; out.u = ur; out.p = pr; }
+      else {
+        const double cmr = R.c * pow(p / pr, (g - 1.0) / (2.0 * g));
+        const double str = us + cmr;
+        if (S <= str) { out.rho = rr * pow(p / pr, 1.0 / g); out.u = us; out.p = p; }
+        else fan_right(g, R, S, out.rho, out.u, out.p);
+      }
+    }
+  }
+  return out;
+}
+
+static inline void axes(int ax, int& n, int& t1, int& t2) {
+  if (ax == 0) { n = MU; t1 = MV; t2 = MW; }
+  else if (ax == 1) { n = MV; t1 = MU; t2 = MW; }
+  else { n = MW; t1 = MU; t2 = MV; }
+}
+
+// Sect. 2.6: flux F(E*) of the exact Riemann solution at the face, from the
+// reconstructed left and right conservative gas states.  Flux components of
+// App. B with the energy flux of reading R3.
+static void gas_flux(Oracle& o, int ax, const double UL[5], const double UR[5], double F[5]) {
+  const double g = o.d.gamma;
+  int n, t1, t2;
+  axes(ax, n, t1, t2);
+  for (int f = 0; f < 5; ++f) F[f] = 0.0;
+  const double rl = UL[RHO], rr = UR[RHO];
+  if (!(rl > 0.0) || !(rr > 0.0)) { o.status |= ST_NONPHYSICAL; return; }
+  const double pl = pressure(g, UL), pr = pressure(g, UR);
+  if (!(pl > 0.0) || !(pr > 0.0)) { o.status |= ST_NONPHYSICAL; return; }
+  const RiemannResult s = riemann(g, rl, UL[n] / rl, pl, rr, UR[n] / rr, pr, 0.0);
+  o.riemann_calls++;
+  o.newton_iters += s.iters;
+  if (!s.converged) o.status |= ST_RIEMANN;
+  double ut1 = 0.0, ut2 = 0.0;
+  if (s.side < 0) { ut1 = UL[t1] / rl; ut2 = UL[t2] / rl; }
+  else if (s.side > 0) { ut1 = UR[t1] / rr; ut2 = UR[t2] / rr; }
+  const double m = s.rho * s.u;
+  F[RHO] = m;
+  F[n] = m * s.u + s.p;
+  F[t1] = m * ut1;
+  F[t2] = m * ut2;
+  F[EN] = (0.5 * s.rho * (s.u * s.u + ut1 * ut1 + ut2 * ut2) + s.p / (g - 1.0) + s.p) * s.u;
+}
+
+// Sect. 2.9 / reading R5: upwind flux of the pressureless dust fluid.
+static void dust_flux(int ax, const double UL[9], const double UR[9], double F[9]) {
+  int n, t1, t2;
+  axes(ax, n, t1, t2);
+  n += 5; t1 += 5; t2 += 5;
+  const double rl = UL[DRHO], rr = UR[DRHO];
+  const double ul = rl > 0.0 ? UL[n] / rl : 0.0;
+  const double ur = rr > 0.0 ? UR[n] / rr : 0.0;
+  int pick;  // -1 left, +1 right, 0 none, 2 average
+  if (ul <= 0.0 && ur >= 0.0) pick = 0;
+  else if (ul >= 0.0 && ur >= 0.0) pick = -1;
+  else if (ul <= 0.0 && ur <= 0.0) pick = 1;
+  else {
+    const double vs = (sqrt(rl) * ul + sqrt(rr) * ur) / (sqrt(rl) + sqrt(rr));
+    pick = vs > 0.0 ? -1 : (vs < 0.0 ? 1 : 2);
+  }
+  double FL[4] = {0, 0, 0, 0}, FR[4] = {0, 0, 0, 0};
+  if (pick != 1 && rl > 0.0) {
+    const double m = rl * ul;
+    FL[0] = m; FL[1] = m * ul; FL[2] = m * UL[t1] / rl; FL[3] = m * UL[t2] / rl;
+  }
+  if (pick != -1 && rr > 0.0) {
+    const double m = rr * ur;
+    FR[0] = m; FR[1] = m * ur; FR[2] = m * UR[t1] / rr; FR[3] = m * UR[t2] / rr;
+  }
+  double Fs[4];
+  for (int q = 0; q < 4; ++q)
+    Fs[q] = pick == -1 ? FL[q] : pick == 1 ? FR[q] : pick == 2 ? 0.5 * (FL[q] + FR[q]) : 0.0;
+  F[DRHO] = Fs[0];
+  F[n] = Fs[1];
+  F[t1] = Fs[2];
+  F[t2] = Fs[3];
+}
+
+// ---------------------------------------------------------------- sources
+// App. B source vector in cylindrical coordinates, with stellar gravity
+// (Sect. 2.1) and the rotating-frame terms of reading R6; per unit volume,
+// at the cell centre.  The Box has no source terms.
+static void sources(const Oracle& o, int i, int k, const double U[9], double S[9]) {
+  for (int f = 0; f < o.nf; ++f) S[f] = 0.0;
+  if (o.d.geometry != GEOM_CYL) return;
+  const double r = XC(o, 0, i), z = XC(o, 2, k);
+  const double R2 = r * r + z * z;
+  const double R3 = R2 * sqrt(R2);
+  const double fr = -o.d.gm * r / R3, fz = -o.d.gm * z / R3;
+  const double Om = o.d.omega_frame;
+  {
+    const double rho = U[RHO];
+    const double u = U[MU] / rho, v = U[MV] / rho, w = U[MW] / rho;
+    const double P = pressure(o.d.gamma, U);
+    S[MU] = rho * v * v / r + P / r + rho * fr + 2.0 * Om * rho * v + rho * Om * Om * r;
+    S[MV] = -rho * u * v / r - 2.0 * Om * rho * u;
+    S[MW] = rho * fz;
+    S[EN] = rho * u * (fr + Om * Om * r) + rho * w * fz;
+    S[RHO] = 0.0;
+  }
+  if (o.nf > 5 && U[DRHO] > 0.0) {
+    const double rho = U[DRHO];
+    const double u = U[DMU] / rho, v = U[DMV] / rho;
+    S[DMU] = rho * v * v / r + rho * fr + 2.0 * Om * rho * v + rho * Om * Om * r;
+    S[DMV] = -rho * u * v / r - 2.0 * Om * rho * u;
+    S[DMW] = rho * fz;
+    S[DRHO] = 0.0;
+  }
+}
+
+// ---------------------------------------------------------------- G(E) per cell
+// Sect. 2.2, Eq. (compact form): G = S V - sum_faces A F.n, for one cell.
+template <class Acc>
+static void G_cell(Oracle& o, const Acc& E, int i, int j, int k, double G[9]) {
+  const Metric m = metric(o, i);
+  for (int f = 0; f < o.nf; ++f) G[f] = 0.0;
+  const int cell[3] = {i, j, k};
+  for (int ax = 0; ax < 3; ++ax) {
+    double qm_c[9], qp_c[9], qm_m[9], qp_m[9], qm_p[9], qp_p[9];
+    int cm[3] = {i, j, k}, cp[3] = {i, j, k};
+    cm[ax] -= 1;
+    cp[ax] += 1;
+    recon(o, E, ax, cm, qm_m, qp_m);
+    recon(o, E, ax, cell, qm_c, qp_c);
+    recon(o, E, ax, cp, qm_p, qp_p);
+    const int c = cell[ax];
+    for (int side = 0; side < 2; ++side) {
+      const int fc = side == 0 ? c : c + 1;           // face index (lower face of cell fc)
+      const double* ql = side == 0 ? qp_m : qp_c;     // left state of the face
+      const double* qr = side == 0 ? qm_c : qm_p;     // right state of the face
+      double e0[5], UL[9], UR[9], F[9];
+      eq_face(o, ax, i, k, fc, e0);
+      for (int f = 0; f < 5; ++f) { UL[f] = e0[f] + ql[f]; UR[f] = e0[f] + qr[f]; }
+      for (int f = 5; f < o.nf; ++f) { UL[f] = ql[f]; UR[f] = qr[f]; }
+      gas_flux(o, ax, UL, UR, F);
+      if (o.nf > 5) dust_flux(ax, UL, UR, F);
+      const double A = side == 0 ? m.A_lo[ax] : m.A_hi[ax];
+      for (int f = 0; f < o.nf; ++f) G[f] += side == 0 ? A * F[f] : -A * F[f];
+    }
+  }
+  double U[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, S[9];
+  const long lin = ((long)k * o.n[1] + j) * o.n[0] + i;
+  for (int f = 0; f < o.nf; ++f) U[f] = E.get(f, lin);
+  if (!(U[RHO] > 0.0) || !(pressure(o.d.gamma, U) > 0.0)) o.status |= ST_NONPHYSICAL;
+  if (o.nf > 5 && U[DRHO] < 0.0) o.status |= ST_NONPHYSICAL;
+  sources(o, i, k, U, S);
+  for (int f = 0; f < o.nf; ++f) G[f] += m.V * S[f];
+}
+
+// ---------------------------------------------------------------- drag
+struct DustParams {
+  double stokes;
+  int drag_law;  // 0: constant Stokes number St = t_s Omega_K(r); 1: Epstein, St fixed at (r=1, z=0)
+};
+// Sect. 2.9 drag law with the semi-implicit integration of reading R7.
+static void drag(const Oracle& o, int i, double U[9], double tau, const DustParams& dp) {
+  if (o.nf < 9) return;
+  const double rg = U[RHO], rd = U[DRHO];
+  if (!(rd > 0.0) || !(rg > 0.0)) return;
+  double ts;
+  if (dp.drag_law == 0) {
+    ts = o.d.geometry == GEOM_CYL ? dp.stokes / sqrt(o.d.gm / pow(XC(o, 0, i), 3)) : dp.stokes;
+  } else {
+    // Epstein t_s = rho_s r_p / (rho_g c_s), with rho_s r_p fixed so that St holds at r = 1, z = 0
+    double rho1, vth1, p1;
+    eq_prim(o, 1.0, 0.0, rho1, vth1, p1);
+    const double rhos_rp = dp.stokes * rho1 * sqrt(o.d.gamma * p1 / rho1) / sqrt(o.d.gm);
+    const double cs = sqrt(o.d.gamma * pressure(o.d.gamma, U) / rg);
+    ts = rhos_rp / (rg * cs);
+  }
+  const double eps = rd / rg;
+  const double kk = tau * (1.0 + eps) / ts;
+  const double mu = rg * rd / (rg + rd);
+  double dE = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    const double vg_ex = U[MU + c] / rg;
+    const double vd_ex = U[DMU + c] / rd;
+    const double X = mu * (vd_ex - vg_ex) * (kk / (1.0 + kk));
+    U[MU + c] += X;
+    U[DMU + c] -= X;
+    dE += 0.5 * X * (U[MU + c] / rg + vg_ex);
+  }
+  U[EN] += dE;
+}
+
+// One RK stage at one cell: Eout = Ebase + tau G(Ein)/V, then drag (Sect. 2.5).
+template <class Acc>
+static void stage_cell(Oracle& o, const Acc& Ein, const double* Ebase, long lin, double tau, const DustParams& dp,
+                       double out[9]) {
+  const int i = (int)(lin % o.n[0]);
+  const int j = (int)((lin / o.n[0]) % o.n[1]);
+  const int k = (int)(lin / ((long)o.n[0] * o.n[1]));
+  double G[9];
+  G_cell(o, Ein, i, j, k, G);
+  if (!o.r0.empty())
+    for (int f = 0; f < o.nf; ++f) G[f] -= o.r0[(size_t)f * o.ncell + lin];  // Sect. 2.8 balanced scheme
+  const double V = metric(o, i).V;
+  for (int f = 0; f < o.nf; ++f) out[f] = Ebase[(size_t)f * o.ncell + lin] + tau * G[f] / V;
+  drag(o, i, out, tau, dp);
+}
+
+static void stage_all(Oracle& o, const double* Ein, const double* Ebase, double* Eout, double tau,
+                      const DustParams& dp) {
+  const ArrAcc A{Ein, o.ncell};
+  double out[9];
+  for (long lin = 0; lin < o.ncell; ++lin) {
+    stage_cell(o, A, Ebase, lin, tau, dp, out);
+    for (int f = 0; f < o.nf; ++f) Eout[(size_t)f * o.ncell + lin] = out[f];
+  }
+}
+
+// Stage-1 state E* evaluated lazily, one cell at a time, for sampled checks.
+struct LazyStageAcc {
+  Oracle* o;
+  const double* En;
+  double tau;
+  DustParams dp;
+  mutable std::unordered_map<long, std::array<double, 9>> cache;
+  double get(int f, long lin) const {
+    auto it = cache.find(lin);
+    if (it == cache.end()) {
+      std::array<double, 9> v{};
+      const ArrAcc A{En, o->ncell};
+      stage_cell(*o, A, En, lin, tau, dp, v.data());
+      it = cache.emplace(lin, v).first;
+    }
+    return it->second[f];
+  }
+};
+
+static double cell_dt(const Oracle& o, const double U[9], int i) {
+  const Metric m = metric(o, i);
+  const double rho = U[RHO];
+  const double vel = sqrt(U[MU] * U[MU] + U[MV] * U[MV] + U[MW] * U[MW]) / rho;
+  const double cs = sqrt(o.d.gamma * pressure(o.d.gamma, U) / rho);
+  double dt = o.d.cfl * m.V / ((vel + cs) * m.maxA);  // Sect. 2.5, Eq. (cfl condition)
+  if (o.nf > 5 && U[DRHO] > 0.0) {
+    const double vd = sqrt(U[DMU] * U[DMU] + U[DMV] * U[DMV] + U[DMW] * U[DMW]) / U[DRHO];
+    if (vd > 0.0) dt = std::min(dt, o.d.cfl * m.V / (vd * m.maxA));
+  }
+  return dt;
+}
+
+static void build_tables(Oracle& o) {
+  const int nrx = o.n[0] + 2 * NG, nzx = o.n[2] + 2 * NG;
+  o.e0c.assign((size_t)nzx * nrx * 5, 0.0);
+  o.e0r.assign((size_t)nzx * (nrx + 1) * 5, 0.0);
+  o.e0z.assign((size_t)(nzx + 1) * nrx * 5, 0.0);
+  if (!o.has_eq) return;
+  for (int k = -NG; k < o.n[2] + NG; ++k)
+    for (int i = -NG; i < o.n[0] + NG; ++i)
+      eq_cons(o, XC(o, 0, i), XC(o, 2, k), &o.e0c[((size_t)(k + NG) * nrx + (i + NG)) * 5]);
+  for (int k = -NG; k < o.n[2] + NG; ++k)
+    for (int i = -NG; i <= o.n[0] + NG; ++i)
+      eq_cons(o, XF(o, 0, i), XC(o, 2, k), &o.e0r[((size_t)(k + NG) * (nrx + 1) + (i + NG)) * 5]);
+  for (int k = -NG; k <= o.n[2] + NG; ++k)
+    for (int i = -NG; i < o.n[0] + NG; ++i)
+      eq_cons(o, XC(o, 0, i), XF(o, 2, k), &o.e0z[((size_t)(k + NG) * nrx + (i + NG)) * 5]);
+}
+
+static void equilibrium_state(const Oracle& o, double* E) {
+  for (long lin = 0; lin < o.ncell; ++lin) {
+    const int i = (int)(lin % o.n[0]);
+    const int k = (int)(lin / ((long)o.n[0] * o.n[1]));
+    for (int f = 0; f < o.nf; ++f) E[(size_t)f * o.ncell + lin] = (f < 5 && o.has_eq) ? E0C(o, i, k)[f] : 0.0;
+  }
+}
+
+}  // namespace orc
+
+using namespace orc;
+
+extern "C" {
+
+void* orc_create(const Desc* d) {
+  Oracle* o = new Oracle();
+  o->d = *d;
+  o->n[0] = d->nr;
+  o->n[1] = d->nth;
+  o->n[2] = d->nz;
+  o->nf = 5 + (d->n_dust > 0 ? 4 : 0);
+  o->ncell = (long)d->nr * d->nth * d->nz;
+  for (int ax = 0; ax < 3; ++ax) {
+    o->xc[ax].resize(o->n[ax] + 2 * NG);
+    o->xf[ax].resize(o->n[ax] + 2 * NG + 1);
+    for (int c = -NG; c < o->n[ax] + NG; ++c) o->xc[ax][c + NG] = centre_coord(*o, ax, c);
+    for (int c = -NG; c <= o->n[ax] + NG; ++c) o->xf[ax][c + NG] = face_coord(*o, ax, c);
+  }
+  build_tables(*o);
+  return o;
+}
+
+void orc_destroy(void* h) { delete (Oracle*)h; }
+
+int orc_nfields(void* h) { return ((Oracle*)h)->nf; }
+
+// Sets the disc equilibrium (App. A) and runs the empty run of Sect. 2.8.
+// disc = {sigma0, beta_sigma, T0, beta_T}, or NULL for no equilibrium.
+int orc_set_equilibrium(void* h, const double* disc) {
+  Oracle& o = *(Oracle*)h;
+  o.has_eq = disc != nullptr;
+  if (disc) {
+    o.sigma0 = disc[0];
+    o.beta_sigma = disc[1];
+    o.T0 = disc[2];
+    o.beta_T = disc[3];
+  }
+  build_tables(o);
+  o.r0.clear();
+  if (!o.has_eq) return 0;
+  std::vector<double> E0((size_t)o.nf * o.ncell), R((size_t)o.nf * o.ncell);
+  equilibrium_state(o, E0.data());
+  const ArrAcc A{E0.data(), o.ncell};
+  double G[9];
+  for (long lin = 0; lin < o.ncell; ++lin) {
+    const int i = (int)(lin % o.n[0]);
+    const int j = (int)((lin / o.n[0]) % o.n[1]);
+    const int k = (int)(lin / ((long)o.n[0] * o.n[1]));
+    G_cell(o, A, i, j, k, G);
+    for (int f = 0; f < o.nf; ++f) R[(size_t)f * o.ncell + lin] = G[f];
+  }
+  o.r0.swap(R);
+  const int st = o.status;
+  o.status = 0;
+  return st;
+}
+
+void orc_equilibrium_state(void* h, double* E) { equilibrium_state(*(Oracle*)h, E); }
+
+void orc_eq_prim(void* h, double r, double z, double* out) {
+  eq_prim(*(Oracle*)h, r, z, out[0], out[1], out[2]);
+}
+
+void orc_coords(void* h, int ax, double* centres, double* faces) {
+  const Oracle& o = *(Oracle*)h;
+  for (int c = 0; c < o.n[ax] + 2 * NG; ++c) centres[c] = o.xc[ax][c];
+  for (int c = 0; c <= o.n[ax] + 2 * NG; ++c) faces[c] = o.xf[ax][c];
+}
+
+void orc_metric(void* h, int i, double* out /* V, A_lo[3], A_hi[3], maxA */) {
+  const Metric m = metric(*(Oracle*)h, i);
+  out[0] = m.V;
+  for (int a = 0; a < 3; ++a) { out[1 + a] = m.A_lo[a]; out[4 + a] = m.A_hi[a]; }
+  out[7] = m.maxA;
+}
+
+// Balanced right-hand side G(E) - R0 for every cell (no drag).
+int orc_rhs(void* h, const double* E, double* G) {
+  Oracle& o = *(Oracle*)h;
+  const ArrAcc A{E, o.ncell};
+  double g[9];
+  for (long lin = 0; lin < o.ncell; ++lin) {
+    const int i = (int)(lin % o.n[0]);
+    const int j = (int)((lin / o.n[0]) % o.n[1]);
+    const int k = (int)(lin / ((long)o.n[0] * o.n[1]));
+    G_cell(o, A, i, j, k, g);
+    for (int f = 0; f < o.nf; ++f)
+      G[(size_t)f * o.ncell + lin] = g[f] - (o.r0.empty() ? 0.0 : o.r0[(size_t)f * o.ncell + lin]);
+  }
+  const int st = o.status;
+  o.status = 0;
+  return st;
+}
+
+int orc_stage(void* h, const double* Ein, const double* Ebase, double* Eout, double tau, double stokes, int law) {
+  Oracle& o = *(Oracle*)h;
+  stage_all(o, Ein, Ebase, Eout, tau, DustParams{stokes, law});
+  const int st = o.status;
+  o.status = 0;
+  return st;
+}
+
+// Sect. 2.5: midpoint RK2, E^{n+1} = E^n + dt G(E^n + dt/2 G(E^n)/V)/V, in place.
+int orc_step(void* h, double* E, double dt, double stokes, int law) {
+  Oracle& o = *(Oracle*)h;
+  const DustParams dp{stokes, law};
+  std::vector<double> Es((size_t)o.nf * o.ncell), En((size_t)o.nf * o.ncell);
+  stage_all(o, E, E, Es.data(), 0.5 * dt, dp);
+  stage_all(o, Es.data(), E, En.data(), dt, dp);
+  std::memcpy(E, En.data(), sizeof(double) * En.size());
+  const int st = o.status;
+  o.status = 0;
+  return st;
+}
+
+// One RK2 step evaluated only at the listed cells (linear indices); out is
+// ncells x nf.  E* is evaluated lazily on the neighbourhood the stencil needs.
+int orc_step_sampled(void* h, const double* E, double dt, double stokes, int law, const long* cells, long ncells,
+                     double* out) {
+  Oracle& o = *(Oracle*)h;
+  const DustParams dp{stokes, law};
+  LazyStageAcc S{&o, E, 0.5 * dt, dp, {}};
+  for (long s = 0; s < ncells; ++s) stage_cell(o, S, E, cells[s], dt, dp, out + (size_t)s * o.nf);
+  const int st = o.status;
+  o.status = 0;
+  return st;
+}
+
+double orc_cfl_dt(void* h, const double* E) {
+  const Oracle& o = *(Oracle*)h;
+  double dt = INFINITY, U[9];
+  for (long lin = 0; lin < o.ncell; ++lin) {
+    for (int f = 0; f < o.nf; ++f) U[f] = E[(size_t)f * o.ncell + lin];
+    dt = std::min(dt, cell_dt(o, U, (int)(lin % o.n[0])));
+  }
+  return dt;
+}
+
+void orc_sums(void* h, const double* E, double* sums) {
+  const Oracle& o = *(Oracle*)h;
+  for (int f = 0; f < o.nf; ++f) {
+    double s = 0.0;
+    for (long lin = 0; lin < o.ncell; ++lin) s += metric(o, (int)(lin % o.n[0])).V * E[(size_t)f * o.ncell + lin];
+    sums[f] = s;
+  }
+}
+
+void orc_counters(void* h, long* out) {
+  const Oracle& o = *(Oracle*)h;
+  out[0] = o.riemann_calls;
+  out[1] = o.newton_iters;
+}
+
+// ---- single-function entry points used by the pins ----
+int orc_riemann(double gamma, const double* WL, const double* WR, double S, double* W, double* star) {
+  const RiemannResult r = riemann(gamma, WL[0], WL[1], WL[2], WR[0], WR[1], WR[2], S);
+  W[0] = r.rho;
+  W[1] = r.u;
+  W[2] = r.p;
+  star[0] = r.pstar;
+  star[1] = r.ustar;
+  star[2] = r.iters;
+  star[3] = r.converged ? 1.0 : 0.0;
+  star[4] = r.side;
+  return r.vacuum ? 1 : 0;
+}
+
+int orc_parabola(double em, double e0, double ep, double xm, double x0, double xp, double fm, double fp,
+                 double* q) {
+  return parabola(em, e0, ep, xm, x0, xp, fm, fp, q[0], q[1]) ? 1 : 0;
+}
+
+void orc_gas_flux(void* h, int ax, const double* UL, const double* UR, double* F) {
+  gas_flux(*(Oracle*)h, ax, UL, UR, F);
+}
+
+// UL, UR, F: the four dust fields (rho_d u_d, rho_d v_d, rho_d w_d, rho_d).
+void orc_dust_flux(int ax, const double* UL, const double* UR, double* F) {
+  double F9[9] = {0}, L9[9] = {0}, R9[9] = {0};
+  for (int f = 0; f < 4; ++f) { L9[5 + f] = UL[f]; R9[5 + f] = UR[f]; }
+  dust_flux(ax, L9, R9, F9);
+  for (int f = 5; f < 9; ++f) F[f - 5] = F9[f];
+}
+
+void orc_drag(void* h, int i, double* U, double tau, double stokes, int law) {
+  drag(*(Oracle*)h, i, U, tau, DustParams{stokes, law});
+}
+
+int orc_status(void* h) {
+  Oracle& o = *(Oracle*)h;
+  const int st = o.status;
+  o.status = 0;
+  return st;
+}
+
+}  // extern "C"

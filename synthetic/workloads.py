@@ -1,0 +1,120 @@
+"""Workload descriptions: the synthetic stand-ins for the paper's test problems.
+
+The paper's own workloads (Sect. 4: cylindrical explosion, equilibrium disc,
+Rossby-wave vortices, dust trapping; the "column Gaussian vortex" of its
+scaling runs) use no public dataset.  These five describe the sizes, extents,
+parameters and seeds of the synthetic inputs; the initial-condition recipe is
+written out independently by each side.
+
+Disc parameters: aspect ratio h = H/r = 0.05 with T ~ r^-1, so the locally
+isothermal temperature normalisation is T0 = h^2/2; Sigma ~ r^-0.5; gamma = 1.4;
+GM = 1; the frame rotates at Omega_K(r=1) = 1.  The vertical extent is
++-3 H(r=1) = +-0.15 and r spans [0.5, 2] on a logarithmic mesh.
+"""
+from dataclasses import dataclass, field, replace
+import math
+
+GEOM_BOX, GEOM_CYL = 0, 1
+BC_PERIODIC, BC_OUTFLOW, BC_EQUILIBRIUM = 0, 1, 2
+F_MU, F_MV, F_MW, F_EN, F_RHO, F_DMU, F_DMV, F_DMW, F_DRHO = range(9)
+
+H_ASPECT = 0.05
+DISC_PARAMS = (1.0, -0.5, H_ASPECT * H_ASPECT / 2.0, -1.0)  # sigma0, beta_sigma, T0, beta_T
+Z_HALF = 3.0 * H_ASPECT
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    geometry: int
+    nr: int
+    nth: int
+    nz: int
+    x0: tuple
+    x1: tuple
+    bc_lo: tuple
+    bc_hi: tuple
+    ic: str                      # "sod", "noise", "vortex"
+    steps: int
+    gamma: float = 1.4
+    gm: float = 1.0
+    omega_frame: float = 1.0
+    cfl: float = 0.5
+    n_dust: int = 0
+    disc: tuple = None           # (sigma0, beta_sigma, T0, beta_T) or None
+    seed: int = 0
+    noise_amp: float = 0.0       # relative gas-density noise amplitude
+    vortices: tuple = ()         # ((r_v, theta_v), ...)
+    vortex_amp: float = 0.2      # centre vorticity / local shear rate (3/2 Omega_K)
+    vortex_chi: float = 4.0      # azimuthal / radial Gaussian width
+    vortex_width_h: float = 2.0  # radial width in units of H(r_v)
+    dust_ratio: float = 0.0
+    dust_noise: float = 0.0
+    stokes: float = 0.0
+    drag_law: int = 0
+    t_end: float = 0.0           # >0: run to this time, clipping the last step
+    checkpoint_every: int = 0
+
+    @property
+    def ncell(self) -> int:
+        return self.nr * self.nth * self.nz
+
+    @property
+    def nfields(self) -> int:
+        return 5 + (4 if self.n_dust > 0 else 0)
+
+    @property
+    def shape(self) -> tuple:
+        return (self.nfields, self.nz, self.nth, self.nr)
+
+
+def _disc(name, nr, nth, nz, steps, **kw) -> Workload:
+    return Workload(
+        name=name, geometry=GEOM_CYL, nr=nr, nth=nth, nz=nz,
+        x0=(0.5, 0.0, -Z_HALF), x1=(2.0, 2.0 * math.pi, Z_HALF),
+        bc_lo=(BC_EQUILIBRIUM, BC_PERIODIC, BC_EQUILIBRIUM),
+        bc_hi=(BC_EQUILIBRIUM, BC_PERIODIC, BC_EQUILIBRIUM),
+        disc=DISC_PARAMS, steps=steps, **kw)
+
+
+# Sod shock tube along x in a 256x4x4 Box (gamma = 1.4, diaphragm at x = 0.5, t = 0.2).
+SOD = Workload(
+    name="sod_box_256x4x4", geometry=GEOM_BOX, nr=256, nth=4, nz=4,
+    x0=(0.0, 0.0, 0.0), x1=(1.0, 4.0 / 256, 4.0 / 256),
+    bc_lo=(BC_OUTFLOW, BC_PERIODIC, BC_PERIODIC), bc_hi=(BC_OUTFLOW, BC_PERIODIC, BC_PERIODIC),
+    ic="sod", steps=0, omega_frame=0.0, t_end=0.2)
+
+# Stratified Keplerian disc equilibrium with 1e-4 seeded density noise, gas only.
+DISC_NOISE = _disc("disc_eq_noise_128x256x32", 128, 256, 32, 100, ic="noise", seed=2207, noise_amp=1e-4)
+
+# Bi-fluid disc with one Gaussian vortex at r = 1, St = 0.1, dust/gas = 0.01 (+1e-3 noise).
+VORTEX = _disc("bifluid_vortex_256x512x64", 256, 512, 64, 200, ic="vortex", n_dust=1, seed=4252,
+               vortices=((1.0, math.pi),), dust_ratio=0.01, dust_noise=1e-3, stokes=0.1)
+
+# Adjoint workload: the bi-fluid vortex at 128x256x32, checkpoints every 20 steps.
+ADJOINT = _disc("adjoint_vortex_128x256x32", 128, 256, 32, 200, ic="vortex", n_dust=1, seed=2207,
+                vortices=((1.0, math.pi),), dust_ratio=0.01, dust_noise=1e-3, stokes=0.1,
+                checkpoint_every=20)
+
+# Throughput workload: 512x1024x128 (~67M cells), two vortices, St = 0.05.
+THROUGHPUT = _disc("bifluid_two_vortices_512x1024x128", 512, 1024, 128, 50, ic="vortex", n_dust=1,
+                   seed=4252, vortices=((0.8, 0.0), (1.3, math.pi)), dust_ratio=0.01, dust_noise=1e-3,
+                   stokes=0.05)
+
+ALL = (SOD, DISC_NOISE, VORTEX, ADJOINT, THROUGHPUT)
+
+
+def by_name(name: str) -> Workload:
+    for w in ALL:
+        if w.name == name:
+            return w
+    raise KeyError(name)
+
+
+def scaled(w: Workload, nr: int, nth: int, nz: int, steps: int = None, **kw) -> Workload:
+    """Same workload on another grid (same extents and physics); for tests."""
+    x1 = w.x1
+    if w.geometry == GEOM_BOX and w.ic == "sod":
+        x1 = (w.x1[0], nth * (w.x1[0] - w.x0[0]) / nr, nz * (w.x1[0] - w.x0[0]) / nr)
+    return replace(w, name=f"{w.name}@{nr}x{nth}x{nz}", nr=nr, nth=nth, nz=nz, x1=x1,
+                   steps=w.steps if steps is None else steps, **kw)
