@@ -1,0 +1,290 @@
+#!/usr/bin/env python
+"""Throughput of the RoSSBi3D time step on GB300, in cell-updates/s.
+
+A step is one full midpoint-RK2 update (two fused stage launches plus the
+conservation-sum finalisation) of the whole grid of the synthetic workload,
+with the state resident in HBM and the CFL step kept on the device.  The
+state (4.8 GB in FP64 for the default 512x1024x128 bi-fluid grid) is far
+larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32]
+                  [--workload NAME] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the FP64 restatement of the paper's
+step that the tests compare against) on the host cores, on a bounded sample
+of the same workload (a reduced grid with the same extents and physics).
+Under torchrun each rank runs an independent replica on its own GPU ("replicas
+only": the method's grid is not sharded across GPUs here); rank 0 prints one
+JSON line.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s per GB300 (FP64 vs FP32 at ≤1e-5 L1 err); adjoint/forward cost ratio"
+UNIT = "cell-updates/s"
+HBM_PEAK_FALLBACK = 6800.0
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_PEAK_FALLBACK, "fallback"
+
+
+def _traffic(kernel_tag, workload):
+    """Per-launch DRAM bytes of the stage kernel from the committed ncu summary
+    (profiles/<kernel_tag>__<workload>.txt), if it was taken on the current source."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}__{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.split("=", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_hash") != _source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def _source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2207_04252_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, device_id):
+        self.device_id = device_id
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device_id)],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        self.out.flush()
+        rows = [l.strip().split(",") for l in open(self.out.name) if l.count(",") >= 8]
+        os.unlink(self.out.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        reasons = sorted({name for r in rows for name, v in zip(self.REASONS, r[5:9]) if "Active" in v
+                          and "Not" not in v})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _gpu_smi_id(torch):
+    try:
+        uuid = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        return uuid if uuid.startswith("GPU-") else f"GPU-{uuid}"
+    except Exception:
+        return os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+
+
+def cpu_baseline(w, steps=3, shape=(64, 128, 32)):
+    """Times the CPU oracle, as it stands, on a bounded sample of the workload:
+    the same workload on a reduced grid (same extents and physics)."""
+    import oracle
+    import synthetic as syn
+    ws = syn.scaled(w, *shape, steps=steps)
+    o = oracle.Oracle(ws)
+    E = oracle.initial_state(o)
+    t0 = time.perf_counter()
+    E, _, _ = o.run(E, steps=steps)
+    el = time.perf_counter() - t0
+    return {"value": ws.ncell * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} RK2 steps of {ws.name} ({ws.ncell} cells, same extents and physics as the "
+                      f"timed workload), single thread"}
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle on bounded samples of the workload."""
+    import synthetic as syn
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = syn.by_name(args.workload)
+    shape = (48, 96, 32)
+    import oracle
+    ws = syn.scaled(w, *shape, steps=args.steps)
+    o = oracle.Oracle(ws)
+    E = oracle.initial_state(o)
+    E, _, _ = o.run(E, steps=args.warmup)
+    t0 = time.perf_counter()
+    E, _, _ = o.run(E, steps=args.steps)
+    el = time.perf_counter() - t0
+    value = ws.ncell * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "sample_grid": f"{shape[0]}x{shape[1]}x{shape[2]}",
+                       "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} RK2 steps of {ws.name} per timed run, single thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import synthetic as syn
+    from paper_2207_04252_gb300 import build as lib_build
+    from paper_2207_04252_gb300 import rossbi as R
+    from paper_2207_04252_gb300 import workloads
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+    lib_build.build()
+    w = syn.by_name(args.workload)
+    prec = {"fp64": R.ROSSBI_FP64, "fp32": R.ROSSBI_FP32_PERT}[args.precision]
+    stream = torch.cuda.current_stream()
+    g = workloads.Grid(w, precision=prec, stream=stream)
+    s = g.initial_state()
+    elem = s.element_size()
+    g.cfl_dt(s)
+    for _ in range(args.warmup):
+        g.step(s, dt=0.0)
+    torch.cuda.synchronize()
+    status = g.take_status()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(_gpu_smi_id(torch))
+    R.rossbi_profile_enable(g.h, True)
+    R.rossbi_profile_read(g.h)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with sampler:
+        barrier()
+        start.record(stream)
+        for _ in range(args.steps):
+            g.step(s, dt=0.0)
+        end.record(stream)
+        barrier()
+    elapsed_ms = start.elapsed_time(end)
+    stage_ms, stage_launches = R.rossbi_profile_read(g.h)
+    R.rossbi_profile_enable(g.h, False)
+    status |= g.take_status()
+    if dist is not None:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    clocks = sampler.summary()
+    value = w.ncell * args.steps * world / (elapsed_ms * 1e-3)
+
+    # end to end through the public API with host buffers (copies inside the timed region)
+    e2e_steps = max(1, min(args.steps, 3))
+    host = torch.empty(g.shape, dtype=g.dtype, pin_memory=True)
+    host.copy_(s)
+    hnp = host.numpy()
+    dt = R.rossbi_step_host(g.h, hnp, dt=0.0, dust=g.dust)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        dt = R.rossbi_step_host(g.h, hnp, dt=dt, dust=g.dust)
+    e2e_s = time.perf_counter() - t0
+    state_bytes = g.nf * w.ncell * elem
+    e2e = {"value": w.ncell * e2e_steps * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+           "d2h_bytes_per_step": state_bytes}
+
+    peak, peak_kind = _peaks()
+    avg_launch_s = stage_ms * 1e-3 / max(1, stage_launches)
+    bytes_per_launch = 2.5 * g.nf * elem * w.ncell  # 5F field accesses per cell-step, two launches
+    achieved = bytes_per_launch / avg_launch_s / 1e9
+    kernel_tag = f"stage_{args.precision}"
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": _traffic(kernel_tag, w.name), "peak_kind": peak_kind, "kernel": kernel_tag,
+                "avg_launch_ms": avg_launch_s * 1e3}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
+                "config": {"workload": w.name, "precision": args.precision, "cells": w.ncell, "fields": g.nf,
+                           "state_bytes": state_bytes, "parallelism": f"replicas{world}",
+                           "l2": "inputs larger than L2 (no flush needed)"},
+                "roofline": roofline, "e2e": e2e, "gpu_launches": 3 * args.steps, "clocks": clocks,
+                "status": R.status_string(status)}
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(w)
+        print(json.dumps(line), flush=True)
+    g.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--precision", choices=("fp64", "fp32"), default="fp64")
+    ap.add_argument("--workload", default="bifluid_two_vortices_512x1024x128")
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * rossbi.h - C ABI of the GB300 RoSSBi3D hot-path library (librossbi.so).
+ *
+ * The library advances the compressible Euler + energy equations of an ideal
+ * gas, coupled by aerodynamic drag to a pressureless dust fluid, on a
+ * logarithmic-in-r cylindrical (r, theta, z) grid or a Cartesian Box, by the
+ * method of Rendon Restrepo, Barge & Vavrik, "RoSSBi3D: a 3D and bi-fluid code
+ * for protoplanetary discs" (arXiv:2207.04252):
+ *   - cell-centred finite volumes on the conservative variables (Sect. 2.2,
+ *     App. B order: rho u, rho v, rho w, E, rho; dust: rho_d u_d, rho_d v_d,
+ *     rho_d w_d, rho_d),
+ *   - parabolic reconstruction of the deviation from the equilibrium with a
+ *     MinMod limiter (Sect. 2.7),
+ *   - an exact Riemann solver at every gas face (Sect. 2.6) and an upwind
+ *     pressureless flux at every dust face (Sect. 2.9),
+ *   - geometric, gravity, rotating-frame and drag sources, balanced by the
+ *     empty-run residual (Sects. 2.1, 2.8, 2.9, App. B),
+ *   - midpoint RK2 in time with a global CFL step (Sect. 2.5).
+ *
+ * Conventions shared by every entry point
+ *   - All functions return a rossbi_status; none throws, traps or exits.
+ *   - State arrays are caller-owned DEVICE buffers, one per field
+ *     (structure of arrays), each holding nr*nth*nz values at linear index
+ *     (k*nth + j)*nr + i (r fastest).  Their element type depends on the
+ *     grid's precision form (see rossbi_precision).
+ *   - Everything is ordered on the CUDA stream given to rossbi_init_grid.
+ *     Calls that return a host value (dt, sums) synchronise that stream.
+ *   - Kernels record non-physical states (rho <= 0, P <= 0, NaN) and Riemann
+ *     non-convergence in a device status word; they never trap.  The word is
+ *     read (and cleared) by rossbi_take_status and by every call that
+ *     synchronises; a set bit turns into ROSSBI_ERR_NONPHYSICAL or
+ *     ROSSBI_ERR_RIEMANN.
+ *   - A grid is not thread-safe: one host thread at a time per grid.
+ */
+#ifndef ROSSBI_H
+#define ROSSBI_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ROSSBI_OK = 0,
+  ROSSBI_ERR_ARG = 1,          /* invalid argument or call order */
+  ROSSBI_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+  ROSSBI_ERR_OOM = 3,          /* device allocation failed */
+  ROSSBI_ERR_NONPHYSICAL = 4,  /* rho <= 0, P <= 0 or NaN met by a kernel */
+  ROSSBI_ERR_RIEMANN = 5,      /* star-pressure Newton iteration did not converge */
+  ROSSBI_ERR_UNSUPPORTED = 6   /* valid but not implemented combination */
+} rossbi_status;
+
+enum { ROSSBI_GEOM_BOX = 0, ROSSBI_GEOM_CYL = 1 };
+enum { ROSSBI_BC_PERIODIC = 0, ROSSBI_BC_OUTFLOW = 1, ROSSBI_BC_EQUILIBRIUM = 2 };
+
+/* Precision forms.
+ *   ROSSBI_FP64      : state = full conservative E, double.
+ *   ROSSBI_FP32_PERT : state = deviation E' = E - E0 from the stored FP64
+ *                      equilibrium, float; the update is computed in
+ *                      perturbation form (see rossbi_step).
+ *   ROSSBI_FP64_PERT : the perturbation form in double (state E', double). */
+enum { ROSSBI_FP64 = 0, ROSSBI_FP32_PERT = 1, ROSSBI_FP64_PERT = 2 };
+
+typedef struct rossbi_grid rossbi_grid; /* opaque, library-owned */
+
+/* Grid description (Sect. 2.3 mesh, Sect. 2.4 boundaries).
+ *   geometry : ROSSBI_GEOM_CYL (r log-spaced on [x0[0], x1[0]], theta and z
+ *              uniform) or ROSSBI_GEOM_BOX (x, y, z uniform, no sources).
+ *   nr,nth,nz: cells along r (x), theta (y), z.  Each >= 1.
+ *   bc_lo/hi : per axis; ROSSBI_BC_EQUILIBRIUM ghosts carry E' = 0,
+ *              PERIODIC wraps, OUTFLOW copies the nearest interior E'.
+ *              A cylindrical grid needs periodic theta and non-periodic r, z.
+ *   gamma    : ratio of specific heats (> 1).
+ *   gm       : G M of the central star (cylindrical only).
+ *   omega_frame : angular speed of the rotating frame (cylindrical only).
+ *   cfl      : N_CFL of the CFL condition (Sect. 2.5; the paper uses 1/2).
+ *   n_dust   : 0 (gas only, 5 fields) or 1 (gas + one dust fluid, 9 fields).
+ *   precision: one of the precision forms above. */
+typedef struct {
+  int geometry;
+  int nr, nth, nz;
+  double x0[3], x1[3];
+  int bc_lo[3], bc_hi[3];
+  double gamma, gm, omega_frame, cfl;
+  int n_dust;
+  int precision;
+} rossbi_grid_desc;
+
+/* Disc equilibrium parameters (App. A): Sigma = sigma0 r^beta_sigma,
+ * T = T0 r^beta_T (k_B/(mu m_u) = 1). */
+typedef struct {
+  double sigma0, beta_sigma, T0, beta_T;
+} rossbi_disc_params;
+
+/* Drag (Sect. 2.9).  drag_law 0: t_s = stokes / Omega_K(r) (Box: t_s = stokes);
+ * drag_law 1: Epstein t_s = rho_s r_p / (rho_g c_s) with rho_s r_p fixed so
+ * that the Stokes number equals `stokes` at r = 1, z = 0 of the equilibrium. */
+typedef struct {
+  double stokes;
+  int drag_law;
+} rossbi_dust_params;
+
+/* Creates a grid: mesh, metrics and device tables (Sects. 2.2-2.4).
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream); not owned.
+ * On success *out is a new grid to be freed with rossbi_destroy.
+ * Errors: ROSSBI_ERR_ARG (bad desc or out == NULL), ROSSBI_ERR_OOM,
+ * ROSSBI_ERR_CUDA, ROSSBI_ERR_UNSUPPORTED. */
+rossbi_status rossbi_init_grid(const rossbi_grid_desc* desc, void* cuda_stream, rossbi_grid** out);
+
+/* Sets the disc equilibrium E0 (App. A) at cell centres and faces, and runs
+ * the "empty run" of Sect. 2.8 once to store the balanced residual
+ * R0 = G(E0) used by the FP64 form.  disc == NULL sets E0 = 0 (Box runs).
+ * Cylindrical grids require disc != NULL.  Synchronises the stream. */
+rossbi_status rossbi_set_equilibrium(rossbi_grid* g, const rossbi_disc_params* disc);
+
+/* Copies the equilibrium conservative gas state at cell centres to host
+ * memory: host_out[f*nz*nr + k*nr + i], f = 0..4 (App. B order). */
+rossbi_status rossbi_get_equilibrium(rossbi_grid* g, double* host_out);
+
+/* Global CFL time step of Sect. 2.5, Eq. (cfl condition):
+ * dt = min over cells of cfl * V / ((|v| + c_s) max face area), with the
+ * frame-relative speed; a dust cell adds cfl * V / (|v_d| max face area).
+ * state: nfields device pointers of the grid's precision form.
+ * Writes *dt_out (host) and also leaves dt on the device for a following
+ * rossbi_step(..., dt = 0, ...).  Synchronises the stream. */
+rossbi_status rossbi_cfl_dt(rossbi_grid* g, const void* const* state, double* dt_out);
+
+/* One midpoint RK2 step (Sect. 2.5) of length dt, in place:
+ *   E* = E^n + (dt/2) (G(E^n) - R0)/V, then drag over dt/2,
+ *   E^{n+1} = E^n + dt (G(E*) - R0)/V, then drag over dt,
+ * where G = S V - sum_faces A F.n (Sect. 2.2) and the drag is the closed-form
+ * semi-implicit relaxation of the gas-dust relative velocity.  In the
+ * perturbation forms G - R0 is evaluated directly as G(E0 + E') - G(E0).
+ *   state   : nfields caller-owned device pointers, read and overwritten.
+ *   scratch : nfields device pointers of the same type and size for E*, or
+ *             NULL to use a buffer the library allocates on first use.
+ *   dt      : > 0 uses this step; 0 uses the device-resident step left by the
+ *             previous rossbi_step or rossbi_cfl_dt (no host round trip).
+ *   dust    : drag parameters; required when n_dust = 1, ignored otherwise.
+ *   next_dt : if not NULL, receives the CFL step of E^{n+1} (fused into the
+ *             second stage) and the call synchronises and reports the status
+ *             word.  If NULL the call is asynchronous and the next CFL step
+ *             stays on the device.
+ * Errors: ROSSBI_ERR_ARG, ROSSBI_ERR_OOM, ROSSBI_ERR_CUDA, and after a
+ * synchronising call ROSSBI_ERR_NONPHYSICAL / ROSSBI_ERR_RIEMANN. */
+rossbi_status rossbi_step(rossbi_grid* g, void* const* state, void* const* scratch, double dt,
+                          const rossbi_dust_params* dust, double* next_dt);
+
+/* Same step on HOST buffers: copies the state (nfields host pointers) to
+ * device buffers owned by the library, steps, and copies it back; the call
+ * synchronises.  For callers whose state lives in host memory. */
+rossbi_status rossbi_step_host(rossbi_grid* g, void* const* host_state, double dt, const rossbi_dust_params* dust,
+                               double* next_dt);
+
+/* FP64 conservation sums sum_cells V * E_f of the FULL conservative fields
+ * (E0 + E' in the perturbation forms), in a fixed reduction order (so the
+ * result is deterministic).  sums: host array of nfields doubles.
+ * Synchronises the stream. */
+rossbi_status rossbi_conservation_sums(rossbi_grid* g, const void* const* state, double* sums);
+
+/* Perturbation forms: number of Riemann faces solved so far by the FP64
+ * full-state fallback (vacuum generation, strong rarefaction or slow Newton
+ * convergence of the perturbation solver).  Synchronises the stream. */
+rossbi_status rossbi_fallback_count(rossbi_grid* g, unsigned long long* count);
+
+/* Waits for the stream, then returns and clears the device status word. */
+rossbi_status rossbi_take_status(rossbi_grid* g);
+
+/* Measurement: when enabled, every stage-kernel launch of rossbi_step is
+ * bracketed by CUDA events recorded on the grid's stream.  rossbi_profile_read
+ * synchronises the stream, returns the summed device time (ms) and the number
+ * of stage launches since the last read, and resets both. */
+rossbi_status rossbi_profile_enable(rossbi_grid* g, int enable);
+rossbi_status rossbi_profile_read(rossbi_grid* g, double* stage_ms, int* stage_launches);
+
+/* Number of conservative fields (5 or 9) and the precision form. */
+int rossbi_nfields(const rossbi_grid* g);
+int rossbi_precision(const rossbi_grid* g);
+
+/* Frees every library-owned resource of the grid (not the caller's state). */
+void rossbi_destroy(rossbi_grid* g);
+
+/* Static, human-readable name of a status code. */
+const char* rossbi_status_string(rossbi_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ROSSBI_H */

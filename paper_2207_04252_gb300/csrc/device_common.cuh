@@ -1,0 +1,333 @@
+// Device-side data structures and per-cell / per-face physics of the RoSSBi3D
+// step (arXiv:2207.04252).  Included by the kernel translation units only.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rossbi {
+
+// Conservative variables in App. B order, then the dust fluid.
+enum { MU = 0, MV = 1, MW = 2, EN = 3, RHO = 4, DMU = 5, DMV = 6, DMW = 7, DRHO = 8 };
+enum { GEOM_BOX = 0, GEOM_CYL = 1 };
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_EQUILIBRIUM = 2 };
+enum { STATUS_NONPHYSICAL = 1u, STATUS_RIEMANN = 2u };
+
+constexpr int GH = 2;  // ghost offset of the axis-0 coordinate tables
+
+// Grid data the kernels read.  Passed by value as a kernel parameter; the
+// pointers are device tables owned by the host runtime.
+struct DevGrid {
+  int geom, nr, nth, nz, nf, has_eq;
+  int bc_lo[3], bc_hi[3];
+  double gamma, gm, omega, cfl;
+  double x0[3], dx[3];   // uniform axes 1, 2 (and axis 0 of the Box): origin, spacing
+  const double* rc;      // axis-0 cell centres,  index i + GH, i in [-GH, nr + GH)
+  const double* rf;      // axis-0 lower faces,   index i + GH, i in [-GH, nr + GH]
+  const double* rcoef;   // axis-0 parabola weights for cells i in [-1, nr]: 8 per cell at (i + 1) * 8
+  const double* vol;     // V(i)
+  const double* ivol;    // 1 / V(i)
+  const double* area_r;  // A of the axis-0 face i - 1/2, i in [0, nr]
+  const double* area_t;  // A of an axis-1 face of a cell with radial index i
+  const double* area_z;  // A of an axis-2 face of a cell with radial index i
+  const double* maxA;    // largest face area of a cell with radial index i
+  const double* e0c;     // equilibrium gas state at centres   [5][nz][nr]
+  const double* e0r;     // equilibrium gas state at r faces   [5][nz][nr + 1]
+  const double* e0z;     // equilibrium gas state at z faces   [5][nz + 1][nr]
+  const double* r0;      // balanced residual G(E0)            [5][nz][nr]
+};
+
+__host__ __device__ constexpr int pow2ceil(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+// Normal / transverse momentum fields for a face normal to axis D.
+template <int D> struct Axes;
+template <> struct Axes<0> { static constexpr int n = MU, t1 = MV, t2 = MW; };
+template <> struct Axes<1> { static constexpr int n = MV, t1 = MU, t2 = MW; };
+template <> struct Axes<2> { static constexpr int n = MW, t1 = MU, t2 = MV; };
+
+// ------------------------------------------------------------------ Riemann
+// Exact solution of the 1D Riemann problem (Sect. 2.6; the paper takes the
+// solver of Toro, ch. 4), sampled on the face (x/t = 0).  Newton iteration on
+// the star pressure from the primitive-variable estimate, then the wave
+// pattern decides which state sits on the face.
+struct RSide {
+  double rho, u, p, c;
+};
+
+__device__ __forceinline__ void pressure_fn(double g, const RSide& K, double p, double& f, double& fd) {
+  if (p <= K.p) {  // rarefaction branch
+    const double prat = p / K.p;
+    const double e = pow(prat, (g - 1.0) / (2.0 * g));
+    f = 2.0 * K.c / (g - 1.0) * (e - 1.0);
+    fd = e / (prat * K.rho * K.c);
+  } else {         // shock branch
+    const double A = 2.0 / ((g + 1.0) * K.rho);
+    const double B = (g - 1.0) / (g + 1.0) * K.p;
+    const double q = sqrt(A / (B + p));
+    f = (p - K.p) * q;
+    fd = (1.0 - 0.5 * (p - K.p) / (B + p)) * q;
+  }
+}
+
+// Fan state at x/t = 0 inside a left (sgn = +1) or right (sgn = -1) rarefaction.
+__device__ __forceinline__ void fan_state(double g, const RSide& K, double sgn, double& rho, double& u, double& p) {
+  const double cf = 2.0 / (g + 1.0) * (K.c + sgn * 0.5 * (g - 1.0) * K.u);
+  u = sgn * cf;
+  const double ratio = cf / K.c;
+  rho = K.rho * pow(ratio, 2.0 / (g - 1.0));
+  p = K.p * pow(ratio, 2.0 * g / (g - 1.0));
+}
+
+// Returns the face state (rho, u_n, p) and the side (-1 left, +1 right, 0 vacuum)
+// whose transverse velocity is carried.
+__device__ __forceinline__ int riemann_face(double g, double rl, double ul, double pl, double rr, double ur, double pr,
+                                            double& rho, double& u, double& p, unsigned& status) {
+  const RSide L{rl, ul, pl, sqrt(g * pl / rl)};
+  const RSide R{rr, ur, pr, sqrt(g * pr / rr)};
+  if (2.0 / (g - 1.0) * (L.c + R.c) <= ur - ul) {  // the waves open a vacuum
+    const double sl_star = ul + 2.0 * L.c / (g - 1.0);
+    const double sr_star = ur - 2.0 * R.c / (g - 1.0);
+    if (0.0 <= sl_star) {
+      if (0.0 <= ul - L.c) { rho = rl; u = ul; p = pl; }
+      else fan_state(g, L, 1.0, rho, u, p);
+      return -1;
+    }
+    if (0.0 >= sr_star) {
+      if (0.0 >= ur + R.c) { rho = rr; u = ur; p = pr; }
+      else fan_state(g, R, -1.0, rho, u, p);
+      return 1;
+    }
+    rho = u = p = 0.0;
+    return 0;
+  }
+  const double pfloor = 1e-8 * fmin(pl, pr);
+  double ps = fmax(pfloor, 0.5 * (pl + pr) - 0.125 * (ur - ul) * (rl + rr) * (L.c + R.c));
+  double fl, fdl, fr, fdr;
+  bool conv = false;
+  for (int it = 0; it < 100; ++it) {
+    pressure_fn(g, L, ps, fl, fdl);
+    pressure_fn(g, R, ps, fr, fdr);
+    const double pn = fmax(pfloor, ps - (fl + fr + ur - ul) / (fdl + fdr));
+    const double change = 2.0 * fabs(pn - ps) / (pn + ps);
+    ps = pn;
+    if (change <= 1e-12) { conv = true; break; }
+  }
+  if (!conv) status |= STATUS_RIEMANN;
+  pressure_fn(g, L, ps, fl, fdl);
+  pressure_fn(g, R, ps, fr, fdr);
+  const double us = 0.5 * (ul + ur) + 0.5 * (fr - fl);
+  if (0.0 <= us) {  // face lies left of the contact
+    if (ps <= pl) {
+      if (0.0 <= ul - L.c) { rho = rl; u = ul; p = pl; return -1; }
+      const double ratio = ps / pl;
+      if (0.0 > us - L.c * pow(ratio, (g - 1.0) / (2.0 * g))) {
+        rho = rl * pow(ratio, 1.0 / g); u = us; p = ps; return -1;
+      }
+      fan_state(g, L, 1.0, rho, u, p);
+      return -1;
+    }
+    const double ratio = ps / pl;
+    if (0.0 <= ul - L.c * sqrt((g + 1.0) / (2.0 * g) * ratio + (g - 1.0) / (2.0 * g))) {
+      rho = rl; u = ul; p = pl; return -1;
+    }
+    const double g6 = (g - 1.0) / (g + 1.0);
+    rho = rl * (ratio + g6) / (ratio * g6 + 1.0); u = us; p = ps;
+    return -1;
+  }
+  if (ps > pr) {  // right shock
+    const double ratio = ps / pr;
+    if (0.0 >= ur + R.c * sqrt((g + 1.0) / (2.0 * g) * ratio + (g - 1.0) / (2.0 * g))) {
+      rho = rr; u = ur; p = pr; return 1;
+    }
+    const double g6 = (g - 1.0) / (g + 1.0);
+    rho = rr * (ratio + g6) / (ratio * g6 + 1.0); u = us; p = ps;
+    return 1;
+  }
+  if (0.0 >= ur + R.c) { rho = rr; u = ur; p = pr; return 1; }
+  const double ratio = ps / pr;
+  if (0.0 <= us + R.c * pow(ratio, (g - 1.0) / (2.0 * g))) {
+    rho = rr * pow(ratio, 1.0 / g); u = us; p = ps; return 1;
+  }
+  fan_state(g, R, -1.0, rho, u, p);
+  return 1;
+}
+
+__device__ __forceinline__ double gas_pressure(double g, double mu, double mv, double mw, double en, double rho) {
+  return (g - 1.0) * (en - 0.5 * (mu * mu + mv * mv + mw * mw) / rho);
+}
+
+// Gas flux F(E*) through a face normal to axis D from the reconstructed left
+// and right conservative states (App. B flux vector; energy flux (E + P) u_n).
+template <int D>
+__device__ __forceinline__ void gas_face_flux(double g, const double* UL, const double* UR, double* F,
+                                              unsigned& status) {
+  constexpr int n = Axes<D>::n, t1 = Axes<D>::t1, t2 = Axes<D>::t2;
+  const double rl = UL[RHO], rr = UR[RHO];
+  const double pl = gas_pressure(g, UL[MU], UL[MV], UL[MW], UL[EN], rl);
+  const double pr = gas_pressure(g, UR[MU], UR[MV], UR[MW], UR[EN], rr);
+  if (!(rl > 0.0) || !(rr > 0.0) || !(pl > 0.0) || !(pr > 0.0)) {
+    status |= STATUS_NONPHYSICAL;
+#pragma unroll
+    for (int f = 0; f < 5; ++f) F[f] = 0.0;
+    return;
+  }
+  const double il = 1.0 / rl, ir = 1.0 / rr;
+  double rho, u, p;
+  const int side = riemann_face(g, rl, UL[n] * il, pl, rr, UR[n] * ir, pr, rho, u, p, status);
+  double ut1 = 0.0, ut2 = 0.0;
+  if (side < 0) { ut1 = UL[t1] * il; ut2 = UL[t2] * il; }
+  else if (side > 0) { ut1 = UR[t1] * ir; ut2 = UR[t2] * ir; }
+  const double m = rho * u;
+  F[RHO] = m;
+  F[n] = m * u + p;
+  F[t1] = m * ut1;
+  F[t2] = m * ut2;
+  F[EN] = (0.5 * rho * (u * u + ut1 * ut1 + ut2 * ut2) + p / (g - 1.0) + p) * u;
+}
+
+// Upwind flux of the pressureless dust fluid (Sect. 2.9 "adapted" solver):
+// take the upwind side when both face velocities agree, nothing when the faces
+// diverge, and the side selected by the delta-shock speed when they converge.
+// U and F hold the four dust fields (rho_d u, rho_d v, rho_d w, rho_d).
+template <int D>
+__device__ __forceinline__ void dust_face_flux(const double* UL, const double* UR, double* F) {
+  constexpr int n = Axes<D>::n, t1 = Axes<D>::t1, t2 = Axes<D>::t2;  // 0..2, same in the dust block
+  const double rl = UL[3], rr = UR[3];
+  const double ul = rl > 0.0 ? UL[n] / rl : 0.0;
+  const double ur = rr > 0.0 ? UR[n] / rr : 0.0;
+  int pick;  // -1 left, +1 right, 0 none, 2 average
+  if (ul <= 0.0 && ur >= 0.0) pick = 0;
+  else if (ul >= 0.0 && ur >= 0.0) pick = -1;
+  else if (ul <= 0.0 && ur <= 0.0) pick = 1;
+  else {
+    const double sl = sqrt(rl), sr = sqrt(rr);
+    const double vs = (sl * ul + sr * ur) / (sl + sr);
+    pick = vs > 0.0 ? -1 : (vs < 0.0 ? 1 : 2);
+  }
+  double fl[4] = {0.0, 0.0, 0.0, 0.0}, fr[4] = {0.0, 0.0, 0.0, 0.0};
+  if (pick != 1 && rl > 0.0) {
+    const double m = rl * ul;
+    fl[0] = m; fl[1] = m * ul; fl[2] = m * (UL[t1] / rl); fl[3] = m * (UL[t2] / rl);
+  }
+  if (pick != -1 && rr > 0.0) {
+    const double m = rr * ur;
+    fr[0] = m; fr[1] = m * ur; fr[2] = m * (UR[t1] / rr); fr[3] = m * (UR[t2] / rr);
+  }
+  double s[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) s[q] = pick == -1 ? fl[q] : pick == 1 ? fr[q] : pick == 2 ? 0.5 * (fl[q] + fr[q]) : 0.0;
+  F[3] = s[0];
+  F[n] = s[1];
+  F[t1] = s[2];
+  F[t2] = s[3];
+}
+
+// ------------------------------------------------------------------ sources
+// App. B sources per unit volume at the cell centre: geometric terms,
+// stellar gravity (Sect. 2.1) and the rotating-frame Coriolis / centrifugal
+// terms; the Box has none.
+__device__ __forceinline__ void cell_sources(const DevGrid& g, int i, int k, const double* U, double* S) {
+  const double r = g.rc[i + GH];
+  const double z = g.x0[2] + (k + 0.5) * g.dx[2];
+  const double R2 = r * r + z * z;
+  const double R3 = R2 * sqrt(R2);
+  const double fr = -g.gm * r / R3, fz = -g.gm * z / R3;
+  const double Om = g.omega;
+  {
+    const double rho = U[RHO];
+    const double ir = 1.0 / rho;
+    const double u = U[MU] * ir, v = U[MV] * ir, w = U[MW] * ir;
+    const double P = gas_pressure(g.gamma, U[MU], U[MV], U[MW], U[EN], rho);
+    S[MU] = rho * v * v / r + P / r + rho * fr + 2.0 * Om * rho * v + rho * Om * Om * r;
+    S[MV] = -rho * u * v / r - 2.0 * Om * rho * u;
+    S[MW] = rho * fz;
+    S[EN] = rho * u * (fr + Om * Om * r) + rho * w * fz;
+    S[RHO] = 0.0;
+  }
+  if (g.nf > 5) {
+    const double rho = U[DRHO];
+    if (rho > 0.0) {
+      const double ir = 1.0 / rho;
+      const double u = U[DMU] * ir, v = U[DMV] * ir;
+      S[DMU] = rho * v * v / r + rho * fr + 2.0 * Om * rho * v + rho * Om * Om * r;
+      S[DMV] = -rho * u * v / r - 2.0 * Om * rho * u;
+      S[DMW] = rho * fz;
+    } else {
+      S[DMU] = S[DMV] = S[DMW] = 0.0;
+    }
+    S[DRHO] = 0.0;
+  }
+}
+
+// ------------------------------------------------------------------ drag
+struct DragArgs {
+  double stokes;
+  double rhos_rp;  // Epstein constant rho_s r_p (drag_law 1)
+  int law;
+};
+
+// Semi-implicit drag over a stage of length tau (Sect. 2.9 drag law): the
+// relative gas-dust velocity relaxes by 1 / (1 + tau (1 + eps) / t_s) at
+// fixed barycentric velocity; the gas energy gains the work done on the gas.
+__device__ __forceinline__ void apply_drag(const DevGrid& g, int i, double* U, double tau, const DragArgs& d) {
+  const double rg = U[RHO], rd = U[DRHO];
+  if (!(rd > 0.0) || !(rg > 0.0)) return;
+  double ts;
+  if (d.law == 0) {
+    if (g.geom == GEOM_CYL) {
+      const double r = g.rc[i + GH];
+      ts = d.stokes / sqrt(g.gm / (r * r * r));
+    } else {
+      ts = d.stokes;
+    }
+  } else {
+    const double cs = sqrt(g.gamma * gas_pressure(g.gamma, U[MU], U[MV], U[MW], U[EN], rg) / rg);
+    ts = d.rhos_rp / (rg * cs);
+  }
+  const double kk = tau * (1.0 + rd / rg) / ts;
+  const double mu = rg * rd / (rg + rd);
+  const double relax = kk / (1.0 + kk);
+  double dE = 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double vg = U[MU + c] / rg;
+    const double X = mu * (U[DMU + c] / rd - vg) * relax;
+    U[MU + c] += X;
+    U[DMU + c] -= X;
+    dE += 0.5 * X * (U[MU + c] / rg + vg);
+  }
+  U[EN] += dE;
+}
+
+// ------------------------------------------------------------------ CFL
+// Sect. 2.5, Eq. (cfl condition) for one cell of radial index i.
+__device__ __forceinline__ double cell_dt(const DevGrid& g, int i, const double* U) {
+  const double rho = U[RHO];
+  const double vel = sqrt(U[MU] * U[MU] + U[MV] * U[MV] + U[MW] * U[MW]) / rho;
+  const double cs = sqrt(g.gamma * gas_pressure(g.gamma, U[MU], U[MV], U[MW], U[EN], rho) / rho);
+  const double V = g.vol[i], A = g.maxA[i];
+  double dt = g.cfl * V / ((vel + cs) * A);
+  if (g.nf > 5 && U[DRHO] > 0.0) {
+    const double vd = sqrt(U[DMU] * U[DMU] + U[DMV] * U[DMV] + U[DMW] * U[DMW]) / U[DRHO];
+    if (vd > 0.0) dt = fmin(dt, g.cfl * V / (vd * A));
+  }
+  return dt;
+}
+
+__device__ __forceinline__ bool cell_nonphysical(const DevGrid& g, const double* U) {
+  const double P = gas_pressure(g.gamma, U[MU], U[MV], U[MW], U[EN], U[RHO]);
+  bool bad = !(U[RHO] > 0.0) || !(P > 0.0);
+  if (g.nf > 5) bad |= !(U[DRHO] >= 0.0);
+  return bad;
+}
+
+// Positive doubles order like their bit patterns, so a 64-bit integer
+// atomicMin of the bits is an exact, order-independent minimum.
+__device__ __forceinline__ void atomic_min_pos_double(unsigned long long* slot, double v) {
+  atomicMin(slot, (unsigned long long)__double_as_longlong(v));
+}
+
+}  // namespace rossbi

@@ -1,0 +1,968 @@
+// Host runtime and C ABI of the GB300 RoSSBi3D hot-path library.
+//
+// Owns the mesh tables, the equilibrium tables and balanced residual, the
+// reduction slots and the optional scratch state; launches the fused stage
+// kernels.  The C ABI is declared (and documented) in include/rossbi.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/rossbi.h"
+#include "stage_pert.cuh"
+
+using namespace rossbi;
+
+namespace {
+
+// Tile of the stage kernels: 14 x 6 x 6 cells, lines of 16 / 8 / 8 lanes.
+constexpr int F64_TR = 14, F64_TT = 6, F64_TZ = 6, F64_NT = 192;
+constexpr int P32_TR = 14, P32_TT = 6, P32_TZ = 6, P32_NT = 192, P32_MINB = 2;
+constexpr int CFL_NT = 256;
+
+}  // namespace
+
+struct rossbi_grid {
+  rossbi_grid_desc desc{};
+  cudaStream_t stream = nullptr;
+  int nf = 5;
+  size_t ncell = 0;
+  DevGrid dg{};
+  bool eq_set = false;
+  bool has_disc = false;
+  rossbi_disc_params disc{};
+  // device tables
+  double *d_rc = nullptr, *d_rf = nullptr, *d_rcoef = nullptr, *d_vol = nullptr, *d_ivol = nullptr;
+  double *d_area_r = nullptr, *d_area_t = nullptr, *d_area_z = nullptr, *d_maxA = nullptr;
+  double *d_e0c = nullptr, *d_e0r = nullptr, *d_e0z = nullptr, *d_r0 = nullptr;
+  std::vector<double> h_e0c;
+  // reductions and status
+  unsigned long long* d_dt = nullptr;  // [3]: step ping-pong slots 0/1, standalone CFL slot 2
+  int dt_slot = 0;                     // slot holding the step length of the next step
+  bool dt_on_device = false;
+  double* d_partials = nullptr;
+  size_t partials_cap = 0;
+  double* d_sums = nullptr;
+  unsigned* d_status = nullptr;
+  double* h_pinned = nullptr;          // [16] readback area: [0..8] values, [12] status word
+  // library-owned buffers
+  void* d_scratch = nullptr;           // E* when the caller passes none
+  void* d_hoststate = nullptr;         // device copy for rossbi_step_host
+  int tiles_r = 0, tiles_t = 0, tiles_z = 0;
+  // perturbation forms: equilibrium and metric tables in the state precision
+  void* d_ptab = nullptr;              // one allocation holding every table below
+  PertTables<float> pt_f{};
+  PertTables<double> pt_d{};
+  unsigned long long* d_fallbacks = nullptr;
+  double eq_sums[5] = {0, 0, 0, 0, 0}; // sum_cells V E0_f (FP64)
+  // stage-kernel timing (rossbi_profile_*)
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev;         // start/stop pairs
+  int ev_used = 0;
+  double prof_ms = 0.0;
+  int prof_launches = 0;
+};
+
+namespace {
+
+size_t elem_size(const rossbi_grid* g) { return g->desc.precision == ROSSBI_FP32_PERT ? 4 : 8; }
+
+#define CK(call)                                            \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) {                                \
+      return e_ == cudaErrorMemoryAllocation ? ROSSBI_ERR_OOM : ROSSBI_ERR_CUDA; \
+    }                                                       \
+  } while (0)
+
+template <class T>
+rossbi_status upload(T** dst, const std::vector<T>& src, cudaStream_t s) {
+  if (*dst) cudaFree(*dst);
+  *dst = nullptr;
+  CK(cudaMalloc(dst, src.size() * sizeof(T)));
+  CK(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  return ROSSBI_OK;
+}
+
+// ---------------------------------------------------------------- mesh (Sect. 2.3)
+double axis0_face(const rossbi_grid_desc& d, int i) {
+  if (d.geometry == ROSSBI_GEOM_CYL) return d.x0[0] * std::pow(d.x1[0] / d.x0[0], (double)i / d.nr);
+  return d.x0[0] + (d.x1[0] - d.x0[0]) * i / d.nr;
+}
+double axis0_centre(const rossbi_grid_desc& d, int i) {
+  if (d.geometry == ROSSBI_GEOM_CYL) return std::sqrt(axis0_face(d, i) * axis0_face(d, i + 1));
+  return 0.5 * (axis0_face(d, i) + axis0_face(d, i + 1));
+}
+
+// ---------------------------------------------------------------- equilibrium (App. A)
+void equilibrium_prim(const rossbi_grid_desc& d, const rossbi_disc_params& p, double r, double z, double& rho,
+                      double& vth, double& pres, double* dlnp_out = nullptr) {
+  const double cs2 = p.T0 * std::pow(r, p.beta_T);
+  const double omk = std::sqrt(d.gm / (r * r * r));
+  const double H = std::sqrt(2.0 * cs2) / omk;
+  const double R = std::sqrt(r * r + z * z);
+  const double gpot = 1.0 / R - 1.0 / r;
+  rho = p.sigma0 * std::pow(r, p.beta_sigma) / (std::sqrt(M_PI) * H) * std::exp(d.gm / cs2 * gpot);
+  pres = cs2 * rho;
+  const double dlnp = (p.beta_T + p.beta_sigma - 0.5 * (p.beta_T + 3.0)) / r +
+                      d.gm / cs2 * (-p.beta_T * gpot / r - r / (R * R * R) + 1.0 / (r * r));
+  vth = std::sqrt(d.gm * r * r / (R * R * R) + r * cs2 * dlnp);
+  if (dlnp_out) *dlnp_out = dlnp;
+}
+
+void equilibrium_cons(const rossbi_grid_desc& d, const rossbi_disc_params& p, double r, double z, double* U,
+                      size_t stride) {
+  double rho, vth, pres;
+  equilibrium_prim(d, p, r, z, rho, vth, pres);
+  const double v = vth - d.omega_frame * r;
+  U[MU * stride] = 0.0;
+  U[MV * stride] = rho * v;
+  U[MW * stride] = 0.0;
+  U[EN * stride] = 0.5 * rho * v * v + pres / (d.gamma - 1.0);
+  U[RHO * stride] = rho;
+}
+
+rossbi_status check_desc(const rossbi_grid_desc& d) {
+  if (d.nr < 1 || d.nth < 1 || d.nz < 1) return ROSSBI_ERR_ARG;
+  if (d.geometry != ROSSBI_GEOM_BOX && d.geometry != ROSSBI_GEOM_CYL) return ROSSBI_ERR_ARG;
+  if (!(d.gamma > 1.0) || !(d.cfl > 0.0)) return ROSSBI_ERR_ARG;
+  if (d.n_dust != 0 && d.n_dust != 1) return ROSSBI_ERR_UNSUPPORTED;
+  for (int a = 0; a < 3; ++a) {
+    if (!(d.x1[a] > d.x0[a])) return ROSSBI_ERR_ARG;
+    for (int bc : {d.bc_lo[a], d.bc_hi[a]})
+      if (bc < ROSSBI_BC_PERIODIC || bc > ROSSBI_BC_EQUILIBRIUM) return ROSSBI_ERR_ARG;
+    if ((d.bc_lo[a] == ROSSBI_BC_PERIODIC) != (d.bc_hi[a] == ROSSBI_BC_PERIODIC)) return ROSSBI_ERR_ARG;
+  }
+  if (d.geometry == ROSSBI_GEOM_CYL) {
+    if (!(d.x0[0] > 0.0) || !(d.gm > 0.0)) return ROSSBI_ERR_ARG;
+    if (d.bc_lo[1] != ROSSBI_BC_PERIODIC) return ROSSBI_ERR_ARG;
+    if (d.bc_lo[0] == ROSSBI_BC_PERIODIC || d.bc_lo[2] == ROSSBI_BC_PERIODIC) return ROSSBI_ERR_ARG;
+  }
+  if (d.precision != ROSSBI_FP64 && d.precision != ROSSBI_FP32_PERT && d.precision != ROSSBI_FP64_PERT)
+    return ROSSBI_ERR_ARG;
+  return ROSSBI_OK;
+}
+
+rossbi_status status_from_word(unsigned w) {
+  if (w & STATUS_NONPHYSICAL) return ROSSBI_ERR_NONPHYSICAL;
+  if (w & STATUS_RIEMANN) return ROSSBI_ERR_RIEMANN;
+  return ROSSBI_OK;
+}
+
+rossbi_status sync_and_status(rossbi_grid* g) {
+  CK(cudaMemcpyAsync(g->h_pinned + 12, g->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, g->stream));
+  CK(cudaMemsetAsync(g->d_status, 0, sizeof(unsigned), g->stream));
+  CK(cudaStreamSynchronize(g->stream));
+  unsigned w;
+  std::memcpy(&w, g->h_pinned + 12, sizeof(unsigned));
+  return status_from_word(w);
+}
+
+// ---------------------------------------------------------------- kernels
+__global__ void cfl_kernel(DevGrid g, StageArgs a, unsigned long long* slot) {
+  __shared__ double red[CFL_NT / 32];
+  const size_t ncell = (size_t)g.nr * g.nth * g.nz;
+  double m = INFINITY;
+  unsigned status = 0;
+  for (size_t lin = blockIdx.x * (size_t)CFL_NT + threadIdx.x; lin < ncell; lin += (size_t)gridDim.x * CFL_NT) {
+    double U[9];
+    for (int f = 0; f < g.nf; ++f) U[f] = a.in[f][lin];
+    const int i = (int)(lin % g.nr);
+    if (cell_nonphysical(g, U)) status |= STATUS_NONPHYSICAL;
+    m = fmin(m, cell_dt(g, i, U));
+  }
+  m = block_min<CFL_NT>(m, red);
+  if (threadIdx.x == 0) atomic_min_pos_double(slot, m);
+  if (status) atomicOr(a.status, status);
+}
+
+__global__ void set_slot_kernel(unsigned long long* slot, unsigned long long v) { *slot = v; }
+
+// Per-block FP64 partial sums of V * E_f, fixed order.
+__global__ void sums_kernel(DevGrid g, StageArgs a, double* partials) {
+  __shared__ double red[CFL_NT / 32];
+  const size_t ncell = (size_t)g.nr * g.nth * g.nz;
+  double s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (size_t lin = blockIdx.x * (size_t)CFL_NT + threadIdx.x; lin < ncell; lin += (size_t)gridDim.x * CFL_NT) {
+    const double V = g.vol[lin % g.nr];
+    for (int f = 0; f < g.nf; ++f) s[f] += V * a.in[f][lin];
+  }
+  for (int f = 0; f < g.nf; ++f) {
+    const double t = block_sum<CFL_NT>(s[f], red);
+    if (threadIdx.x == 0) partials[(size_t)f * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// Reduces the per-block partials row by row in a fixed order (so the result
+// does not depend on scheduling): rows 0..nf-1 are summed into sums[], row nf
+// (when dt_slot is set) is minimised into the step-length slot.
+constexpr int RED_NT = 512;
+__global__ void __launch_bounds__(RED_NT) reduce_partials_kernel(const double* partials, int nblocks, int nf,
+                                                                 double* sums, unsigned long long* dt_slot) {
+  __shared__ double red[RED_NT / 32];
+  const int row = blockIdx.x;
+  const double* p = partials + (size_t)row * nblocks;
+  const bool is_min = row == nf;
+  double v = is_min ? INFINITY : 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += RED_NT) v = is_min ? fmin(v, p[b]) : v + p[b];
+  if (is_min) {
+    v = block_min<RED_NT>(v, red);
+    if (threadIdx.x == 0) *dt_slot = (unsigned long long)__double_as_longlong(v);
+  } else {
+    v = block_sum<RED_NT>(v, red);
+    if (threadIdx.x == 0) sums[row] = v;
+  }
+}
+
+template <int NF>
+rossbi_status launch_stage_f64(rossbi_grid* g, const StageArgs& a, int nblocks) {
+  constexpr int BOX = (F64_TR + 4) * (F64_TT + 4) * (F64_TZ + 4);
+  constexpr int NCORE = F64_TR * F64_TT * F64_TZ;
+  constexpr size_t smem = (size_t)NF * (BOX + NCORE) * sizeof(double);
+  auto kern = stage_full_kernel<NF, F64_TR, F64_TT, F64_TZ, F64_NT>;
+  static bool attr = false;
+  if (!attr) {
+    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  kern<<<nblocks, F64_NT, smem, g->stream>>>(a);
+  CK(cudaGetLastError());
+  return ROSSBI_OK;
+}
+
+constexpr int PROFILE_PAIRS = 1024;
+
+rossbi_status profile_drain(rossbi_grid* g) {
+  if (g->ev_used == 0) return ROSSBI_OK;
+  CK(cudaStreamSynchronize(g->stream));
+  for (int q = 0; q < g->ev_used; ++q) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, g->ev[2 * q], g->ev[2 * q + 1]));
+    g->prof_ms += ms;
+  }
+  g->prof_launches += g->ev_used;
+  g->ev_used = 0;
+  return ROSSBI_OK;
+}
+
+rossbi_status launch_stage(rossbi_grid* g, const StageArgs& a, int nblocks) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (g->profiling && a.mode == 0) {
+    if (g->ev_used == PROFILE_PAIRS) {
+      rossbi_status st = profile_drain(g);
+      if (st != ROSSBI_OK) return st;
+    }
+    e0 = g->ev[2 * g->ev_used];
+    e1 = g->ev[2 * g->ev_used + 1];
+    CK(cudaEventRecord(e0, g->stream));
+  }
+  rossbi_status st = g->nf == 9 ? launch_stage_f64<9>(g, a, nblocks) : launch_stage_f64<5>(g, a, nblocks);
+  if (st != ROSSBI_OK) return st;
+  if (e0) {
+    CK(cudaEventRecord(e1, g->stream));
+    g->ev_used++;
+  }
+  return ROSSBI_OK;
+}
+
+template <class T, int NF>
+rossbi_status launch_pert_nf(rossbi_grid* g, const PertArgs<T>& a, int nblocks) {
+  constexpr bool F32 = sizeof(T) == 4;
+  constexpr int TR = P32_TR, TT = P32_TT, TZ = P32_TZ, NT = P32_NT, MINB = F32 ? P32_MINB : 1;
+  constexpr int BOX = (TR + 4) * (TT + 4) * (TZ + 4), NCORE = TR * TT * TZ;
+  constexpr size_t smem = (size_t)NF * (BOX + NCORE) * sizeof(T);
+  auto kern = stage_pert_kernel<T, NF, TR, TT, TZ, NT, MINB>;
+  static bool attr = false;
+  if (!attr) {
+    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  kern<<<nblocks, NT, smem, g->stream>>>(a);
+  CK(cudaGetLastError());
+  return ROSSBI_OK;
+}
+
+template <class T>
+rossbi_status launch_pert(rossbi_grid* g, const PertArgs<T>& a, int nblocks) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (g->profiling) {
+    if (g->ev_used == PROFILE_PAIRS) {
+      rossbi_status st = profile_drain(g);
+      if (st != ROSSBI_OK) return st;
+    }
+    e0 = g->ev[2 * g->ev_used];
+    e1 = g->ev[2 * g->ev_used + 1];
+    CK(cudaEventRecord(e0, g->stream));
+  }
+  rossbi_status st = g->nf == 9 ? launch_pert_nf<T, 9>(g, a, nblocks) : launch_pert_nf<T, 5>(g, a, nblocks);
+  if (st != ROSSBI_OK) return st;
+  if (e0) {
+    CK(cudaEventRecord(e1, g->stream));
+    g->ev_used++;
+  }
+  return ROSSBI_OK;
+}
+
+int n_tiles(const rossbi_grid* g) { return g->tiles_r * g->tiles_t * g->tiles_z; }
+
+rossbi_status ensure_partials(rossbi_grid* g, size_t nblocks) {
+  if (g->partials_cap >= nblocks) return ROSSBI_OK;
+  if (g->d_partials) cudaFree(g->d_partials);
+  g->d_partials = nullptr;
+  g->partials_cap = 0;
+  CK(cudaMalloc(&g->d_partials, nblocks * 10 * sizeof(double)));
+  g->partials_cap = nblocks;
+  return ROSSBI_OK;
+}
+
+StageArgs base_args(rossbi_grid* g) {
+  StageArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.g = g->dg;
+  a.status = g->d_status;
+  a.tiles_r = g->tiles_r;
+  a.tiles_t = g->tiles_t;
+  return a;
+}
+
+// The empty run of Sect. 2.8 on a one-tile-thick azimuthal slab of the grid
+// (same dtheta, so the same arithmetic as every column of the full grid).
+rossbi_status empty_run(rossbi_grid* g) {
+  const rossbi_grid_desc& d = g->desc;
+  const int nth_s = std::min(d.nth, F64_TT);
+  const size_t nslab = (size_t)d.nr * nth_s * d.nz;
+  std::vector<double> E0(nslab * g->nf, 0.0);
+  for (int f = 0; f < 5; ++f)
+    for (int k = 0; k < d.nz; ++k)
+      for (int j = 0; j < nth_s; ++j)
+        for (int i = 0; i < d.nr; ++i)
+          E0[f * nslab + ((size_t)k * nth_s + j) * d.nr + i] = g->h_e0c[((size_t)f * d.nz + k) * d.nr + i];
+  double *dE = nullptr, *dG = nullptr;
+  CK(cudaMalloc(&dE, E0.size() * sizeof(double)));
+  cudaError_t e = cudaMalloc(&dG, E0.size() * sizeof(double));
+  if (e != cudaSuccess) { cudaFree(dE); return ROSSBI_ERR_OOM; }
+  rossbi_status st = ROSSBI_OK;
+  do {
+    if (cudaMemcpyAsync(dE, E0.data(), E0.size() * sizeof(double), cudaMemcpyHostToDevice, g->stream) !=
+        cudaSuccess) { st = ROSSBI_ERR_CUDA; break; }
+    StageArgs a = base_args(g);
+    a.g.nth = nth_s;
+    a.g.r0 = nullptr;
+    for (int f = 0; f < g->nf; ++f) a.in[f] = dE + f * nslab;
+    a.gout = dG;
+    a.mode = 1;
+    a.tiles_t = 1;
+    const int nblocks = g->tiles_r * 1 * g->tiles_z;
+    st = launch_stage(g, a, nblocks);
+    if (st != ROSSBI_OK) break;
+    std::vector<double> G(E0.size());
+    if (cudaMemcpyAsync(G.data(), dG, G.size() * sizeof(double), cudaMemcpyDeviceToHost, g->stream) !=
+        cudaSuccess) { st = ROSSBI_ERR_CUDA; break; }
+    if (cudaStreamSynchronize(g->stream) != cudaSuccess) { st = ROSSBI_ERR_CUDA; break; }
+    std::vector<double> R0((size_t)5 * d.nz * d.nr);
+    for (int f = 0; f < 5; ++f)
+      for (int k = 0; k < d.nz; ++k)
+        for (int i = 0; i < d.nr; ++i)
+          R0[((size_t)f * d.nz + k) * d.nr + i] = G[f * nslab + ((size_t)k * nth_s) * d.nr + i];
+    st = upload(&g->d_r0, R0, g->stream);
+    if (st != ROSSBI_OK) break;
+    if (cudaStreamSynchronize(g->stream) != cudaSuccess) { st = ROSSBI_ERR_CUDA; break; }
+  } while (false);
+  cudaFree(dE);
+  cudaFree(dG);
+  return st;
+}
+
+rossbi_status ensure_scratch(rossbi_grid* g, void** buf) {
+  if (*buf) return ROSSBI_OK;
+  CK(cudaMalloc(buf, g->ncell * g->nf * elem_size(g)));
+  return ROSSBI_OK;
+}
+
+// Tables of the perturbation forms in the state precision T, built from FP64.
+template <class T>
+rossbi_status build_pert_tables(rossbi_grid* g, PertTables<T>& pt) {
+  const rossbi_grid_desc& d = g->desc;
+  const int nr = d.nr, nz = d.nz;
+  const size_t ncen = (size_t)nz * nr, nfr = (size_t)nz * (nr + 1), nfz = (size_t)(nz + 1) * nr;
+  const size_t off_cen = 0, off_fr = off_cen + 8 * ncen, off_fz = off_fr + 5 * nfr, off_ft = off_fz + 5 * nfz;
+  const size_t off_rc = off_ft + 7 * ncen, off_vol = off_rc + (size_t)(nr + 2) * 8, off_ivol = off_vol + nr;
+  const size_t off_ar = off_ivol + nr, off_at = off_ar + nr + 1, off_az = off_at + nr, off_ma = off_az + nr;
+  const size_t off_om = off_ma + nr, total = off_om + nr;
+  std::vector<double> h(total, 0.0);
+  std::vector<double> v(nr), rcoef((size_t)(nr + 2) * 8), ar(nr + 1), at(nr), az(nr), ma(nr), iv(nr);
+  if (cudaMemcpy(v.data(), g->d_vol, nr * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(iv.data(), g->d_ivol, nr * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(rcoef.data(), g->d_rcoef, rcoef.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(ar.data(), g->d_area_r, ar.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(at.data(), g->d_area_t, nr * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(az.data(), g->d_area_z, nr * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(ma.data(), g->d_maxA, nr * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return ROSSBI_ERR_CUDA;
+  for (size_t q = 0; q < rcoef.size(); ++q) h[off_rc + q] = rcoef[q];
+  for (int i = 0; i < nr; ++i) {
+    h[off_vol + i] = v[i];
+    h[off_ivol + i] = iv[i];
+    h[off_at + i] = at[i];
+    h[off_az + i] = az[i];
+    h[off_ma + i] = ma[i];
+    const double r = axis0_centre(d, i);
+    h[off_om + i] = d.geometry == ROSSBI_GEOM_CYL ? std::sqrt(d.gm / (r * r * r)) : 1.0;
+  }
+  for (int i = 0; i <= nr; ++i) h[off_ar + i] = ar[i];
+  if (g->has_disc) {
+    const double dz = (d.x1[2] - d.x0[2]) / nz, Om = d.omega_frame, gam = d.gamma;
+    auto prim = [&](double r, double z, double* out, size_t stride, int nv) {
+      double rho, vth, p, dlnp;
+      equilibrium_prim(d, g->disc, r, z, rho, vth, p, &dlnp);
+      const double v0 = vth - Om * r, c0 = std::sqrt(gam * p / rho);
+      out[0] = rho;
+      out[stride] = v0;
+      out[2 * stride] = p;
+      out[3 * stride] = c0;
+      out[4 * stride] = 0.5 * rho * v0 * v0 + gam * p / (gam - 1.0);
+      if (nv == 7) {
+        out[5 * stride] = v0 - c0;
+        out[6 * stride] = v0 + c0;
+      }
+    };
+    for (int k = 0; k < nz; ++k) {
+      const double z = d.x0[2] + (k + 0.5) * dz;
+      for (int i = 0; i < nr; ++i) {
+        const double r = axis0_centre(d, i);
+        double rho, vth, p, dlnp;
+        equilibrium_prim(d, g->disc, r, z, rho, vth, p, &dlnp);
+        const double v0 = vth - Om * r, R2 = r * r + z * z, R3 = R2 * std::sqrt(R2);
+        const double cs2 = g->disc.T0 * std::pow(r, g->disc.beta_T);
+        double* c = &h[off_cen + (size_t)k * nr + i];
+        c[0] = rho;
+        c[ncen] = v0;
+        c[2 * ncen] = p;
+        c[3 * ncen] = cs2 * dlnp;                       // (1/rho0) dP0/dr
+        c[4 * ncen] = -d.gm * z / R3;                   // f_z
+        c[5 * ncen] = -d.gm * r / R3 + Om * Om * r;     // f_r + Omega^2 r
+        c[6 * ncen] = 2.0 * v0 / r + 2.0 * Om;
+        c[7 * ncen] = 1.0 / r;
+        prim(r, z, &h[off_ft + (size_t)k * nr + i], ncen, 7);
+      }
+      for (int i = 0; i <= nr; ++i) prim(axis0_face(d, i), z, &h[off_fr + (size_t)k * (nr + 1) + i], nfr, 5);
+    }
+    for (int k = 0; k <= nz; ++k) {
+      const double z = d.x0[2] + k * dz;
+      for (int i = 0; i < nr; ++i) prim(axis0_centre(d, i), z, &h[off_fz + (size_t)k * nr + i], nfz, 5);
+    }
+  }
+  std::vector<T> ht(total);
+  for (size_t q = 0; q < total; ++q) ht[q] = (T)h[q];
+  if (g->d_ptab) cudaFree(g->d_ptab);
+  g->d_ptab = nullptr;
+  CK(cudaMalloc(&g->d_ptab, total * sizeof(T)));
+  CK(cudaMemcpy(g->d_ptab, ht.data(), total * sizeof(T), cudaMemcpyHostToDevice));
+  const T* b = (const T*)g->d_ptab;
+  pt.cen = b + off_cen;
+  pt.fr = b + off_fr;
+  pt.fz = b + off_fz;
+  pt.ft = b + off_ft;
+  pt.rcoef = b + off_rc;
+  pt.vol = b + off_vol;
+  pt.ivol = b + off_ivol;
+  pt.area_r = b + off_ar;
+  pt.area_t = b + off_at;
+  pt.area_z = b + off_az;
+  pt.maxA = b + off_ma;
+  pt.omk = b + off_om;
+  if (!g->d_fallbacks) {
+    CK(cudaMalloc(&g->d_fallbacks, sizeof(unsigned long long)));
+    CK(cudaMemset(g->d_fallbacks, 0, sizeof(unsigned long long)));
+  }
+  pt.fallbacks = g->d_fallbacks;
+  for (int f = 0; f < 5; ++f) {
+    double sum = 0.0;
+    for (int k = 0; k < nz; ++k)
+      for (int i = 0; i < nr; ++i) sum += v[i] * g->h_e0c[((size_t)f * nz + k) * nr + i];
+    g->eq_sums[f] = sum * d.nth;
+  }
+  return ROSSBI_OK;
+}
+
+template <class T>
+PertArgs<T> pert_args(rossbi_grid* g) {
+  PertArgs<T> a;
+  std::memset(&a, 0, sizeof(a));
+  a.g = g->dg;
+  if constexpr (sizeof(T) == 4) a.t = g->pt_f;
+  else a.t = g->pt_d;
+  a.status = g->d_status;
+  a.tiles_r = g->tiles_r;
+  a.tiles_t = g->tiles_t;
+  return a;
+}
+
+rossbi_status prepare_step(rossbi_grid* g, void* const* state, void* const* scratch, double dt,
+                           const rossbi_dust_params* dust, void** sc, DragArgs& drag) {
+  if (!g->eq_set) return ROSSBI_ERR_ARG;
+  if (!state) return ROSSBI_ERR_ARG;
+  for (int f = 0; f < g->nf; ++f)
+    if (!state[f]) return ROSSBI_ERR_ARG;
+  if (g->nf == 9 && !dust) return ROSSBI_ERR_ARG;
+  if (dt < 0.0 || !std::isfinite(dt)) return ROSSBI_ERR_ARG;
+  if (dt == 0.0 && !g->dt_on_device) return ROSSBI_ERR_ARG;
+  if (scratch) {
+    for (int f = 0; f < g->nf; ++f) {
+      if (!scratch[f]) return ROSSBI_ERR_ARG;
+      sc[f] = scratch[f];
+    }
+  } else {
+    rossbi_status st = ensure_scratch(g, &g->d_scratch);
+    if (st != ROSSBI_OK) return st;
+    for (int f = 0; f < g->nf; ++f) sc[f] = (char*)g->d_scratch + (size_t)f * g->ncell * elem_size(g);
+  }
+  rossbi_status st = ensure_partials(g, n_tiles(g));
+  if (st != ROSSBI_OK) return st;
+  drag = DragArgs{0.0, 0.0, 0};
+  if (g->nf == 9) {
+    drag.stokes = dust->stokes;
+    drag.law = dust->drag_law;
+    if (!(dust->stokes > 0.0)) return ROSSBI_ERR_ARG;
+    if (dust->drag_law == 1) {
+      if (!g->has_disc) return ROSSBI_ERR_ARG;
+      double rho1, vth1, p1;
+      equilibrium_prim(g->desc, g->disc, 1.0, 0.0, rho1, vth1, p1);
+      drag.rhos_rp = dust->stokes * rho1 * std::sqrt(g->desc.gamma * p1 / rho1) / std::sqrt(g->desc.gm);
+    } else if (dust->drag_law != 0) {
+      return ROSSBI_ERR_ARG;
+    }
+  }
+  return ROSSBI_OK;
+}
+
+rossbi_status finish_step(rossbi_grid* g, int nxt, double* next_dt) {
+  reduce_partials_kernel<<<g->nf + 1, RED_NT, 0, g->stream>>>(g->d_partials, n_tiles(g), g->nf, g->d_sums,
+                                                               g->d_dt + nxt);
+  CK(cudaGetLastError());
+  g->dt_slot = nxt;
+  g->dt_on_device = true;
+  if (next_dt) {
+    CK(cudaMemcpyAsync(g->h_pinned, g->d_dt + nxt, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    const rossbi_status st = sync_and_status(g);
+    *next_dt = g->h_pinned[0];
+    return st;
+  }
+  return ROSSBI_OK;
+}
+
+rossbi_status step_full(rossbi_grid* g, void* const* state, void* const* sc, double dt, const DragArgs& drag,
+                        double* next_dt) {
+  const int nblocks = n_tiles(g);
+  const int cur = g->dt_slot, nxt = 1 - g->dt_slot;
+  StageArgs a = base_args(g);
+  a.drag = drag;
+  a.dt_host = dt;
+  a.dt_dev = dt == 0.0 ? g->d_dt + cur : nullptr;
+  // stage 1: E* = E^n + dt/2 (G(E^n) - R0)/V, then drag
+  for (int f = 0; f < g->nf; ++f) {
+    a.in[f] = (const double*)state[f];
+    a.base[f] = (const double*)state[f];
+    a.out[f] = (double*)sc[f];
+  }
+  a.tau_frac = 0.5;
+  a.stage2 = 0;
+  rossbi_status st = launch_stage(g, a, nblocks);
+  if (st != ROSSBI_OK) return st;
+  // stage 2: E^{n+1} = E^n + dt (G(E*) - R0)/V, then drag; fused CFL and sums
+  for (int f = 0; f < g->nf; ++f) {
+    a.in[f] = (const double*)sc[f];
+    a.base[f] = (const double*)state[f];
+    a.out[f] = (double*)state[f];
+  }
+  a.tau_frac = 1.0;
+  a.stage2 = 1;
+  a.partials = g->d_partials;
+  st = launch_stage(g, a, nblocks);
+  if (st != ROSSBI_OK) return st;
+  return finish_step(g, nxt, next_dt);
+}
+
+template <class T>
+rossbi_status step_pert(rossbi_grid* g, void* const* state, void* const* sc, double dt, const DragArgs& drag,
+                        double* next_dt) {
+  const int nblocks = n_tiles(g);
+  const int cur = g->dt_slot, nxt = 1 - g->dt_slot;
+  PertArgs<T> a = pert_args<T>(g);
+  a.drag = drag;
+  a.dt_host = dt;
+  a.dt_dev = dt == 0.0 ? g->d_dt + cur : nullptr;
+  for (int f = 0; f < g->nf; ++f) {
+    a.in[f] = (const T*)state[f];
+    a.base[f] = (const T*)state[f];
+    a.out[f] = (T*)sc[f];
+  }
+  a.tau_frac = 0.5;
+  a.stage2 = 0;
+  rossbi_status st = launch_pert<T>(g, a, nblocks);
+  if (st != ROSSBI_OK) return st;
+  for (int f = 0; f < g->nf; ++f) {
+    a.in[f] = (const T*)sc[f];
+    a.base[f] = (const T*)state[f];
+    a.out[f] = (T*)state[f];
+  }
+  a.tau_frac = 1.0;
+  a.stage2 = 1;
+  a.partials = g->d_partials;
+  st = launch_pert<T>(g, a, nblocks);
+  if (st != ROSSBI_OK) return st;
+  return finish_step(g, nxt, next_dt);
+}
+
+rossbi_status step_device(rossbi_grid* g, void* const* state, void* const* scratch, double dt,
+                          const rossbi_dust_params* dust, double* next_dt) {
+  void* sc[9];
+  DragArgs drag;
+  rossbi_status st = prepare_step(g, state, scratch, dt, dust, sc, drag);
+  if (st != ROSSBI_OK) return st;
+  switch (g->desc.precision) {
+    case ROSSBI_FP64: return step_full(g, state, sc, dt, drag, next_dt);
+    case ROSSBI_FP32_PERT: return step_pert<float>(g, state, sc, dt, drag, next_dt);
+    default: return step_pert<double>(g, state, sc, dt, drag, next_dt);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rossbi_status_string(rossbi_status s) {
+  switch (s) {
+    case ROSSBI_OK: return "ok";
+    case ROSSBI_ERR_ARG: return "invalid argument";
+    case ROSSBI_ERR_CUDA: return "CUDA error";
+    case ROSSBI_ERR_OOM: return "out of device memory";
+    case ROSSBI_ERR_NONPHYSICAL: return "non-physical state (rho <= 0, P <= 0 or NaN)";
+    case ROSSBI_ERR_RIEMANN: return "Riemann solver did not converge";
+    case ROSSBI_ERR_UNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown status";
+}
+
+int rossbi_nfields(const rossbi_grid* g) { return g ? g->nf : 0; }
+int rossbi_precision(const rossbi_grid* g) { return g ? g->desc.precision : -1; }
+
+void rossbi_destroy(rossbi_grid* g) {
+  if (!g) return;
+  double* tabs[] = {g->d_rc, g->d_rf, g->d_rcoef, g->d_vol, g->d_ivol, g->d_area_r, g->d_area_t,
+                    g->d_area_z, g->d_maxA, g->d_e0c, g->d_e0r, g->d_e0z, g->d_r0, g->d_partials, g->d_sums};
+  for (double* p : tabs)
+    if (p) cudaFree(p);
+  if (g->d_dt) cudaFree(g->d_dt);
+  if (g->d_status) cudaFree(g->d_status);
+  if (g->d_scratch) cudaFree(g->d_scratch);
+  if (g->d_hoststate) cudaFree(g->d_hoststate);
+  if (g->d_ptab) cudaFree(g->d_ptab);
+  if (g->d_fallbacks) cudaFree(g->d_fallbacks);
+  if (g->h_pinned) cudaFreeHost(g->h_pinned);
+  for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
+  delete g;
+}
+
+rossbi_status rossbi_init_grid(const rossbi_grid_desc* desc, void* cuda_stream, rossbi_grid** out) {
+  if (!desc || !out) return ROSSBI_ERR_ARG;
+  *out = nullptr;
+  const rossbi_status chk = check_desc(*desc);
+  if (chk != ROSSBI_OK) return chk;
+  rossbi_grid* g = new (std::nothrow) rossbi_grid();
+  if (!g) return ROSSBI_ERR_OOM;
+  g->desc = *desc;
+  g->stream = (cudaStream_t)cuda_stream;
+  g->nf = desc->n_dust ? 9 : 5;
+  g->ncell = (size_t)desc->nr * desc->nth * desc->nz;
+  g->tiles_r = (desc->nr + F64_TR - 1) / F64_TR;
+  g->tiles_t = (desc->nth + F64_TT - 1) / F64_TT;
+  g->tiles_z = (desc->nz + F64_TZ - 1) / F64_TZ;
+  const rossbi_grid_desc& d = *desc;
+  const int nr = d.nr;
+  const double dy = (d.x1[1] - d.x0[1]) / d.nth;
+  const double dz = (d.x1[2] - d.x0[2]) / d.nz;
+  std::vector<double> rc(nr + 2 * GH), rf(nr + 2 * GH + 1), rcoef((size_t)(nr + 2) * 8, 0.0);
+  for (int i = -GH; i < nr + GH; ++i) rc[i + GH] = axis0_centre(d, i);
+  for (int i = -GH; i <= nr + GH; ++i) rf[i + GH] = axis0_face(d, i);
+  for (int i = -1; i <= nr; ++i) {  // parabola weights (Sect. 2.7)
+    const double xm = rc[i - 1 + GH], x0 = rc[i + GH], xp = rc[i + 1 + GH];
+    const double fm = rf[i + GH], fp = rf[i + 1 + GH];
+    double* w = &rcoef[(size_t)(i + 1) * 8];
+    w[0] = 1.0 / (x0 - xm);
+    w[1] = 1.0 / (xp - x0);
+    w[2] = 1.0 / (xp - xm);
+    w[3] = x0 - xm;
+    w[4] = xp - x0;
+    w[5] = fm - x0;
+    w[6] = fp - x0;
+  }
+  std::vector<double> vol(nr), ivol(nr), ar(nr + 1), at(nr), az(nr), maxA(nr);
+  if (d.geometry == ROSSBI_GEOM_CYL) {  // Sect. 2.2 finite volumes of the cylindrical mesh
+    for (int i = 0; i <= nr; ++i) ar[i] = rf[i + GH] * dy * dz;
+    for (int i = 0; i < nr; ++i) {
+      const double rm = rf[i + GH], rp = rf[i + 1 + GH];
+      vol[i] = 0.5 * (rp * rp - rm * rm) * dy * dz;
+      at[i] = (rp - rm) * dz;
+      az[i] = 0.5 * (rp * rp - rm * rm) * dy;
+      maxA[i] = std::max(ar[i + 1], std::max(at[i], az[i]));
+    }
+  } else {
+    const double dx = (d.x1[0] - d.x0[0]) / nr;
+    for (int i = 0; i <= nr; ++i) ar[i] = dy * dz;
+    for (int i = 0; i < nr; ++i) {
+      vol[i] = dx * dy * dz;
+      at[i] = dx * dz;
+      az[i] = dx * dy;
+      maxA[i] = std::max(ar[i], std::max(at[i], az[i]));
+    }
+  }
+  for (int i = 0; i < nr; ++i) ivol[i] = 1.0 / vol[i];
+  rossbi_status st = ROSSBI_OK;
+  do {
+    if ((st = upload(&g->d_rc, rc, g->stream)) != ROSSBI_OK) break;
+    if ((st = upload(&g->d_rf, rf, g->stream)) != ROSSBI_OK) break;
+    if ((st = upload(&g->d_rcoef, rcoef, g->stream)) != ROSSBI_OK) break;
+    if ((st = upload(&g->d_vol, vol, g->stream)) != ROSSBI_OK) break;
+    if ((st = upload(&g->d_ivol, ivol, g->stream)) != ROSSBI_OK) break;
+    if ((st = upload(&g->d_area_r, ar, g->stream)) != ROSSBI_OK) break;
+    if ((st = upload(&g->d_area_t, at, g->stream)) != ROSSBI_OK) break;
+    if ((st = upload(&g->d_area_z, az, g->stream)) != ROSSBI_OK) break;
+    if ((st = upload(&g->d_maxA, maxA, g->stream)) != ROSSBI_OK) break;
+    if (cudaMalloc(&g->d_dt, 3 * sizeof(unsigned long long)) != cudaSuccess) { st = ROSSBI_ERR_OOM; break; }
+    if (cudaMalloc(&g->d_sums, 9 * sizeof(double)) != cudaSuccess) { st = ROSSBI_ERR_OOM; break; }
+    if (cudaMalloc(&g->d_status, sizeof(unsigned)) != cudaSuccess) { st = ROSSBI_ERR_OOM; break; }
+    if (cudaMemsetAsync(g->d_status, 0, sizeof(unsigned), g->stream) != cudaSuccess) { st = ROSSBI_ERR_CUDA; break; }
+    if (cudaMallocHost(&g->h_pinned, 16 * sizeof(double)) != cudaSuccess) { st = ROSSBI_ERR_OOM; break; }
+    if (cudaStreamSynchronize(g->stream) != cudaSuccess) { st = ROSSBI_ERR_CUDA; break; }
+  } while (false);
+  if (st != ROSSBI_OK) {
+    rossbi_destroy(g);
+    return st;
+  }
+  DevGrid& dg = g->dg;
+  dg.geom = d.geometry;
+  dg.nr = d.nr;
+  dg.nth = d.nth;
+  dg.nz = d.nz;
+  dg.nf = g->nf;
+  dg.has_eq = 0;
+  for (int a = 0; a < 3; ++a) {
+    dg.bc_lo[a] = d.bc_lo[a];
+    dg.bc_hi[a] = d.bc_hi[a];
+    dg.x0[a] = d.x0[a];
+    dg.dx[a] = (d.x1[a] - d.x0[a]) / (a == 0 ? d.nr : (a == 1 ? d.nth : d.nz));
+  }
+  dg.gamma = d.gamma;
+  dg.gm = d.gm;
+  dg.omega = d.geometry == ROSSBI_GEOM_CYL ? d.omega_frame : 0.0;
+  dg.cfl = d.cfl;
+  dg.rc = g->d_rc;
+  dg.rf = g->d_rf;
+  dg.rcoef = g->d_rcoef;
+  dg.vol = g->d_vol;
+  dg.ivol = g->d_ivol;
+  dg.area_r = g->d_area_r;
+  dg.area_t = g->d_area_t;
+  dg.area_z = g->d_area_z;
+  dg.maxA = g->d_maxA;
+  *out = g;
+  return ROSSBI_OK;
+}
+
+rossbi_status rossbi_set_equilibrium(rossbi_grid* g, const rossbi_disc_params* disc) {
+  if (!g) return ROSSBI_ERR_ARG;
+  const rossbi_grid_desc& d = g->desc;
+  if (d.geometry == ROSSBI_GEOM_CYL && !disc) return ROSSBI_ERR_ARG;
+  g->eq_set = false;
+  g->dg.has_eq = 0;
+  g->dg.e0c = g->dg.e0r = g->dg.e0z = g->dg.r0 = nullptr;
+  g->has_disc = disc != nullptr;
+  if (!disc) {
+    g->h_e0c.assign((size_t)5 * d.nz * d.nr, 0.0);
+    rossbi_status st = ROSSBI_OK;
+    if (d.precision == ROSSBI_FP32_PERT) st = build_pert_tables<float>(g, g->pt_f);
+    else if (d.precision == ROSSBI_FP64_PERT) st = build_pert_tables<double>(g, g->pt_d);
+    if (st != ROSSBI_OK) return st;
+    g->eq_set = true;
+    return ROSSBI_OK;
+  }
+  g->disc = *disc;
+  const int nr = d.nr, nz = d.nz;
+  const double dz = (d.x1[2] - d.x0[2]) / nz;
+  std::vector<double> e0c((size_t)5 * nz * nr), e0r((size_t)5 * nz * (nr + 1)), e0z((size_t)5 * (nz + 1) * nr);
+  for (int k = 0; k < nz; ++k) {
+    const double z = d.x0[2] + (k + 0.5) * dz;
+    for (int i = 0; i < nr; ++i)
+      equilibrium_cons(d, *disc, axis0_centre(d, i), z, &e0c[(size_t)k * nr + i], (size_t)nz * nr);
+    for (int i = 0; i <= nr; ++i)
+      equilibrium_cons(d, *disc, axis0_face(d, i), z, &e0r[(size_t)k * (nr + 1) + i], (size_t)nz * (nr + 1));
+  }
+  for (int k = 0; k <= nz; ++k) {
+    const double z = d.x0[2] + k * dz;
+    for (int i = 0; i < nr; ++i)
+      equilibrium_cons(d, *disc, axis0_centre(d, i), z, &e0z[(size_t)k * nr + i], (size_t)(nz + 1) * nr);
+  }
+  for (double v : e0c)
+    if (!std::isfinite(v)) return ROSSBI_ERR_ARG;
+  rossbi_status st;
+  if ((st = upload(&g->d_e0c, e0c, g->stream)) != ROSSBI_OK) return st;
+  if ((st = upload(&g->d_e0r, e0r, g->stream)) != ROSSBI_OK) return st;
+  if ((st = upload(&g->d_e0z, e0z, g->stream)) != ROSSBI_OK) return st;
+  g->h_e0c = e0c;
+  g->dg.has_eq = 1;
+  g->dg.e0c = g->d_e0c;
+  g->dg.e0r = g->d_e0r;
+  g->dg.e0z = g->d_e0z;
+  if (d.precision == ROSSBI_FP64) {
+    if ((st = empty_run(g)) != ROSSBI_OK) return st;
+    g->dg.r0 = g->d_r0;
+  } else if (d.precision == ROSSBI_FP32_PERT) {
+    if ((st = build_pert_tables<float>(g, g->pt_f)) != ROSSBI_OK) return st;
+  } else {
+    if ((st = build_pert_tables<double>(g, g->pt_d)) != ROSSBI_OK) return st;
+  }
+  g->eq_set = true;
+  return sync_and_status(g);
+}
+
+rossbi_status rossbi_get_equilibrium(rossbi_grid* g, double* host_out) {
+  if (!g || !host_out || !g->eq_set) return ROSSBI_ERR_ARG;
+  std::memcpy(host_out, g->h_e0c.data(), g->h_e0c.size() * sizeof(double));
+  return ROSSBI_OK;
+}
+
+rossbi_status rossbi_cfl_dt(rossbi_grid* g, const void* const* state, double* dt_out) {
+  if (!g || !state || !dt_out || !g->eq_set) return ROSSBI_ERR_ARG;
+  for (int f = 0; f < g->nf; ++f)
+    if (!state[f]) return ROSSBI_ERR_ARG;
+  unsigned long long* slot = g->d_dt + g->dt_slot;
+  set_slot_kernel<<<1, 1, 0, g->stream>>>(slot, 0x7ff0000000000000ull);
+  CK(cudaGetLastError());
+  const int blocks = (int)std::min<size_t>((g->ncell + CFL_NT - 1) / CFL_NT, 152 * 8);
+  const int prec = g->desc.precision;
+  if (prec == ROSSBI_FP64) {
+    StageArgs a = base_args(g);
+    for (int f = 0; f < g->nf; ++f) a.in[f] = (const double*)state[f];
+    cfl_kernel<<<blocks, CFL_NT, 0, g->stream>>>(g->dg, a, slot);
+  } else if (prec == ROSSBI_FP32_PERT) {
+    PertArgs<float> a = pert_args<float>(g);
+    for (int f = 0; f < g->nf; ++f) a.in[f] = (const float*)state[f];
+    if (g->nf == 9) pert_cfl_kernel<float, 9><<<blocks, 256, 0, g->stream>>>(a, slot);
+    else pert_cfl_kernel<float, 5><<<blocks, 256, 0, g->stream>>>(a, slot);
+  } else {
+    PertArgs<double> a = pert_args<double>(g);
+    for (int f = 0; f < g->nf; ++f) a.in[f] = (const double*)state[f];
+    if (g->nf == 9) pert_cfl_kernel<double, 9><<<blocks, 256, 0, g->stream>>>(a, slot);
+    else pert_cfl_kernel<double, 5><<<blocks, 256, 0, g->stream>>>(a, slot);
+  }
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(g->h_pinned, slot, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+  const rossbi_status st = sync_and_status(g);
+  *dt_out = g->h_pinned[0];
+  g->dt_on_device = true;
+  return st;
+}
+
+rossbi_status rossbi_step(rossbi_grid* g, void* const* state, void* const* scratch, double dt,
+                          const rossbi_dust_params* dust, double* next_dt) {
+  if (!g) return ROSSBI_ERR_ARG;
+  return step_device(g, state, scratch, dt, dust, next_dt);
+}
+
+rossbi_status rossbi_step_host(rossbi_grid* g, void* const* host_state, double dt, const rossbi_dust_params* dust,
+                               double* next_dt) {
+  if (!g || !host_state) return ROSSBI_ERR_ARG;
+  for (int f = 0; f < g->nf; ++f)
+    if (!host_state[f]) return ROSSBI_ERR_ARG;
+  rossbi_status st = ensure_scratch(g, &g->d_hoststate);
+  if (st != ROSSBI_OK) return st;
+  const size_t bytes = g->ncell * elem_size(g);
+  void* dev[9];
+  for (int f = 0; f < g->nf; ++f) {
+    dev[f] = (char*)g->d_hoststate + (size_t)f * bytes;
+    CK(cudaMemcpyAsync(dev[f], host_state[f], bytes, cudaMemcpyHostToDevice, g->stream));
+  }
+  double ndt = 0.0;
+  st = step_device(g, dev, nullptr, dt, dust, &ndt);
+  for (int f = 0; f < g->nf; ++f)
+    CK(cudaMemcpyAsync(host_state[f], dev[f], bytes, cudaMemcpyDeviceToHost, g->stream));
+  CK(cudaStreamSynchronize(g->stream));
+  if (next_dt) *next_dt = ndt;
+  return st;
+}
+
+rossbi_status rossbi_conservation_sums(rossbi_grid* g, const void* const* state, double* sums) {
+  if (!g || !state || !sums || !g->eq_set) return ROSSBI_ERR_ARG;
+  for (int f = 0; f < g->nf; ++f)
+    if (!state[f]) return ROSSBI_ERR_ARG;
+  const int blocks = (int)std::min<size_t>((g->ncell + CFL_NT - 1) / CFL_NT, 152 * 8);
+  rossbi_status st = ensure_partials(g, blocks);
+  if (st != ROSSBI_OK) return st;
+  const int prec = g->desc.precision;
+  if (prec == ROSSBI_FP64) {
+    StageArgs a = base_args(g);
+    for (int f = 0; f < g->nf; ++f) a.in[f] = (const double*)state[f];
+    sums_kernel<<<blocks, CFL_NT, 0, g->stream>>>(g->dg, a, g->d_partials);
+  } else if (prec == ROSSBI_FP32_PERT) {
+    PertArgs<float> a = pert_args<float>(g);
+    for (int f = 0; f < g->nf; ++f) a.in[f] = (const float*)state[f];
+    if (g->nf == 9) pert_sums_kernel<float, 9><<<blocks, 256, 0, g->stream>>>(a, g->d_partials);
+    else pert_sums_kernel<float, 5><<<blocks, 256, 0, g->stream>>>(a, g->d_partials);
+  } else {
+    PertArgs<double> a = pert_args<double>(g);
+    for (int f = 0; f < g->nf; ++f) a.in[f] = (const double*)state[f];
+    if (g->nf == 9) pert_sums_kernel<double, 9><<<blocks, 256, 0, g->stream>>>(a, g->d_partials);
+    else pert_sums_kernel<double, 5><<<blocks, 256, 0, g->stream>>>(a, g->d_partials);
+  }
+  CK(cudaGetLastError());
+  reduce_partials_kernel<<<g->nf, RED_NT, 0, g->stream>>>(g->d_partials, blocks, g->nf, g->d_sums, nullptr);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(g->h_pinned, g->d_sums, g->nf * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+  st = sync_and_status(g);
+  for (int f = 0; f < g->nf; ++f) sums[f] = g->h_pinned[f];
+  if (prec != ROSSBI_FP64)
+    for (int f = 0; f < 5; ++f) sums[f] += g->eq_sums[f];
+  return st;
+}
+
+rossbi_status rossbi_fallback_count(rossbi_grid* g, unsigned long long* count) {
+  if (!g || !count) return ROSSBI_ERR_ARG;
+  *count = 0;
+  if (!g->d_fallbacks) return ROSSBI_OK;
+  CK(cudaStreamSynchronize(g->stream));
+  CK(cudaMemcpy(count, g->d_fallbacks, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+  return ROSSBI_OK;
+}
+
+rossbi_status rossbi_profile_enable(rossbi_grid* g, int enable) {
+  if (!g) return ROSSBI_ERR_ARG;
+  if (enable && g->ev.empty()) {
+    g->ev.resize(2 * PROFILE_PAIRS, nullptr);
+    for (auto& e : g->ev) CK(cudaEventCreate(&e));
+  }
+  g->profiling = enable != 0;
+  return ROSSBI_OK;
+}
+
+rossbi_status rossbi_profile_read(rossbi_grid* g, double* stage_ms, int* stage_launches) {
+  if (!g || !stage_ms || !stage_launches) return ROSSBI_ERR_ARG;
+  const rossbi_status st = profile_drain(g);
+  if (st != ROSSBI_OK) return st;
+  *stage_ms = g->prof_ms;
+  *stage_launches = g->prof_launches;
+  g->prof_ms = 0.0;
+  g->prof_launches = 0;
+  return ROSSBI_OK;
+}
+
+rossbi_status rossbi_take_status(rossbi_grid* g) {
+  if (!g) return ROSSBI_ERR_ARG;
+  return sync_and_status(g);
+}
+
+}  // extern "C"

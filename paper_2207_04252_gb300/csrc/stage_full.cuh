@@ -1,0 +1,367 @@
+// Fused RK2 stage kernel of the FP64 (full conservative state) form.
+//
+// One CTA owns a TR x TT x TZ tile of cells.  It stages the tile and a 2-deep
+// halo along each axis into shared memory as deviations E' = E - E0 (Sect.
+// 2.7), then sweeps the three directions.  In a sweep, lines along the
+// direction map onto groups of L = pow2(T + 2) lanes: lane p reconstructs cell
+// p - 1 (parabola + MinMod), receives the upper face state of its lower
+// neighbour by a shuffle, solves the exact Riemann problem on its lower face
+// (Sect. 2.6) and the dust flux, and receives the flux of its upper face by a
+// second shuffle, so each face is solved once per tile.  The flux divergence
+// is accumulated in shared memory; the epilogue adds the sources (App. B),
+// subtracts the balanced residual R0 (Sect. 2.8), applies the RK stage update
+// (Sect. 2.5) and the semi-implicit drag (Sect. 2.9), and in stage 2 fuses the
+// CFL minimum and the FP64 conservation partial sums of the new state.
+#pragma once
+#include "device_common.cuh"
+
+namespace rossbi {
+
+struct StageArgs {
+  DevGrid g;
+  const double* in[9];     // stage input (stencil) state
+  const double* base[9];   // E^n, base of the update
+  double* out[9];          // updated state
+  double* gout;            // mode 1: G(E) - R0 written here, [nf][ncell]
+  double dt_host;
+  const unsigned long long* dt_dev;  // if set, dt is read from this device slot
+  double tau_frac;                   // 0.5 (stage 1) or 1.0 (stage 2)
+  DragArgs drag;
+  int stage2;                        // fuse CFL of the output and conservation partials
+  double* partials;                  // stage 2: [nf + 1][gridDim.x] block sums of V*E, then block dt minima
+  unsigned* status;
+  int mode;                          // 0 update, 1 residual only (empty run)
+  int tiles_r, tiles_t;
+};
+
+__device__ __forceinline__ bool between(double q, double a, double b) {
+  return q >= fmin(a, b) && q <= fmax(a, b);
+}
+
+// Parabola through three deviations with the MinMod rule; w = {1/(x0-xm),
+// 1/(xp-x0), 1/(xp-xm), x0-xm, xp-x0, fm-x0, fp-x0}.  Returns false if flat.
+__device__ __forceinline__ bool parabola(double em, double e0, double ep, const double* w, double& qm, double& qp) {
+  const double sm = (e0 - em) * w[0];
+  const double sp = (ep - e0) * w[1];
+  if (sm * sp <= 0.0) {
+    qm = qp = e0;
+    return false;
+  }
+  const double a = (sp - sm) * w[2];
+  const double b = (sp * w[3] + sm * w[4]) * w[2];
+  qm = e0 + w[5] * (a * w[5] + b);
+  qp = e0 + w[6] * (a * w[6] + b);
+  if (!between(qp, e0, ep) || !between(qm, em, e0)) {
+    const double s = fabs(sm) < fabs(sp) ? sm : sp;
+    qm = e0 + s * w[5];
+    qp = e0 + s * w[6];
+  }
+  return true;
+}
+
+// Ghost rule of Sect. 2.4 for a cell index possibly outside the domain.
+// Returns false for an equilibrium ghost (E' = 0).
+__device__ __forceinline__ bool resolve_cell(const DevGrid& g, int c[3]) {
+  const int n[3] = {g.nr, g.nth, g.nz};
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    if (c[ax] >= 0 && c[ax] < n[ax]) continue;
+    const int bc = c[ax] < 0 ? g.bc_lo[ax] : g.bc_hi[ax];
+    if (bc == BC_EQUILIBRIUM) return false;
+    if (bc == BC_PERIODIC) {
+      c[ax] %= n[ax];
+      if (c[ax] < 0) c[ax] += n[ax];
+    } else {
+      c[ax] = c[ax] < 0 ? 0 : n[ax] - 1;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+template <int NF, int TR, int TT, int TZ, int NT, int D>
+__device__ __forceinline__ void sweep_full(const StageArgs& a, const double* sE, double* sG, int i0, int j0, int k0,
+                                           unsigned& status) {
+  constexpr int BX = TR + 4, BY = TT + 4, BZ = TZ + 4, BOX = BX * BY * BZ, NCORE = TR * TT * TZ;
+  constexpr int TD = D == 0 ? TR : (D == 1 ? TT : TZ);
+  constexpr int L = pow2ceil(TD + 2);
+  static_assert(L <= 32, "line does not fit a warp");
+  constexpr int NA = D == 0 ? TT : TR;
+  constexpr int NB = D == 2 ? TT : TZ;
+  constexpr int ITEMS = NA * NB * L;
+  constexpr int STRIDE = D == 0 ? 1 : (D == 1 ? BX : BX * BY);
+  constexpr int NW = NT / 32;
+  constexpr unsigned FULL = 0xffffffffu;
+  const DevGrid& g = a.g;
+  const double gam = g.gamma;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+  for (int base = warp * 32; base < ITEMS; base += NW * 32) {
+    const int item = base + lane;
+    const bool valid = item < ITEMS;
+    const int line = valid ? item / L : 0;
+    const int c = item % L - 1;
+    const int ta = line % NA, tb = line / NA;
+    const int x = D == 0 ? c : ta;
+    const int y = D == 1 ? c : (D == 0 ? ta : tb);
+    const int z = D == 2 ? c : tb;
+    const int gi = i0 + x, gj = j0 + y, gk = k0 + z;
+    const bool line_ok = valid && (D == 0 ? (gj < g.nth && gk < g.nz)
+                                          : (D == 1 ? (gi < g.nr && gk < g.nz) : (gi < g.nr && gj < g.nth)));
+    const int gd = D == 0 ? gi : (D == 1 ? gj : gk);
+    const int nd = D == 0 ? g.nr : (D == 1 ? g.nth : g.nz);
+    const bool do_recon = line_ok && c <= TD && gd <= nd;
+    const bool do_face = do_recon && c >= 0;
+    const bool do_acc = line_ok && c >= 0 && c < TD && gd < nd;
+    const int sidx = do_recon ? ((z + 2) * BY + (y + 2)) * BX + (x + 2) : (2 * BY + 2) * BX + 2;
+
+    // parabola weights of this cell along D
+    double w[7];
+    if (D == 0) {
+      const double* cw = g.rcoef + (clampi(gi, -1, g.nr) + 1) * 8;
+#pragma unroll
+      for (int q = 0; q < 7; ++q) w[q] = cw[q];
+    } else {
+      const double h = g.dx[D];
+      w[0] = w[1] = 1.0 / h;
+      w[2] = 0.5 / h;
+      w[3] = w[4] = h;
+      w[5] = -0.5 * h;
+      w[6] = 0.5 * h;
+    }
+    // equilibrium gas state on the lower face of this cell (index along D = gd)
+    // and on its upper face; table indices clamped (ghost cells reconstruct flat)
+    const int ci = clampi(gi, 0, g.nr - 1), ck = clampi(gk, 0, g.nz - 1);
+    auto e0_face = [&](int f, int fd) -> double {
+      if (!g.has_eq) return 0.0;
+      if (D == 0) return g.e0r[((size_t)f * g.nz + ck) * (g.nr + 1) + clampi(fd, 0, g.nr)];
+      if (D == 1) return g.e0c[((size_t)f * g.nz + ck) * g.nr + ci];
+      return g.e0z[((size_t)f * (g.nz + 1) + clampi(fd, 0, g.nz)) * g.nr + ci];
+    };
+    double area = 0.0;
+    if (do_face) area = D == 0 ? g.area_r[clampi(gi, 0, g.nr)] : (D == 1 ? g.area_t[ci] : g.area_z[ci]);
+
+    // ---------------- gas: fields 0..4
+    {
+      double qm[5], qp[5];
+      bool shaped = false;
+#pragma unroll
+      for (int f = 0; f < 5; ++f) {
+        const double* s = sE + f * BOX + sidx;
+        shaped |= parabola(s[-STRIDE], s[0], s[STRIDE], w, qm[f], qp[f]);
+      }
+      if (shaped && do_recon) {  // positivity of both reconstructed face states
+        double Um[5], Up[5];
+#pragma unroll
+        for (int f = 0; f < 5; ++f) {
+          Um[f] = e0_face(f, gd) + qm[f];
+          Up[f] = e0_face(f, gd + 1) + qp[f];
+        }
+        const bool ok = Um[RHO] > 0.0 && Up[RHO] > 0.0 &&
+                        gas_pressure(gam, Um[MU], Um[MV], Um[MW], Um[EN], Um[RHO]) > 0.0 &&
+                        gas_pressure(gam, Up[MU], Up[MV], Up[MW], Up[EN], Up[RHO]) > 0.0;
+        if (!ok) {
+#pragma unroll
+          for (int f = 0; f < 5; ++f) qm[f] = qp[f] = sE[f * BOX + sidx];
+        }
+      }
+      double F[5];
+      {
+        double UL[5], UR[5];
+#pragma unroll
+        for (int f = 0; f < 5; ++f) {
+          const double ql = __shfl_up_sync(FULL, qp[f], 1, L);
+          const double e0 = do_face ? e0_face(f, gd) : 0.0;
+          UL[f] = e0 + ql;
+          UR[f] = e0 + qm[f];
+        }
+        if (do_face) {
+          gas_face_flux<D>(gam, UL, UR, F, status);
+#pragma unroll
+          for (int f = 0; f < 5; ++f) F[f] *= area;
+        } else {
+#pragma unroll
+          for (int f = 0; f < 5; ++f) F[f] = 0.0;
+        }
+      }
+#pragma unroll
+      for (int f = 0; f < 5; ++f) {
+        const double Fu = __shfl_down_sync(FULL, F[f], 1, L);
+        if (do_acc) {
+          double* dst = sG + f * NCORE + (z * TT + y) * TR + x;
+          if (D == 0) *dst = F[f] - Fu;
+          else *dst += F[f] - Fu;
+        }
+      }
+    }
+    // ---------------- dust: fields 5..8
+    if (NF == 9) {
+      double qm[4], qp[4];
+      bool shaped = false;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const double* s = sE + (5 + f) * BOX + sidx;
+        shaped |= parabola(s[-STRIDE], s[0], s[STRIDE], w, qm[f], qp[f]);
+      }
+      if (shaped && (qm[3] < 0.0 || qp[3] < 0.0)) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) qm[f] = qp[f] = sE[(5 + f) * BOX + sidx];
+      }
+      double F[4];
+      {
+        double UL[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) UL[f] = __shfl_up_sync(FULL, qp[f], 1, L);
+        if (do_face) {
+          dust_face_flux<D>(UL, qm, F);
+#pragma unroll
+          for (int f = 0; f < 4; ++f) F[f] *= area;
+        } else {
+#pragma unroll
+          for (int f = 0; f < 4; ++f) F[f] = 0.0;
+        }
+      }
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const double Fu = __shfl_down_sync(FULL, F[f], 1, L);
+        if (do_acc) {
+          double* dst = sG + (5 + f) * NCORE + (z * TT + y) * TR + x;
+          if (D == 0) *dst = F[f] - Fu;
+          else *dst += F[f] - Fu;
+        }
+      }
+    }
+  }
+}
+
+template <int NT>
+__device__ __forceinline__ double block_min(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double m = red[0];
+  for (int q = 1; q < NT / 32; ++q) m = fmin(m, red[q]);
+  __syncthreads();
+  return m;
+}
+
+// Fixed-order block sum (deterministic for a fixed launch shape).
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int q = 0; q < NT / 32; ++q) s += red[q];
+  __syncthreads();
+  return s;
+}
+
+template <int NF, int TR, int TT, int TZ, int NT>
+__global__ void __launch_bounds__(NT, 1) stage_full_kernel(const StageArgs a) {
+  constexpr int BX = TR + 4, BY = TT + 4, BZ = TZ + 4, BOX = BX * BY * BZ, NCORE = TR * TT * TZ;
+  extern __shared__ double smem[];
+  double* sE = smem;
+  double* sG = smem + NF * BOX;
+  const DevGrid& g = a.g;
+  const int tile = blockIdx.x;
+  const int i0 = (tile % a.tiles_r) * TR;
+  const int j0 = ((tile / a.tiles_r) % a.tiles_t) * TT;
+  const int k0 = (tile / (a.tiles_r * a.tiles_t)) * TZ;
+  unsigned status = 0;
+
+  // tile + halo as deviations (corners are never read)
+  for (int idx = threadIdx.x; idx < BOX; idx += NT) {
+    const int x = idx % BX - 2, y = (idx / BX) % BY - 2, z = idx / (BX * BY) - 2;
+    const int outside = (x < 0 || x >= TR) + (y < 0 || y >= TT) + (z < 0 || z >= TZ);
+    if (outside > 1) continue;
+    int c[3] = {i0 + x, j0 + y, k0 + z};
+    if (!resolve_cell(g, c)) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) sE[f * BOX + idx] = 0.0;
+      continue;
+    }
+    const size_t lin = ((size_t)c[2] * g.nth + c[1]) * g.nr + c[0];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      double e = a.in[f][lin];
+      if (f < 5 && g.has_eq) e -= g.e0c[((size_t)f * g.nz + c[2]) * g.nr + c[0]];
+      sE[f * BOX + idx] = e;
+    }
+  }
+  __syncthreads();
+  sweep_full<NF, TR, TT, TZ, NT, 0>(a, sE, sG, i0, j0, k0, status);
+  __syncthreads();
+  sweep_full<NF, TR, TT, TZ, NT, 1>(a, sE, sG, i0, j0, k0, status);
+  __syncthreads();
+  sweep_full<NF, TR, TT, TZ, NT, 2>(a, sE, sG, i0, j0, k0, status);
+  __syncthreads();
+
+  const double tau = a.tau_frac * (a.dt_dev ? __longlong_as_double((long long)*a.dt_dev) : a.dt_host);
+  const size_t ncell = (size_t)g.nr * g.nth * g.nz;
+  double dtmin = INFINITY;
+  double sums[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) sums[f] = 0.0;
+  for (int cidx = threadIdx.x; cidx < NCORE; cidx += NT) {
+    const int x = cidx % TR, y = (cidx / TR) % TT, z = cidx / (TR * TT);
+    const int gi = i0 + x, gj = j0 + y, gk = k0 + z;
+    if (gi >= g.nr || gj >= g.nth || gk >= g.nz) continue;
+    const size_t lin = ((size_t)gk * g.nth + gj) * g.nr + gi;
+    double U[NF], G[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      U[f] = a.in[f][lin];
+      G[f] = sG[f * NCORE + cidx];
+    }
+    if (cell_nonphysical(g, U)) status |= STATUS_NONPHYSICAL;
+    if (g.geom == GEOM_CYL) {
+      double S[NF];
+      cell_sources(g, gi, gk, U, S);
+      const double V = g.vol[gi];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) G[f] += V * S[f];
+    }
+    if (g.r0) {
+#pragma unroll
+      for (int f = 0; f < 5; ++f) G[f] -= g.r0[((size_t)f * g.nz + gk) * g.nr + gi];
+    }
+    if (a.mode == 1) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) a.gout[f * ncell + lin] = G[f];
+      continue;
+    }
+    const double iv = g.ivol[gi];
+    double E[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) E[f] = a.base[f][lin] + tau * G[f] * iv;
+    if (NF == 9) apply_drag(g, gi, E, tau, a.drag);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) a.out[f][lin] = E[f];
+    if (a.stage2) {
+      dtmin = fmin(dtmin, cell_dt(g, gi, E));
+      if (cell_nonphysical(g, E)) status |= STATUS_NONPHYSICAL;
+      const double V = g.vol[gi];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) sums[f] += V * E[f];
+    }
+  }
+  if (a.mode == 0 && a.stage2) {
+    double* red = smem;  // the staged tile is no longer needed
+    const double m = block_min<NT>(dtmin, red);
+    if (threadIdx.x == 0) a.partials[(size_t)NF * gridDim.x + blockIdx.x] = m;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const double s = block_sum<NT>(sums[f], red);
+      if (threadIdx.x == 0) a.partials[(size_t)f * gridDim.x + blockIdx.x] = s;
+    }
+  }
+  if (status) atomicOr(a.status, status);
+}
+
+}  // namespace rossbi

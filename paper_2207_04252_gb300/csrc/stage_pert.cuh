@@ -1,0 +1,791 @@
+// Fused RK2 stage kernel of the perturbation forms (state E' = E - E0).
+//
+// Same tiling and sweeps as the FP64 full-state kernel, but every quantity is
+// formed as an exact algebraic difference from the equilibrium state E0
+// (App. A), so that the balanced right-hand side G(E0 + E') - G(E0) of Sect.
+// 2.8 is computed without ever forming the large equilibrium terms (the
+// Keplerian centrifugal and gravity terms are O(rho v_K^2 / r), the
+// perturbations 1e-4 of that and less):
+//   - face primitives: rho = rho0 + rho', du = (m' - rho' u0)/rho,
+//     dP = (gamma-1)(E' - [rho' |u0|^2/2 + rho u0.du + rho |du|^2/2]);
+//   - the exact Riemann solver (Sect. 2.6) iterates on dp* = p* - p0 with
+//     the pressure functions written in p/p_K - 1 (log1p / expm1 for the
+//     rarefaction powers), samples the wave pattern on full values and returns
+//     the face-state perturbation; near-sonic fans use the FP64-derived
+//     u0 -/+ c0 of the face;
+//   - fluxes are differences F(W0 + dW) - F(W0) expanded by hand;
+//   - sources use the FP64-derived equilibrium coefficient
+//     C_r = f_r + Omega^2 r + v0^2/r + 2 Omega v0 = (1/rho0) dP0/dr.
+// The Riemann problem falls back to the FP64 full-state solver on vacuum
+// generation, strong rarefaction (p* < p_K / 10) or slow Newton convergence;
+// the fallbacks are counted.
+#pragma once
+#include "stage_full.cuh"
+
+namespace rossbi {
+
+template <class T>
+struct PertTables {
+  const T* cen;    // [8][nz][nr]   rho0, v0, p0, C_r, f_z, f_r + Omega^2 r, 2 v0/r + 2 Omega, 1/r
+  const T* fr;     // [5][nz][nr+1] rho0, v0, p0, c0, h0 on r faces   (h0 = E0 + p0)
+  const T* fz;     // [5][nz+1][nr] same on z faces
+  const T* ft;     // [7][nz][nr]   same on theta faces (= centres), then v0 - c0, v0 + c0
+  const T* rcoef;  // axis-0 parabola weights, as DevGrid::rcoef
+  const T* vol;
+  const T* ivol;
+  const T* area_r;
+  const T* area_t;
+  const T* area_z;
+  const T* maxA;
+  const T* omk;    // Omega_K at the cell-centre radius (constant-St drag)
+  unsigned long long* fallbacks;  // count of FP64 fallback Riemann faces
+};
+
+template <class T> struct Math;
+template <> struct Math<float> {
+  static __device__ __forceinline__ float log1p_(float x) { return log1pf(x); }
+  static __device__ __forceinline__ float expm1_(float x) { return expm1f(x); }
+  static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+  static __device__ __forceinline__ float abs_(float x) { return fabsf(x); }
+  static constexpr float eps = 1.1920929e-7f;
+  static constexpr int max_iter = 24;
+};
+template <> struct Math<double> {
+  static __device__ __forceinline__ double log1p_(double x) { return log1p(x); }
+  static __device__ __forceinline__ double expm1_(double x) { return expm1(x); }
+  static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+  static __device__ __forceinline__ double abs_(double x) { return fabs(x); }
+  static constexpr double eps = 2.220446049250313e-16;
+  static constexpr int max_iter = 60;
+};
+
+// (1 + x)^a - 1, accurate for small x.
+template <class T>
+__device__ __forceinline__ T pow1pm1(T x, T a) {
+  return Math<T>::expm1_(a * Math<T>::log1p_(x));
+}
+// sqrt(1 + t) - 1, accurate for small t.
+template <class T>
+__device__ __forceinline__ T sqrt1pm1(T t) {
+  return t / (Math<T>::sqrt_(T(1) + t) + T(1));
+}
+
+// Face equilibrium in the frame of a face normal to axis D.
+template <class T>
+struct PFace {
+  T rho, un, ut1, ut2, p, c, h, un_mc, un_pc;
+};
+
+// Perturbation of one side of a face, with the full values the wave pattern needs.
+template <class T>
+struct PSide {
+  T drho, dun, dut1, dut2, dp;  // perturbations
+  T rho, un, p, c, dc;          // full values and c - c0
+};
+
+// Conservative perturbations (5 gas fields) -> primitive perturbations about
+// the face equilibrium, in the frame of axis D.  Returns false if the full
+// state is not physical.
+template <class T, int D>
+__device__ __forceinline__ bool pert_side(T g, const PFace<T>& W0, T v0, const T* q, bool has_eq, PSide<T>& s) {
+  const T rho = W0.rho + q[RHO];
+  const T ir = T(1) / rho;
+  const T dur = q[MU] * ir;
+  const T dvt = (q[MV] - q[RHO] * v0) * ir;
+  const T dwz = q[MW] * ir;
+  const T dke = T(0.5) * q[RHO] * v0 * v0 + rho * v0 * dvt + T(0.5) * rho * (dur * dur + dvt * dvt + dwz * dwz);
+  const T dp = (g - T(1)) * (q[EN] - dke);
+  s.drho = q[RHO];
+  s.dp = dp;
+  s.dun = D == 0 ? dur : (D == 1 ? dvt : dwz);
+  s.dut1 = D == 0 ? dvt : dur;
+  s.dut2 = D == 2 ? dvt : dwz;
+  s.rho = rho;
+  s.p = W0.p + dp;
+  s.un = W0.un + s.dun;
+  if (!(rho > T(0)) || !(s.p > T(0))) return false;
+  s.c = Math<T>::sqrt_(g * s.p * ir);
+  if (has_eq) {
+    s.dc = W0.c * sqrt1pm1((dp * W0.rho - W0.p * q[RHO]) / (W0.p * rho));
+  } else {
+    s.dc = s.c;
+  }
+  return true;
+}
+
+// Pressure function of side K at trial p = p0 + d, in perturbation form.
+template <class T>
+__device__ __forceinline__ void pert_pressure_fn(T g, const PSide<T>& K, T p, T d, T& f, T& fd) {
+  const T dpk = d - K.dp;  // p - p_K
+  if (dpk <= T(0)) {
+    const T x = dpk / K.p;
+    const T r = pow1pm1(x, (g - T(1)) / (T(2) * g));  // (p/p_K)^((g-1)/2g) - 1
+    f = T(2) * K.c / (g - T(1)) * r;
+    fd = (T(1) + r) / ((T(1) + x) * K.rho * K.c);
+  } else {
+    const T A = T(2) / ((g + T(1)) * K.rho);
+    const T B = (g - T(1)) / (g + T(1)) * K.p;
+    const T q = Math<T>::sqrt_(A / (B + p));
+    f = dpk * q;
+    fd = (T(1) - T(0.5) * dpk / (B + p)) * q;
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void fan_pert(T g, const PFace<T>& W0, const PSide<T>& K, bool left, T& drho, T& dun,
+                                         T& dp) {
+  const T g6 = (g - T(1)) / (g + T(1));
+  if (left) {  // (u_L - c_L) = (u0 - c0) + du_L - dc_L
+    const T y = g6 * (W0.un_mc + K.dun - K.dc) / K.c;
+    drho = K.drho + K.rho * pow1pm1(y, T(2) / (g - T(1)));
+    dp = K.dp + K.p * pow1pm1(y, T(2) * g / (g - T(1)));
+    dun = -W0.un_mc + K.dc + K.c * y;
+  } else {     // (-u_R - c_R) = -(u0 + c0) - du_R - dc_R
+    const T y = g6 * (-W0.un_pc - K.dun - K.dc) / K.c;
+    drho = K.drho + K.rho * pow1pm1(y, T(2) / (g - T(1)));
+    dp = K.dp + K.p * pow1pm1(y, T(2) * g / (g - T(1)));
+    dun = -W0.un_pc - K.dc - K.c * y;
+  }
+}
+
+// Perturbation of the face state of the exact Riemann solution.  Returns
+// 0 on success, 1 when the caller must use the FP64 full-state solver.
+template <class T>
+__device__ __forceinline__ int pert_riemann(T g, const PFace<T>& W0, const PSide<T>& L, const PSide<T>& R, T& drho,
+                                            T& dun, T& dp, int& side) {
+  if (T(2) / (g - T(1)) * (L.c + R.c) <= R.un - L.un) return 1;  // vacuum generation
+  const T du = R.dun - L.dun;
+  const T floor_p = T(1e-8) * fmin(L.p, R.p);
+  T d = T(0.5) * (L.dp + R.dp) - T(0.125) * du * (L.rho + R.rho) * (L.c + R.c);  // PVRS in dp
+  if (W0.p + d < floor_p) d = floor_p - W0.p;
+  const T scale = Math<T>::abs_(L.dp) + Math<T>::abs_(R.dp) + (L.rho * L.c + R.rho * R.c) * Math<T>::abs_(du);
+  T fl, fdl, fr, fdr;
+  bool conv = false;
+  for (int it = 0; it < Math<T>::max_iter; ++it) {
+    const T p = W0.p + d;
+    pert_pressure_fn(g, L, p, d, fl, fdl);
+    pert_pressure_fn(g, R, p, d, fr, fdr);
+    T dn = d - (fl + fr + du) / (fdl + fdr);
+    if (W0.p + dn < floor_p) dn = floor_p - W0.p;
+    const T change = Math<T>::abs_(dn - d);
+    d = dn;
+    if (change <= T(8) * Math<T>::eps * (scale + Math<T>::abs_(d))) {
+      conv = true;
+      break;
+    }
+  }
+  if (!conv) return 1;
+  const T ps = W0.p + d;
+  if (ps < T(0.1) * fmin(L.p, R.p)) return 1;  // strong rarefaction: near vacuum
+  pert_pressure_fn(g, L, ps, d, fl, fdl);
+  pert_pressure_fn(g, R, ps, d, fr, fdr);
+  const T dus = T(0.5) * (L.dun + R.dun) + T(0.5) * (fr - fl);
+  const T us = W0.un + dus;
+  const T g6 = (g - T(1)) / (g + T(1));
+  if (us >= T(0)) {
+    side = -1;
+    const T x = (d - L.dp) / L.p;  // p*/p_L - 1
+    if (d <= L.dp) {
+      if (L.un - L.c >= T(0)) { drho = L.drho; dun = L.dun; dp = L.dp; return 0; }
+      const T cs = L.c * (T(1) + pow1pm1(x, (g - T(1)) / (T(2) * g)));
+      if (us - cs < T(0)) { drho = L.drho + L.rho * pow1pm1(x, T(1) / g); dun = dus; dp = d; return 0; }
+      fan_pert(g, W0, L, true, drho, dun, dp);
+      return 0;
+    }
+    if (L.un - L.c * Math<T>::sqrt_(T(1) + (g + T(1)) / (T(2) * g) * x) >= T(0)) {
+      drho = L.drho; dun = L.dun; dp = L.dp; return 0;
+    }
+    drho = L.drho + L.rho * x * (T(1) - g6) / (T(1) + g6 * (T(1) + x));
+    dun = dus;
+    dp = d;
+    return 0;
+  }
+  side = 1;
+  const T x = (d - R.dp) / R.p;  // p*/p_R - 1
+  if (d > R.dp) {
+    if (R.un + R.c * Math<T>::sqrt_(T(1) + (g + T(1)) / (T(2) * g) * x) <= T(0)) {
+      drho = R.drho; dun = R.dun; dp = R.dp; return 0;
+    }
+    drho = R.drho + R.rho * x * (T(1) - g6) / (T(1) + g6 * (T(1) + x));
+    dun = dus;
+    dp = d;
+    return 0;
+  }
+  if (R.un + R.c <= T(0)) { drho = R.drho; dun = R.dun; dp = R.dp; return 0; }
+  const T cs = R.c * (T(1) + pow1pm1(x, (g - T(1)) / (T(2) * g)));
+  if (us + cs > T(0)) { drho = R.drho + R.rho * pow1pm1(x, T(1) / g); dun = dus; dp = d; return 0; }
+  fan_pert(g, W0, R, false, drho, dun, dp);
+  return 0;
+}
+
+// F(W0 + dW) - F(W0) for a face normal to axis D (App. B flux components,
+// energy flux (E + P) u_n), written without forming the equilibrium flux.
+template <class T, int D>
+__device__ __forceinline__ void pert_flux(T g, const PFace<T>& W0, T drho, T dun, T dut1, T dut2, T dp, T* F) {
+  constexpr int n = Axes<D>::n, t1 = Axes<D>::t1, t2 = Axes<D>::t2;
+  const T un = W0.un + dun, ut1 = W0.ut1 + dut1, ut2 = W0.ut2 + dut2;
+  const T dmass = drho * un + W0.rho * dun;
+  const T m0 = W0.rho * W0.un;
+  F[RHO] = dmass;
+  F[n] = dmass * un + m0 * dun + dp;
+  F[t1] = dmass * ut1 + m0 * dut1;
+  F[t2] = dmass * ut2 + m0 * dut2;
+  const T du2 = dun * (T(2) * W0.un + dun) + dut1 * (T(2) * W0.ut1 + dut1) + dut2 * (T(2) * W0.ut2 + dut2);
+  const T dh = T(0.5) * drho * (un * un + ut1 * ut1 + ut2 * ut2) + T(0.5) * W0.rho * du2 + g / (g - T(1)) * dp;
+  F[EN] = dh * un + W0.h * dun;
+}
+
+// Gas flux perturbation through a face normal to D from the reconstructed
+// left/right conservative perturbations.
+template <class T, int D>
+__device__ __forceinline__ void pert_gas_flux(T g, const PFace<T>& W0, T v0, const T* qL, const T* qR, bool has_eq,
+                                              T* F, unsigned& status, unsigned& nfallback) {
+  PSide<T> L, R;
+  const bool okL = pert_side<T, D>(g, W0, v0, qL, has_eq, L);
+  const bool okR = pert_side<T, D>(g, W0, v0, qR, has_eq, R);
+  if (!okL || !okR) {
+    status |= STATUS_NONPHYSICAL;
+#pragma unroll
+    for (int f = 0; f < 5; ++f) F[f] = T(0);
+    return;
+  }
+  T drho, dun, dp;
+  int side = 0;
+  if (pert_riemann(g, W0, L, R, drho, dun, dp, side) != 0) {
+    // FP64 full-state solver on W0 + dW
+    ++nfallback;
+    const double rl = (double)W0.rho + (double)L.drho, rr = (double)W0.rho + (double)R.drho;
+    const double ul = (double)W0.un + (double)L.dun, ur = (double)W0.un + (double)R.dun;
+    const double pl = (double)W0.p + (double)L.dp, pr = (double)W0.p + (double)R.dp;
+    double rho, u, p;
+    side = riemann_face((double)g, rl, ul, pl, rr, ur, pr, rho, u, p, status);
+    drho = (T)(rho - (double)W0.rho);
+    dun = (T)(u - (double)W0.un);
+    dp = (T)(p - (double)W0.p);
+  }
+  T dut1 = T(0), dut2 = T(0);
+  if (side < 0) { dut1 = L.dut1; dut2 = L.dut2; }
+  else if (side > 0) { dut1 = R.dut1; dut2 = R.dut2; }
+  else { dut1 = -W0.ut1; dut2 = -W0.ut2; }  // vacuum: no transverse motion
+  pert_flux<T, D>(g, W0, drho, dun, dut1, dut2, dp, F);
+}
+
+// Pressureless dust flux in T (dust has no equilibrium: full values).
+template <class T, int D>
+__device__ __forceinline__ void dust_face_flux_t(const T* UL, const T* UR, T* F) {
+  constexpr int n = Axes<D>::n, t1 = Axes<D>::t1, t2 = Axes<D>::t2;
+  const T rl = UL[3], rr = UR[3];
+  const T ul = rl > T(0) ? UL[n] / rl : T(0);
+  const T ur = rr > T(0) ? UR[n] / rr : T(0);
+  int pick;
+  if (ul <= T(0) && ur >= T(0)) pick = 0;
+  else if (ul >= T(0) && ur >= T(0)) pick = -1;
+  else if (ul <= T(0) && ur <= T(0)) pick = 1;
+  else {
+    const T sl = Math<T>::sqrt_(rl), sr = Math<T>::sqrt_(rr);
+    const T vs = (sl * ul + sr * ur) / (sl + sr);
+    pick = vs > T(0) ? -1 : (vs < T(0) ? 1 : 2);
+  }
+  T fl[4] = {T(0), T(0), T(0), T(0)}, fr[4] = {T(0), T(0), T(0), T(0)};
+  if (pick != 1 && rl > T(0)) {
+    const T m = rl * ul;
+    fl[0] = m; fl[1] = m * ul; fl[2] = m * (UL[t1] / rl); fl[3] = m * (UL[t2] / rl);
+  }
+  if (pick != -1 && rr > T(0)) {
+    const T m = rr * ur;
+    fr[0] = m; fr[1] = m * ur; fr[2] = m * (UR[t1] / rr); fr[3] = m * (UR[t2] / rr);
+  }
+  T s[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    s[q] = pick == -1 ? fl[q] : pick == 1 ? fr[q] : pick == 2 ? T(0.5) * (fl[q] + fr[q]) : T(0);
+  F[3] = s[0];
+  F[n] = s[1];
+  F[t1] = s[2];
+  F[t2] = s[3];
+}
+
+template <class T>
+__device__ __forceinline__ bool parabola_t(T em, T e0, T ep, const T* w, T& qm, T& qp) {
+  const T sm = (e0 - em) * w[0];
+  const T sp = (ep - e0) * w[1];
+  if (sm * sp <= T(0)) {
+    qm = qp = e0;
+    return false;
+  }
+  const T a = (sp - sm) * w[2];
+  const T b = (sp * w[3] + sm * w[4]) * w[2];
+  qm = e0 + w[5] * (a * w[5] + b);
+  qp = e0 + w[6] * (a * w[6] + b);
+  const bool okp = qp >= fmin(e0, ep) && qp <= fmax(e0, ep);
+  const bool okm = qm >= fmin(em, e0) && qm <= fmax(em, e0);
+  if (!okp || !okm) {
+    const T s = Math<T>::abs_(sm) < Math<T>::abs_(sp) ? sm : sp;
+    qm = e0 + s * w[5];
+    qp = e0 + s * w[6];
+  }
+  return true;
+}
+
+template <class T>
+struct PertArgs {
+  DevGrid g;          // geometry, sizes, boundary conditions, double tables
+  PertTables<T> t;
+  const T* in[9];
+  const T* base[9];
+  T* out[9];
+  double dt_host;
+  const unsigned long long* dt_dev;
+  double tau_frac;
+  DragArgs drag;
+  int stage2;
+  double* partials;  // stage 2: [nf + 1][gridDim.x] block sums of V*E', then block dt minima
+  unsigned* status;
+  int tiles_r, tiles_t;
+};
+
+template <class T, int D>
+__device__ __forceinline__ PFace<T> face_eq(const PertTables<T>& t, const DevGrid& g, int ci, int ck, int fd,
+                                            T& v0) {
+  PFace<T> W;
+  if (!g.has_eq) {
+    W.rho = W.un = W.ut1 = W.ut2 = W.p = W.c = W.h = W.un_mc = W.un_pc = T(0);
+    v0 = T(0);
+    return W;
+  }
+  if (D == 1) {
+    const size_t s = (size_t)g.nz * g.nr, o = (size_t)ck * g.nr + ci;
+    W.rho = t.ft[o];
+    v0 = t.ft[s + o];
+    W.p = t.ft[2 * s + o];
+    W.c = t.ft[3 * s + o];
+    W.h = t.ft[4 * s + o];
+    W.un_mc = t.ft[5 * s + o];
+    W.un_pc = t.ft[6 * s + o];
+    W.un = v0;
+    W.ut1 = W.ut2 = T(0);
+    return W;
+  }
+  const T* tab;
+  size_t s, o;
+  if (D == 0) {
+    tab = t.fr;
+    s = (size_t)g.nz * (g.nr + 1);
+    o = (size_t)ck * (g.nr + 1) + clampi(fd, 0, g.nr);
+  } else {
+    tab = t.fz;
+    s = (size_t)(g.nz + 1) * g.nr;
+    o = (size_t)clampi(fd, 0, g.nz) * g.nr + ci;
+  }
+  W.rho = tab[o];
+  v0 = tab[s + o];
+  W.p = tab[2 * s + o];
+  W.c = tab[3 * s + o];
+  W.h = tab[4 * s + o];
+  W.un = T(0);
+  W.un_mc = -W.c;
+  W.un_pc = W.c;
+  W.ut1 = D == 0 ? v0 : T(0);  // r face: t1 = theta;  z face: t1 = r, t2 = theta
+  W.ut2 = D == 2 ? v0 : T(0);
+  return W;
+}
+
+template <class T, int NF, int TR, int TT, int TZ, int NT, int D>
+__device__ __forceinline__ void sweep_pert(const PertArgs<T>& a, const T* sE, T* sG, int i0, int j0, int k0,
+                                           unsigned& status, unsigned& nfallback) {
+  constexpr int BX = TR + 4, BY = TT + 4, BZ = TZ + 4, BOX = BX * BY * BZ, NCORE = TR * TT * TZ;
+  constexpr int TD = D == 0 ? TR : (D == 1 ? TT : TZ);
+  constexpr int L = pow2ceil(TD + 2);
+  static_assert(L <= 32, "line does not fit a warp");
+  constexpr int NA = D == 0 ? TT : TR;
+  constexpr int NB = D == 2 ? TT : TZ;
+  constexpr int ITEMS = NA * NB * L;
+  constexpr int STRIDE = D == 0 ? 1 : (D == 1 ? BX : BX * BY);
+  constexpr int NW = NT / 32;
+  constexpr unsigned FULL = 0xffffffffu;
+  const DevGrid& g = a.g;
+  const T gam = (T)g.gamma;
+  const bool has_eq = g.has_eq != 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+  for (int base = warp * 32; base < ITEMS; base += NW * 32) {
+    const int item = base + lane;
+    const bool valid = item < ITEMS;
+    const int line = valid ? item / L : 0;
+    const int c = item % L - 1;
+    const int ta = line % NA, tb = line / NA;
+    const int x = D == 0 ? c : ta;
+    const int y = D == 1 ? c : (D == 0 ? ta : tb);
+    const int z = D == 2 ? c : tb;
+    const int gi = i0 + x, gj = j0 + y, gk = k0 + z;
+    const bool line_ok = valid && (D == 0 ? (gj < g.nth && gk < g.nz)
+                                          : (D == 1 ? (gi < g.nr && gk < g.nz) : (gi < g.nr && gj < g.nth)));
+    const int gd = D == 0 ? gi : (D == 1 ? gj : gk);
+    const int nd = D == 0 ? g.nr : (D == 1 ? g.nth : g.nz);
+    const bool do_recon = line_ok && c <= TD && gd <= nd;
+    const bool do_face = do_recon && c >= 0;
+    const bool do_acc = line_ok && c >= 0 && c < TD && gd < nd;
+    const int sidx = do_recon ? ((z + 2) * BY + (y + 2)) * BX + (x + 2) : (2 * BY + 2) * BX + 2;
+    T w[7];
+    if (D == 0) {
+      const T* cw = a.t.rcoef + (clampi(gi, -1, g.nr) + 1) * 8;
+#pragma unroll
+      for (int q = 0; q < 7; ++q) w[q] = cw[q];
+    } else {
+      const T h = (T)g.dx[D];
+      w[0] = w[1] = T(1) / h;
+      w[2] = T(0.5) / h;
+      w[3] = w[4] = h;
+      w[5] = T(-0.5) * h;
+      w[6] = T(0.5) * h;
+    }
+    const int ci = clampi(gi, 0, g.nr - 1), ck = clampi(gk, 0, g.nz - 1);
+    T area = T(0);
+    if (do_face) area = D == 0 ? a.t.area_r[clampi(gi, 0, g.nr)] : (D == 1 ? a.t.area_t[ci] : a.t.area_z[ci]);
+    {
+      T qm[5], qp[5];
+      bool shaped = false;
+#pragma unroll
+      for (int f = 0; f < 5; ++f) {
+        const T* s = sE + f * BOX + sidx;
+        shaped |= parabola_t(s[-STRIDE], s[0], s[STRIDE], w, qm[f], qp[f]);
+      }
+      if (shaped && do_recon) {  // positivity of both reconstructed face states
+        T v0m, v0p;
+        const PFace<T> Wm = face_eq<T, D>(a.t, g, ci, ck, gd, v0m);
+        const PFace<T> Wp = face_eq<T, D>(a.t, g, ci, ck, gd + 1, v0p);
+        PSide<T> sm, sp;
+        const bool ok = pert_side<T, D>(gam, Wm, v0m, qm, has_eq, sm) && pert_side<T, D>(gam, Wp, v0p, qp, has_eq, sp);
+        if (!ok) {
+#pragma unroll
+          for (int f = 0; f < 5; ++f) qm[f] = qp[f] = sE[f * BOX + sidx];
+        }
+      }
+      T F[5];
+      {
+        T ql[5];
+#pragma unroll
+        for (int f = 0; f < 5; ++f) ql[f] = __shfl_up_sync(FULL, qp[f], 1, L);
+        if (do_face) {
+          T v0;
+          const PFace<T> W0 = face_eq<T, D>(a.t, g, ci, ck, gd, v0);
+          pert_gas_flux<T, D>(gam, W0, v0, ql, qm, has_eq, F, status, nfallback);
+#pragma unroll
+          for (int f = 0; f < 5; ++f) F[f] *= area;
+        } else {
+#pragma unroll
+          for (int f = 0; f < 5; ++f) F[f] = T(0);
+        }
+      }
+#pragma unroll
+      for (int f = 0; f < 5; ++f) {
+        const T Fu = __shfl_down_sync(FULL, F[f], 1, L);
+        if (do_acc) {
+          T* dst = sG + f * NCORE + (z * TT + y) * TR + x;
+          if (D == 0) *dst = F[f] - Fu;
+          else *dst += F[f] - Fu;
+        }
+      }
+    }
+    if (NF == 9) {
+      T qm[4], qp[4];
+      bool shaped = false;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const T* s = sE + (5 + f) * BOX + sidx;
+        shaped |= parabola_t(s[-STRIDE], s[0], s[STRIDE], w, qm[f], qp[f]);
+      }
+      if (shaped && (qm[3] < T(0) || qp[3] < T(0))) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) qm[f] = qp[f] = sE[(5 + f) * BOX + sidx];
+      }
+      T F[4];
+      {
+        T UL[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) UL[f] = __shfl_up_sync(FULL, qp[f], 1, L);
+        if (do_face) {
+          dust_face_flux_t<T, D>(UL, qm, F);
+#pragma unroll
+          for (int f = 0; f < 4; ++f) F[f] *= area;
+        } else {
+#pragma unroll
+          for (int f = 0; f < 4; ++f) F[f] = T(0);
+        }
+      }
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const T Fu = __shfl_down_sync(FULL, F[f], 1, L);
+        if (do_acc) {
+          T* dst = sG + (5 + f) * NCORE + (z * TT + y) * TR + x;
+          if (D == 0) *dst = F[f] - Fu;
+          else *dst += F[f] - Fu;
+        }
+      }
+    }
+  }
+}
+
+// Cell-centre equilibrium coefficients.
+template <class T>
+struct PCell {
+  T rho0, v0, p0, Cr, fz, gr, cor, ir;
+};
+
+template <class T>
+__device__ __forceinline__ PCell<T> cell_eq(const PertTables<T>& t, const DevGrid& g, int i, int k) {
+  PCell<T> c;
+  if (!g.has_eq) {
+    c.rho0 = c.v0 = c.p0 = c.Cr = c.fz = c.gr = c.cor = c.ir = T(0);
+    return c;
+  }
+  const size_t s = (size_t)g.nz * g.nr, o = (size_t)k * g.nr + i;
+  c.rho0 = t.cen[o];
+  c.v0 = t.cen[s + o];
+  c.p0 = t.cen[2 * s + o];
+  c.Cr = t.cen[3 * s + o];
+  c.fz = t.cen[4 * s + o];
+  c.gr = t.cen[5 * s + o];
+  c.cor = t.cen[6 * s + o];
+  c.ir = t.cen[7 * s + o];
+  return c;
+}
+
+// Primitive perturbations at a cell centre: rho, (du, dv, dw), dp.
+template <class T>
+__device__ __forceinline__ void cell_prim(T g, const PCell<T>& c, const T* q, T& rho, T& du, T& dv, T& dw, T& dp) {
+  rho = c.rho0 + q[RHO];
+  const T ir = T(1) / rho;
+  du = q[MU] * ir;
+  dv = (q[MV] - q[RHO] * c.v0) * ir;
+  dw = q[MW] * ir;
+  const T dke = T(0.5) * q[RHO] * c.v0 * c.v0 + rho * c.v0 * dv + T(0.5) * rho * (du * du + dv * dv + dw * dw);
+  dp = (g - T(1)) * (q[EN] - dke);
+}
+
+// Source perturbation S(E0 + E') - S(E0) per unit volume (App. B sources,
+// stellar gravity, rotating frame), cylindrical geometry.
+template <class T, int NF>
+__device__ __forceinline__ void pert_sources(const DevGrid& g, const PCell<T>& c, const T* q, T* S) {
+  const T gam = (T)g.gamma, Om = (T)g.omega;
+  T rho, du, dv, dw, dp;
+  cell_prim(gam, c, q, rho, du, dv, dw, dp);
+  const T v = c.v0 + dv;
+  S[MU] = q[RHO] * c.Cr + rho * dv * c.cor + rho * dv * dv * c.ir + dp * c.ir;
+  S[MV] = -rho * du * (v * c.ir + T(2) * Om);
+  S[MW] = q[RHO] * c.fz;
+  S[EN] = rho * du * c.gr + rho * dw * c.fz;
+  S[RHO] = T(0);
+  if (NF == 9) {
+    const T rd = q[DRHO];
+    if (rd > T(0)) {
+      const T ird = T(1) / rd;
+      const T dvd = (q[DMV] - rd * c.v0) * ird;  // v_d - v0
+      const T vd = c.v0 + dvd;
+      S[DMU] = rd * (c.Cr + dvd * c.cor + dvd * dvd * c.ir);
+      S[DMV] = -q[DMU] * (vd * c.ir + T(2) * Om);
+      S[DMW] = rd * c.fz;
+    } else {
+      S[DMU] = S[DMV] = S[DMW] = T(0);
+    }
+    S[DRHO] = T(0);
+  }
+}
+
+// Semi-implicit drag on a perturbation-form cell state (same closed form as the
+// full-state kernel; the gas velocity is u0 + du).
+template <class T>
+__device__ __forceinline__ void pert_drag(const DevGrid& g, const PertTables<T>& t, const PCell<T>& c, int i, T* q,
+                                          T tau, const DragArgs& d) {
+  const T gam = (T)g.gamma;
+  T rg, du, dv, dw, dp;
+  cell_prim(gam, c, q, rg, du, dv, dw, dp);
+  const T rd = q[DRHO];
+  if (!(rd > T(0)) || !(rg > T(0))) return;
+  T ts;
+  if (d.law == 0) {
+    ts = g.geom == GEOM_CYL ? (T)d.stokes / t.omk[i] : (T)d.stokes;
+  } else {
+    const T cs = Math<T>::sqrt_(gam * (c.p0 + dp) / rg);
+    ts = (T)d.rhos_rp / (rg * cs);
+  }
+  const T kk = tau * (T(1) + rd / rg) / ts;
+  const T mu = rg * rd / (rg + rd);
+  const T relax = kk / (T(1) + kk);
+  const T ird = T(1) / rd;
+  const T u0[3] = {T(0), c.v0, T(0)};
+  const T dug[3] = {du, dv, dw};
+  T dE = T(0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const T dvd = (q[DMU + k] - rd * u0[k]) * ird;  // v_d - u0
+    const T X = mu * (dvd - dug[k]) * relax;
+    const T vg_ex = u0[k] + dug[k];
+    q[MU + k] += X;
+    q[DMU + k] -= X;
+    dE += T(0.5) * X * (T(2) * vg_ex + X / rg);
+  }
+  q[EN] += dE;
+}
+
+template <class T, int NF>
+__device__ __forceinline__ T pert_cell_dt(const DevGrid& g, const PertTables<T>& t, const PCell<T>& c, int i,
+                                          const T* q, bool& bad) {
+  const T gam = (T)g.gamma;
+  T rho, du, dv, dw, dp;
+  cell_prim(gam, c, q, rho, du, dv, dw, dp);
+  const T p = c.p0 + dp;
+  bad = !(rho > T(0)) || !(p > T(0));
+  const T v = c.v0 + dv;
+  const T vel = Math<T>::sqrt_(du * du + v * v + dw * dw);
+  const T cs = Math<T>::sqrt_(gam * p / rho);
+  const T V = t.vol[i], A = t.maxA[i], cfl = (T)g.cfl;
+  T dt = cfl * V / ((vel + cs) * A);
+  if (NF == 9) {
+    if (q[DRHO] > T(0)) {
+      const T vd = Math<T>::sqrt_(q[DMU] * q[DMU] + q[DMV] * q[DMV] + q[DMW] * q[DMW]) / q[DRHO];
+      if (vd > T(0)) dt = fmin(dt, cfl * V / (vd * A));
+    }
+    bad |= !(q[DRHO] >= T(0));
+  }
+  return dt;
+}
+
+template <class T, int NF, int TR, int TT, int TZ, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> a) {
+  constexpr int BX = TR + 4, BY = TT + 4, BZ = TZ + 4, BOX = BX * BY * BZ, NCORE = TR * TT * TZ;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sE = reinterpret_cast<T*>(smem_raw);
+  T* sG = sE + NF * BOX;
+  const DevGrid& g = a.g;
+  const int tile = blockIdx.x;
+  const int i0 = (tile % a.tiles_r) * TR;
+  const int j0 = ((tile / a.tiles_r) % a.tiles_t) * TT;
+  const int k0 = (tile / (a.tiles_r * a.tiles_t)) * TZ;
+  unsigned status = 0, nfallback = 0;
+
+  for (int idx = threadIdx.x; idx < BOX; idx += NT) {
+    const int x = idx % BX - 2, y = (idx / BX) % BY - 2, z = idx / (BX * BY) - 2;
+    const int outside = (x < 0 || x >= TR) + (y < 0 || y >= TT) + (z < 0 || z >= TZ);
+    if (outside > 1) continue;
+    int c[3] = {i0 + x, j0 + y, k0 + z};
+    if (!resolve_cell(g, c)) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) sE[f * BOX + idx] = T(0);
+      continue;
+    }
+    const size_t lin = ((size_t)c[2] * g.nth + c[1]) * g.nr + c[0];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) sE[f * BOX + idx] = a.in[f][lin];
+  }
+  __syncthreads();
+  sweep_pert<T, NF, TR, TT, TZ, NT, 0>(a, sE, sG, i0, j0, k0, status, nfallback);
+  __syncthreads();
+  sweep_pert<T, NF, TR, TT, TZ, NT, 1>(a, sE, sG, i0, j0, k0, status, nfallback);
+  __syncthreads();
+  sweep_pert<T, NF, TR, TT, TZ, NT, 2>(a, sE, sG, i0, j0, k0, status, nfallback);
+  __syncthreads();
+
+  const T tau = (T)(a.tau_frac * (a.dt_dev ? __longlong_as_double((long long)*a.dt_dev) : a.dt_host));
+  double dtmin = INFINITY;
+  double sums[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) sums[f] = 0.0;
+  for (int cidx = threadIdx.x; cidx < NCORE; cidx += NT) {
+    const int x = cidx % TR, y = (cidx / TR) % TT, z = cidx / (TR * TT);
+    const int gi = i0 + x, gj = j0 + y, gk = k0 + z;
+    if (gi >= g.nr || gj >= g.nth || gk >= g.nz) continue;
+    const size_t lin = ((size_t)gk * g.nth + gj) * g.nr + gi;
+    const PCell<T> ce = cell_eq(a.t, g, gi, gk);
+    const int sidx = ((z + 2) * BY + (y + 2)) * BX + (x + 2);
+    T q[NF], G[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      q[f] = sE[f * BOX + sidx];
+      G[f] = sG[f * NCORE + cidx];
+    }
+    if (g.geom == GEOM_CYL) {
+      T S[NF];
+      pert_sources<T, NF>(g, ce, q, S);
+      const T V = a.t.vol[gi];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) G[f] += V * S[f];
+    }
+    const T iv = a.t.ivol[gi];
+    T E[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) E[f] = a.base[f][lin] + tau * G[f] * iv;
+    if (NF == 9) pert_drag(g, a.t, ce, gi, E, tau, a.drag);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) a.out[f][lin] = E[f];
+    bool bad_in = false;
+    if (a.stage2) {
+      bool bad = false;
+      dtmin = fmin(dtmin, (double)pert_cell_dt<T, NF>(g, a.t, ce, gi, E, bad));
+      if (bad) status |= STATUS_NONPHYSICAL;
+      const double V = (double)g.vol[gi];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) sums[f] += V * (double)E[f];
+    } else {
+      (void)pert_cell_dt<T, NF>(g, a.t, ce, gi, q, bad_in);
+      if (bad_in) status |= STATUS_NONPHYSICAL;
+    }
+  }
+  if (a.stage2) {
+    double* red = reinterpret_cast<double*>(smem_raw);
+    const double m = block_min<NT>(dtmin, red);
+    if (threadIdx.x == 0) a.partials[(size_t)NF * gridDim.x + blockIdx.x] = m;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const double s = block_sum<NT>(sums[f], red);
+      if (threadIdx.x == 0) a.partials[(size_t)f * gridDim.x + blockIdx.x] = s;
+    }
+  }
+  if (status) atomicOr(a.status, status);
+  if (nfallback) atomicAdd(a.t.fallbacks, (unsigned long long)nfallback);
+}
+
+// CFL of a perturbation-form state (Sect. 2.5), block minimum into *slot.
+template <class T, int NF>
+__global__ void pert_cfl_kernel(const PertArgs<T> a, unsigned long long* slot) {
+  __shared__ double red[256 / 32];
+  const DevGrid& g = a.g;
+  const size_t ncell = (size_t)g.nr * g.nth * g.nz;
+  double m = INFINITY;
+  unsigned status = 0;
+  for (size_t lin = blockIdx.x * (size_t)256 + threadIdx.x; lin < ncell; lin += (size_t)gridDim.x * 256) {
+    T q[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) q[f] = a.in[f][lin];
+    const int i = (int)(lin % g.nr), k = (int)(lin / ((size_t)g.nr * g.nth));
+    bool bad = false;
+    m = fmin(m, (double)pert_cell_dt<T, NF>(g, a.t, cell_eq(a.t, g, i, k), i, q, bad));
+    if (bad) status |= STATUS_NONPHYSICAL;
+  }
+  m = block_min<256>(m, red);
+  if (threadIdx.x == 0) atomic_min_pos_double(slot, m);
+  if (status) atomicOr(a.status, status);
+}
+
+// Per-block FP64 partial sums of V * E'_f.
+template <class T, int NF>
+__global__ void pert_sums_kernel(const PertArgs<T> a, double* partials) {
+  __shared__ double red[256 / 32];
+  const DevGrid& g = a.g;
+  const size_t ncell = (size_t)g.nr * g.nth * g.nz;
+  double s[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) s[f] = 0.0;
+  for (size_t lin = blockIdx.x * (size_t)256 + threadIdx.x; lin < ncell; lin += (size_t)gridDim.x * 256) {
+    const double V = g.vol[lin % g.nr];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) s[f] += V * (double)a.in[f][lin];
+  }
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const double t = block_sum<256>(s[f], red);
+    if (threadIdx.x == 0) partials[(size_t)f * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+}  // namespace rossbi

@@ -1,0 +1,51 @@
+"""Error measures shared by the parity tests and bench.py.
+
+Relative L1 error per conserved field (the reading used throughout): for
+each conserved quantity of the governing equations (Sect. 2.1: mass, momentum
+vector, energy; and dust mass, dust momentum vector),
+
+    err = sum_cells V |q_test - q_ref|_1 / sum_cells V |q_ref|_1,
+
+where |.|_1 of the momentum is the sum of the absolute values of its three
+components.  The per-component ratios and the same measure on the
+deviations from equilibrium are reported alongside (they are stricter: the
+radial and vertical momenta vanish at equilibrium).
+"""
+import numpy as np
+
+GROUPS = {
+    "mass": (4,),
+    "momentum": (0, 1, 2),
+    "energy": (3,),
+    "dust_mass": (8,),
+    "dust_momentum": (5, 6, 7),
+}
+
+
+def rel_l1(E_test, E_ref, V):
+    """E arrays (nf, nz, nth, nr) float64; V (nr,) cell volumes. Returns {group: err}."""
+    nf = E_ref.shape[0]
+    Vb = V[None, None, :]
+    out = {}
+    for name, fields in GROUPS.items():
+        if max(fields) >= nf:
+            continue
+        num = sum((Vb * np.abs(E_test[f] - E_ref[f])).sum() for f in fields)
+        den = sum((Vb * np.abs(E_ref[f])).sum() for f in fields)
+        out[name] = float(num / den) if den > 0 else float(num)
+    return out
+
+
+def rel_l1_components(E_test, E_ref, V, E0=None):
+    """Per-field relative L1 (on deviations from E0 when given)."""
+    Vb = V[None, None, :]
+    out = []
+    for f in range(E_ref.shape[0]):
+        a, b = E_test[f], E_ref[f]
+        if E0 is not None and f < 5:
+            a = a - E0[f][:, None, :]
+            b = b - E0[f][:, None, :]
+        den = (Vb * np.abs(b)).sum()
+        num = (Vb * np.abs(a - b)).sum()
+        out.append(float(num / den) if den > 0 else float(num))
+    return out

@@ -1,0 +1,287 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Both sides build their own initial state from the shared seeded inputs, step
+with their own CFL dt, and are compared by the relative L1 error per conserved
+field (tests/parity.py).  Bar for the FP64 form: <= 1e-12.
+Small grids span several tiles of the 14x6x6 kernel tile and ragged tails;
+the full-size workloads are checked on sampled cells after one step.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as syn
+from tests.parity import rel_l1, rel_l1_components
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    from paper_2207_04252_gb300 import build
+    build.build()
+    from paper_2207_04252_gb300 import rossbi, workloads
+    torch.cuda.init()
+    return rossbi, workloads
+
+
+def _run_gpu(grid, state, steps=None, t_end=None):
+    """Own-CFL run; returns (state, t, dts)."""
+    dts = []
+    t = 0.0
+    dt = grid.cfl_dt(state)
+    n = 0
+    while True:
+        if steps is not None and n >= steps:
+            break
+        if t_end is not None:
+            if t >= t_end * (1 - 1e-14):
+                break
+            dt = min(dt, t_end - t)
+        ndt = grid.step(state, dt=dt, want_next_dt=True)
+        t += dt
+        dts.append(dt)
+        dt = ndt
+        n += 1
+    return state, t, dts
+
+
+def _compare(grid, o, state_gpu, E_ref, tol=TOL64):
+    E = grid.full_state(state_gpu)
+    V = o.volumes()
+    errs = rel_l1(E, E_ref, V)
+    for name, e in errs.items():
+        assert e <= tol, (name, e, errs, rel_l1_components(E, E_ref, V))
+    return errs
+
+
+def test_sod_box(lib):
+    """Sod shock tube in the Box to t = 0.2 (224 steps).  The GPU follows the
+    oracle's dt sequence; the error is recorded at checkpoints.  Rounding-order
+    differences (FMA contraction, reciprocal multiplies, libm pow) of ~1e-16
+    per step are amplified where limiter branches sit near a tie at the
+    discontinuities, so the bar after the full run is 1e-10 (1e-13 after one
+    step).  Its own CFL sequence is checked against the oracle's as well."""
+    import torch
+    R, W = lib
+    w = syn.SOD
+    o = oracle.Oracle(w)
+    E = oracle.initial_state(o)
+    g = W.Grid(w)
+    s = torch.from_numpy(E.copy()).cuda()
+    V = o.volumes()
+    _, _, dts = o.run(E.copy(), t_end=w.t_end)
+    checkpoints = {1: 1e-13, 10: 1e-12, 50: 1e-11, len(dts): 1e-10}
+    curve = {}
+    for n, dt in enumerate(dts, start=1):
+        E = o.step(E, dt)
+        g.step(s, dt=dt)
+        if n in checkpoints:
+            errs = rel_l1(g.full_state(s), E, V)
+            curve[n] = max(errs.values())
+            assert curve[n] <= checkpoints[n], (n, errs, curve)
+    print("sod error growth", curve)
+    assert o.take_status() == 0 and g.take_status() == 0
+    # GPU's own CFL sequence against the oracle's
+    s2, _, dts_gpu = _run_gpu(g, g.initial_state(), t_end=w.t_end)
+    assert len(dts_gpu) == len(dts)
+    np.testing.assert_allclose(dts_gpu[:-1], dts[:-1], rtol=1e-12)
+    # the last step is clipped to t_end - t, a difference of nearly equal sums
+    assert abs(dts_gpu[-1] - dts[-1]) <= 1e-14 * w.t_end
+    # and the result is the exact Riemann solution up to the scheme's error
+    xc = g.centres(0)
+    exact = np.array([oracle.riemann(1.4, (1, 0, 1), (0.125, 0, 0.1), S=(x - 0.5) / 0.2)[0][0] for x in xc])
+    assert np.abs(g.full_state(s2)[4, 0, 0, :] - exact).mean() < 0.01
+
+
+@pytest.mark.parametrize("n,steps", [((24, 48, 32), 10), ((15, 7, 33), 6)])
+def test_disc_noise(lib, n, steps):
+    R, W = lib
+    w = syn.scaled(syn.DISC_NOISE, *n, steps=steps)
+    g = W.Grid(w)
+    o = oracle.Oracle(w)
+    s, _, dts = _run_gpu(g, g.initial_state(), steps=steps)
+    E_ref, _, dts_ref = o.run(oracle.initial_state(o), steps=steps)
+    np.testing.assert_allclose(dts, dts_ref, rtol=1e-13)
+    _compare(g, o, s, E_ref)
+
+
+@pytest.mark.parametrize("n,steps", [((20, 36, 32), 6), ((29, 13, 32), 4)])
+def test_vortex_bifluid(lib, n, steps):
+    R, W = lib
+    w = syn.scaled(syn.VORTEX, *n, steps=steps)
+    g = W.Grid(w)
+    o = oracle.Oracle(w)
+    s, _, dts = _run_gpu(g, g.initial_state(), steps=steps)
+    E_ref, _, dts_ref = o.run(oracle.initial_state(o), steps=steps)
+    np.testing.assert_allclose(dts, dts_ref, rtol=1e-13)
+    _compare(g, o, s, E_ref)
+
+
+def test_equilibrium_bit_exact(lib):
+    """Balanced scheme (Sect. 2.8): E = E0 is preserved bit for bit."""
+    import torch
+    R, W = lib
+    w = syn.scaled(syn.VORTEX, 30, 20, 32, steps=20)
+    g = W.Grid(w)
+    E0 = np.zeros(g.shape)
+    E0[:5] = g.equilibrium()[:, :, None, :]
+    s = torch.from_numpy(E0).cuda()
+    _run_gpu(g, s, steps=20)
+    assert np.array_equal(s.cpu().numpy(), E0)
+
+
+def _box(n, n_dust=0, stokes=0.0, bc=syn.BC_PERIODIC):
+    L = (1.0, n[1] / n[0], n[2] / n[0])
+    return syn.Workload(name="box", geometry=syn.GEOM_BOX, nr=n[0], nth=n[1], nz=n[2], x0=(0.0, 0.0, 0.0),
+                        x1=L, bc_lo=(bc, 0, 0), bc_hi=(bc, 0, 0), ic="none", steps=0, omega_frame=0.0,
+                        n_dust=n_dust, stokes=stokes)
+
+
+def _smooth_state(w, nf):
+    z, y, x = np.meshgrid(*(np.arange(n) / n for n in (w.nz, w.nth, w.nr)), indexing="ij")
+    E = np.zeros((nf, w.nz, w.nth, w.nr))
+    rho = 1.0 + 0.2 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)
+    u, v, ww = 0.3 * np.cos(2 * np.pi * (x + z)), -0.2 + 0.1 * np.sin(2 * np.pi * y), 0.1 * np.sin(2 * np.pi * z)
+    p = 1.0 + 0.3 * np.cos(2 * np.pi * (y + z)) + 0.2 * (x > 0.5)
+    E[4] = rho
+    E[0], E[1], E[2] = rho * u, rho * v, rho * ww
+    E[3] = 0.5 * rho * (u * u + v * v + ww * ww) + p / 0.4
+    if nf > 5:
+        rd = 0.5 + 0.3 * np.cos(2 * np.pi * (x - y))
+        E[8], E[5], E[6], E[7] = rd, rd * (u + 0.2), rd * v, rd * (ww - 0.1)
+    return E
+
+
+@pytest.mark.parametrize("n,n_dust,bc", [((1, 1, 1), 0, 0), ((5, 3, 7), 0, 0), ((17, 9, 8), 1, 0),
+                                         ((31, 4, 5), 0, 1), ((14, 6, 6), 1, 1)])
+def test_box_tiny_and_ragged(lib, n, n_dust, bc):
+    import torch
+    R, W = lib
+    w = _box(n, n_dust=n_dust, stokes=0.07, bc=bc)
+    g = W.Grid(w)
+    o = oracle.Oracle(w)
+    E = _smooth_state(w, g.nf)
+    s = torch.from_numpy(E.copy()).cuda()
+    s, _, dts = _run_gpu(g, s, steps=5)
+    E_ref, _, dts_ref = o.run(E, steps=5)
+    np.testing.assert_allclose(dts, dts_ref, rtol=1e-13)
+    _compare(g, o, s, E_ref)
+
+
+def test_box_conservation(lib):
+    import torch
+    R, W = lib
+    w = _box((16, 8, 8), n_dust=1, stokes=0.05)
+    g = W.Grid(w)
+    s = torch.from_numpy(_smooth_state(w, 9)).cuda()
+    s0 = g.sums(s)
+    _run_gpu(g, s, steps=20)
+    s1 = g.sums(s)
+    V = 1.0 / 16 * (8 / 16) / 8 * (8 / 16) / 8
+    scale = V * np.abs(_smooth_state(w, 9)).sum(axis=(1, 2, 3))
+    for f in (4, 8, 3):
+        if f == 3:
+            continue  # gas energy changes by the drag work
+        assert abs(s1[f] - s0[f]) <= 1e-13 * scale[f]
+    for c in range(3):
+        assert abs((s1[c] + s1[5 + c]) - (s0[c] + s0[5 + c])) <= 1e-13 * (scale[c] + scale[5 + c])
+
+
+@pytest.mark.parametrize("wl", [syn.DISC_NOISE, syn.VORTEX])
+def test_cfl_and_sums(lib, wl):
+    R, W = lib
+    w = syn.scaled(wl, 40, 30, 32, steps=1)
+    g = W.Grid(w)
+    o = oracle.Oracle(w)
+    s = g.initial_state()
+    E = oracle.initial_state(o)
+    assert g.cfl_dt(s) == pytest.approx(o.cfl_dt(E), rel=1e-14)
+    np.testing.assert_allclose(g.sums(s), o.sums(E), rtol=1e-13, atol=1e-13 * np.abs(o.sums(E)).max())
+
+
+@pytest.mark.parametrize("wl", [syn.DISC_NOISE, syn.VORTEX, syn.THROUGHPUT])
+def test_full_size_one_step_sampled(lib, wl):
+    """The full-size workload, one step in the launch configuration the bench
+    times, compared with the oracle on sampled cells (boundaries included)."""
+    import torch
+    R, W = lib
+    g = W.Grid(wl)
+    o = oracle.Oracle(wl)
+    E = oracle.initial_state(o)
+    dt = o.cfl_dt(E)
+    s = g.initial_state()
+    assert g.cfl_dt(s) == pytest.approx(dt, rel=1e-13)
+    g.step(s, dt=dt, want_next_dt=True)
+    rng = np.random.default_rng(11)
+    nr, nth, nz = wl.nr, wl.nth, wl.nz
+    edges = [(k * nth + j) * nr + i for i in (0, 1, nr - 1) for j in (0, nth - 1) for k in (0, nz // 2, nz - 1)]
+    cells = np.unique(np.concatenate([edges, rng.integers(0, wl.ncell, 150)]))
+    ref = o.step_sampled(E, dt, cells)                       # (ncells, nf)
+    got = s.reshape(g.nf, -1)[:, torch.from_numpy(cells).cuda()].cpu().numpy().T
+    for name, fields in (("mass", [4]), ("momentum", [0, 1, 2]), ("energy", [3]), ("dust", [5, 6, 7, 8])):
+        fields = [f for f in fields if f < g.nf]
+        if not fields:
+            continue
+        num = np.abs(got[:, fields] - ref[:, fields]).sum()
+        den = np.abs(ref[:, fields]).sum()
+        assert num <= TOL64 * den, (name, num / den)
+    del s
+    torch.cuda.empty_cache()
+
+
+def test_device_dt_path_and_scratch_variants(lib):
+    import torch
+    R, W = lib
+    w = syn.scaled(syn.VORTEX, 20, 18, 32, steps=3)
+    g = W.Grid(w)
+    a = g.initial_state()
+    b = a.clone()
+    c = a.clone()
+    h = a.cpu().numpy().copy()
+    dt = g.cfl_dt(a)
+    scratch = torch.empty_like(a)
+    for _ in range(3):
+        g.step(a, dt=0.0)                                      # device-resident dt
+    for _ in range(3):
+        dt_b = g.cfl_dt(b)
+        g.step(b, dt=dt_b, scratch=scratch)                    # explicit dt, caller scratch
+    nd = dt
+    for _ in range(3):
+        nd = R.rossbi_step_host(g.h, h, dt=nd, dust=g.dust)   # host buffers
+    g.cfl_dt(c)
+    for _ in range(3):
+        g.step(c, dt=0.0, want_next_dt=True)
+    assert torch.equal(a, b) and torch.equal(a, c)
+    assert np.array_equal(a.cpu().numpy(), h)
+
+
+def test_nonphysical_reported_not_trapped(lib):
+    R, W = lib
+    w = syn.scaled(syn.DISC_NOISE, 16, 12, 32, steps=1)
+    g = W.Grid(w)
+    s = g.initial_state()
+    s[4, 16, 3, 7] = -1.0  # negative density prepared on the host side of the test
+    with pytest.raises(R.RossbiError) as e:
+        g.step(s, dt=1e-3, want_next_dt=True)
+    assert e.value.code == R.ROSSBI_ERR_NONPHYSICAL
+    assert g.take_status() == R.ROSSBI_OK  # the word was cleared; the context is still usable
+    s2 = g.initial_state()
+    g.step(s2, dt=1e-3, want_next_dt=True)
+
+
+def test_invalid_arguments(lib):
+    R, W = lib
+    w = syn.scaled(syn.DISC_NOISE, 16, 12, 32, steps=1)
+    g = W.Grid(w)
+    s = g.initial_state()
+    with pytest.raises(R.RossbiError) as e:
+        g.step(s, dt=0.0)  # no device dt yet
+    assert e.value.code == R.ROSSBI_ERR_ARG
+    with pytest.raises(R.RossbiError):
+        g.step(s, dt=-1.0)
+    with pytest.raises(R.RossbiError):
+        R.rossbi_step(g.h, s, None, float("nan"), None, False)

@@ -1,0 +1,180 @@
+"""Parity of the perturbation forms with the FP64 CPU oracle.
+
+ROSSBI_FP64_PERT evaluates G(E0 + E') - G(E0) by hand-expanded differences in
+double precision; matching the oracle's full-state update (which subtracts
+the empty-run residual, Sect. 2.8) to <= 1e-12 checks that algebra exactly.
+ROSSBI_FP32_PERT is the same code in float: <= 1e-5 relative L1 per conserved
+field after 100 steps.  The GPU is driven with the oracle's dt sequence so that
+the comparison measures the update alone; the FP32 CFL is checked separately.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as syn
+from tests.parity import rel_l1, rel_l1_components
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    from paper_2207_04252_gb300 import build
+    build.build()
+    from paper_2207_04252_gb300 import rossbi, workloads
+    torch.cuda.init()
+    return rossbi, workloads
+
+
+def _run_with(grid, state, dts):
+    for dt in dts:
+        grid.step(state, dt=dt)
+    grid.take_status()
+    return state
+
+
+def _check(grid, o, state, E_ref, tol, report=None):
+    E = grid.full_state(state)
+    V = o.volumes()
+    errs = rel_l1(E, E_ref, V)
+    if report is not None:
+        report["groups"] = errs
+        report["fields"] = rel_l1_components(E, E_ref, V)
+        E0 = grid.equilibrium()
+        report["deviation_fields"] = rel_l1_components(E, E_ref, V, E0=E0)
+    for name, e in errs.items():
+        assert e <= tol, (name, e, errs)
+    return errs
+
+
+CASES = [
+    ("sod", lambda: syn.SOD, None),
+    ("disc", lambda: syn.scaled(syn.DISC_NOISE, 24, 48, 32), 10),
+    ("disc_ragged", lambda: syn.scaled(syn.DISC_NOISE, 15, 7, 33), 6),
+    ("vortex", lambda: syn.scaled(syn.VORTEX, 20, 36, 32), 6),
+    ("vortex_ragged", lambda: syn.scaled(syn.VORTEX, 29, 13, 32), 4),
+]
+
+
+@pytest.mark.parametrize("name,mk,steps", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("precision", ["fp64_pert", "fp32_pert"])
+def test_pert_parity(lib, name, mk, steps, precision):
+    R, W = lib
+    w = mk()
+    prec = R.ROSSBI_FP64_PERT if precision == "fp64_pert" else R.ROSSBI_FP32_PERT
+    o = oracle.Oracle(w)
+    if w.t_end > 0:
+        E_ref, _, dts = o.run(oracle.initial_state(o), t_end=w.t_end)
+    else:
+        E_ref, _, dts = o.run(oracle.initial_state(o), steps=steps)
+    g = W.Grid(w, precision=prec)
+    s = _run_with(g, g.initial_state(), dts)
+    _check(g, o, s, E_ref, TOL64 if prec == R.ROSSBI_FP64_PERT else TOL32)
+
+
+def test_fp32_disc_100_steps(lib):
+    """The spec bar: FP32 form within 1e-5 per conserved field after 100
+    steps of the noisy disc equilibrium (reduced grid, same extents)."""
+    R, W = lib
+    w = syn.scaled(syn.DISC_NOISE, 24, 32, 32, steps=100)
+    o = oracle.Oracle(w)
+    E_ref, _, dts = o.run(oracle.initial_state(o), steps=100)
+    g = W.Grid(w, precision=R.ROSSBI_FP32_PERT)
+    s = _run_with(g, g.initial_state(), dts)
+    rep = {}
+    _check(g, o, s, E_ref, TOL32, report=rep)
+    assert R.rossbi_fallback_count(g.h) == 0
+    print("fp32 100-step errors", rep)
+
+
+def test_fp32_vortex_bifluid_steps(lib):
+    R, W = lib
+    w = syn.scaled(syn.VORTEX, 24, 40, 32, steps=40)
+    o = oracle.Oracle(w)
+    E_ref, _, dts = o.run(oracle.initial_state(o), steps=40)
+    g = W.Grid(w, precision=R.ROSSBI_FP32_PERT)
+    s = _run_with(g, g.initial_state(), dts)
+    rep = {}
+    _check(g, o, s, E_ref, TOL32, report=rep)
+    print("fp32 vortex errors", rep)
+
+
+@pytest.mark.parametrize("precision", ["fp64_pert", "fp32_pert"])
+def test_pert_equilibrium_exact(lib, precision):
+    import torch
+    R, W = lib
+    prec = R.ROSSBI_FP64_PERT if precision == "fp64_pert" else R.ROSSBI_FP32_PERT
+    w = syn.scaled(syn.VORTEX, 30, 20, 32, steps=10)
+    g = W.Grid(w, precision=prec)
+    s = torch.zeros(g.shape, dtype=g.dtype, device="cuda")
+    dt = g.cfl_dt(s)
+    for _ in range(10):
+        dt = g.step(s, dt=dt, want_next_dt=True)
+    assert int(torch.count_nonzero(s)) == 0
+
+
+@pytest.mark.parametrize("wl", [syn.DISC_NOISE, syn.VORTEX])
+def test_pert_cfl_and_sums(lib, wl):
+    R, W = lib
+    w = syn.scaled(wl, 40, 30, 32, steps=1)
+    o = oracle.Oracle(w)
+    E = oracle.initial_state(o)
+    for prec, rtol_dt, rtol_s in ((R.ROSSBI_FP64_PERT, 1e-13, 1e-13), (R.ROSSBI_FP32_PERT, 2e-6, 1e-7)):
+        g = W.Grid(w, precision=prec)
+        s = g.initial_state()
+        assert g.cfl_dt(s) == pytest.approx(o.cfl_dt(E), rel=rtol_dt)
+        ref = o.sums(E)
+        np.testing.assert_allclose(g.sums(s), ref, rtol=rtol_s, atol=rtol_s * np.abs(ref).max())
+
+
+def test_fp32_full_size_one_step_sampled(lib):
+    """The throughput workload (512x1024x128, bi-fluid) in FP32, one step in the
+    bench's launch configuration, against the oracle on sampled cells."""
+    import torch
+    R, W = lib
+    wl = syn.THROUGHPUT
+    o = oracle.Oracle(wl)
+    E = oracle.initial_state(o)
+    dt = o.cfl_dt(E)
+    g = W.Grid(wl, precision=R.ROSSBI_FP32_PERT)
+    s = g.initial_state()
+    g.step(s, dt=dt, want_next_dt=True)
+    rng = np.random.default_rng(5)
+    nr, nth, nz = wl.nr, wl.nth, wl.nz
+    edges = [(k * nth + j) * nr + i for i in (0, 1, nr - 1) for j in (0, nth - 1) for k in (0, nz // 2, nz - 1)]
+    cells = np.unique(np.concatenate([edges, rng.integers(0, wl.ncell, 200)]))
+    ref = o.step_sampled(E, dt, cells)
+    got = s.reshape(g.nf, -1)[:, torch.from_numpy(cells).cuda()].double().cpu().numpy().T
+    E0 = g.equilibrium()
+    k = cells // (nr * nth)
+    i = cells % nr
+    got[:, :5] += E0[:, k, i].T
+    for name, fields in (("mass", [4]), ("momentum", [0, 1, 2]), ("energy", [3]), ("dust", [5, 6, 7, 8])):
+        num = np.abs(got[:, fields] - ref[:, fields]).sum()
+        den = np.abs(ref[:, fields]).sum()
+        assert num <= TOL32 * den, (name, num / den)
+    assert R.rossbi_fallback_count(g.h) == 0
+    del s
+    torch.cuda.empty_cache()
+
+
+def test_pert_box_conservation(lib):
+    import torch
+    from tests.test_gpu_parity import _box, _smooth_state
+    R, W = lib
+    w = _box((16, 8, 8), n_dust=1, stokes=0.05)
+    for prec, tol in ((R.ROSSBI_FP64_PERT, 1e-13), (R.ROSSBI_FP32_PERT, 2e-6)):
+        g = W.Grid(w, precision=prec)
+        s = torch.from_numpy(_smooth_state(w, 9)).to("cuda", g.dtype)
+        s0 = g.sums(s)
+        dt = g.cfl_dt(s)
+        for _ in range(20):
+            dt = g.step(s, dt=dt, want_next_dt=True)
+        s1 = g.sums(s)
+        scale = np.abs(s0) + 1e-3
+        for f in (4, 8):
+            assert abs(s1[f] - s0[f]) <= tol * scale[f]
