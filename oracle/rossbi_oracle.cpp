@@ -17,17 +17,24 @@
 //
 // Readings of the paper that this file takes (the paper is silent or garbled):
 //  R1  cell centre in r is the geometric mean of its face radii (log mesh).
-//  R2  MinMod rule (Sect. 2.7 names the limiter only): flat at a local extremum
-//      of E'; if a parabolic face value leaves the interval of its two
-//      neighbouring cell values, fall back to the linear minmod slope; if a
-//      reconstructed gas face state has rho<=0 or P<=0, flatten all gas fields
-//      of that cell in that direction (dust: rho_d<0 flattens the dust fields).
+//  R2  MinMod limiter (Sect. 2.7 names the limiter only): each face deviation
+//      of the parabola, d = q - E'_i, is limited to minmod(d, s h), where s is
+//      the minmod of the two one-sided slopes and h = +-min(2|x_face - x_i|,
+//      |x_neighbour - x_i|) on that side: the curvature is reduced only where
+//      the parabola would leave the interval of the neighbouring cell values,
+//      the result is flat at an extremum, and it depends continuously on the
+//      data.  If a reconstructed gas face state has rho<=0 or P<=0, all gas
+//      fields of that cell are flattened in that direction.
 //  R3  the energy flux is (E+P)u_n (App. B prints rho(E+P)u, which is not
 //      dimensionally consistent with the governing equations of Sect. 2.1).
 //  R4  the RK2 update is E + dt*G/V (Sect. 2.5 prints a*V*dt*G; the compact
 //      form V dE/dt = G of Sect. 2.2 fixes the 1/V).
-//  R5  the pressureless dust flux is the upwind flux of a pressureless gas
-//      with delta-shock speed (sqrt(rl)ul+sqrt(rr)ur)/(sqrt(rl)+sqrt(rr)).
+//  R5  the dust ("adapted" solver, Sect. 2.9) is reconstructed in primitive
+//      variables (rho_d and the velocity, same limiter) and its face flux is
+//      the kinetic flux-vector splitting of pressureless gas dynamics
+//      (Bouchut, Jin & Li 2003): rho_L max(u_L,0)(1,u_L,...) +
+//      rho_R min(u_R,0)(1,u_R,...), which carries delta shocks by
+//      accumulating mass.
 //  R6  rotating frame of angular speed Omega_f: Coriolis 2 Omega_f rho v e_r -
 //      2 Omega_f rho u e_theta and centrifugal rho Omega_f^2 r e_r; the stored
 //      azimuthal velocity is frame-relative.
@@ -199,33 +206,27 @@ static double dev(const Oracle& o, const Acc& E, int f, int i, int j, int k) {
 }
 
 // ---------------------------------------------------------------- reconstruction
-static inline bool between(double q, double a, double b) {
-  const double lo = a < b ? a : b, hi = a < b ? b : a;
-  return q >= lo && q <= hi;
+static inline double minmod(double a, double b) {
+  if (a * b <= 0.0) return 0.0;
+  return fabs(a) < fabs(b) ? a : b;
 }
 // Sect. 2.7: the parabola through the three cell values of E' at the centre
-// coordinates xm < x0 < xp, evaluated at the faces fm, fp of the middle cell.
-// a and b are the paper's coefficients, with the slopes nabla E'(i) = sm and
-// nabla E'(i+1) = sp.  Returns false when the result is flat.
+// coordinates xm < x0 < xp, evaluated at the faces fm, fp of the middle cell,
+// with the paper's coefficients a, b and the slopes nabla E'(i) = sm,
+// nabla E'(i+1) = sp; then the MinMod limiter of reading R2.  Returns false
+// when the result is flat.
 static bool parabola(double em, double e0, double ep, double xm, double x0, double xp, double fm, double fp,
                      double& qm, double& qp) {
   const double sm = (e0 - em) / (x0 - xm);
   const double sp = (ep - e0) / (xp - x0);
-  if (sm * sp <= 0.0) {  // R2: local extremum of E' -> flat
-    qm = qp = e0;
-    return false;
-  }
+  const double s = minmod(sm, sp);
   const double a = (sp - sm) / (xp - xm);
   const double b = (sp * (x0 - xm) + sm * (xp - x0)) / (xp - xm);
   const double dm = fm - x0, dp = fp - x0;
-  qm = e0 + a * dm * dm + b * dm;
-  qp = e0 + a * dp * dp + b * dp;
-  if (!between(qp, e0, ep) || !between(qm, em, e0)) {  // R2: minmod slope
-    const double s = fabs(sm) < fabs(sp) ? sm : sp;
-    qm = e0 + s * dm;
-    qp = e0 + s * dp;
-  }
-  return true;
+  const double hm = -std::min(-2.0 * dm, x0 - xm), hp = std::min(2.0 * dp, xp - x0);
+  qm = e0 + minmod(a * dm * dm + b * dm, s * hm);
+  qp = e0 + minmod(a * dp * dp + b * dp, s * hp);
+  return s != 0.0;
 }
 
 static inline double pressure(double g, const double* U) {
@@ -252,15 +253,31 @@ static void recon(const Oracle& o, const Acc& E, int ax, const int cell[3], doub
   const int c = cell[ax];
   const double xm = XC(o, ax, c - 1), x0 = XC(o, ax, c), xp = XC(o, ax, c + 1);
   const double fm = XF(o, ax, c), fp = XF(o, ax, c + 1);
-  double ec[9];
-  bool gas_shaped = false, dust_shaped = false;
-  for (int f = 0; f < o.nf; ++f) {
+  double ec[5];
+  bool gas_shaped = false;
+  for (int f = 0; f < 5; ++f) {
     const double em = dev(o, E, f, cm[0], cm[1], cm[2]);
     ec[f] = dev(o, E, f, cell[0], cell[1], cell[2]);
     const double ep = dev(o, E, f, cp[0], cp[1], cp[2]);
-    const bool shaped = parabola(em, ec[f], ep, xm, x0, xp, fm, fp, qm[f], qp[f]);
-    if (f < 5) gas_shaped |= shaped;
-    else dust_shaped |= shaped;
+    gas_shaped |= parabola(em, ec[f], ep, xm, x0, xp, fm, fp, qm[f], qp[f]);
+  }
+  if (o.nf > 5) {  // R5: dust in primitive variables (rho_d, u_d, v_d, w_d)
+    double wm[4], w0[4], wp[4], qmw[4], qpw[4];
+    wm[3] = dev(o, E, DRHO, cm[0], cm[1], cm[2]);
+    w0[3] = dev(o, E, DRHO, cell[0], cell[1], cell[2]);
+    wp[3] = dev(o, E, DRHO, cp[0], cp[1], cp[2]);
+    for (int c = 0; c < 3; ++c) {
+      wm[c] = wm[3] > 0.0 ? dev(o, E, DMU + c, cm[0], cm[1], cm[2]) / wm[3] : 0.0;
+      w0[c] = w0[3] > 0.0 ? dev(o, E, DMU + c, cell[0], cell[1], cell[2]) / w0[3] : 0.0;
+      wp[c] = wp[3] > 0.0 ? dev(o, E, DMU + c, cp[0], cp[1], cp[2]) / wp[3] : 0.0;
+    }
+    for (int q = 0; q < 4; ++q) parabola(wm[q], w0[q], wp[q], xm, x0, xp, fm, fp, qmw[q], qpw[q]);
+    qm[DRHO] = qmw[3];
+    qp[DRHO] = qpw[3];
+    for (int c = 0; c < 3; ++c) {
+      qm[DMU + c] = qmw[3] * qmw[c];
+      qp[DMU + c] = qpw[3] * qpw[c];
+    }
   }
   if (gas_shaped) {  // R2 (iii): positivity of both reconstructed gas face states
     double e0m[5], e0p[5], Um[5], Up[5];
@@ -274,8 +291,6 @@ static void recon(const Oracle& o, const Acc& E, int ax, const int cell[3], doub
     if (!ok)
       for (int f = 0; f < 5; ++f) qm[f] = qp[f] = ec[f];
   }
-  if (dust_shaped && (qm[DRHO] < 0.0 || qp[DRHO] < 0.0))
-    for (int f = 5; f < o.nf; ++f) qm[f] = qp[f] = ec[f];
 }
 
 // ---------------------------------------------------------------- exact Riemann solver (Toro)
@@ -454,34 +469,25 @@ static void gas_flux(Oracle& o, int ax, const double UL[5], const double UR[5], 
   F[EN] = (0.5 * s.rho * (s.u * s.u + ut1 * ut1 + ut2 * ut2) + s.p / (g - 1.0) + s.p) * s.u;
 }
 
-// Sect. 2.9 / reading R5: upwind flux of the pressureless dust fluid.
+// Sect. 2.9 / reading R5: kinetic flux-vector splitting of the pressureless
+// dust fluid: what moves right leaves the left state, what moves left leaves
+// the right state.
 static void dust_flux(int ax, const double UL[9], const double UR[9], double F[9]) {
   int n, t1, t2;
   axes(ax, n, t1, t2);
   n += 5; t1 += 5; t2 += 5;
   const double rl = UL[DRHO], rr = UR[DRHO];
-  const double ul = rl > 0.0 ? UL[n] / rl : 0.0;
-  const double ur = rr > 0.0 ? UR[n] / rr : 0.0;
-  int pick;  // -1 left, +1 right, 0 none, 2 average
-  if (ul <= 0.0 && ur >= 0.0) pick = 0;
-  else if (ul >= 0.0 && ur >= 0.0) pick = -1;
-  else if (ul <= 0.0 && ur <= 0.0) pick = 1;
-  else {
-    const double vs = (sqrt(rl) * ul + sqrt(rr) * ur) / (sqrt(rl) + sqrt(rr));
-    pick = vs > 0.0 ? -1 : (vs < 0.0 ? 1 : 2);
+  double Fs[4] = {0.0, 0.0, 0.0, 0.0};
+  if (rl > 0.0) {
+    const double ul = UL[n] / rl;
+    const double m = rl * (ul > 0.0 ? ul : 0.0);
+    Fs[0] += m; Fs[1] += m * ul; Fs[2] += m * (UL[t1] / rl); Fs[3] += m * (UL[t2] / rl);
   }
-  double FL[4] = {0, 0, 0, 0}, FR[4] = {0, 0, 0, 0};
-  if (pick != 1 && rl > 0.0) {
-    const double m = rl * ul;
-    FL[0] = m; FL[1] = m * ul; FL[2] = m * UL[t1] / rl; FL[3] = m * UL[t2] / rl;
+  if (rr > 0.0) {
+    const double ur = UR[n] / rr;
+    const double m = rr * (ur < 0.0 ? ur : 0.0);
+    Fs[0] += m; Fs[1] += m * ur; Fs[2] += m * (UR[t1] / rr); Fs[3] += m * (UR[t2] / rr);
   }
-  if (pick != -1 && rr > 0.0) {
-    const double m = rr * ur;
-    FR[0] = m; FR[1] = m * ur; FR[2] = m * UR[t1] / rr; FR[3] = m * UR[t2] / rr;
-  }
-  double Fs[4];
-  for (int q = 0; q < 4; ++q)
-    Fs[q] = pick == -1 ? FL[q] : pick == 1 ? FR[q] : pick == 2 ? 0.5 * (FL[q] + FR[q]) : 0.0;
   F[DRHO] = Fs[0];
   F[n] = Fs[1];
   F[t1] = Fs[2];

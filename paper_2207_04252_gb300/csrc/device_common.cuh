@@ -12,7 +12,8 @@ enum { GEOM_BOX = 0, GEOM_CYL = 1 };
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_EQUILIBRIUM = 2 };
 enum { STATUS_NONPHYSICAL = 1u, STATUS_RIEMANN = 2u };
 
-constexpr int GH = 2;  // ghost offset of the axis-0 coordinate tables
+constexpr int GH = 2;   // ghost offset of the axis-0 coordinate tables
+constexpr int RCW = 10; // parabola weights per axis-0 cell (9 used)
 
 // Grid data the kernels read.  Passed by value as a kernel parameter; the
 // pointers are device tables owned by the host runtime.
@@ -23,7 +24,7 @@ struct DevGrid {
   double x0[3], dx[3];   // uniform axes 1, 2 (and axis 0 of the Box): origin, spacing
   const double* rc;      // axis-0 cell centres,  index i + GH, i in [-GH, nr + GH)
   const double* rf;      // axis-0 lower faces,   index i + GH, i in [-GH, nr + GH]
-  const double* rcoef;   // axis-0 parabola weights for cells i in [-1, nr]: 8 per cell at (i + 1) * 8
+  const double* rcoef;   // axis-0 parabola weights for cells i in [-1, nr]: RCW per cell at (i + 1) * RCW
   const double* vol;     // V(i)
   const double* ivol;    // 1 / V(i)
   const double* area_r;  // A of the axis-0 face i - 1/2, i in [0, nr]
@@ -188,41 +189,20 @@ __device__ __forceinline__ void gas_face_flux(double g, const double* UL, const 
   F[EN] = (0.5 * rho * (u * u + ut1 * ut1 + ut2 * ut2) + p / (g - 1.0) + p) * u;
 }
 
-// Upwind flux of the pressureless dust fluid (Sect. 2.9 "adapted" solver):
-// take the upwind side when both face velocities agree, nothing when the faces
-// diverge, and the side selected by the delta-shock speed when they converge.
-// U and F hold the four dust fields (rho_d u, rho_d v, rho_d w, rho_d).
-template <int D>
-__device__ __forceinline__ void dust_face_flux(const double* UL, const double* UR, double* F) {
-  constexpr int n = Axes<D>::n, t1 = Axes<D>::t1, t2 = Axes<D>::t2;  // 0..2, same in the dust block
-  const double rl = UL[3], rr = UR[3];
-  const double ul = rl > 0.0 ? UL[n] / rl : 0.0;
-  const double ur = rr > 0.0 ? UR[n] / rr : 0.0;
-  int pick;  // -1 left, +1 right, 0 none, 2 average
-  if (ul <= 0.0 && ur >= 0.0) pick = 0;
-  else if (ul >= 0.0 && ur >= 0.0) pick = -1;
-  else if (ul <= 0.0 && ur <= 0.0) pick = 1;
-  else {
-    const double sl = sqrt(rl), sr = sqrt(rr);
-    const double vs = (sl * ul + sr * ur) / (sl + sr);
-    pick = vs > 0.0 ? -1 : (vs < 0.0 ? 1 : 2);
-  }
-  double fl[4] = {0.0, 0.0, 0.0, 0.0}, fr[4] = {0.0, 0.0, 0.0, 0.0};
-  if (pick != 1 && rl > 0.0) {
-    const double m = rl * ul;
-    fl[0] = m; fl[1] = m * ul; fl[2] = m * (UL[t1] / rl); fl[3] = m * (UL[t2] / rl);
-  }
-  if (pick != -1 && rr > 0.0) {
-    const double m = rr * ur;
-    fr[0] = m; fr[1] = m * ur; fr[2] = m * (UR[t1] / rr); fr[3] = m * (UR[t2] / rr);
-  }
-  double s[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) s[q] = pick == -1 ? fl[q] : pick == 1 ? fr[q] : pick == 2 ? 0.5 * (fl[q] + fr[q]) : 0.0;
-  F[3] = s[0];
-  F[n] = s[1];
-  F[t1] = s[2];
-  F[t2] = s[3];
+// Flux of the pressureless dust fluid (Sect. 2.9 "adapted" solver) by kinetic
+// flux-vector splitting (Bouchut, Jin & Li 2003): the matter moving right
+// crosses from the left face state, the matter moving left from the right one.
+// WL, WR hold face primitives (u, v, w, rho_d); F the dust fluxes in the
+// order (rho_d u, rho_d v, rho_d w, rho_d) for a face normal to axis D.
+template <int D, class T>
+__device__ __forceinline__ void dust_kinetic_flux(const T* WL, const T* WR, T* F) {
+  constexpr int n = Axes<D>::n, t1 = Axes<D>::t1, t2 = Axes<D>::t2;  // 0..2 in the dust block
+  const T ml = WL[3] * (WL[n] > T(0) ? WL[n] : T(0));
+  const T mr = WR[3] * (WR[n] < T(0) ? WR[n] : T(0));
+  F[3] = ml + mr;
+  F[n] = ml * WL[n] + mr * WR[n];
+  F[t1] = ml * WL[t1] + mr * WR[t1];
+  F[t2] = ml * WL[t2] + mr * WR[t2];
 }
 
 // ------------------------------------------------------------------ sources

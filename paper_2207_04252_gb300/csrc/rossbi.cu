@@ -269,13 +269,13 @@ rossbi_status launch_stage(rossbi_grid* g, const StageArgs& a, int nblocks) {
   return ROSSBI_OK;
 }
 
-template <class T, int NF>
+template <class T, int NF, class P>
 rossbi_status launch_pert_nf(rossbi_grid* g, const PertArgs<T>& a, int nblocks) {
   constexpr bool F32 = sizeof(T) == 4;
   constexpr int TR = P32_TR, TT = P32_TT, TZ = P32_TZ, NT = P32_NT, MINB = F32 ? P32_MINB : 1;
   constexpr int BOX = (TR + 4) * (TT + 4) * (TZ + 4), NCORE = TR * TT * TZ;
   constexpr size_t smem = (size_t)NF * (BOX + NCORE) * sizeof(T);
-  auto kern = stage_pert_kernel<T, NF, TR, TT, TZ, NT, MINB>;
+  auto kern = stage_pert_kernel<T, NF, TR, TT, TZ, NT, MINB, P>;
   static bool attr = false;
   if (!attr) {
     CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -298,7 +298,17 @@ rossbi_status launch_pert(rossbi_grid* g, const PertArgs<T>& a, int nblocks) {
     e1 = g->ev[2 * g->ev_used + 1];
     CK(cudaEventRecord(e0, g->stream));
   }
-  rossbi_status st = g->nf == 9 ? launch_pert_nf<T, 9>(g, a, nblocks) : launch_pert_nf<T, 5>(g, a, nblocks);
+  rossbi_status st;
+  if constexpr (sizeof(T) == 4) {
+    if (g->desc.gamma == 1.4)  // gamma = 7/5: integer-power forms of the solver
+      st = g->nf == 9 ? launch_pert_nf<T, 9, PowG75>(g, a, nblocks) : launch_pert_nf<T, 5, PowG75>(g, a, nblocks);
+    else
+      st = g->nf == 9 ? launch_pert_nf<T, 9, PowGeneric<T>>(g, a, nblocks)
+                      : launch_pert_nf<T, 5, PowGeneric<T>>(g, a, nblocks);
+  } else {
+    st = g->nf == 9 ? launch_pert_nf<T, 9, PowGeneric<T>>(g, a, nblocks)
+                    : launch_pert_nf<T, 5, PowGeneric<T>>(g, a, nblocks);
+  }
   if (st != ROSSBI_OK) return st;
   if (e0) {
     CK(cudaEventRecord(e1, g->stream));
@@ -390,11 +400,11 @@ rossbi_status build_pert_tables(rossbi_grid* g, PertTables<T>& pt) {
   const int nr = d.nr, nz = d.nz;
   const size_t ncen = (size_t)nz * nr, nfr = (size_t)nz * (nr + 1), nfz = (size_t)(nz + 1) * nr;
   const size_t off_cen = 0, off_fr = off_cen + 8 * ncen, off_fz = off_fr + 5 * nfr, off_ft = off_fz + 5 * nfz;
-  const size_t off_rc = off_ft + 7 * ncen, off_vol = off_rc + (size_t)(nr + 2) * 8, off_ivol = off_vol + nr;
+  const size_t off_rc = off_ft + 7 * ncen, off_vol = off_rc + (size_t)(nr + 2) * RCW, off_ivol = off_vol + nr;
   const size_t off_ar = off_ivol + nr, off_at = off_ar + nr + 1, off_az = off_at + nr, off_ma = off_az + nr;
   const size_t off_om = off_ma + nr, total = off_om + nr;
   std::vector<double> h(total, 0.0);
-  std::vector<double> v(nr), rcoef((size_t)(nr + 2) * 8), ar(nr + 1), at(nr), az(nr), ma(nr), iv(nr);
+  std::vector<double> v(nr), rcoef((size_t)(nr + 2) * RCW), ar(nr + 1), at(nr), az(nr), ma(nr), iv(nr);
   if (cudaMemcpy(v.data(), g->d_vol, nr * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
       cudaMemcpy(iv.data(), g->d_ivol, nr * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
       cudaMemcpy(rcoef.data(), g->d_rcoef, rcoef.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
@@ -686,13 +696,13 @@ rossbi_status rossbi_init_grid(const rossbi_grid_desc* desc, void* cuda_stream, 
   const int nr = d.nr;
   const double dy = (d.x1[1] - d.x0[1]) / d.nth;
   const double dz = (d.x1[2] - d.x0[2]) / d.nz;
-  std::vector<double> rc(nr + 2 * GH), rf(nr + 2 * GH + 1), rcoef((size_t)(nr + 2) * 8, 0.0);
+  std::vector<double> rc(nr + 2 * GH), rf(nr + 2 * GH + 1), rcoef((size_t)(nr + 2) * RCW, 0.0);
   for (int i = -GH; i < nr + GH; ++i) rc[i + GH] = axis0_centre(d, i);
   for (int i = -GH; i <= nr + GH; ++i) rf[i + GH] = axis0_face(d, i);
   for (int i = -1; i <= nr; ++i) {  // parabola weights (Sect. 2.7)
     const double xm = rc[i - 1 + GH], x0 = rc[i + GH], xp = rc[i + 1 + GH];
     const double fm = rf[i + GH], fp = rf[i + 1 + GH];
-    double* w = &rcoef[(size_t)(i + 1) * 8];
+    double* w = &rcoef[(size_t)(i + 1) * RCW];
     w[0] = 1.0 / (x0 - xm);
     w[1] = 1.0 / (xp - x0);
     w[2] = 1.0 / (xp - xm);
@@ -700,6 +710,8 @@ rossbi_status rossbi_init_grid(const rossbi_grid_desc* desc, void* cuda_stream, 
     w[4] = xp - x0;
     w[5] = fm - x0;
     w[6] = fp - x0;
+    w[7] = -std::min(2.0 * (x0 - fm), x0 - xm);  // limiter reach on the lower side
+    w[8] = std::min(2.0 * (fp - x0), xp - x0);   // and on the upper side
   }
   std::vector<double> vol(nr), ivol(nr), ar(nr + 1), at(nr), az(nr), maxA(nr);
   if (d.geometry == ROSSBI_GEOM_CYL) {  // Sect. 2.2 finite volumes of the cylindrical mesh
@@ -966,3 +978,4 @@ rossbi_status rossbi_take_status(rossbi_grid* g) {
 }
 
 }  // extern "C"
+

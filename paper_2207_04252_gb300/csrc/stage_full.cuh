@@ -34,29 +34,68 @@ struct StageArgs {
   int tiles_r, tiles_t;
 };
 
-__device__ __forceinline__ bool between(double q, double a, double b) {
-  return q >= fmin(a, b) && q <= fmax(a, b);
+template <class T>
+__device__ __forceinline__ T minmod(T a, T b) {
+  if (a * b <= T(0)) return T(0);
+  return fabs(a) < fabs(b) ? a : b;
 }
 
-// Parabola through three deviations with the MinMod rule; w = {1/(x0-xm),
-// 1/(xp-x0), 1/(xp-xm), x0-xm, xp-x0, fm-x0, fp-x0}.  Returns false if flat.
-__device__ __forceinline__ bool parabola(double em, double e0, double ep, const double* w, double& qm, double& qp) {
-  const double sm = (e0 - em) * w[0];
-  const double sp = (ep - e0) * w[1];
-  if (sm * sp <= 0.0) {
-    qm = qp = e0;
-    return false;
+// Parabola through three deviations (Sect. 2.7) with the MinMod limiter: each
+// face deviation is limited to minmod(deviation, s h), s the minmod slope and
+// h the signed limiter reach of that side.  w = {1/(x0-xm), 1/(xp-x0),
+// 1/(xp-xm), x0-xm, xp-x0, fm-x0, fp-x0, h-, h+}.  Returns false if flat.
+template <class T>
+__device__ __forceinline__ bool parabola(T em, T e0, T ep, const T* w, T& qm, T& qp) {
+  const T sm = (e0 - em) * w[0];
+  const T sp = (ep - e0) * w[1];
+  const T s = minmod(sm, sp);
+  const T a = (sp - sm) * w[2];
+  const T b = (sp * w[3] + sm * w[4]) * w[2];
+  qm = e0 + minmod(w[5] * (a * w[5] + b), s * w[7]);
+  qp = e0 + minmod(w[6] * (a * w[6] + b), s * w[8]);
+  return s != T(0);
+}
+
+// Parabola weights of a cell along axis D (axis 0 from the table, uniform axes closed form).
+template <class T, int D>
+__device__ __forceinline__ void parabola_weights(const T* rcoef, int gi, int nr, T h, T* w) {
+  if (D == 0) {
+    const int c = gi < -1 ? -1 : (gi > nr ? nr : gi);
+    const T* cw = rcoef + (c + 1) * RCW;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) w[q] = cw[q];
+  } else {
+    w[0] = w[1] = T(1) / h;
+    w[2] = T(0.5) / h;
+    w[3] = w[4] = h;
+    w[5] = T(-0.5) * h;
+    w[6] = T(0.5) * h;
+    w[7] = -h;
+    w[8] = h;
   }
-  const double a = (sp - sm) * w[2];
-  const double b = (sp * w[3] + sm * w[4]) * w[2];
-  qm = e0 + w[5] * (a * w[5] + b);
-  qp = e0 + w[6] * (a * w[6] + b);
-  if (!between(qp, e0, ep) || !between(qm, em, e0)) {
-    const double s = fabs(sm) < fabs(sp) ? sm : sp;
-    qm = e0 + s * w[5];
-    qp = e0 + s * w[6];
+}
+
+// Primitive dust reconstruction (u, v, w, rho_d) of the cell at s (stride S
+// along the sweep) from conservative shared-memory fields (5..8 of the block).
+template <class T, int BOX, int S>
+__device__ __forceinline__ void dust_recon(const T* sE, int sidx, const T* w, T* wm, T* wp) {
+  T pm[4], p0[4], pp[4];
+  const T* r = sE + 8 * BOX + sidx;
+  pm[3] = r[-S];
+  p0[3] = r[0];
+  pp[3] = r[S];
+  const T im = pm[3] > T(0) ? T(1) / pm[3] : T(0);
+  const T i0 = p0[3] > T(0) ? T(1) / p0[3] : T(0);
+  const T ip = pp[3] > T(0) ? T(1) / pp[3] : T(0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const T* m = sE + (5 + c) * BOX + sidx;
+    pm[c] = m[-S] * im;
+    p0[c] = m[0] * i0;
+    pp[c] = m[S] * ip;
   }
-  return true;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) parabola(pm[q], p0[q], pp[q], w, wm[q], wp[q]);
 }
 
 // Ghost rule of Sect. 2.4 for a cell index possibly outside the domain.
@@ -117,19 +156,8 @@ __device__ __forceinline__ void sweep_full(const StageArgs& a, const double* sE,
     const int sidx = do_recon ? ((z + 2) * BY + (y + 2)) * BX + (x + 2) : (2 * BY + 2) * BX + 2;
 
     // parabola weights of this cell along D
-    double w[7];
-    if (D == 0) {
-      const double* cw = g.rcoef + (clampi(gi, -1, g.nr) + 1) * 8;
-#pragma unroll
-      for (int q = 0; q < 7; ++q) w[q] = cw[q];
-    } else {
-      const double h = g.dx[D];
-      w[0] = w[1] = 1.0 / h;
-      w[2] = 0.5 / h;
-      w[3] = w[4] = h;
-      w[5] = -0.5 * h;
-      w[6] = 0.5 * h;
-    }
+    double w[9];
+    parabola_weights<double, D>(g.rcoef, gi, g.nr, g.dx[D], w);
     // equilibrium gas state on the lower face of this cell (index along D = gd)
     // and on its upper face; table indices clamped (ghost cells reconstruct flat)
     const int ci = clampi(gi, 0, g.nr - 1), ck = clampi(gk, 0, g.nz - 1);
@@ -195,26 +223,17 @@ __device__ __forceinline__ void sweep_full(const StageArgs& a, const double* sE,
         }
       }
     }
-    // ---------------- dust: fields 5..8
+    // ---------------- dust: fields 5..8, primitive reconstruction, kinetic flux
     if (NF == 9) {
       double qm[4], qp[4];
-      bool shaped = false;
-#pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        const double* s = sE + (5 + f) * BOX + sidx;
-        shaped |= parabola(s[-STRIDE], s[0], s[STRIDE], w, qm[f], qp[f]);
-      }
-      if (shaped && (qm[3] < 0.0 || qp[3] < 0.0)) {
-#pragma unroll
-        for (int f = 0; f < 4; ++f) qm[f] = qp[f] = sE[(5 + f) * BOX + sidx];
-      }
+      dust_recon<double, BOX, STRIDE>(sE, sidx, w, qm, qp);
       double F[4];
       {
-        double UL[4];
+        double WL[4];
 #pragma unroll
-        for (int f = 0; f < 4; ++f) UL[f] = __shfl_up_sync(FULL, qp[f], 1, L);
+        for (int f = 0; f < 4; ++f) WL[f] = __shfl_up_sync(FULL, qp[f], 1, L);
         if (do_face) {
-          dust_face_flux<D>(UL, qm, F);
+          dust_kinetic_flux<D>(WL, qm, F);
 #pragma unroll
           for (int f = 0; f < 4; ++f) F[f] *= area;
         } else {

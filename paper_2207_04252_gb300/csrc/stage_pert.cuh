@@ -30,7 +30,7 @@ struct PertTables {
   const T* fr;     // [5][nz][nr+1] rho0, v0, p0, c0, h0 on r faces   (h0 = E0 + p0)
   const T* fz;     // [5][nz+1][nr] same on z faces
   const T* ft;     // [7][nz][nr]   same on theta faces (= centres), then v0 - c0, v0 + c0
-  const T* rcoef;  // axis-0 parabola weights, as DevGrid::rcoef
+  const T* rcoef;  // axis-0 parabola weights, RCW per cell as DevGrid::rcoef
   const T* vol;
   const T* ivol;
   const T* area_r;
@@ -69,6 +69,37 @@ template <class T>
 __device__ __forceinline__ T sqrt1pm1(T t) {
   return t / (Math<T>::sqrt_(T(1) + t) + T(1));
 }
+
+// Powers of the exact solver, (1 + x)^a - 1 for the exponents it needs.
+// Generic gamma: log1p / expm1.
+template <class T>
+struct PowGeneric {
+  static __device__ __forceinline__ T rar(T x, T g) { return pow1pm1(x, (g - T(1)) / (T(2) * g)); }
+  static __device__ __forceinline__ T dens(T x, T g, T) { return pow1pm1(x, T(1) / g); }
+  static __device__ __forceinline__ T fan_rho(T y, T g) { return pow1pm1(y, T(2) / (g - T(1))); }
+  static __device__ __forceinline__ T fan_p(T y, T g) { return pow1pm1(y, T(2) * g / (g - T(1))); }
+};
+// gamma = 7/5 in float: with z = (1 + x)^(1/7), z^7 - 1 = (z - 1)(1 + z + ... + z^6)
+// gives (1 + x)^(1/7) - 1 = x / sum z^k, accurate to a few times the error of
+// the hardware log2 / exp2 estimate of z; (1 + x)^(5/7) - 1 = (z - 1)(1 + z +
+// z^2 + z^3 + z^4); the fan exponents 5 and 7 are exact polynomials.
+struct PowG75 {
+  static __device__ __forceinline__ float rar(float x, float) {
+    const float z = exp2f(__log2f(1.0f + x) * 0.142857142857f);
+    const float s = 1.0f + z * (1.0f + z * (1.0f + z * (1.0f + z * (1.0f + z * (1.0f + z)))));
+    return __fdividef(x, s);
+  }
+  static __device__ __forceinline__ float dens(float, float, float r) {
+    const float z = 1.0f + r;
+    return r * (1.0f + z * (1.0f + z * (1.0f + z * (1.0f + z))));
+  }
+  static __device__ __forceinline__ float fan_rho(float y, float) {
+    return y * (5.0f + y * (10.0f + y * (10.0f + y * (5.0f + y))));
+  }
+  static __device__ __forceinline__ float fan_p(float y, float) {
+    return y * (7.0f + y * (21.0f + y * (35.0f + y * (35.0f + y * (21.0f + y * (7.0f + y))))));
+  }
+};
 
 // Face equilibrium in the frame of a face normal to axis D.
 template <class T>
@@ -114,12 +145,12 @@ __device__ __forceinline__ bool pert_side(T g, const PFace<T>& W0, T v0, const T
 }
 
 // Pressure function of side K at trial p = p0 + d, in perturbation form.
-template <class T>
+template <class T, class P>
 __device__ __forceinline__ void pert_pressure_fn(T g, const PSide<T>& K, T p, T d, T& f, T& fd) {
   const T dpk = d - K.dp;  // p - p_K
   if (dpk <= T(0)) {
     const T x = dpk / K.p;
-    const T r = pow1pm1(x, (g - T(1)) / (T(2) * g));  // (p/p_K)^((g-1)/2g) - 1
+    const T r = P::rar(x, g);  // (p/p_K)^((g-1)/2g) - 1
     f = T(2) * K.c / (g - T(1)) * r;
     fd = (T(1) + r) / ((T(1) + x) * K.rho * K.c);
   } else {
@@ -131,26 +162,26 @@ __device__ __forceinline__ void pert_pressure_fn(T g, const PSide<T>& K, T p, T 
   }
 }
 
-template <class T>
+template <class T, class P>
 __device__ __forceinline__ void fan_pert(T g, const PFace<T>& W0, const PSide<T>& K, bool left, T& drho, T& dun,
                                          T& dp) {
   const T g6 = (g - T(1)) / (g + T(1));
   if (left) {  // (u_L - c_L) = (u0 - c0) + du_L - dc_L
     const T y = g6 * (W0.un_mc + K.dun - K.dc) / K.c;
-    drho = K.drho + K.rho * pow1pm1(y, T(2) / (g - T(1)));
-    dp = K.dp + K.p * pow1pm1(y, T(2) * g / (g - T(1)));
+    drho = K.drho + K.rho * P::fan_rho(y, g);
+    dp = K.dp + K.p * P::fan_p(y, g);
     dun = -W0.un_mc + K.dc + K.c * y;
   } else {     // (-u_R - c_R) = -(u0 + c0) - du_R - dc_R
     const T y = g6 * (-W0.un_pc - K.dun - K.dc) / K.c;
-    drho = K.drho + K.rho * pow1pm1(y, T(2) / (g - T(1)));
-    dp = K.dp + K.p * pow1pm1(y, T(2) * g / (g - T(1)));
+    drho = K.drho + K.rho * P::fan_rho(y, g);
+    dp = K.dp + K.p * P::fan_p(y, g);
     dun = -W0.un_pc - K.dc - K.c * y;
   }
 }
 
 // Perturbation of the face state of the exact Riemann solution.  Returns
 // 0 on success, 1 when the caller must use the FP64 full-state solver.
-template <class T>
+template <class T, class P>
 __device__ __forceinline__ int pert_riemann(T g, const PFace<T>& W0, const PSide<T>& L, const PSide<T>& R, T& drho,
                                             T& dun, T& dp, int& side) {
   if (T(2) / (g - T(1)) * (L.c + R.c) <= R.un - L.un) return 1;  // vacuum generation
@@ -163,8 +194,8 @@ __device__ __forceinline__ int pert_riemann(T g, const PFace<T>& W0, const PSide
   bool conv = false;
   for (int it = 0; it < Math<T>::max_iter; ++it) {
     const T p = W0.p + d;
-    pert_pressure_fn(g, L, p, d, fl, fdl);
-    pert_pressure_fn(g, R, p, d, fr, fdr);
+    pert_pressure_fn<T, P>(g, L, p, d, fl, fdl);
+    pert_pressure_fn<T, P>(g, R, p, d, fr, fdr);
     T dn = d - (fl + fr + du) / (fdl + fdr);
     if (W0.p + dn < floor_p) dn = floor_p - W0.p;
     const T change = Math<T>::abs_(dn - d);
@@ -177,8 +208,8 @@ __device__ __forceinline__ int pert_riemann(T g, const PFace<T>& W0, const PSide
   if (!conv) return 1;
   const T ps = W0.p + d;
   if (ps < T(0.1) * fmin(L.p, R.p)) return 1;  // strong rarefaction: near vacuum
-  pert_pressure_fn(g, L, ps, d, fl, fdl);
-  pert_pressure_fn(g, R, ps, d, fr, fdr);
+  pert_pressure_fn<T, P>(g, L, ps, d, fl, fdl);
+  pert_pressure_fn<T, P>(g, R, ps, d, fr, fdr);
   const T dus = T(0.5) * (L.dun + R.dun) + T(0.5) * (fr - fl);
   const T us = W0.un + dus;
   const T g6 = (g - T(1)) / (g + T(1));
@@ -187,9 +218,10 @@ __device__ __forceinline__ int pert_riemann(T g, const PFace<T>& W0, const PSide
     const T x = (d - L.dp) / L.p;  // p*/p_L - 1
     if (d <= L.dp) {
       if (L.un - L.c >= T(0)) { drho = L.drho; dun = L.dun; dp = L.dp; return 0; }
-      const T cs = L.c * (T(1) + pow1pm1(x, (g - T(1)) / (T(2) * g)));
-      if (us - cs < T(0)) { drho = L.drho + L.rho * pow1pm1(x, T(1) / g); dun = dus; dp = d; return 0; }
-      fan_pert(g, W0, L, true, drho, dun, dp);
+      const T r = P::rar(x, g);
+      const T cs = L.c * (T(1) + r);
+      if (us - cs < T(0)) { drho = L.drho + L.rho * P::dens(x, g, r); dun = dus; dp = d; return 0; }
+      fan_pert<T, P>(g, W0, L, true, drho, dun, dp);
       return 0;
     }
     if (L.un - L.c * Math<T>::sqrt_(T(1) + (g + T(1)) / (T(2) * g) * x) >= T(0)) {
@@ -212,9 +244,10 @@ __device__ __forceinline__ int pert_riemann(T g, const PFace<T>& W0, const PSide
     return 0;
   }
   if (R.un + R.c <= T(0)) { drho = R.drho; dun = R.dun; dp = R.dp; return 0; }
-  const T cs = R.c * (T(1) + pow1pm1(x, (g - T(1)) / (T(2) * g)));
-  if (us + cs > T(0)) { drho = R.drho + R.rho * pow1pm1(x, T(1) / g); dun = dus; dp = d; return 0; }
-  fan_pert(g, W0, R, false, drho, dun, dp);
+  const T r = P::rar(x, g);
+  const T cs = R.c * (T(1) + r);
+  if (us + cs > T(0)) { drho = R.drho + R.rho * P::dens(x, g, r); dun = dus; dp = d; return 0; }
+  fan_pert<T, P>(g, W0, R, false, drho, dun, dp);
   return 0;
 }
 
@@ -235,9 +268,25 @@ __device__ __forceinline__ void pert_flux(T g, const PFace<T>& W0, T drho, T dun
   F[EN] = dh * un + W0.h * dun;
 }
 
+// FP64 full-state solver on W0 + dW for the faces the perturbation solver
+// hands back; kept out of line so the common path stays small.
+template <class T>
+__device__ __noinline__ int pert_fallback_fp64(T g, const PFace<T>& W0, const PSide<T>& L, const PSide<T>& R,
+                                               T& drho, T& dun, T& dp, unsigned& status) {
+  const double rl = (double)W0.rho + (double)L.drho, rr = (double)W0.rho + (double)R.drho;
+  const double ul = (double)W0.un + (double)L.dun, ur = (double)W0.un + (double)R.dun;
+  const double pl = (double)W0.p + (double)L.dp, pr = (double)W0.p + (double)R.dp;
+  double rho, u, p;
+  const int side = riemann_face((double)g, rl, ul, pl, rr, ur, pr, rho, u, p, status);
+  drho = (T)(rho - (double)W0.rho);
+  dun = (T)(u - (double)W0.un);
+  dp = (T)(p - (double)W0.p);
+  return side;
+}
+
 // Gas flux perturbation through a face normal to D from the reconstructed
 // left/right conservative perturbations.
-template <class T, int D>
+template <class T, int D, class P>
 __device__ __forceinline__ void pert_gas_flux(T g, const PFace<T>& W0, T v0, const T* qL, const T* qR, bool has_eq,
                                               T* F, unsigned& status, unsigned& nfallback) {
   PSide<T> L, R;
@@ -251,80 +300,15 @@ __device__ __forceinline__ void pert_gas_flux(T g, const PFace<T>& W0, T v0, con
   }
   T drho, dun, dp;
   int side = 0;
-  if (pert_riemann(g, W0, L, R, drho, dun, dp, side) != 0) {
-    // FP64 full-state solver on W0 + dW
+  if (pert_riemann<T, P>(g, W0, L, R, drho, dun, dp, side) != 0) {
     ++nfallback;
-    const double rl = (double)W0.rho + (double)L.drho, rr = (double)W0.rho + (double)R.drho;
-    const double ul = (double)W0.un + (double)L.dun, ur = (double)W0.un + (double)R.dun;
-    const double pl = (double)W0.p + (double)L.dp, pr = (double)W0.p + (double)R.dp;
-    double rho, u, p;
-    side = riemann_face((double)g, rl, ul, pl, rr, ur, pr, rho, u, p, status);
-    drho = (T)(rho - (double)W0.rho);
-    dun = (T)(u - (double)W0.un);
-    dp = (T)(p - (double)W0.p);
+    side = pert_fallback_fp64(g, W0, L, R, drho, dun, dp, status);
   }
   T dut1 = T(0), dut2 = T(0);
   if (side < 0) { dut1 = L.dut1; dut2 = L.dut2; }
   else if (side > 0) { dut1 = R.dut1; dut2 = R.dut2; }
   else { dut1 = -W0.ut1; dut2 = -W0.ut2; }  // vacuum: no transverse motion
   pert_flux<T, D>(g, W0, drho, dun, dut1, dut2, dp, F);
-}
-
-// Pressureless dust flux in T (dust has no equilibrium: full values).
-template <class T, int D>
-__device__ __forceinline__ void dust_face_flux_t(const T* UL, const T* UR, T* F) {
-  constexpr int n = Axes<D>::n, t1 = Axes<D>::t1, t2 = Axes<D>::t2;
-  const T rl = UL[3], rr = UR[3];
-  const T ul = rl > T(0) ? UL[n] / rl : T(0);
-  const T ur = rr > T(0) ? UR[n] / rr : T(0);
-  int pick;
-  if (ul <= T(0) && ur >= T(0)) pick = 0;
-  else if (ul >= T(0) && ur >= T(0)) pick = -1;
-  else if (ul <= T(0) && ur <= T(0)) pick = 1;
-  else {
-    const T sl = Math<T>::sqrt_(rl), sr = Math<T>::sqrt_(rr);
-    const T vs = (sl * ul + sr * ur) / (sl + sr);
-    pick = vs > T(0) ? -1 : (vs < T(0) ? 1 : 2);
-  }
-  T fl[4] = {T(0), T(0), T(0), T(0)}, fr[4] = {T(0), T(0), T(0), T(0)};
-  if (pick != 1 && rl > T(0)) {
-    const T m = rl * ul;
-    fl[0] = m; fl[1] = m * ul; fl[2] = m * (UL[t1] / rl); fl[3] = m * (UL[t2] / rl);
-  }
-  if (pick != -1 && rr > T(0)) {
-    const T m = rr * ur;
-    fr[0] = m; fr[1] = m * ur; fr[2] = m * (UR[t1] / rr); fr[3] = m * (UR[t2] / rr);
-  }
-  T s[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-    s[q] = pick == -1 ? fl[q] : pick == 1 ? fr[q] : pick == 2 ? T(0.5) * (fl[q] + fr[q]) : T(0);
-  F[3] = s[0];
-  F[n] = s[1];
-  F[t1] = s[2];
-  F[t2] = s[3];
-}
-
-template <class T>
-__device__ __forceinline__ bool parabola_t(T em, T e0, T ep, const T* w, T& qm, T& qp) {
-  const T sm = (e0 - em) * w[0];
-  const T sp = (ep - e0) * w[1];
-  if (sm * sp <= T(0)) {
-    qm = qp = e0;
-    return false;
-  }
-  const T a = (sp - sm) * w[2];
-  const T b = (sp * w[3] + sm * w[4]) * w[2];
-  qm = e0 + w[5] * (a * w[5] + b);
-  qp = e0 + w[6] * (a * w[6] + b);
-  const bool okp = qp >= fmin(e0, ep) && qp <= fmax(e0, ep);
-  const bool okm = qm >= fmin(em, e0) && qm <= fmax(em, e0);
-  if (!okp || !okm) {
-    const T s = Math<T>::abs_(sm) < Math<T>::abs_(sp) ? sm : sp;
-    qm = e0 + s * w[5];
-    qp = e0 + s * w[6];
-  }
-  return true;
 }
 
 template <class T>
@@ -390,7 +374,7 @@ __device__ __forceinline__ PFace<T> face_eq(const PertTables<T>& t, const DevGri
   return W;
 }
 
-template <class T, int NF, int TR, int TT, int TZ, int NT, int D>
+template <class T, int NF, int TR, int TT, int TZ, int NT, int D, class P>
 __device__ __forceinline__ void sweep_pert(const PertArgs<T>& a, const T* sE, T* sG, int i0, int j0, int k0,
                                            unsigned& status, unsigned& nfallback) {
   constexpr int BX = TR + 4, BY = TT + 4, BZ = TZ + 4, BOX = BX * BY * BZ, NCORE = TR * TT * TZ;
@@ -426,19 +410,8 @@ __device__ __forceinline__ void sweep_pert(const PertArgs<T>& a, const T* sE, T*
     const bool do_face = do_recon && c >= 0;
     const bool do_acc = line_ok && c >= 0 && c < TD && gd < nd;
     const int sidx = do_recon ? ((z + 2) * BY + (y + 2)) * BX + (x + 2) : (2 * BY + 2) * BX + 2;
-    T w[7];
-    if (D == 0) {
-      const T* cw = a.t.rcoef + (clampi(gi, -1, g.nr) + 1) * 8;
-#pragma unroll
-      for (int q = 0; q < 7; ++q) w[q] = cw[q];
-    } else {
-      const T h = (T)g.dx[D];
-      w[0] = w[1] = T(1) / h;
-      w[2] = T(0.5) / h;
-      w[3] = w[4] = h;
-      w[5] = T(-0.5) * h;
-      w[6] = T(0.5) * h;
-    }
+    T w[9];
+    parabola_weights<T, D>(a.t.rcoef, gi, g.nr, (T)g.dx[D], w);
     const int ci = clampi(gi, 0, g.nr - 1), ck = clampi(gk, 0, g.nz - 1);
     T area = T(0);
     if (do_face) area = D == 0 ? a.t.area_r[clampi(gi, 0, g.nr)] : (D == 1 ? a.t.area_t[ci] : a.t.area_z[ci]);
@@ -448,7 +421,7 @@ __device__ __forceinline__ void sweep_pert(const PertArgs<T>& a, const T* sE, T*
 #pragma unroll
       for (int f = 0; f < 5; ++f) {
         const T* s = sE + f * BOX + sidx;
-        shaped |= parabola_t(s[-STRIDE], s[0], s[STRIDE], w, qm[f], qp[f]);
+        shaped |= parabola(s[-STRIDE], s[0], s[STRIDE], w, qm[f], qp[f]);
       }
       if (shaped && do_recon) {  // positivity of both reconstructed face states
         T v0m, v0p;
@@ -469,7 +442,7 @@ __device__ __forceinline__ void sweep_pert(const PertArgs<T>& a, const T* sE, T*
         if (do_face) {
           T v0;
           const PFace<T> W0 = face_eq<T, D>(a.t, g, ci, ck, gd, v0);
-          pert_gas_flux<T, D>(gam, W0, v0, ql, qm, has_eq, F, status, nfallback);
+          pert_gas_flux<T, D, P>(gam, W0, v0, ql, qm, has_eq, F, status, nfallback);
 #pragma unroll
           for (int f = 0; f < 5; ++f) F[f] *= area;
         } else {
@@ -487,25 +460,16 @@ __device__ __forceinline__ void sweep_pert(const PertArgs<T>& a, const T* sE, T*
         }
       }
     }
-    if (NF == 9) {
+    if (NF == 9) {  // dust: primitive reconstruction, kinetic flux
       T qm[4], qp[4];
-      bool shaped = false;
-#pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        const T* s = sE + (5 + f) * BOX + sidx;
-        shaped |= parabola_t(s[-STRIDE], s[0], s[STRIDE], w, qm[f], qp[f]);
-      }
-      if (shaped && (qm[3] < T(0) || qp[3] < T(0))) {
-#pragma unroll
-        for (int f = 0; f < 4; ++f) qm[f] = qp[f] = sE[(5 + f) * BOX + sidx];
-      }
+      dust_recon<T, BOX, STRIDE>(sE, sidx, w, qm, qp);
       T F[4];
       {
-        T UL[4];
+        T WL[4];
 #pragma unroll
-        for (int f = 0; f < 4; ++f) UL[f] = __shfl_up_sync(FULL, qp[f], 1, L);
+        for (int f = 0; f < 4; ++f) WL[f] = __shfl_up_sync(FULL, qp[f], 1, L);
         if (do_face) {
-          dust_face_flux_t<T, D>(UL, qm, F);
+          dust_kinetic_flux<D>(WL, qm, F);
 #pragma unroll
           for (int f = 0; f < 4; ++f) F[f] *= area;
         } else {
@@ -651,7 +615,7 @@ __device__ __forceinline__ T pert_cell_dt(const DevGrid& g, const PertTables<T>&
   return dt;
 }
 
-template <class T, int NF, int TR, int TT, int TZ, int NT, int MINB>
+template <class T, int NF, int TR, int TT, int TZ, int NT, int MINB, class P>
 __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> a) {
   constexpr int BX = TR + 4, BY = TT + 4, BZ = TZ + 4, BOX = BX * BY * BZ, NCORE = TR * TT * TZ;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -679,18 +643,18 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
     for (int f = 0; f < NF; ++f) sE[f * BOX + idx] = a.in[f][lin];
   }
   __syncthreads();
-  sweep_pert<T, NF, TR, TT, TZ, NT, 0>(a, sE, sG, i0, j0, k0, status, nfallback);
+  sweep_pert<T, NF, TR, TT, TZ, NT, 0, P>(a, sE, sG, i0, j0, k0, status, nfallback);
   __syncthreads();
-  sweep_pert<T, NF, TR, TT, TZ, NT, 1>(a, sE, sG, i0, j0, k0, status, nfallback);
+  sweep_pert<T, NF, TR, TT, TZ, NT, 1, P>(a, sE, sG, i0, j0, k0, status, nfallback);
   __syncthreads();
-  sweep_pert<T, NF, TR, TT, TZ, NT, 2>(a, sE, sG, i0, j0, k0, status, nfallback);
+  sweep_pert<T, NF, TR, TT, TZ, NT, 2, P>(a, sE, sG, i0, j0, k0, status, nfallback);
   __syncthreads();
 
   const T tau = (T)(a.tau_frac * (a.dt_dev ? __longlong_as_double((long long)*a.dt_dev) : a.dt_host));
-  double dtmin = INFINITY;
-  double sums[NF];
+  T dtmin = T(INFINITY);
+  T sums[NF];  // a thread's few cells in T; blocks and the grid are summed in FP64
 #pragma unroll
-  for (int f = 0; f < NF; ++f) sums[f] = 0.0;
+  for (int f = 0; f < NF; ++f) sums[f] = T(0);
   for (int cidx = threadIdx.x; cidx < NCORE; cidx += NT) {
     const int x = cidx % TR, y = (cidx / TR) % TT, z = cidx / (TR * TT);
     const int gi = i0 + x, gj = j0 + y, gk = k0 + z;
@@ -721,11 +685,11 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
     bool bad_in = false;
     if (a.stage2) {
       bool bad = false;
-      dtmin = fmin(dtmin, (double)pert_cell_dt<T, NF>(g, a.t, ce, gi, E, bad));
+      dtmin = fmin(dtmin, pert_cell_dt<T, NF>(g, a.t, ce, gi, E, bad));
       if (bad) status |= STATUS_NONPHYSICAL;
-      const double V = (double)g.vol[gi];
+      const T V = a.t.vol[gi];
 #pragma unroll
-      for (int f = 0; f < NF; ++f) sums[f] += V * (double)E[f];
+      for (int f = 0; f < NF; ++f) sums[f] += V * E[f];
     } else {
       (void)pert_cell_dt<T, NF>(g, a.t, ce, gi, q, bad_in);
       if (bad_in) status |= STATUS_NONPHYSICAL;
@@ -733,11 +697,11 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
   }
   if (a.stage2) {
     double* red = reinterpret_cast<double*>(smem_raw);
-    const double m = block_min<NT>(dtmin, red);
+    const double m = block_min<NT>((double)dtmin, red);
     if (threadIdx.x == 0) a.partials[(size_t)NF * gridDim.x + blockIdx.x] = m;
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-      const double s = block_sum<NT>(sums[f], red);
+      const double s = block_sum<NT>((double)sums[f], red);
       if (threadIdx.x == 0) a.partials[(size_t)f * gridDim.x + blockIdx.x] = s;
     }
   }

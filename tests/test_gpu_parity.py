@@ -1,10 +1,19 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
-Both sides build their own initial state from the shared seeded inputs, step
-with their own CFL dt, and are compared by the relative L1 error per conserved
-field (tests/parity.py).  Bar for the FP64 form: <= 1e-12.
-Small grids span several tiles of the 14x6x6 kernel tile and ragged tails;
-the full-size workloads are checked on sampled cells after one step.
+Both sides build their own initial state from the shared seeded inputs and are
+compared by the relative L1 error per conserved field (tests/parity.py); the
+GPU follows the oracle's dt sequence, and its own CFL sequence is checked
+against the oracle's separately.  Bar for the FP64 form: <= 1e-12.
+
+Horizons.  Two correct FP64 implementations differ by rounding order, so a
+multi-step comparison is only as good as the trajectory's own conditioning.
+Measured on the oracle against itself with a 1e-15 relative input
+perturbation: the 1-D Sod tube stays <= 1e-15 over all 224 steps; the noisy
+disc (24x32x32) stays <= 1e-13 for 100 steps (it separates after ~120); the
+bi-fluid vortex reaches 1e-12 after ~20 steps (its Mach ~0.7 perturbations
+steepen).  The tests run the disc 100 steps and the vortex 15.
+Small grids span several 14x6x6 kernel tiles and ragged tails; the full-size
+workloads are checked on sampled cells after one step.
 """
 import numpy as np
 import pytest
@@ -59,12 +68,9 @@ def _compare(grid, o, state_gpu, E_ref, tol=TOL64):
 
 
 def test_sod_box(lib):
-    """Sod shock tube in the Box to t = 0.2 (224 steps).  The GPU follows the
-    oracle's dt sequence; the error is recorded at checkpoints.  Rounding-order
-    differences (FMA contraction, reciprocal multiplies, libm pow) of ~1e-16
-    per step are amplified where limiter branches sit near a tie at the
-    discontinuities, so the bar after the full run is 1e-10 (1e-13 after one
-    step).  Its own CFL sequence is checked against the oracle's as well."""
+    """Sod shock tube in the Box to t = 0.2 (224 steps), the GPU following the
+    oracle's dt sequence, checked at several steps; then the GPU's own CFL
+    sequence against the oracle's, and the result against the exact solution."""
     import torch
     R, W = lib
     w = syn.SOD
@@ -74,7 +80,7 @@ def test_sod_box(lib):
     s = torch.from_numpy(E.copy()).cuda()
     V = o.volumes()
     _, _, dts = o.run(E.copy(), t_end=w.t_end)
-    checkpoints = {1: 1e-13, 10: 1e-12, 50: 1e-11, len(dts): 1e-10}
+    checkpoints = {1: 1e-13, 10: TOL64, 50: TOL64, len(dts): TOL64}
     curve = {}
     for n, dt in enumerate(dts, start=1):
         E = o.step(E, dt)
@@ -97,28 +103,33 @@ def test_sod_box(lib):
     assert np.abs(g.full_state(s2)[4, 0, 0, :] - exact).mean() < 0.01
 
 
-@pytest.mark.parametrize("n,steps", [((24, 48, 32), 10), ((15, 7, 33), 6)])
+def _parity_run(lib, w, steps, tol=TOL64, precision=None):
+    import torch
+    R, W = lib
+    o = oracle.Oracle(w)
+    E = oracle.initial_state(o)
+    dts = []
+    for _ in range(steps):
+        dt = o.cfl_dt(E)
+        dts.append(dt)
+        E = o.step(E, dt)
+    g = W.Grid(w) if precision is None else W.Grid(w, precision=precision)
+    s = g.initial_state()
+    assert g.cfl_dt(s) == pytest.approx(dts[0], rel=1e-13 if g.dtype == torch.float64 else 1e-6)
+    for dt in dts:
+        g.step(s, dt=dt)
+    assert g.take_status() == 0 and o.take_status() == 0
+    return _compare(g, o, s, E, tol)
+
+
+@pytest.mark.parametrize("n,steps", [((24, 32, 32), 100), ((15, 7, 33), 20)])
 def test_disc_noise(lib, n, steps):
-    R, W = lib
-    w = syn.scaled(syn.DISC_NOISE, *n, steps=steps)
-    g = W.Grid(w)
-    o = oracle.Oracle(w)
-    s, _, dts = _run_gpu(g, g.initial_state(), steps=steps)
-    E_ref, _, dts_ref = o.run(oracle.initial_state(o), steps=steps)
-    np.testing.assert_allclose(dts, dts_ref, rtol=1e-13)
-    _compare(g, o, s, E_ref)
+    _parity_run(lib, syn.scaled(syn.DISC_NOISE, *n, steps=steps), steps)
 
 
-@pytest.mark.parametrize("n,steps", [((20, 36, 32), 6), ((29, 13, 32), 4)])
+@pytest.mark.parametrize("n,steps", [((20, 36, 32), 15), ((29, 13, 32), 10)])
 def test_vortex_bifluid(lib, n, steps):
-    R, W = lib
-    w = syn.scaled(syn.VORTEX, *n, steps=steps)
-    g = W.Grid(w)
-    o = oracle.Oracle(w)
-    s, _, dts = _run_gpu(g, g.initial_state(), steps=steps)
-    E_ref, _, dts_ref = o.run(oracle.initial_state(o), steps=steps)
-    np.testing.assert_allclose(dts, dts_ref, rtol=1e-13)
-    _compare(g, o, s, E_ref)
+    _parity_run(lib, syn.scaled(syn.VORTEX, *n, steps=steps), steps)
 
 
 def test_equilibrium_bit_exact(lib):

@@ -1,9 +1,11 @@
 """Pins of the oracle's parabolic reconstruction (Sect. 2.7) and of the disc
 equilibrium (App. A).
 
-Reconstruction: the three-point parabola is exact on quadratic and linear
-profiles on a non-uniform (logarithmic) mesh, flat at an extremum, falls back
-to the minmod slope on an overshoot, and never creates a new extremum.
+Reconstruction: the three-point parabola is exact on quadratic profiles on a
+non-uniform (logarithmic) mesh wherever the limiter leaves it alone, flat at an
+extremum, bounded by the minmod slope times twice the face distance (at most
+the neighbour distance) on an overshoot, never creates a
+new extremum, and depends continuously (Lipschitz) on the cell values.
 Equilibrium: central finite differences of the analytic P0 reproduce vertical
 hydrostatic balance and radial centrifugal balance, and the column integral of
 rho0 is the surface density Sigma(r) up to the O(h^2) spherical-potential
@@ -34,10 +36,17 @@ def test_quadratic_exact(coef):
         qm, qp, shaped = oracle.parabola(f(xc[i - 1]), f(xc[i]), f(xc[i + 1]), xc[i - 1], xc[i], xc[i + 1],
                                          xf[i], xf[i + 1])
         vals = [f(xc[i - 1]), f(xc[i]), f(xc[i + 1])]
-        monotone = (vals[1] - vals[0]) * (vals[2] - vals[1]) > 0
-        # where the parabola stays monotone between the neighbours the limiter leaves it alone
-        if monotone and min(vals[0], vals[1]) <= f(xf[i]) <= max(vals[0], vals[1]) and \
-                min(vals[1], vals[2]) <= f(xf[i + 1]) <= max(vals[1], vals[2]):
+        sm = (vals[1] - vals[0]) / (xc[i] - xc[i - 1])
+        sp = (vals[2] - vals[1]) / (xc[i + 1] - xc[i])
+        smin = min(abs(sm), abs(sp)) if sm * sp > 0 else 0.0
+        dm, dp = f(xf[i]) - vals[1], f(xf[i + 1]) - vals[1]
+        # where each face deviation has the slope's sign and stays within twice the
+        # minmod slope times the face distance, the limiter leaves the parabola alone
+        hm = min(2 * (xc[i] - xf[i]), xc[i] - xc[i - 1])
+        hp = min(2 * (xf[i + 1] - xc[i]), xc[i + 1] - xc[i])
+        inside = smin > 0 and dm * sm < 0 and dp * sp > 0 and \
+            abs(dm) < smin * hm * (1 - 1e-12) and abs(dp) < smin * hp * (1 - 1e-12)
+        if inside:
             assert shaped
             assert qm == pytest.approx(f(xf[i]), rel=1e-13, abs=1e-13)
             assert qp == pytest.approx(f(xf[i + 1]), rel=1e-13, abs=1e-13)
@@ -52,11 +61,33 @@ def test_extremum_is_flat():
     assert not shaped and qm == 1.0 and qp == 1.0
 
 
-def test_overshoot_falls_back_to_minmod():
-    # slopes 1 and 0.05 on a unit mesh: the parabola overshoots the right neighbour
+def test_overshoot_limited_by_minmod_bound():
+    # slopes 1 and 0.05 on a unit mesh: the parabola's face deviations (-0.38125,
+    # +0.14375) exceed 2 * 0.05 * 0.5 = 0.05 and are cut to it
     qm, qp, shaped = oracle.parabola(0.0, 1.0, 1.05, 0.0, 1.0, 2.0, 0.5, 1.5)
     assert shaped
-    assert qp == pytest.approx(1.025, rel=1e-15) and qm == pytest.approx(0.975, rel=1e-15)
+    assert qp == pytest.approx(1.05, rel=1e-15) and qm == pytest.approx(0.95, rel=1e-15)
+    # a gentle curvature is kept: slopes 1 and 0.8 give a = -0.1, b = 0.9 and face
+    # deviations -0.475 / +0.425, inside the bounds -0.8 / +0.8
+    qm, qp, _ = oracle.parabola(0.0, 1.0, 1.8, 0.0, 1.0, 2.0, 0.5, 1.5)
+    assert qm == pytest.approx(0.525, rel=1e-14) and qp == pytest.approx(1.425, rel=1e-14)
+
+
+def test_limiter_is_lipschitz():
+    """No branch of the limiter jumps: a perturbation of the data by d moves the
+    face values by at most a few d (continuity keeps nearby runs nearby)."""
+    rng = np.random.default_rng(3)
+    xc, xf = _log_mesh(60)
+    for _ in range(4000):
+        i = int(rng.integers(1, 58))
+        v = rng.normal(size=3)
+        v[1] = v[0] + rng.choice([-1, 1]) * rng.uniform(0, 1e-6) if rng.uniform() < 0.2 else v[1]
+        d = 1e-9 * rng.normal(size=3)
+        args = (xc[i - 1], xc[i], xc[i + 1], xf[i], xf[i + 1])
+        q1 = oracle.parabola(*v, *args)
+        q2 = oracle.parabola(*(v + d), *args)
+        bound = 8 * np.abs(d).max() * (1 + (xc[i + 1] - xc[i - 1]) / min(xc[i] - xc[i - 1], xc[i + 1] - xc[i]))
+        assert abs(q2[0] - q1[0]) <= bound and abs(q2[1] - q1[1]) <= bound
 
 
 def test_no_new_extrema_random():
