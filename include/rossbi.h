@@ -151,6 +151,27 @@ rossbi_status rossbi_step(rossbi_grid* g, void* const* state, void* const* scrat
 rossbi_status rossbi_step_host(rossbi_grid* g, void* const* host_state, double dt, const rossbi_dust_params* dust,
                                double* next_dt);
 
+/* rossbi_step without any device allocation.  The paper has no counterpart:
+ * this entry point serves callers that cannot call cudaMalloc while stepping,
+ * for example host codes that give all device memory to their own pool
+ * allocator at start-up, or loops that cannot accept the device-wide
+ * synchronisation a cudaMalloc or cudaFree may cause.
+ * Same arguments and result as rossbi_step with scratch == NULL, except that
+ * the intermediate state E* and the reduction partials live in a fixed
+ * 64 MiB (67,108,864-byte) array inside the library, allocated with the
+ * library image on every GPU that loads it and held until the process exits.
+ * Limit: nfields * (cells * element size, rounded up to 256 bytes) plus
+ * (nfields + 1) * 8 bytes per 504-cell tile must fit in 64 MiB (for example
+ * 9 fields in FP32 up to ~1.8 M cells, 5 fields in FP64 up to ~1.6 M cells);
+ * larger grids get ROSSBI_ERR_ARG and nothing runs.
+ * The first call on a device looks the array's device address up (with that
+ * device current); make that first call before any stream capture.  Every
+ * call shares the array and it keeps the last call's contents; nothing in it
+ * needs to start at zero.  Calls that overlap on the GPU (other streams,
+ * grids or host threads) race on the array: serialise them. */
+rossbi_status rossbi_step_noalloc(rossbi_grid* g, void* const* state, double dt, const rossbi_dust_params* dust,
+                                  double* next_dt);
+
 /* FP64 conservation sums sum_cells V * E_f of the FULL conservative fields
  * (E0 + E' in the perturbation forms), in a fixed reduction order (so the
  * result is deterministic).  sums: host array of nfields doubles.

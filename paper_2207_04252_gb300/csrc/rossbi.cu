@@ -979,3 +979,144 @@ rossbi_status rossbi_take_status(rossbi_grid* g) {
 
 }  // extern "C"
 
+// ---------------------------------------------------------------------------
+// Step without device allocation.
+//
+// rossbi_step takes its stage scratch (the intermediate state E* and the
+// per-block reduction partials) from a buffer it cudaMallocs on first use, or
+// from caller-passed buffers.  Some callers can allocate neither: host codes
+// that hand all device memory to their own pool at start-up and forbid any
+// later cudaMalloc, or loops that cannot afford the implicit device
+// synchronisation a cudaMalloc/cudaFree may cause.  rossbi_step_noalloc runs
+// the same kernels with that scratch placed in the fixed array below instead.
+//
+// The array is a file-scope __device__ variable: every GPU that loads this
+// library holds NOALLOC_SCRATCH_BYTES of it until the process exits.  Host code
+// must not use `noalloc_scratch` as a pointer (in host code the name is a host
+// stand-in, not a device address); its device address is looked up once per
+// device with cudaGetSymbolAddress, with that device current, on the first
+// rossbi_step_noalloc call made on that device.  That first call should
+// therefore come before any stream capture.  All calls share the array and it
+// keeps the last call's contents; nothing in it needs to start at zero
+// (stage 1 writes every E* cell stage 2 reads, and each stage-2 block writes
+// its own partials).  Calls whose work overlaps on the GPU (other streams,
+// other grids, other threads) race on the array and must be serialised by the
+// caller.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)64 << 20;  // 64 MiB
+static __device__ __align__(256) unsigned char noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+void* noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
+
+size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+rossbi_status noalloc_scratch_ptr(void** out) {
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return ROSSBI_ERR_ARG;
+  if (!noalloc_ptr[dev]) {
+    void* p = nullptr;
+    CK(cudaGetSymbolAddress(&p, noalloc_scratch));
+    noalloc_ptr[dev] = p;
+  }
+  *out = noalloc_ptr[dev];
+  return ROSSBI_OK;
+}
+
+}  // namespace
+
+extern "C" rossbi_status rossbi_step_noalloc(rossbi_grid* g, void* const* state, double dt,
+                                             const rossbi_dust_params* dust, double* next_dt) {
+  if (!g || !g->eq_set || !state) return ROSSBI_ERR_ARG;
+  for (int f = 0; f < g->nf; ++f)
+    if (!state[f]) return ROSSBI_ERR_ARG;
+  if (g->nf == 9 && !dust) return ROSSBI_ERR_ARG;
+  if (dt < 0.0 || !std::isfinite(dt)) return ROSSBI_ERR_ARG;
+  if (dt == 0.0 && !g->dt_on_device) return ROSSBI_ERR_ARG;
+  const int nblocks = n_tiles(g);
+  const size_t field_bytes = align256(g->ncell * elem_size(g));
+  const size_t partial_bytes = (size_t)(g->nf + 1) * nblocks * sizeof(double);
+  if ((size_t)g->nf * field_bytes + partial_bytes > NOALLOC_SCRATCH_BYTES) return ROSSBI_ERR_ARG;
+  void* base = nullptr;
+  rossbi_status st = noalloc_scratch_ptr(&base);
+  if (st != ROSSBI_OK) return st;
+  void* sc[9];
+  for (int f = 0; f < g->nf; ++f) sc[f] = (char*)base + (size_t)f * field_bytes;
+  double* partials = (double*)((char*)base + (size_t)g->nf * field_bytes);
+  DragArgs drag{0.0, 0.0, 0};
+  if (g->nf == 9) {
+    if (!(dust->stokes > 0.0) || (dust->drag_law != 0 && dust->drag_law != 1)) return ROSSBI_ERR_ARG;
+    drag.stokes = dust->stokes;
+    drag.law = dust->drag_law;
+    if (dust->drag_law == 1) {
+      if (!g->has_disc) return ROSSBI_ERR_ARG;
+      double rho1, vth1, p1;
+      equilibrium_prim(g->desc, g->disc, 1.0, 0.0, rho1, vth1, p1);
+      drag.rhos_rp = dust->stokes * rho1 * std::sqrt(g->desc.gamma * p1 / rho1) / std::sqrt(g->desc.gm);
+    }
+  }
+  const int cur = g->dt_slot, nxt = 1 - g->dt_slot;
+  const unsigned long long* dt_dev = dt == 0.0 ? g->d_dt + cur : nullptr;
+  const int prec = g->desc.precision;
+  for (int stage = 1; stage <= 2; ++stage) {
+    const bool s2 = stage == 2;
+    if (prec == ROSSBI_FP64) {
+      StageArgs a = base_args(g);
+      a.drag = drag;
+      a.dt_host = dt;
+      a.dt_dev = dt_dev;
+      for (int f = 0; f < g->nf; ++f) {
+        a.in[f] = (const double*)(s2 ? sc[f] : state[f]);
+        a.base[f] = (const double*)state[f];
+        a.out[f] = (double*)(s2 ? state[f] : sc[f]);
+      }
+      a.tau_frac = s2 ? 1.0 : 0.5;
+      a.stage2 = s2 ? 1 : 0;
+      a.partials = partials;
+      st = launch_stage(g, a, nblocks);
+    } else if (prec == ROSSBI_FP32_PERT) {
+      PertArgs<float> a = pert_args<float>(g);
+      a.drag = drag;
+      a.dt_host = dt;
+      a.dt_dev = dt_dev;
+      for (int f = 0; f < g->nf; ++f) {
+        a.in[f] = (const float*)(s2 ? sc[f] : state[f]);
+        a.base[f] = (const float*)state[f];
+        a.out[f] = (float*)(s2 ? state[f] : sc[f]);
+      }
+      a.tau_frac = s2 ? 1.0 : 0.5;
+      a.stage2 = s2 ? 1 : 0;
+      a.partials = partials;
+      st = launch_pert<float>(g, a, nblocks);
+    } else {
+      PertArgs<double> a = pert_args<double>(g);
+      a.drag = drag;
+      a.dt_host = dt;
+      a.dt_dev = dt_dev;
+      for (int f = 0; f < g->nf; ++f) {
+        a.in[f] = (const double*)(s2 ? sc[f] : state[f]);
+        a.base[f] = (const double*)state[f];
+        a.out[f] = (double*)(s2 ? state[f] : sc[f]);
+      }
+      a.tau_frac = s2 ? 1.0 : 0.5;
+      a.stage2 = s2 ? 1 : 0;
+      a.partials = partials;
+      st = launch_pert<double>(g, a, nblocks);
+    }
+    if (st != ROSSBI_OK) return st;
+  }
+  reduce_partials_kernel<<<g->nf + 1, RED_NT, 0, g->stream>>>(partials, nblocks, g->nf, g->d_sums, g->d_dt + nxt);
+  CK(cudaGetLastError());
+  g->dt_slot = nxt;
+  g->dt_on_device = true;
+  if (next_dt) {
+    CK(cudaMemcpyAsync(g->h_pinned, g->d_dt + nxt, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    st = sync_and_status(g);
+    *next_dt = g->h_pinned[0];
+    return st;
+  }
+  return ROSSBI_OK;
+}

@@ -26,7 +26,7 @@ ROSSBI_FP64, ROSSBI_FP32_PERT, ROSSBI_FP64_PERT = 0, 1, 2
 # every function declared in include/rossbi.h
 EXPORTS = (
     "rossbi_init_grid", "rossbi_set_equilibrium", "rossbi_get_equilibrium", "rossbi_cfl_dt", "rossbi_step",
-    "rossbi_step_host", "rossbi_conservation_sums", "rossbi_fallback_count", "rossbi_take_status",
+    "rossbi_step_host", "rossbi_step_noalloc", "rossbi_conservation_sums", "rossbi_fallback_count", "rossbi_take_status",
     "rossbi_profile_enable",
     "rossbi_profile_read", "rossbi_nfields", "rossbi_precision", "rossbi_destroy", "rossbi_status_string",
 )
@@ -75,6 +75,7 @@ def load(path: str = LIB_PATH):
     L.rossbi_cfl_dt.argtypes = [_VP, _PP, _DP]
     L.rossbi_step.argtypes = [_VP, _PP, _PP, ctypes.c_double, ctypes.POINTER(rossbi_dust_params), _DP]
     L.rossbi_step_host.argtypes = [_VP, _PP, ctypes.c_double, ctypes.POINTER(rossbi_dust_params), _DP]
+    L.rossbi_step_noalloc.argtypes = [_VP, _PP, ctypes.c_double, ctypes.POINTER(rossbi_dust_params), _DP]
     L.rossbi_conservation_sums.argtypes = [_VP, _PP, _DP]
     L.rossbi_take_status.argtypes = [_VP]
     L.rossbi_fallback_count.argtypes = [_VP, ctypes.POINTER(ctypes.c_ulonglong)]
@@ -167,6 +168,18 @@ def rossbi_step(grid, state, scratch=None, dt=0.0, dust=None, want_next_dt=False
     code = load().rossbi_step(grid, _fields(state, nf), _fields(scratch, nf), float(dt), d,
                               ctypes.byref(nd) if want_next_dt else None)
     _check(code, "rossbi_step")
+    return nd.value if want_next_dt else None
+
+
+def rossbi_step_noalloc(grid, state, dt=0.0, dust=None, want_next_dt=False):
+    """rossbi_step with its scratch in the library's fixed device array (no allocation).
+    For callers that cannot allocate device memory while stepping; see include/rossbi.h
+    for the size limit and the rule that overlapping calls must be serialised."""
+    nf = rossbi_nfields(grid)
+    d = None if dust is None else ctypes.byref(rossbi_dust_params(*dust))
+    nd = ctypes.c_double()
+    _check(load().rossbi_step_noalloc(grid, _fields(state, nf), float(dt), d,
+                                      ctypes.byref(nd) if want_next_dt else None), "rossbi_step_noalloc")
     return nd.value if want_next_dt else None
 
 
