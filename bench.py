@@ -4,8 +4,11 @@
 A step is one full midpoint-RK2 update (two fused stage launches plus the
 conservation-sum finalisation) of the whole grid of the synthetic workload,
 with the state resident in HBM and the CFL step kept on the device.  The
-state (4.8 GB in FP64 for the default 512x1024x128 bi-fluid grid) is far
-larger than L2, so no flush is needed between steps.
+state (2.4 GB in the default FP32 perturbation form, 4.8 GB in FP64, for the
+512x1024x128 bi-fluid grid) is far larger than L2, so no flush is needed
+between steps.  The line also carries the FP64 form's throughput on the same
+grid and the FP32 form's relative L1 error against the FP64 form after 100
+steps of the 128x256x32 noisy disc.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32]
                   [--workload NAME] [--impl ours|reference]
@@ -43,32 +46,43 @@ def _peaks():
         return HBM_PEAK_FALLBACK, "fallback"
 
 
-def _traffic(kernel_tag, workload):
-    """Per-launch DRAM bytes of the stage kernel from the committed ncu summary
-    (profiles/<kernel_tag>__<workload>.txt), if it was taken on the current source."""
-    path = os.path.join(ROOT, "profiles", f"{kernel_tag}__{workload}.txt")
-    if not os.path.exists(path):
-        return None
-    vals = {}
-    for line in open(path):
-        if "=" in line and not line.startswith("#"):
-            k, v = line.split("=", 1)
-            vals[k.strip()] = v.strip()
-    if vals.get("source_hash") != _source_hash():
-        return None
-    try:
-        return float(vals["dram_bytes_per_launch"])
-    except (KeyError, ValueError):
-        return None
+def _traffic(kernel_tag, cells):
+    """Per-launch DRAM bytes (read + write) of the stage kernel from a committed
+    ncu summary (profiles/<kernel_tag>__<workload>.txt) taken on the current
+    kernel source, scaled from the captured grid to `cells` (the stage kernels
+    stream the grid once per launch, so traffic grows with the cell count).
+    Returns (bytes, summary file name) or (None, None)."""
+    import glob
+    want = _source_hash(kernel_tag)
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{kernel_tag}__*.txt"))):
+        vals = {}
+        for line in open(path):
+            if "=" in line and not line.startswith("#"):
+                k, v = line.split("=", 1)
+                vals[k.strip()] = v.split("#")[0].strip()
+        if vals.get("source_hash") != want:
+            continue
+        try:
+            return float(vals["dram_bytes_per_launch"]) * cells / float(vals["cells"]), os.path.basename(path)
+        except (KeyError, ValueError):
+            continue
+    return None, None
 
 
-def _source_hash():
+KERNEL_SOURCES = {
+    "stage_fp32": ("device_common.cuh", "stage_pert.cuh"),
+    "stage_fp64pert": ("device_common.cuh", "stage_pert.cuh"),
+    "stage_fp64": ("device_common.cuh", "stage_full.cuh"),
+}
+
+
+def _source_hash(kernel_tag):
+    """Hash of the headers that define a kernel (its code, not its callers)."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2207_04252_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, name), "rb").read())
+    for name in KERNEL_SOURCES[kernel_tag]:
+        h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -172,6 +186,57 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def fp32_error_vs_fp64(R, W, syn, torch):
+    """Relative L1 error per conserved quantity of the FP32 form against the FP64
+    form (itself within 1e-12 of the CPU oracle) after 100 steps of the noisy-disc
+    workload at its full size, both driven by the FP64 form's dt sequence."""
+    import numpy as np
+    w = syn.DISC_NOISE
+    g64 = W.Grid(w, precision=R.ROSSBI_FP64)
+    g32 = W.Grid(w, precision=R.ROSSBI_FP32_PERT)
+    a = g64.initial_state()
+    b = g32.initial_state()
+    dt = g64.cfl_dt(a)
+    for _ in range(w.steps):
+        ndt = g64.step(a, dt=dt, want_next_dt=True)
+        g32.step(b, dt=dt)
+        dt = ndt
+    E64, E32 = g64.full_state(a), g32.full_state(b)
+    V = np.zeros(w.nr)
+    f = w.x0[0] * (w.x1[0] / w.x0[0]) ** (np.arange(w.nr + 1) / w.nr)
+    V[:] = 0.5 * (f[1:] ** 2 - f[:-1] ** 2)
+    out = {}
+    for name, fields in (("mass", (4,)), ("momentum", (0, 1, 2)), ("energy", (3,))):
+        num = sum((V * np.abs(E32[q] - E64[q])).sum() for q in fields)
+        den = sum((V * np.abs(E64[q])).sum() for q in fields)
+        out[name] = float(num / den)
+    nfb = R.rossbi_fallback_count(g32.h)
+    g64.close()
+    g32.close()
+    return {"workload": w.name, "steps": w.steps, "rel_l1": out, "fallback_faces": nfb, "bar": 1e-5}
+
+
+def measure_fp64(R, W, w, torch, steps=2, warmup=3):
+    g = W.Grid(w, precision=R.ROSSBI_FP64, stream=torch.cuda.current_stream())
+    s = g.initial_state()
+    g.cfl_dt(s)
+    for _ in range(warmup):
+        g.step(s, dt=0.0)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(steps):
+        g.step(s, dt=0.0)
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    g.close()
+    del s
+    torch.cuda.empty_cache()
+    return {"value": w.ncell / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps, "warmup": warmup,
+            "dtype": "f64"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -250,8 +315,12 @@ def run_ours(args):
     achieved = bytes_per_launch / avg_launch_s / 1e9
     kernel_tag = f"stage_{args.precision}"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": _traffic(kernel_tag, w.name), "peak_kind": peak_kind, "kernel": kernel_tag,
+                "traffic": None, "peak_kind": peak_kind, "kernel": kernel_tag,
                 "avg_launch_ms": avg_launch_s * 1e3}
+    traffic, src = _traffic(kernel_tag, w.ncell)
+    if traffic is not None:
+        roofline["traffic"] = traffic
+        roofline["traffic_source"] = src
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -262,6 +331,12 @@ def run_ours(args):
                            "l2": "inputs larger than L2 (no flush needed)"},
                 "roofline": roofline, "e2e": e2e, "gpu_launches": 3 * args.steps, "clocks": clocks,
                 "status": R.status_string(status)}
+        if args.precision == "fp32" and not args.no_extras:
+            fp64 = measure_fp64(R, workloads, w, torch)
+            line["fp64_form"] = fp64
+            line["fp32_over_fp64"] = value / world / fp64["value"]
+            line["fp32_error_vs_fp64"] = fp32_error_vs_fp64(R, workloads, syn, torch)
+        line["adjoint_over_forward"] = None
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(line), flush=True)
@@ -275,10 +350,11 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", choices=("fp64", "fp32"), default="fp64")
+    ap.add_argument("--precision", choices=("fp64", "fp32"), default="fp32")
     ap.add_argument("--workload", default="bifluid_two_vortices_512x1024x128")
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64-form and FP32-error side measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -14,6 +14,9 @@ DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
     "-O3", "-lineinfo", "-std=c++17",
+    # single-precision division and square root by the hardware approximations
+    # (2 ulp); only the FP32 perturbation kernels use float arithmetic
+    "-prec-div=false", "-prec-sqrt=false",
     "-Xcompiler", "-fPIC,-ffp-contract=off",
     "-cudart", "shared",
     "-Xlinker", "-rpath,/usr/local/cuda/lib64",

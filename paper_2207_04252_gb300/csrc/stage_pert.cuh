@@ -251,21 +251,21 @@ __device__ __forceinline__ int pert_riemann(T g, const PFace<T>& W0, const PSide
   return 0;
 }
 
-// F(W0 + dW) - F(W0) for a face normal to axis D (App. B flux components,
-// energy flux (E + P) u_n), written without forming the equilibrium flux.
-template <class T, int D>
+// F(W0 + dW) - F(W0) through a face (App. B flux components, energy flux
+// (E + P) u_n), written without forming the equilibrium flux.  F is in face
+// order: mass, normal momentum, transverse momenta t1, t2, energy.
+template <class T>
 __device__ __forceinline__ void pert_flux(T g, const PFace<T>& W0, T drho, T dun, T dut1, T dut2, T dp, T* F) {
-  constexpr int n = Axes<D>::n, t1 = Axes<D>::t1, t2 = Axes<D>::t2;
   const T un = W0.un + dun, ut1 = W0.ut1 + dut1, ut2 = W0.ut2 + dut2;
   const T dmass = drho * un + W0.rho * dun;
   const T m0 = W0.rho * W0.un;
-  F[RHO] = dmass;
-  F[n] = dmass * un + m0 * dun + dp;
-  F[t1] = dmass * ut1 + m0 * dut1;
-  F[t2] = dmass * ut2 + m0 * dut2;
+  F[0] = dmass;
+  F[1] = dmass * un + m0 * dun + dp;
+  F[2] = dmass * ut1 + m0 * dut1;
+  F[3] = dmass * ut2 + m0 * dut2;
   const T du2 = dun * (T(2) * W0.un + dun) + dut1 * (T(2) * W0.ut1 + dut1) + dut2 * (T(2) * W0.ut2 + dut2);
   const T dh = T(0.5) * drho * (un * un + ut1 * ut1 + ut2 * ut2) + T(0.5) * W0.rho * du2 + g / (g - T(1)) * dp;
-  F[EN] = dh * un + W0.h * dun;
+  F[4] = dh * un + W0.h * dun;
 }
 
 // FP64 full-state solver on W0 + dW for the faces the perturbation solver
@@ -284,31 +284,40 @@ __device__ __noinline__ int pert_fallback_fp64(T g, const PFace<T>& W0, const PS
   return side;
 }
 
-// Gas flux perturbation through a face normal to D from the reconstructed
-// left/right conservative perturbations.
-template <class T, int D, class P>
-__device__ __forceinline__ void pert_gas_flux(T g, const PFace<T>& W0, T v0, const T* qL, const T* qR, bool has_eq,
-                                              T* F, unsigned& status, unsigned& nfallback) {
-  PSide<T> L, R;
-  const bool okL = pert_side<T, D>(g, W0, v0, qL, has_eq, L);
-  const bool okR = pert_side<T, D>(g, W0, v0, qR, has_eq, R);
-  if (!okL || !okR) {
-    status |= STATUS_NONPHYSICAL;
-#pragma unroll
-    for (int f = 0; f < 5; ++f) F[f] = T(0);
-    return;
-  }
+// Gas flux perturbation through a face from the primitive perturbations of
+// its two reconstructed states (already checked physical); face-order output
+// as pert_flux.  One out-of-line copy serves the three sweep directions.
+template <class T, class P>
+__device__ __noinline__ void pert_face_flux(T g, const PFace<T> W0, const PSide<T> L, const PSide<T> R, T* F,
+                                            unsigned* status, unsigned* nfallback) {
   T drho, dun, dp;
   int side = 0;
   if (pert_riemann<T, P>(g, W0, L, R, drho, dun, dp, side) != 0) {
-    ++nfallback;
-    side = pert_fallback_fp64(g, W0, L, R, drho, dun, dp, status);
+    ++*nfallback;
+    side = pert_fallback_fp64(g, W0, L, R, drho, dun, dp, *status);
   }
   T dut1 = T(0), dut2 = T(0);
   if (side < 0) { dut1 = L.dut1; dut2 = L.dut2; }
   else if (side > 0) { dut1 = R.dut1; dut2 = R.dut2; }
   else { dut1 = -W0.ut1; dut2 = -W0.ut2; }  // vacuum: no transverse motion
-  pert_flux<T, D>(g, W0, drho, dun, dut1, dut2, dp, F);
+  pert_flux<T>(g, W0, drho, dun, dut1, dut2, dp, F);
+}
+
+template <class T>
+__device__ __forceinline__ PSide<T> shfl_up_side(const PSide<T>& s, int width) {
+  constexpr unsigned FULL = 0xffffffffu;
+  PSide<T> o;
+  o.drho = __shfl_up_sync(FULL, s.drho, 1, width);
+  o.dun = __shfl_up_sync(FULL, s.dun, 1, width);
+  o.dut1 = __shfl_up_sync(FULL, s.dut1, 1, width);
+  o.dut2 = __shfl_up_sync(FULL, s.dut2, 1, width);
+  o.dp = __shfl_up_sync(FULL, s.dp, 1, width);
+  o.rho = __shfl_up_sync(FULL, s.rho, 1, width);
+  o.un = __shfl_up_sync(FULL, s.un, 1, width);
+  o.p = __shfl_up_sync(FULL, s.p, 1, width);
+  o.c = __shfl_up_sync(FULL, s.c, 1, width);
+  o.dc = __shfl_up_sync(FULL, s.dc, 1, width);
+  return o;
 }
 
 template <class T>
@@ -423,28 +432,36 @@ __device__ __forceinline__ void sweep_pert(const PertArgs<T>& a, const T* sE, T*
         const T* s = sE + f * BOX + sidx;
         shaped |= parabola(s[-STRIDE], s[0], s[STRIDE], w, qm[f], qp[f]);
       }
-      if (shaped && do_recon) {  // positivity of both reconstructed face states
-        T v0m, v0p;
-        const PFace<T> Wm = face_eq<T, D>(a.t, g, ci, ck, gd, v0m);
-        const PFace<T> Wp = face_eq<T, D>(a.t, g, ci, ck, gd + 1, v0p);
-        PSide<T> sm, sp;
-        const bool ok = pert_side<T, D>(gam, Wm, v0m, qm, has_eq, sm) && pert_side<T, D>(gam, Wp, v0p, qp, has_eq, sp);
-        if (!ok) {
+      // primitive perturbations of both face states, used for the positivity
+      // check of Sect. 2.7's reconstruction and then by the two faces' solvers
+      T v0m, v0p;
+      const PFace<T> Wm = face_eq<T, D>(a.t, g, ci, ck, gd, v0m);
+      const PFace<T> Wp = face_eq<T, D>(a.t, g, ci, ck, gd + 1, v0p);
+      PSide<T> sm, sp;
+      bool ok = pert_side<T, D>(gam, Wm, v0m, qm, has_eq, sm) & pert_side<T, D>(gam, Wp, v0p, qp, has_eq, sp);
+      if (!ok && shaped) {  // positivity fallback: flat reconstruction of the gas fields
 #pragma unroll
-          for (int f = 0; f < 5; ++f) qm[f] = qp[f] = sE[f * BOX + sidx];
-        }
+        for (int f = 0; f < 5; ++f) qm[f] = qp[f] = sE[f * BOX + sidx];
+        ok = pert_side<T, D>(gam, Wm, v0m, qm, has_eq, sm) & pert_side<T, D>(gam, Wp, v0p, qp, has_eq, sp);
       }
       T F[5];
       {
-        T ql[5];
-#pragma unroll
-        for (int f = 0; f < 5; ++f) ql[f] = __shfl_up_sync(FULL, qp[f], 1, L);
+        const PSide<T> sl = shfl_up_side(sp, L);  // upper face state of the lower neighbour
+        const bool okl = __shfl_up_sync(FULL, ok ? 1 : 0, 1, L) != 0;
         if (do_face) {
-          T v0;
-          const PFace<T> W0 = face_eq<T, D>(a.t, g, ci, ck, gd, v0);
-          pert_gas_flux<T, D, P>(gam, W0, v0, ql, qm, has_eq, F, status, nfallback);
+          if (ok && okl) {
+            T Ff[5];
+            pert_face_flux<T, P>(gam, Wm, sl, sm, Ff, &status, &nfallback);
+            F[RHO] = Ff[0] * area;
+            F[Axes<D>::n] = Ff[1] * area;
+            F[Axes<D>::t1] = Ff[2] * area;
+            F[Axes<D>::t2] = Ff[3] * area;
+            F[EN] = Ff[4] * area;
+          } else {
+            status |= STATUS_NONPHYSICAL;
 #pragma unroll
-          for (int f = 0; f < 5; ++f) F[f] *= area;
+            for (int f = 0; f < 5; ++f) F[f] = T(0);
+          }
         } else {
 #pragma unroll
           for (int f = 0; f < 5; ++f) F[f] = T(0);
