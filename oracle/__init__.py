@@ -65,6 +65,8 @@ def lib():
         L.orc_rhs.argtypes = [ctypes.c_void_p, _D, _D]
         L.orc_stage.argtypes = [ctypes.c_void_p, _D, _D, _D, ctypes.c_double, ctypes.c_double, ctypes.c_int]
         L.orc_step.argtypes = [ctypes.c_void_p, _D, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+        L.orc_step_tlm.argtypes = [ctypes.c_void_p, _D, _D, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_int]
         L.orc_step_sampled.argtypes = [ctypes.c_void_p, _D, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                        _L, ctypes.c_long, _D]
         L.orc_cfl_dt.restype = ctypes.c_double
@@ -176,6 +178,15 @@ class Oracle:
         E = np.array(E, dtype=np.float64, order="C", copy=True)
         self.status |= lib().orc_step(self.h, _p(E), dt, self.w.stokes, self.w.drag_law)
         return E
+
+    def step_tlm(self, E, dE, dt, dstokes=0.0, stokes=None):
+        """Tangent-linear RK2 step at fixed dt: returns (E^{n+1}, dE^{n+1}) for the
+        direction (dE, dstokes); Stokes number defaults to the workload's."""
+        E = np.array(E, dtype=np.float64, order="C", copy=True)
+        dE = np.array(dE, dtype=np.float64, order="C", copy=True)
+        st = self.w.stokes if stokes is None else stokes
+        self.status |= lib().orc_step_tlm(self.h, _p(E), _p(dE), dt, st, dstokes, self.w.drag_law)
+        return E, dE
 
     def step_sampled(self, E, dt, cells):
         E = np.ascontiguousarray(E, dtype=np.float64)

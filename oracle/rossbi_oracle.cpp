@@ -176,38 +176,85 @@ static inline const double* E0Z(const Oracle& o, int i, int kface) {
   return &o.e0z[((size_t)(kface + NG) * (o.n[0] + 2 * NG) + (i + NG)) * 5];
 }
 
-// ---------------------------------------------------------------- state access
-struct ArrAcc {
-  const double* E;
-  long ncell;
-  double get(int f, long lin) const { return E[(size_t)f * ncell + lin]; }
+// ---------------------------------------------------------------- scalar types
+// The numeric core below is written once for a scalar type T: double for the
+// oracle itself, Dual (value + one tangent) for its tangent-linear mode.
+// Every branch is decided on the value, so the tangent is the derivative of
+// the branch that was taken.
+struct Dual {
+  double v, d;
+  Dual(double v_ = 0.0, double d_ = 0.0) : v(v_), d(d_) {}
 };
+static inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+static inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+static inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+static inline Dual operator/(Dual a, Dual b) { return Dual(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)); }
+static inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+static inline Dual operator+(Dual a, double b) { return Dual(a.v + b, a.d); }
+static inline Dual operator+(double a, Dual b) { return Dual(a + b.v, b.d); }
+static inline Dual operator-(Dual a, double b) { return Dual(a.v - b, a.d); }
+static inline Dual operator-(double a, Dual b) { return Dual(a - b.v, -b.d); }
+static inline Dual operator*(Dual a, double b) { return Dual(a.v * b, a.d * b); }
+static inline Dual operator*(double a, Dual b) { return Dual(a * b.v, a * b.d); }
+static inline Dual operator/(Dual a, double b) { return Dual(a.v / b, a.d / b); }
+static inline Dual operator/(double a, Dual b) { return Dual(a / b.v, -a * b.d / (b.v * b.v)); }
+static inline Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
+static inline Dual& operator-=(Dual& a, Dual b) { a = a - b; return a; }
+static inline bool operator<(Dual a, Dual b) { return a.v < b.v; }
+static inline bool operator<=(Dual a, Dual b) { return a.v <= b.v; }
+static inline bool operator>(Dual a, Dual b) { return a.v > b.v; }
+static inline bool operator>=(Dual a, Dual b) { return a.v >= b.v; }
+static inline bool operator!=(Dual a, Dual b) { return a.v != b.v; }
+static inline Dual sqrt(Dual a) {
+  const double r = std::sqrt(a.v);
+  return Dual(r, a.d / (2.0 * r));
+}
+static inline Dual pow(Dual a, double e) {
+  const double r = std::pow(a.v, e);
+  return Dual(r, e * std::pow(a.v, e - 1.0) * a.d);
+}
+static inline Dual fabs(Dual a) { return a.v < 0.0 ? -a : a; }
+static inline double val(double x) { return x; }
+static inline double val(Dual x) { return x.v; }
+template <class T> static inline T tmin(T a, T b) { return b < a ? b : a; }
+
+// ---------------------------------------------------------------- state access
+template <class T>
+struct ArrAccT {
+  using value_type = T;
+  const T* E;
+  long ncell;
+  T get(int f, long lin) const { return E[(size_t)f * ncell + lin]; }
+};
+using ArrAcc = ArrAccT<double>;
 
 // Deviation E' = E - E0 (Sect. 2.7) of field f at cell (i, j, k); at most one
 // index may lie outside the domain, where the ghost rule of Sect. 2.4 applies:
 // equilibrium ghosts carry E' = 0, periodic ghosts wrap, outflow ghosts copy
 // the nearest interior deviation.
 template <class Acc>
-static double dev(const Oracle& o, const Acc& E, int f, int i, int j, int k) {
+static typename Acc::value_type dev(const Oracle& o, const Acc& E, int f, int i, int j, int k) {
+  using T = typename Acc::value_type;
   int c[3] = {i, j, k};
   for (int ax = 0; ax < 3; ++ax) {
     if (c[ax] >= 0 && c[ax] < o.n[ax]) continue;
     const int bc = c[ax] < 0 ? o.d.bc_lo[ax] : o.d.bc_hi[ax];
-    if (bc == BC_EQUILIBRIUM) return 0.0;
+    if (bc == BC_EQUILIBRIUM) return T(0.0);
     if (bc == BC_PERIODIC)
       c[ax] = ((c[ax] % o.n[ax]) + o.n[ax]) % o.n[ax];
     else
       c[ax] = c[ax] < 0 ? 0 : o.n[ax] - 1;
   }
   const long lin = ((long)c[2] * o.n[1] + c[1]) * o.n[0] + c[0];
-  double e = E.get(f, lin);
+  T e = E.get(f, lin);
   if (f < 5 && o.has_eq) e -= E0C(o, c[0], c[2])[f];
   return e;
 }
 
 // ---------------------------------------------------------------- reconstruction
-static inline double minmod(double a, double b) {
-  if (a * b <= 0.0) return 0.0;
+template <class T>
+static inline T minmod(T a, T b) {
+  if (a * b <= 0.0) return T(0.0);
   return fabs(a) < fabs(b) ? a : b;
 }
 // Sect. 2.7: the parabola through the three cell values of E' at the centre
@@ -215,13 +262,13 @@ static inline double minmod(double a, double b) {
 // with the paper's coefficients a, b and the slopes nabla E'(i) = sm,
 // nabla E'(i+1) = sp; then the MinMod limiter of reading R2.  Returns false
 // when the result is flat.
-static bool parabola(double em, double e0, double ep, double xm, double x0, double xp, double fm, double fp,
-                     double& qm, double& qp) {
-  const double sm = (e0 - em) / (x0 - xm);
-  const double sp = (ep - e0) / (xp - x0);
-  const double s = minmod(sm, sp);
-  const double a = (sp - sm) / (xp - xm);
-  const double b = (sp * (x0 - xm) + sm * (xp - x0)) / (xp - xm);
+template <class T>
+static bool parabola(T em, T e0, T ep, double xm, double x0, double xp, double fm, double fp, T& qm, T& qp) {
+  const T sm = (e0 - em) / (x0 - xm);
+  const T sp = (ep - e0) / (xp - x0);
+  const T s = minmod(sm, sp);
+  const T a = (sp - sm) / (xp - xm);
+  const T b = (sp * (x0 - xm) + sm * (xp - x0)) / (xp - xm);
   const double dm = fm - x0, dp = fp - x0;
   const double hm = -std::min(-2.0 * dm, x0 - xm), hp = std::min(2.0 * dp, xp - x0);
   qm = e0 + minmod(a * dm * dm + b * dm, s * hm);
@@ -229,7 +276,8 @@ static bool parabola(double em, double e0, double ep, double xm, double x0, doub
   return s != 0.0;
 }
 
-static inline double pressure(double g, const double* U) {
+template <class T>
+static inline T pressure(double g, const T* U) {
   return (g - 1.0) * (U[EN] - 0.5 * (U[MU] * U[MU] + U[MV] * U[MV] + U[MW] * U[MW]) / U[RHO]);
 }
 
@@ -245,31 +293,31 @@ static void eq_face(const Oracle& o, int ax, int i, int k, int fc, double e0[5])
 }
 
 // Face deviations q- (lower face) and q+ (upper face) of cell `cell` along ax.
-template <class Acc>
-static void recon(const Oracle& o, const Acc& E, int ax, const int cell[3], double qm[9], double qp[9]) {
+template <class Acc, class T = typename Acc::value_type>
+static void recon(const Oracle& o, const Acc& E, int ax, const int cell[3], T qm[9], T qp[9]) {
   int cm[3] = {cell[0], cell[1], cell[2]}, cp[3] = {cell[0], cell[1], cell[2]};
   cm[ax] -= 1;
   cp[ax] += 1;
   const int c = cell[ax];
   const double xm = XC(o, ax, c - 1), x0 = XC(o, ax, c), xp = XC(o, ax, c + 1);
   const double fm = XF(o, ax, c), fp = XF(o, ax, c + 1);
-  double ec[5];
+  T ec[5];
   bool gas_shaped = false;
   for (int f = 0; f < 5; ++f) {
-    const double em = dev(o, E, f, cm[0], cm[1], cm[2]);
+    const T em = dev(o, E, f, cm[0], cm[1], cm[2]);
     ec[f] = dev(o, E, f, cell[0], cell[1], cell[2]);
-    const double ep = dev(o, E, f, cp[0], cp[1], cp[2]);
+    const T ep = dev(o, E, f, cp[0], cp[1], cp[2]);
     gas_shaped |= parabola(em, ec[f], ep, xm, x0, xp, fm, fp, qm[f], qp[f]);
   }
   if (o.nf > 5) {  // R5: dust in primitive variables (rho_d, u_d, v_d, w_d)
-    double wm[4], w0[4], wp[4], qmw[4], qpw[4];
+    T wm[4], w0[4], wp[4], qmw[4], qpw[4];
     wm[3] = dev(o, E, DRHO, cm[0], cm[1], cm[2]);
     w0[3] = dev(o, E, DRHO, cell[0], cell[1], cell[2]);
     wp[3] = dev(o, E, DRHO, cp[0], cp[1], cp[2]);
     for (int c = 0; c < 3; ++c) {
-      wm[c] = wm[3] > 0.0 ? dev(o, E, DMU + c, cm[0], cm[1], cm[2]) / wm[3] : 0.0;
-      w0[c] = w0[3] > 0.0 ? dev(o, E, DMU + c, cell[0], cell[1], cell[2]) / w0[3] : 0.0;
-      wp[c] = wp[3] > 0.0 ? dev(o, E, DMU + c, cp[0], cp[1], cp[2]) / wp[3] : 0.0;
+      wm[c] = wm[3] > 0.0 ? dev(o, E, DMU + c, cm[0], cm[1], cm[2]) / wm[3] : T(0.0);
+      w0[c] = w0[3] > 0.0 ? dev(o, E, DMU + c, cell[0], cell[1], cell[2]) / w0[3] : T(0.0);
+      wp[c] = wp[3] > 0.0 ? dev(o, E, DMU + c, cp[0], cp[1], cp[2]) / wp[3] : T(0.0);
     }
     for (int q = 0; q < 4; ++q) parabola(wm[q], w0[q], wp[q], xm, x0, xp, fm, fp, qmw[q], qpw[q]);
     qm[DRHO] = qmw[3];
@@ -280,7 +328,8 @@ static void recon(const Oracle& o, const Acc& E, int ax, const int cell[3], doub
     }
   }
   if (gas_shaped) {  // R2 (iii): positivity of both reconstructed gas face states
-    double e0m[5], e0p[5], Um[5], Up[5];
+    double e0m[5], e0p[5];
+    T Um[5], Up[5];
     eq_face(o, ax, cell[0], cell[2], c, e0m);
     eq_face(o, ax, cell[0], cell[2], c + 1, e0p);
     for (int f = 0; f < 5; ++f) {
@@ -294,59 +343,83 @@ static void recon(const Oracle& o, const Acc& E, int ax, const int cell[3], doub
 }
 
 // ---------------------------------------------------------------- exact Riemann solver (Toro)
+template <class T>
 struct Side {
-  double rho, u, p, c;
+  T rho, u, p, c;
 };
 // Pressure function f_K(p) of the star-region pressure and its derivative
 // (Toro ch. 4.2-4.3): rarefaction branch for p <= p_K, shock branch above.
-static void prefun(double g, const Side& K, double p, double& f, double& fd) {
+template <class T>
+static void prefun(double g, const Side<T>& K, T p, T& f, T& fd) {
   if (p <= K.p) {  // rarefaction
-    const double prat = p / K.p;
+    const T prat = p / K.p;
     f = 2.0 * K.c / (g - 1.0) * (pow(prat, (g - 1.0) / (2.0 * g)) - 1.0);
     fd = 1.0 / (K.rho * K.c) * pow(prat, -(g + 1.0) / (2.0 * g));
   } else {  // shock
-    const double A = 2.0 / ((g + 1.0) * K.rho);
-    const double B = (g - 1.0) / (g + 1.0) * K.p;
-    const double q = sqrt(A / (B + p));
+    const T A = 2.0 / ((g + 1.0) * K.rho);
+    const T B = (g - 1.0) / (g + 1.0) * K.p;
+    const T q = sqrt(A / (B + p));
     f = (p - K.p) * q;
     fd = (1.0 - 0.5 * (p - K.p) / (B + p)) * q;
   }
 }
 
+template <class T>
 struct RiemannResult {
-  double rho, u, p;   // state at x/t = S
+  T rho, u, p;        // state at x/t = S
   int side;           // -1: left of the contact, +1: right, 0: vacuum
-  double pstar, ustar;
+  T pstar, ustar;
   int iters;
   bool converged, vacuum;
 };
 
-static void fan_left(double g, const Side& L, double S, double& rho, double& u, double& p) {
-  const double c = 2.0 / (g + 1.0) * (L.c + 0.5 * (g - 1.0) * (L.u - S));
+template <class T>
+static void fan_left(double g, const Side<T>& L, double S, T& rho, T& u, T& p) {
+  const T c = 2.0 / (g + 1.0) * (L.c + 0.5 * (g - 1.0) * (L.u - S));
   u = 2.0 / (g + 1.0) * (L.c + 0.5 * (g - 1.0) * L.u + S);
   rho = L.rho * pow(c / L.c, 2.0 / (g - 1.0));
   p = L.p * pow(c / L.c, 2.0 * g / (g - 1.0));
 }
-static void fan_right(double g, const Side& R, double S, double& rho, double& u, double& p) {
-  const double c = 2.0 / (g + 1.0) * (R.c - 0.5 * (g - 1.0) * (R.u - S));
+template <class T>
+static void fan_right(double g, const Side<T>& R, double S, T& rho, T& u, T& p) {
+  const T c = 2.0 / (g + 1.0) * (R.c - 0.5 * (g - 1.0) * (R.u - S));
   u = 2.0 / (g + 1.0) * (-R.c + 0.5 * (g - 1.0) * R.u + S);
   rho = R.rho * pow(c / R.c, 2.0 / (g - 1.0));
   p = R.p * pow(c / R.c, 2.0 * g / (g - 1.0));
 }
 
+// Tangent of the star pressure.  The converged p* is a function of the two
+// states through f_L(p*) + f_R(p*) + u_R - u_L = 0, so by the implicit
+// function theorem dp* = -(df_L + df_R + du_R - du_L) / (f_L' + f_R') at p*,
+// the partials taken with p held fixed; this replaces the tangent carried
+// through the Newton iterates.  A p* held at the floor follows the floor.
+static inline void star_tangent(double, const Side<double>&, const Side<double>&, double, double, double, double&) {}
+static void star_tangent(double g, const Side<Dual>& L, const Side<Dual>& R, Dual ul, Dual ur, Dual floor_p, Dual& p) {
+  if (p.v == floor_p.v) {
+    p.d = floor_p.d;
+    return;
+  }
+  Dual fl, fdl, fr, fdr;
+  const Dual p0(p.v, 0.0);
+  prefun(g, L, p0, fl, fdl);
+  prefun(g, R, p0, fr, fdr);
+  p.d = -(fl.d + fr.d + ur.d - ul.d) / (fdl.v + fdr.v);
+}
+
 // Sect. 2.6 / Toro ch. 4: exact solution of the Riemann problem between the
 // primitive states L and R, sampled at x/t = S.
-static RiemannResult riemann(double g, double rl, double ul, double pl, double rr, double ur, double pr, double S) {
-  RiemannResult out{};
-  const Side L{rl, ul, pl, sqrt(g * pl / rl)};
-  const Side R{rr, ur, pr, sqrt(g * pr / rr)};
+template <class T>
+static RiemannResult<T> riemann(double g, T rl, T ul, T pl, T rr, T ur, T pr, double S) {
+  RiemannResult<T> out{};
+  const Side<T> L{rl, ul, pl, sqrt(g * pl / rl)};
+  const Side<T> R{rr, ur, pr, sqrt(g * pr / rr)};
   if (2.0 / (g - 1.0) * (L.c + R.c) <= R.u - L.u) {  // vacuum generated (Toro 4.6)
     out.vacuum = true;
     out.converged = true;
-    const double sl_star = L.u + 2.0 * L.c / (g - 1.0);
-    const double sr_star = R.u - 2.0 * R.c / (g - 1.0);
-    out.pstar = 0.0;
-    out.ustar = 0.0;
+    const T sl_star = L.u + 2.0 * L.c / (g - 1.0);
+    const T sr_star = R.u - 2.0 * R.c / (g - 1.0);
+    out.pstar = T(0.0);
+    out.ustar = T(0.0);
     if (S <= sl_star) {
       out.side = -1;
       if (S <= L.u - L.c) { out.rho = L.rho; out.u = L.u; out.p = L.p; }
@@ -357,32 +430,33 @@ static RiemannResult riemann(double g, double rl, double ul, double pl, double r
       else fan_right(g, R, S, out.rho, out.u, out.p);
     } else {
       out.side = 0;
-      out.rho = out.u = out.p = 0.0;
+      out.rho = out.u = out.p = T(0.0);
     }
     return out;
   }
   // Newton iteration on the star pressure (reading R9)
-  const double floor_p = 1e-8 * std::min(pl, pr);
-  double p = 0.5 * (pl + pr) - 0.125 * (ur - ul) * (rl + rr) * (L.c + R.c);  // PVRS
+  const T floor_p = 1e-8 * tmin(pl, pr);
+  T p = 0.5 * (pl + pr) - 0.125 * (ur - ul) * (rl + rr) * (L.c + R.c);  // PVRS
   if (p < floor_p) p = floor_p;
-  double fl, fdl, fr, fdr;
+  T fl, fdl, fr, fdr;
   int it = 0;
   bool conv = false;
   for (it = 1; it <= 100; ++it) {
     prefun(g, L, p, fl, fdl);
     prefun(g, R, p, fr, fdr);
-    double pn = p - (fl + fr + ur - ul) / (fdl + fdr);
+    T pn = p - (fl + fr + ur - ul) / (fdl + fdr);
     if (pn < floor_p) pn = floor_p;
-    const double change = 2.0 * fabs(pn - p) / (pn + p);
+    const double change = 2.0 * std::fabs(val(pn) - val(p)) / (val(pn) + val(p));
     p = pn;
     if (change <= 1e-12) {
       conv = true;
       break;
     }
   }
+  star_tangent(g, L, R, ul, ur, floor_p, p);
   prefun(g, L, p, fl, fdl);
   prefun(g, R, p, fr, fdr);
-  const double us = 0.5 * (ul + ur) + 0.5 * (fr - fl);
+  const T us = 0.5 * (ul + ur) + 0.5 * (fr - fl);
   out.pstar = p;
   out.ustar = us;
   out.iters = it;
@@ -391,17 +465,17 @@ static RiemannResult riemann(double g, double rl, double ul, double pl, double r
   if (S <= us) {
     out.side = -1;
     if (p <= pl) {  // left rarefaction
-      const double shl = ul - L.c;
+      const T shl = ul - L.c;
       if (S <= shl) { out.rho = rl; out.u = ul; out.p = pl; }
       else {
-        const double cml = L.c * pow(p / pl, (g - 1.0) / (2.0 * g));
-        const double stl = us - cml;
+        const T cml = L.c * pow(p / pl, (g - 1.0) / (2.0 * g));
+        const T stl = us - cml;
         if (S > stl) { out.rho = rl * pow(p / pl, 1.0 / g); out.u = us; out.p = p; }
         else fan_left(g, L, S, out.rho, out.u, out.p);
       }
     } else {  // left shock
-      const double pml = p / pl;
-      const double sl = ul - L.c * sqrt((g + 1.0) / (2.0 * g) * pml + (g - 1.0) / (2.0 * g));
+      const T pml = p / pl;
+      const T sl = ul - L.c * sqrt((g + 1.0) / (2.0 * g) * pml + (g - 1.0) / (2.0 * g));
       if (S <= sl) { out.rho = rl; out.u = ul; out.p = pl; }
       else {
         const double g6 = (g - 1.0) / (g + 1.0);
@@ -413,8 +487,8 @@ static RiemannResult riemann(double g, double rl, double ul, double pl, double r
   } else {
     out.side = 1;
     if (p > pr) {  // right shock
-      const double pmr = p / pr;
-      const double sr = ur + R.c * sqrt((g + 1.0) / (2.0 * g) * pmr + (g - 1.0) / (2.0 * g));
+      const T pmr = p / pr;
+      const T sr = ur + R.c * sqrt((g + 1.0) / (2.0 * g) * pmr + (g - 1.0) / (2.0 * g));
       if (S >= sr) { out.rho = rr; out.u = ur; out.p = pr; }
       else {
         const double g6 = (g - 1.0) / (g + 1.0);
@@ -423,11 +497,11 @@ static RiemannResult riemann(double g, double rl, double ul, double pl, double r
         out.p = p;
       }
     } else {  // right rarefaction
-      const double shr = ur + R.c;
+      const T shr = ur + R.c;
       if (S >= shr) { out.rho = rr; out.u = ur; out.p = pr; }
       else {
-        const double cmr = R.c * pow(p / pr, (g - 1.0) / (2.0 * g));
-        const double str = us + cmr;
+        const T cmr = R.c * pow(p / pr, (g - 1.0) / (2.0 * g));
+        const T str = us + cmr;
         if (S <= str) { out.rho = rr * pow(p / pr, 1.0 / g); out.u = us; out.p = p; }
         else fan_right(g, R, S, out.rho, out.u, out.p);
       }
@@ -445,23 +519,24 @@ static inline void axes(int ax, int& n, int& t1, int& t2) {
 // Sect. 2.6: flux F(E*) of the exact Riemann solution at the face, from the
 // reconstructed left and right conservative gas states.  Flux components of
 // App. B with the energy flux of reading R3.
-static void gas_flux(Oracle& o, int ax, const double UL[5], const double UR[5], double F[5]) {
+template <class T>
+static void gas_flux(Oracle& o, int ax, const T UL[5], const T UR[5], T F[5]) {
   const double g = o.d.gamma;
   int n, t1, t2;
   axes(ax, n, t1, t2);
-  for (int f = 0; f < 5; ++f) F[f] = 0.0;
-  const double rl = UL[RHO], rr = UR[RHO];
+  for (int f = 0; f < 5; ++f) F[f] = T(0.0);
+  const T rl = UL[RHO], rr = UR[RHO];
   if (!(rl > 0.0) || !(rr > 0.0)) { o.status |= ST_NONPHYSICAL; return; }
-  const double pl = pressure(g, UL), pr = pressure(g, UR);
+  const T pl = pressure(g, UL), pr = pressure(g, UR);
   if (!(pl > 0.0) || !(pr > 0.0)) { o.status |= ST_NONPHYSICAL; return; }
-  const RiemannResult s = riemann(g, rl, UL[n] / rl, pl, rr, UR[n] / rr, pr, 0.0);
+  const RiemannResult<T> s = riemann(g, rl, UL[n] / rl, pl, rr, UR[n] / rr, pr, 0.0);
   o.riemann_calls++;
   o.newton_iters += s.iters;
   if (!s.converged) o.status |= ST_RIEMANN;
-  double ut1 = 0.0, ut2 = 0.0;
+  T ut1 = T(0.0), ut2 = T(0.0);
   if (s.side < 0) { ut1 = UL[t1] / rl; ut2 = UL[t2] / rl; }
   else if (s.side > 0) { ut1 = UR[t1] / rr; ut2 = UR[t2] / rr; }
-  const double m = s.rho * s.u;
+  const T m = s.rho * s.u;
   F[RHO] = m;
   F[n] = m * s.u + s.p;
   F[t1] = m * ut1;
@@ -472,20 +547,21 @@ static void gas_flux(Oracle& o, int ax, const double UL[5], const double UR[5], 
 // Sect. 2.9 / reading R5: kinetic flux-vector splitting of the pressureless
 // dust fluid: what moves right leaves the left state, what moves left leaves
 // the right state.
-static void dust_flux(int ax, const double UL[9], const double UR[9], double F[9]) {
+template <class T>
+static void dust_flux(int ax, const T UL[9], const T UR[9], T F[9]) {
   int n, t1, t2;
   axes(ax, n, t1, t2);
   n += 5; t1 += 5; t2 += 5;
-  const double rl = UL[DRHO], rr = UR[DRHO];
-  double Fs[4] = {0.0, 0.0, 0.0, 0.0};
+  const T rl = UL[DRHO], rr = UR[DRHO];
+  T Fs[4] = {T(0.0), T(0.0), T(0.0), T(0.0)};
   if (rl > 0.0) {
-    const double ul = UL[n] / rl;
-    const double m = rl * (ul > 0.0 ? ul : 0.0);
+    const T ul = UL[n] / rl;
+    const T m = rl * (ul > 0.0 ? ul : T(0.0));
     Fs[0] += m; Fs[1] += m * ul; Fs[2] += m * (UL[t1] / rl); Fs[3] += m * (UL[t2] / rl);
   }
   if (rr > 0.0) {
-    const double ur = UR[n] / rr;
-    const double m = rr * (ur < 0.0 ? ur : 0.0);
+    const T ur = UR[n] / rr;
+    const T m = rr * (ur < 0.0 ? ur : T(0.0));
     Fs[0] += m; Fs[1] += m * ur; Fs[2] += m * (UR[t1] / rr); Fs[3] += m * (UR[t2] / rr);
   }
   F[DRHO] = Fs[0];
@@ -498,43 +574,44 @@ static void dust_flux(int ax, const double UL[9], const double UR[9], double F[9
 // App. B source vector in cylindrical coordinates, with stellar gravity
 // (Sect. 2.1) and the rotating-frame terms of reading R6; per unit volume,
 // at the cell centre.  The Box has no source terms.
-static void sources(const Oracle& o, int i, int k, const double U[9], double S[9]) {
-  for (int f = 0; f < o.nf; ++f) S[f] = 0.0;
+template <class T>
+static void sources(const Oracle& o, int i, int k, const T U[9], T S[9]) {
+  for (int f = 0; f < o.nf; ++f) S[f] = T(0.0);
   if (o.d.geometry != GEOM_CYL) return;
   const double r = XC(o, 0, i), z = XC(o, 2, k);
   const double R2 = r * r + z * z;
-  const double R3 = R2 * sqrt(R2);
+  const double R3 = R2 * std::sqrt(R2);
   const double fr = -o.d.gm * r / R3, fz = -o.d.gm * z / R3;
   const double Om = o.d.omega_frame;
   {
-    const double rho = U[RHO];
-    const double u = U[MU] / rho, v = U[MV] / rho, w = U[MW] / rho;
-    const double P = pressure(o.d.gamma, U);
+    const T rho = U[RHO];
+    const T u = U[MU] / rho, v = U[MV] / rho, w = U[MW] / rho;
+    const T P = pressure(o.d.gamma, U);
     S[MU] = rho * v * v / r + P / r + rho * fr + 2.0 * Om * rho * v + rho * Om * Om * r;
     S[MV] = -rho * u * v / r - 2.0 * Om * rho * u;
     S[MW] = rho * fz;
     S[EN] = rho * u * (fr + Om * Om * r) + rho * w * fz;
-    S[RHO] = 0.0;
+    S[RHO] = T(0.0);
   }
   if (o.nf > 5 && U[DRHO] > 0.0) {
-    const double rho = U[DRHO];
-    const double u = U[DMU] / rho, v = U[DMV] / rho;
+    const T rho = U[DRHO];
+    const T u = U[DMU] / rho, v = U[DMV] / rho;
     S[DMU] = rho * v * v / r + rho * fr + 2.0 * Om * rho * v + rho * Om * Om * r;
     S[DMV] = -rho * u * v / r - 2.0 * Om * rho * u;
     S[DMW] = rho * fz;
-    S[DRHO] = 0.0;
+    S[DRHO] = T(0.0);
   }
 }
 
 // ---------------------------------------------------------------- G(E) per cell
 // Sect. 2.2, Eq. (compact form): G = S V - sum_faces A F.n, for one cell.
-template <class Acc>
-static void G_cell(Oracle& o, const Acc& E, int i, int j, int k, double G[9]) {
+template <class Acc, class T = typename Acc::value_type>
+static void G_cell(Oracle& o, const Acc& E, int i, int j, int k, T G[9]) {
   const Metric m = metric(o, i);
-  for (int f = 0; f < o.nf; ++f) G[f] = 0.0;
+  for (int f = 0; f < o.nf; ++f) G[f] = T(0.0);
   const int cell[3] = {i, j, k};
   for (int ax = 0; ax < 3; ++ax) {
-    double qm_c[9], qp_c[9], qm_m[9], qp_m[9], qm_p[9], qp_p[9];
+    T qm_c[9], qp_c[9], qm_m[9], qp_m[9], qm_p[9], qp_p[9];
     int cm[3] = {i, j, k}, cp[3] = {i, j, k};
     cm[ax] -= 1;
     cp[ax] += 1;
@@ -543,10 +620,11 @@ static void G_cell(Oracle& o, const Acc& E, int i, int j, int k, double G[9]) {
     recon(o, E, ax, cp, qm_p, qp_p);
     const int c = cell[ax];
     for (int side = 0; side < 2; ++side) {
-      const int fc = side == 0 ? c : c + 1;           // face index (lower face of cell fc)
-      const double* ql = side == 0 ? qp_m : qp_c;     // left state of the face
-      const double* qr = side == 0 ? qm_c : qm_p;     // right state of the face
-      double e0[5], UL[9], UR[9], F[9];
+      const int fc = side == 0 ? c : c + 1;        // face index (lower face of cell fc)
+      const T* ql = side == 0 ? qp_m : qp_c;       // left state of the face
+      const T* qr = side == 0 ? qm_c : qm_p;       // right state of the face
+      double e0[5];
+      T UL[9], UR[9], F[9];
       eq_face(o, ax, i, k, fc, e0);
       for (int f = 0; f < 5; ++f) { UL[f] = e0[f] + ql[f]; UR[f] = e0[f] + qr[f]; }
       for (int f = 5; f < o.nf; ++f) { UL[f] = ql[f]; UR[f] = qr[f]; }
@@ -556,7 +634,8 @@ static void G_cell(Oracle& o, const Acc& E, int i, int j, int k, double G[9]) {
       for (int f = 0; f < o.nf; ++f) G[f] += side == 0 ? A * F[f] : -A * F[f];
     }
   }
-  double U[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, S[9];
+  T U[9], S[9];
+  for (int f = 0; f < 9; ++f) U[f] = T(0.0);
   const long lin = ((long)k * o.n[1] + j) * o.n[0] + i;
   for (int f = 0; f < o.nf; ++f) U[f] = E.get(f, lin);
   if (!(U[RHO] > 0.0) || !(pressure(o.d.gamma, U) > 0.0)) o.status |= ST_NONPHYSICAL;
@@ -566,34 +645,37 @@ static void G_cell(Oracle& o, const Acc& E, int i, int j, int k, double G[9]) {
 }
 
 // ---------------------------------------------------------------- drag
-struct DustParams {
-  double stokes;
+template <class T>
+struct DustParamsT {
+  T stokes;
   int drag_law;  // 0: constant Stokes number St = t_s Omega_K(r); 1: Epstein, St fixed at (r=1, z=0)
 };
+using DustParams = DustParamsT<double>;
 // Sect. 2.9 drag law with the semi-implicit integration of reading R7.
-static void drag(const Oracle& o, int i, double U[9], double tau, const DustParams& dp) {
+template <class T>
+static void drag(const Oracle& o, int i, T U[9], double tau, const DustParamsT<T>& dp) {
   if (o.nf < 9) return;
-  const double rg = U[RHO], rd = U[DRHO];
+  const T rg = U[RHO], rd = U[DRHO];
   if (!(rd > 0.0) || !(rg > 0.0)) return;
-  double ts;
+  T ts;
   if (dp.drag_law == 0) {
-    ts = o.d.geometry == GEOM_CYL ? dp.stokes / sqrt(o.d.gm / pow(XC(o, 0, i), 3)) : dp.stokes;
+    ts = o.d.geometry == GEOM_CYL ? dp.stokes / std::sqrt(o.d.gm / std::pow(XC(o, 0, i), 3)) : dp.stokes;
   } else {
     // Epstein t_s = rho_s r_p / (rho_g c_s), with rho_s r_p fixed so that St holds at r = 1, z = 0
     double rho1, vth1, p1;
     eq_prim(o, 1.0, 0.0, rho1, vth1, p1);
-    const double rhos_rp = dp.stokes * rho1 * sqrt(o.d.gamma * p1 / rho1) / sqrt(o.d.gm);
-    const double cs = sqrt(o.d.gamma * pressure(o.d.gamma, U) / rg);
+    const T rhos_rp = dp.stokes * rho1 * std::sqrt(o.d.gamma * p1 / rho1) / std::sqrt(o.d.gm);
+    const T cs = sqrt(o.d.gamma * pressure(o.d.gamma, U) / rg);
     ts = rhos_rp / (rg * cs);
   }
-  const double eps = rd / rg;
-  const double kk = tau * (1.0 + eps) / ts;
-  const double mu = rg * rd / (rg + rd);
-  double dE = 0.0;
+  const T eps = rd / rg;
+  const T kk = tau * (1.0 + eps) / ts;
+  const T mu = rg * rd / (rg + rd);
+  T dE = T(0.0);
   for (int c = 0; c < 3; ++c) {
-    const double vg_ex = U[MU + c] / rg;
-    const double vd_ex = U[DMU + c] / rd;
-    const double X = mu * (vd_ex - vg_ex) * (kk / (1.0 + kk));
+    const T vg_ex = U[MU + c] / rg;
+    const T vd_ex = U[DMU + c] / rd;
+    const T X = mu * (vd_ex - vg_ex) * (kk / (1.0 + kk));
     U[MU + c] += X;
     U[DMU + c] -= X;
     dE += 0.5 * X * (U[MU + c] / rg + vg_ex);
@@ -602,13 +684,13 @@ static void drag(const Oracle& o, int i, double U[9], double tau, const DustPara
 }
 
 // One RK stage at one cell: Eout = Ebase + tau G(Ein)/V, then drag (Sect. 2.5).
-template <class Acc>
-static void stage_cell(Oracle& o, const Acc& Ein, const double* Ebase, long lin, double tau, const DustParams& dp,
-                       double out[9]) {
+template <class Acc, class T = typename Acc::value_type>
+static void stage_cell(Oracle& o, const Acc& Ein, const T* Ebase, long lin, double tau, const DustParamsT<T>& dp,
+                       T out[9]) {
   const int i = (int)(lin % o.n[0]);
   const int j = (int)((lin / o.n[0]) % o.n[1]);
   const int k = (int)(lin / ((long)o.n[0] * o.n[1]));
-  double G[9];
+  T G[9];
   G_cell(o, Ein, i, j, k, G);
   if (!o.r0.empty())
     for (int f = 0; f < o.nf; ++f) G[f] -= o.r0[(size_t)f * o.ncell + lin];  // Sect. 2.8 balanced scheme
@@ -617,10 +699,10 @@ static void stage_cell(Oracle& o, const Acc& Ein, const double* Ebase, long lin,
   drag(o, i, out, tau, dp);
 }
 
-static void stage_all(Oracle& o, const double* Ein, const double* Ebase, double* Eout, double tau,
-                      const DustParams& dp) {
-  const ArrAcc A{Ein, o.ncell};
-  double out[9];
+template <class T>
+static void stage_all(Oracle& o, const T* Ein, const T* Ebase, T* Eout, double tau, const DustParamsT<T>& dp) {
+  const ArrAccT<T> A{Ein, o.ncell};
+  T out[9];
   for (long lin = 0; lin < o.ncell; ++lin) {
     stage_cell(o, A, Ebase, lin, tau, dp, out);
     for (int f = 0; f < o.nf; ++f) Eout[(size_t)f * o.ncell + lin] = out[f];
@@ -629,6 +711,7 @@ static void stage_all(Oracle& o, const double* Ein, const double* Ebase, double*
 
 // Stage-1 state E* evaluated lazily, one cell at a time, for sampled checks.
 struct LazyStageAcc {
+  using value_type = double;
   Oracle* o;
   const double* En;
   double tau;
@@ -796,6 +879,27 @@ int orc_step(void* h, double* E, double dt, double stokes, int law) {
   stage_all(o, E, E, Es.data(), 0.5 * dt, dp);
   stage_all(o, Es.data(), E, En.data(), dt, dp);
   std::memcpy(E, En.data(), sizeof(double) * En.size());
+  const int st = o.status;
+  o.status = 0;
+  return st;
+}
+
+// Tangent-linear step: E^{n+1} and its directional derivative dE^{n+1} along
+// the direction (dE^n, dSt) in state and Stokes number, at a fixed dt; every
+// branch (limiter, Riemann wave pattern, sampling, positivity) is the one the
+// values take.  E and dE are updated in place.
+int orc_step_tlm(void* h, double* E, double* dE, double dt, double stokes, double dstokes, int law) {
+  Oracle& o = *(Oracle*)h;
+  const DustParamsT<Dual> dp{Dual(stokes, dstokes), law};
+  const size_t n = (size_t)o.nf * o.ncell;
+  std::vector<Dual> X(n), Es(n), En(n);
+  for (size_t q = 0; q < n; ++q) X[q] = Dual(E[q], dE[q]);
+  stage_all(o, X.data(), X.data(), Es.data(), 0.5 * dt, dp);
+  stage_all(o, Es.data(), X.data(), En.data(), dt, dp);
+  for (size_t q = 0; q < n; ++q) {
+    E[q] = En[q].v;
+    dE[q] = En[q].d;
+  }
   const int st = o.status;
   o.status = 0;
   return st;
