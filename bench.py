@@ -237,6 +237,57 @@ def measure_fp64(R, W, w, torch, steps=2, warmup=3):
             "dtype": "f64"}
 
 
+def measure_adjoint(R, W, syn, torch, steps=4, warmup=3):
+    """Cost of the FP64 discrete adjoint on the adjoint workload (128x256x32,
+    bi-fluid): one rossbi_adjoint_step (forward recompute of the step included)
+    over one rossbi_step, both timed with CUDA events on the grid's stream; and
+    a whole gradient (forward run with checkpoints + backward sweep) over the
+    forward run, for 20 steps with checkpoints every 10."""
+    from paper_2207_04252_gb300 import adjoint as adj
+    w = syn.ADJOINT
+    stream = torch.cuda.current_stream()
+    g = W.Grid(w, precision=R.ROSSBI_FP64, stream=stream)
+    s = g.initial_state()
+    dt = g.cfl_dt(s)
+    lam = adj.vortex_core_weights(g).cuda().contiguous()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    fwd_state = s.clone()
+    t_fwd = timed(lambda: g.step(fwd_state, dt=dt))
+    t_adj = timed(lambda: g.adjoint_step(s, dt, lam))
+    # whole gradient through 20 steps
+    dts = [dt] * 20
+    x = s.clone()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    y = s.clone()
+    for d in dts:
+        g.step(y, dt=d)
+    torch.cuda.synchronize()
+    t_run = time.perf_counter() - t0
+    x.requires_grad_(True)
+    t0 = time.perf_counter()
+    out = adj.run_steps(g, x, dts, every=10)
+    (lam * out).sum().backward()
+    torch.cuda.synchronize()
+    t_grad = time.perf_counter() - t0
+    status = g.take_status()
+    g.close()
+    return {"workload": w.name, "forward_step_ms": t_fwd, "adjoint_step_ms": t_adj, "ratio": t_adj / t_fwd,
+            "gradient_20_steps_over_forward_run": t_grad / t_run, "status": R.status_string(status)}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -337,6 +388,10 @@ def run_ours(args):
             line["fp32_over_fp64"] = value / world / fp64["value"]
             line["fp32_error_vs_fp64"] = fp32_error_vs_fp64(R, workloads, syn, torch)
         line["adjoint_over_forward"] = None
+        if not args.no_extras:
+            a = measure_adjoint(R, workloads, syn, torch)
+            line["adjoint"] = a
+            line["adjoint_over_forward"] = a["ratio"]
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(line), flush=True)

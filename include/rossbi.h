@@ -172,6 +172,38 @@ rossbi_status rossbi_step_host(rossbi_grid* g, void* const* host_state, double d
 rossbi_status rossbi_step_noalloc(rossbi_grid* g, void* const* state, double dt, const rossbi_dust_params* dust,
                                   double* next_dt);
 
+/* Discrete adjoint of one rossbi_step at a fixed step length dt (FP64 form
+ * only).  The paper has no adjoint; this is the exact transpose of the
+ * linearised step map E^n -> E^{n+1} of Sect. 2.5: every branch (MinMod
+ * limiter, Riemann wave pattern and sampling of Sect. 2.6, dust upwinding,
+ * positivity fallback) is held where the forward values put it, and the star
+ * pressure's derivative is dp* = -(df_L + df_R + du_R - du_L) / (f_L' + f_R')
+ * at the converged p* (implicit function theorem).  The CFL choice of dt is
+ * not differentiated: dt is an input.
+ *   state_n : nfields device pointers holding E^n (read only); the call
+ *             recomputes E*, the pre-drag stage states and E^{n+1} from it.
+ *   dt      : > 0, the step that took E^n to E^{n+1}.
+ *   dust    : drag parameters (required when n_dust = 1).
+ *   lam_np1 : nfields device pointers, the cotangent of E^{n+1} (FP64).
+ *   lam_n   : nfields device pointers receiving the cotangent of E^n; may
+ *             be the same buffers as lam_np1 (in place).
+ *   dparam  : if not NULL, receives += lam_np1 . dE^{n+1}/dSt (the Stokes
+ *             number of dust), and the call synchronises and reports the
+ *             status word.  The same value is always added to a device-side
+ *             running total (rossbi_adjoint_dstokes), so callers can leave
+ *             dparam NULL and keep the call asynchronous.
+ * The library allocates five FP64 states of scratch on the first call.
+ * Errors: ROSSBI_ERR_ARG, ROSSBI_ERR_UNSUPPORTED (perturbation forms),
+ * ROSSBI_ERR_OOM, ROSSBI_ERR_CUDA, and after a synchronising call
+ * ROSSBI_ERR_NONPHYSICAL / ROSSBI_ERR_RIEMANN. */
+rossbi_status rossbi_adjoint_step(rossbi_grid* g, const void* const* state_n, double dt,
+                                  const rossbi_dust_params* dust, const void* const* lam_np1, void* const* lam_n,
+                                  double* dparam);
+
+/* Running total of the d/dSt terms of every rossbi_adjoint_step on this grid;
+ * reset != 0 sets it back to zero after reading.  Synchronises the stream. */
+rossbi_status rossbi_adjoint_dstokes(rossbi_grid* g, double* total, int reset);
+
 /* FP64 conservation sums sum_cells V * E_f of the FULL conservative fields
  * (E0 + E' in the perturbation forms), in a fixed reduction order (so the
  * result is deterministic).  sums: host array of nfields doubles.

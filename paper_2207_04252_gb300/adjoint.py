@@ -1,0 +1,100 @@
+"""Gradients through many steps: the checkpointed discrete adjoint behind torch.autograd.
+
+``run_steps(grid, E0, dts, stokes)`` advances an FP64 state through
+len(dts) steps of the given lengths (a frozen CFL sequence) and is
+differentiable in the initial state and the Stokes number.  The forward pass
+keeps a copy of the state every ``every`` steps (revolve-style checkpoints);
+the backward pass walks the segments from the last one, recomputes each
+segment's states from its checkpoint and runs ``rossbi_adjoint_step`` back
+through them.  Memory: ceil(K / every) + every states; extra work: one
+forward run.
+
+``vortex_core_weights`` builds dJ/dE for the objective "dust mass inside the
+vortex core", J = sum over cells with ((r - r_v) / s_r)^2 + (r_v dtheta / s_t)^2
+<= 1 (all z) of V rho_d, so that J = (weights * E).sum().
+"""
+import math
+
+import numpy as np
+import torch
+
+import synthetic as syn
+
+from . import rossbi as R
+
+
+class _Steps(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, E0, stokes, grid, dts, every):
+        if grid.precision != R.ROSSBI_FP64:
+            raise R.RossbiError(R.ROSSBI_ERR_UNSUPPORTED, "run_steps (the adjoint is FP64 only)")
+        law = grid.dust[1] if grid.dust else 0
+        grid.dust = (float(stokes), law) if grid.dust else None
+        E = E0.detach().clone().contiguous()
+        ckpts = []
+        for n, dt in enumerate(dts):
+            if n % every == 0:
+                ckpts.append(E.clone())
+            grid.step(E, dt=dt)
+        ctx.grid, ctx.dts, ctx.every, ctx.ckpts = grid, list(dts), every, ckpts
+        return E
+
+    @staticmethod
+    def backward(ctx, lam_out):
+        grid, dts, every = ctx.grid, ctx.dts, ctx.every
+        lam = lam_out.detach().to(torch.float64).clone().contiguous()
+        R.rossbi_adjoint_dstokes(grid.h, reset=True)
+        K = len(dts)
+        for s in reversed(range(len(ctx.ckpts))):
+            start, end = s * every, min((s + 1) * every, K)
+            states = [ctx.ckpts[s]]
+            for n in range(start, end - 1):
+                E = states[-1].clone()
+                grid.step(E, dt=dts[n])
+                states.append(E)
+            for n in reversed(range(start, end)):
+                grid.adjoint_step(states[n - start], dts[n], lam)
+        dst = R.rossbi_adjoint_dstokes(grid.h, reset=True) if grid.dust else 0.0
+        ctx.ckpts = None
+        return lam, torch.tensor(dst, dtype=torch.float64), None, None, None
+
+
+def run_steps(grid, E0, dts, stokes=None, every=20):
+    """E^K from E^0 (FP64 tensor (nf, nz, nth, nr) on the device) through the
+    steps dts; differentiable in E0 and in `stokes` (a 0-d float64 tensor;
+    default: the workload's Stokes number, not tracked)."""
+    if stokes is None:
+        stokes = torch.tensor(grid.w.stokes, dtype=torch.float64)
+    return _Steps.apply(E0, stokes, grid, list(dts), int(every))
+
+
+def cfl_sequence(grid, E0, steps):
+    """The CFL step lengths of a plain forward run of `steps` steps from E0."""
+    E = E0.clone()
+    dt = grid.cfl_dt(E)
+    dts = []
+    for _ in range(steps):
+        dts.append(dt)
+        dt = grid.step(E, dt=dt, want_next_dt=True)
+    return dts
+
+
+def vortex_core_weights(grid, vortex=0):
+    """dJ/dE of J = dust mass inside the core ellipse of a vortex (all z)."""
+    w = grid.w
+    rv, thv = w.vortices[vortex]
+    sigma0, beta_sigma, T0, beta_T = w.disc
+    omk = math.sqrt(w.gm / rv ** 3)
+    s_r = w.vortex_width_h * math.sqrt(2.0 * T0 * rv ** beta_T) / omk
+    s_t = w.vortex_chi * s_r
+    r = grid.centres(0)[None, :]
+    th = grid.centres(1)[:, None]
+    dth = np.mod(th - thv + math.pi, 2.0 * math.pi) - math.pi
+    inside = ((r - rv) / s_r) ** 2 + (rv * dth / s_t) ** 2 <= 1.0
+    f = w.x0[0] * (w.x1[0] / w.x0[0]) ** (np.arange(w.nr + 1) / w.nr)
+    dth_c = (w.x1[1] - w.x0[1]) / w.nth
+    dz = (w.x1[2] - w.x0[2]) / w.nz
+    V = 0.5 * (f[1:] ** 2 - f[:-1] ** 2) * dth_c * dz
+    W = np.zeros(grid.shape)
+    W[syn.F_DRHO] = (inside * V[None, :])[None, :, :]
+    return torch.from_numpy(W)

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/rossbi.h"
+#include "adjoint.cuh"
 #include "stage_pert.cuh"
 
 using namespace rossbi;
@@ -59,6 +60,11 @@ struct rossbi_grid {
   PertTables<double> pt_d{};
   unsigned long long* d_fallbacks = nullptr;
   double eq_sums[5] = {0, 0, 0, 0, 0}; // sum_cells V E0_f (FP64)
+  // adjoint: five FP64 states (Y1, E*, Y2, mu', cotangent of E*), d/dSt partials and slots
+  double* d_adj = nullptr;
+  double* d_adj_part = nullptr;
+  double* d_adj_slots = nullptr;       // [0] this call's d/dSt, [1] running total
+  int adj_blocks = 0;
   // stage-kernel timing (rossbi_profile_*)
   bool profiling = false;
   std::vector<cudaEvent_t> ev;         // start/stop pairs
@@ -512,6 +518,26 @@ PertArgs<T> pert_args(rossbi_grid* g) {
   return a;
 }
 
+// Drag parameters of a step (Sect. 2.9 drag law; Epstein constant fixed so
+// that the Stokes number holds at r = 1, z = 0).
+rossbi_status drag_args(rossbi_grid* g, const rossbi_dust_params* dust, DragArgs& drag) {
+  drag = DragArgs{0.0, 0.0, 0};
+  if (g->nf == 9) {
+    drag.stokes = dust->stokes;
+    drag.law = dust->drag_law;
+    if (!(dust->stokes > 0.0)) return ROSSBI_ERR_ARG;
+    if (dust->drag_law == 1) {
+      if (!g->has_disc) return ROSSBI_ERR_ARG;
+      double rho1, vth1, p1;
+      equilibrium_prim(g->desc, g->disc, 1.0, 0.0, rho1, vth1, p1);
+      drag.rhos_rp = dust->stokes * rho1 * std::sqrt(g->desc.gamma * p1 / rho1) / std::sqrt(g->desc.gm);
+    } else if (dust->drag_law != 0) {
+      return ROSSBI_ERR_ARG;
+    }
+  }
+  return ROSSBI_OK;
+}
+
 rossbi_status prepare_step(rossbi_grid* g, void* const* state, void* const* scratch, double dt,
                            const rossbi_dust_params* dust, void** sc, DragArgs& drag) {
   if (!g->eq_set) return ROSSBI_ERR_ARG;
@@ -533,21 +559,7 @@ rossbi_status prepare_step(rossbi_grid* g, void* const* state, void* const* scra
   }
   rossbi_status st = ensure_partials(g, n_tiles(g));
   if (st != ROSSBI_OK) return st;
-  drag = DragArgs{0.0, 0.0, 0};
-  if (g->nf == 9) {
-    drag.stokes = dust->stokes;
-    drag.law = dust->drag_law;
-    if (!(dust->stokes > 0.0)) return ROSSBI_ERR_ARG;
-    if (dust->drag_law == 1) {
-      if (!g->has_disc) return ROSSBI_ERR_ARG;
-      double rho1, vth1, p1;
-      equilibrium_prim(g->desc, g->disc, 1.0, 0.0, rho1, vth1, p1);
-      drag.rhos_rp = dust->stokes * rho1 * std::sqrt(g->desc.gamma * p1 / rho1) / std::sqrt(g->desc.gm);
-    } else if (dust->drag_law != 0) {
-      return ROSSBI_ERR_ARG;
-    }
-  }
-  return ROSSBI_OK;
+  return drag_args(g, dust, drag);
 }
 
 rossbi_status finish_step(rossbi_grid* g, int nxt, double* next_dt) {
@@ -628,6 +640,158 @@ rossbi_status step_pert(rossbi_grid* g, void* const* state, void* const* sc, dou
   return finish_step(g, nxt, next_dt);
 }
 
+// ---------------------------------------------------------------- adjoint
+constexpr int ADJ_L = 16, ADJ_NL = 16;  // lines of 16 lanes (12 owned cells), 16 lines per block
+
+template <int NF, int D>
+rossbi_status launch_adj_flux(rossbi_grid* g, const AdjFluxArgs& a) {
+  constexpr size_t smem = adj_flux_smem_doubles<NF, ADJ_L, ADJ_NL>() * sizeof(double);
+  constexpr int T = ADJ_L - 4;
+  auto kern = adj_flux_kernel<NF, D, ADJ_L, ADJ_NL>;
+  static bool attr = false;
+  if (!attr) {
+    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  const rossbi_grid_desc& d = g->desc;
+  const long nd = D == 0 ? d.nr : (D == 1 ? d.nth : d.nz);
+  const long nlines = D == 0 ? (long)d.nth * d.nz : (D == 1 ? (long)d.nr * d.nz : (long)d.nr * d.nth);
+  const long nblocks = ((nd + T - 1) / T) * ((nlines + ADJ_NL - 1) / ADJ_NL);
+  kern<<<(unsigned)nblocks, ADJ_L * ADJ_NL, smem, g->stream>>>(a);
+  CK(cudaGetLastError());
+  return ROSSBI_OK;
+}
+
+template <int NF>
+rossbi_status adjoint_reverse(rossbi_grid* g, void* const* state, double dt, const DragArgs& drag,
+                              const void* const* lam_np1, void* const* lam_n, double* const* Y1, double* const* Es,
+                              double* const* Y2, double* const* Mu, double* const* LamS) {
+  const int nb = g->adj_blocks;
+  AdjPointArgs p;
+  std::memset(&p, 0, sizeof(p));
+  p.g = g->dg;
+  p.drag = drag;
+  AdjFluxArgs fa;
+  std::memset(&fa, 0, sizeof(fa));
+  fa.g = g->dg;
+  fa.status = g->d_status;
+  // stage 2: E^{n+1} = D(Y2), Y2 = E^n + dt (G(E*) - R0) / V
+  for (int f = 0; f < NF; ++f) {
+    p.Y[f] = Y2[f];
+    p.lout[f] = (const double*)lam_np1[f];
+    p.Ein[f] = Es[f];
+    p.M[f] = Mu[f];
+    p.lam_n[f] = (double*)lam_n[f];
+    p.lam_in[f] = LamS[f];
+    fa.E[f] = Es[f];
+    fa.M[f] = Mu[f];
+    fa.lam[f] = LamS[f];
+  }
+  p.tau = dt;
+  p.stage2 = 1;
+  p.partials = g->d_adj_part;
+  adj_point_kernel<NF><<<nb, ADJ_PT_NT, 0, g->stream>>>(p);
+  CK(cudaGetLastError());
+  rossbi_status st = launch_adj_flux<NF, 0>(g, fa);
+  if (st == ROSSBI_OK) st = launch_adj_flux<NF, 1>(g, fa);
+  if (st == ROSSBI_OK) st = launch_adj_flux<NF, 2>(g, fa);
+  if (st != ROSSBI_OK) return st;
+  // stage 1: E* = D(Y1), Y1 = E^n + dt/2 (G(E^n) - R0) / V
+  for (int f = 0; f < NF; ++f) {
+    p.Y[f] = Y1[f];
+    p.lout[f] = LamS[f];
+    p.Ein[f] = (const double*)state[f];
+    fa.E[f] = (const double*)state[f];
+    fa.lam[f] = (double*)lam_n[f];
+  }
+  p.tau = 0.5 * dt;
+  p.stage2 = 0;
+  p.partials = g->d_adj_part + nb;
+  adj_point_kernel<NF><<<nb, ADJ_PT_NT, 0, g->stream>>>(p);
+  CK(cudaGetLastError());
+  st = launch_adj_flux<NF, 0>(g, fa);
+  if (st == ROSSBI_OK) st = launch_adj_flux<NF, 1>(g, fa);
+  if (st == ROSSBI_OK) st = launch_adj_flux<NF, 2>(g, fa);
+  if (st != ROSSBI_OK) return st;
+  adj_dst_reduce_kernel<<<1, 512, 0, g->stream>>>(g->d_adj_part, 2 * nb, g->d_adj_slots);
+  CK(cudaGetLastError());
+  return ROSSBI_OK;
+}
+
+rossbi_status adjoint_step(rossbi_grid* g, void* const* state, double dt, const rossbi_dust_params* dust,
+                           const void* const* lam_np1, void* const* lam_n, double* dparam) {
+  if (!g->eq_set || !state || !lam_np1 || !lam_n) return ROSSBI_ERR_ARG;
+  if (g->desc.precision != ROSSBI_FP64) return ROSSBI_ERR_UNSUPPORTED;
+  if (!(dt > 0.0) || !std::isfinite(dt)) return ROSSBI_ERR_ARG;
+  for (int f = 0; f < g->nf; ++f)
+    if (!state[f] || !lam_np1[f] || !lam_n[f]) return ROSSBI_ERR_ARG;
+  if (g->nf == 9 && !dust) return ROSSBI_ERR_ARG;
+  DragArgs drag;
+  rossbi_status st = drag_args(g, dust, drag);
+  if (st != ROSSBI_OK) return st;
+  const size_t nfc = (size_t)g->nf * g->ncell;
+  if (!g->d_adj) {
+    g->adj_blocks = (int)std::min<size_t>((g->ncell + ADJ_PT_NT - 1) / ADJ_PT_NT, 2048);
+    CK(cudaMalloc(&g->d_adj, 5 * nfc * sizeof(double)));
+    CK(cudaMalloc(&g->d_adj_part, 2 * (size_t)g->adj_blocks * sizeof(double)));
+    CK(cudaMalloc(&g->d_adj_slots, 2 * sizeof(double)));
+    CK(cudaMemsetAsync(g->d_adj_slots, 0, 2 * sizeof(double), g->stream));
+  }
+  double *Y1[9], *Es[9], *Y2[9], *Mu[9], *LamS[9];
+  for (int f = 0; f < g->nf; ++f) {
+    Y1[f] = g->d_adj + f * g->ncell;
+    Es[f] = g->d_adj + nfc + f * g->ncell;
+    Y2[f] = g->d_adj + 2 * nfc + f * g->ncell;
+    Mu[f] = g->d_adj + 3 * nfc + f * g->ncell;
+    LamS[f] = g->d_adj + 4 * nfc + f * g->ncell;
+  }
+  // forward recompute from E^n: the stage kernels with the drag switched off
+  // (t_s = infinity makes apply_drag the identity) give the pre-drag states
+  const int nblocks = n_tiles(g);
+  StageArgs a = base_args(g);
+  a.drag = drag;
+  a.drag.stokes = INFINITY;
+  a.drag.rhos_rp = INFINITY;
+  a.dt_host = dt;
+  for (int f = 0; f < g->nf; ++f) {
+    a.in[f] = (const double*)state[f];
+    a.base[f] = (const double*)state[f];
+    a.out[f] = Y1[f];
+  }
+  a.tau_frac = 0.5;
+  st = launch_stage(g, a, nblocks);
+  if (st != ROSSBI_OK) return st;
+  double* const* Estar = Y1;
+  if (g->nf == 9) {
+    Fields9 y, o;
+    for (int f = 0; f < 9; ++f) {
+      y.p[f] = Y1[f];
+      o.p[f] = Es[f];
+    }
+    drag_only_kernel<<<g->adj_blocks, ADJ_PT_NT, 0, g->stream>>>(g->dg, y, o, 0.5 * dt, drag);
+    CK(cudaGetLastError());
+    Estar = Es;
+  }
+  for (int f = 0; f < g->nf; ++f) {
+    a.in[f] = Estar[f];
+    a.base[f] = (const double*)state[f];
+    a.out[f] = Y2[f];
+  }
+  a.tau_frac = 1.0;
+  st = launch_stage(g, a, nblocks);
+  if (st != ROSSBI_OK) return st;
+  st = g->nf == 9 ? adjoint_reverse<9>(g, state, dt, drag, lam_np1, lam_n, Y1, Estar, Y2, Mu, LamS)
+                  : adjoint_reverse<5>(g, state, dt, drag, lam_np1, lam_n, Y1, Estar, Y2, Mu, LamS);
+  if (st != ROSSBI_OK) return st;
+  if (dparam) {
+    CK(cudaMemcpyAsync(g->h_pinned, g->d_adj_slots, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    st = sync_and_status(g);
+    *dparam += g->h_pinned[0];
+    return st;
+  }
+  return ROSSBI_OK;
+}
+
 rossbi_status step_device(rossbi_grid* g, void* const* state, void* const* scratch, double dt,
                           const rossbi_dust_params* dust, double* next_dt) {
   void* sc[9];
@@ -673,6 +837,9 @@ void rossbi_destroy(rossbi_grid* g) {
   if (g->d_hoststate) cudaFree(g->d_hoststate);
   if (g->d_ptab) cudaFree(g->d_ptab);
   if (g->d_fallbacks) cudaFree(g->d_fallbacks);
+  if (g->d_adj) cudaFree(g->d_adj);
+  if (g->d_adj_part) cudaFree(g->d_adj_part);
+  if (g->d_adj_slots) cudaFree(g->d_adj_slots);
   if (g->h_pinned) cudaFreeHost(g->h_pinned);
   for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
   delete g;
@@ -970,6 +1137,27 @@ rossbi_status rossbi_profile_read(rossbi_grid* g, double* stage_ms, int* stage_l
   g->prof_ms = 0.0;
   g->prof_launches = 0;
   return ROSSBI_OK;
+}
+
+rossbi_status rossbi_adjoint_step(rossbi_grid* g, const void* const* state_n, double dt,
+                                  const rossbi_dust_params* dust, const void* const* lam_np1, void* const* lam_n,
+                                  double* dparam) {
+  if (!g) return ROSSBI_ERR_ARG;
+  return adjoint_step(g, (void* const*)state_n, dt, dust, lam_np1, lam_n, dparam);
+}
+
+rossbi_status rossbi_adjoint_dstokes(rossbi_grid* g, double* total, int reset) {
+  if (!g || !total) return ROSSBI_ERR_ARG;
+  *total = 0.0;
+  if (!g->d_adj_slots) return ROSSBI_OK;
+  CK(cudaMemcpyAsync(g->h_pinned, g->d_adj_slots + 1, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+  const rossbi_status st = sync_and_status(g);
+  *total = g->h_pinned[0];
+  if (reset) {
+    CK(cudaMemsetAsync(g->d_adj_slots, 0, 2 * sizeof(double), g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+  }
+  return st;
 }
 
 rossbi_status rossbi_take_status(rossbi_grid* g) {

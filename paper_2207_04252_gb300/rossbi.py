@@ -26,8 +26,8 @@ ROSSBI_FP64, ROSSBI_FP32_PERT, ROSSBI_FP64_PERT = 0, 1, 2
 # every function declared in include/rossbi.h
 EXPORTS = (
     "rossbi_init_grid", "rossbi_set_equilibrium", "rossbi_get_equilibrium", "rossbi_cfl_dt", "rossbi_step",
-    "rossbi_step_host", "rossbi_step_noalloc", "rossbi_conservation_sums", "rossbi_fallback_count", "rossbi_take_status",
-    "rossbi_profile_enable",
+    "rossbi_step_host", "rossbi_step_noalloc", "rossbi_adjoint_step", "rossbi_adjoint_dstokes",
+    "rossbi_conservation_sums", "rossbi_fallback_count", "rossbi_take_status", "rossbi_profile_enable",
     "rossbi_profile_read", "rossbi_nfields", "rossbi_precision", "rossbi_destroy", "rossbi_status_string",
 )
 
@@ -76,6 +76,8 @@ def load(path: str = LIB_PATH):
     L.rossbi_step.argtypes = [_VP, _PP, _PP, ctypes.c_double, ctypes.POINTER(rossbi_dust_params), _DP]
     L.rossbi_step_host.argtypes = [_VP, _PP, ctypes.c_double, ctypes.POINTER(rossbi_dust_params), _DP]
     L.rossbi_step_noalloc.argtypes = [_VP, _PP, ctypes.c_double, ctypes.POINTER(rossbi_dust_params), _DP]
+    L.rossbi_adjoint_step.argtypes = [_VP, _PP, ctypes.c_double, ctypes.POINTER(rossbi_dust_params), _PP, _PP, _DP]
+    L.rossbi_adjoint_dstokes.argtypes = [_VP, _DP, ctypes.c_int]
     L.rossbi_conservation_sums.argtypes = [_VP, _PP, _DP]
     L.rossbi_take_status.argtypes = [_VP]
     L.rossbi_fallback_count.argtypes = [_VP, ctypes.POINTER(ctypes.c_ulonglong)]
@@ -181,6 +183,27 @@ def rossbi_step_noalloc(grid, state, dt=0.0, dust=None, want_next_dt=False):
     _check(load().rossbi_step_noalloc(grid, _fields(state, nf), float(dt), d,
                                       ctypes.byref(nd) if want_next_dt else None), "rossbi_step_noalloc")
     return nd.value if want_next_dt else None
+
+
+def rossbi_adjoint_step(grid, state, dt, dust, lam_np1, lam_n, want_dstokes=False):
+    """Cotangent of E^n from the cotangent of E^{n+1} for one FP64 step of length dt
+    (lam_n may be lam_np1).  Returns this step's lambda . dE^{n+1}/dSt if
+    want_dstokes (the call then synchronises), else None; the library also keeps
+    a running total (rossbi_adjoint_dstokes)."""
+    nf = rossbi_nfields(grid)
+    d = None if dust is None else ctypes.byref(rossbi_dust_params(*dust))
+    v = ctypes.c_double(0.0)
+    _check(load().rossbi_adjoint_step(grid, _fields(state, nf), float(dt), d, _fields(lam_np1, nf),
+                                      _fields(lam_n, nf), ctypes.byref(v) if want_dstokes else None),
+           "rossbi_adjoint_step")
+    return v.value if want_dstokes else None
+
+
+def rossbi_adjoint_dstokes(grid, reset=False) -> float:
+    """Running total of d/dSt over the adjoint steps since the last reset."""
+    v = ctypes.c_double()
+    _check(load().rossbi_adjoint_dstokes(grid, ctypes.byref(v), int(bool(reset))), "rossbi_adjoint_dstokes")
+    return v.value
 
 
 def rossbi_step_host(grid, host_state, dt=0.0, dust=None):

@@ -59,6 +59,11 @@ class Grid:
     def step(self, state, dt=0.0, scratch=None, want_next_dt=False):
         return R.rossbi_step(self.h, state, scratch, dt, self.dust, want_next_dt)
 
+    def adjoint_step(self, state, dt, lam_np1, lam_n=None, want_dstokes=False):
+        """Cotangent of E^n from that of E^{n+1} (in place when lam_n is None)."""
+        return R.rossbi_adjoint_step(self.h, state, dt, self.dust, lam_np1, lam_np1 if lam_n is None else lam_n,
+                                     want_dstokes)
+
     def cfl_dt(self, state):
         return R.rossbi_cfl_dt(self.h, state)
 
@@ -82,6 +87,56 @@ class Grid:
         return w.x0[ax] + (np.arange(n) + 0.5) * (w.x1[ax] - w.x0[ax]) / n
 
     # ---- inputs
+    def _vortex_velocity(self, amp):
+        """Velocity perturbation (u', v') of the vortex recipe, (1, nth, nr) each; linear in amp."""
+        w = self.w
+        r = self.centres(0)[None, None, :]
+        th = self.centres(1)[None, :, None]
+        sigma0, beta_sigma, T0, beta_T = w.disc
+        up = np.zeros((1, w.nth, w.nr))
+        vp = np.zeros((1, w.nth, w.nr))
+        for rv, thv in w.vortices:
+            omk = math.sqrt(w.gm / rv ** 3)
+            s_r = w.vortex_width_h * math.sqrt(2.0 * T0 * rv ** beta_T) / omk
+            s_t = w.vortex_chi * s_r
+            psi0 = -amp * 1.5 * omk / (1.0 / s_r ** 2 + 1.0 / s_t ** 2)
+            dth = np.mod(th - thv + math.pi, 2.0 * math.pi) - math.pi
+            psi = psi0 * np.exp(-(r - rv) ** 2 / (2.0 * s_r ** 2) - (rv * dth) ** 2 / (2.0 * s_t ** 2))
+            up = up - psi * rv * rv * dth / (r * s_t ** 2)
+            vp = vp + psi * (r - rv) / s_r ** 2
+        return up, vp
+
+    def vortex_amp_tangent(self) -> np.ndarray:
+        """dE/d(vortex amplitude) of the initial state, (nf, nz, nth, nr), float64."""
+        w = self.w
+        assert w.ic == "vortex"
+        E0 = self.equilibrium()
+        rho0 = E0[syn.F_RHO][:, None, :]
+        v0 = (E0[syn.F_MV] / E0[syn.F_RHO])[:, None, :]
+        up, vp = self._vortex_velocity(w.vortex_amp)
+        u1, v1 = self._vortex_velocity(1.0)
+        T = np.zeros(self.shape)
+        T[syn.F_MU] = rho0 * u1
+        T[syn.F_MV] = rho0 * v1
+        T[syn.F_EN] = rho0 * (up * u1 + v0 * v1 + vp * v1)
+        if self.nf > 5:
+            xi = syn.uniform_pm1(w.seed, syn.F_DRHO, w.ncell).reshape(w.nz, w.nth, w.nr)
+            rd = w.dust_ratio * rho0 * (1.0 + w.dust_noise * xi)
+            T[syn.F_DMU] = rd * u1
+            T[syn.F_DMV] = rd * v1
+        return T
+
+    def dust_velocity(self) -> np.ndarray:
+        """Initial dust velocity (u, v, w), (3, nz, nth, nr): the gas velocity of the recipe."""
+        w = self.w
+        E0 = self.equilibrium()
+        v0 = (E0[syn.F_MV] / E0[syn.F_RHO])[:, None, :]
+        up, vp = self._vortex_velocity(w.vortex_amp) if w.ic == "vortex" else (0.0, 0.0)
+        out = np.zeros((3, w.nz, w.nth, w.nr))
+        out[0] = up
+        out[1] = v0 + vp
+        return out
+
     def perturbation_state(self) -> np.ndarray:
         """E - E0 in float64, (nf, nz, nth, nr), for the workload's recipe."""
         w = self.w
@@ -104,20 +159,7 @@ class Grid:
             return Ep
         if w.ic != "vortex":
             raise ValueError(w.ic)
-        r = self.centres(0)[None, None, :]
-        th = self.centres(1)[None, :, None]
-        sigma0, beta_sigma, T0, beta_T = w.disc
-        up = np.zeros((1, w.nth, w.nr))
-        vp = np.zeros((1, w.nth, w.nr))
-        for rv, thv in w.vortices:
-            omk = math.sqrt(w.gm / rv ** 3)
-            s_r = w.vortex_width_h * math.sqrt(2.0 * T0 * rv ** beta_T) / omk
-            s_t = w.vortex_chi * s_r
-            psi0 = -w.vortex_amp * 1.5 * omk / (1.0 / s_r ** 2 + 1.0 / s_t ** 2)
-            dth = np.mod(th - thv + math.pi, 2.0 * math.pi) - math.pi
-            psi = psi0 * np.exp(-(r - rv) ** 2 / (2.0 * s_r ** 2) - (rv * dth) ** 2 / (2.0 * s_t ** 2))
-            up = up - psi * rv * rv * dth / (r * s_t ** 2)
-            vp = vp + psi * (r - rv) / s_r ** 2
+        up, vp = self._vortex_velocity(w.vortex_amp)
         Ep[syn.F_MU] = rho0 * up
         Ep[syn.F_MV] = rho0 * vp
         Ep[syn.F_EN] = 0.5 * rho0 * (up * up + 2.0 * v0 * vp + vp * vp)

@@ -1,0 +1,298 @@
+"""Discrete adjoint of the FP64 step (rossbi_adjoint_step) against the oracle.
+
+For a state E, a step dt, a direction delta and a cotangent lambda the
+transpose identity <lambda, J delta> = <J^T lambda, delta> must hold, J the
+derivative of the step map at fixed dt: the left side comes from the
+oracle's dual-number step on the CPU, the right side from the adjoint kernels
+on the GPU.  Single-cell columns compare the adjoint's value at a cell with
+the oracle's response to a unit change there, the Stokes derivative is
+checked the same way, and gradients through many checkpointed steps (the
+torch.autograd driver) are checked against central differences of the GPU
+forward run with the same frozen dt sequence.
+"""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as syn
+from tests.parity import jitter
+
+pytestmark = pytest.mark.gpu
+
+TOL_DOT = 1e-12
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    from paper_2207_04252_gb300 import build
+    build.build()
+    from paper_2207_04252_gb300 import rossbi, workloads
+    torch.cuda.init()
+    return rossbi, workloads
+
+
+def _box_sod():
+    return syn.scaled(syn.SOD, 64, 4, 4)
+
+
+CASES = [
+    ("sod_box", _box_sod, 5),
+    ("disc_ragged", lambda: syn.scaled(syn.DISC_NOISE, 29, 13, 32), 0),
+    ("vortex_ragged", lambda: syn.scaled(syn.VORTEX, 29, 13, 32), 0),
+    ("vortex_epstein", lambda: replace(syn.scaled(syn.VORTEX, 26, 14, 28), drag_law=1), 0),
+]
+
+
+def _setup(mk, presteps, seed=1):
+    w = mk()
+    o = oracle.Oracle(w)
+    E = oracle.initial_state(o)
+    if presteps:
+        E, _, _ = o.run(E, steps=presteps)
+    rng = np.random.default_rng(seed)
+    E = jitter(E, w.gamma, rng, 1e-3)
+    dt = o.cfl_dt(E)
+    scale = np.abs(E).mean(axis=(1, 2, 3), keepdims=True)
+    return w, o, E, dt, scale, rng
+
+
+def _gpu_adjoint(R, W, w, E, dt, lam, want_dstokes=False):
+    import torch
+    g = W.Grid(w, precision=R.ROSSBI_FP64)
+    s = torch.from_numpy(E).cuda().contiguous()
+    L = torch.from_numpy(lam).cuda().contiguous()
+    out = torch.empty_like(L)
+    dst = g.adjoint_step(s, dt, L, out, want_dstokes=want_dstokes)
+    assert g.take_status() == R.ROSSBI_OK
+    res = out.cpu().numpy()
+    g.close()
+    return res, dst
+
+
+@pytest.mark.parametrize("name,mk,presteps", CASES, ids=[c[0] for c in CASES])
+def test_adjoint_dot_product(lib, name, mk, presteps):
+    R, W = lib
+    w, o, E, dt, scale, rng = _setup(mk, presteps)
+    for trial in range(3):
+        lam = rng.standard_normal(E.shape) / scale
+        delta = rng.standard_normal(E.shape) * scale
+        _, t = o.step_tlm(E, delta, dt)
+        assert o.take_status() == 0
+        adj, _ = _gpu_adjoint(R, W, w, E, dt, lam)
+        lhs = float((lam * t).sum())
+        rhs = float((adj * delta).sum())
+        norm = float(np.abs(lam * t).sum())
+        assert abs(lhs - rhs) <= TOL_DOT * norm, (trial, lhs, rhs, abs(lhs - rhs) / norm)
+
+
+@pytest.mark.parametrize("name,mk,presteps", CASES, ids=[c[0] for c in CASES])
+def test_adjoint_single_cell_columns(lib, name, mk, presteps):
+    """Every field at boundary and interior cells: the adjoint's value there
+    equals <lambda, J e_cell> from the oracle."""
+    R, W = lib
+    w, o, E, dt, scale, rng = _setup(mk, presteps, seed=2)
+    lam = rng.standard_normal(E.shape) / scale
+    adj, _ = _gpu_adjoint(R, W, w, E, dt, lam)
+    nr, nth, nz = w.nr, w.nth, w.nz
+    cells = [(0, 0, 0), (nz - 1, nth - 1, nr - 1), (nz // 2, nth // 2, nr // 2), (1, nth - 2, nr - 2), (nz - 2, 1, 1)]
+    for (k, j, i) in cells:
+        for f in range(w.nfields):
+            d = np.zeros_like(E)
+            d[f, k, j, i] = 1.0
+            _, t = o.step_tlm(E, d, dt)
+            ref = float((lam * t).sum())
+            norm = float(np.abs(lam * t).sum()) + 1e-300
+            assert abs(adj[f, k, j, i] - ref) <= 1e-11 * norm, (f, (k, j, i), adj[f, k, j, i], ref)
+
+
+@pytest.mark.parametrize("law", [0, 1])
+def test_adjoint_stokes_derivative(lib, law):
+    R, W = lib
+    w, o, E, dt, scale, rng = _setup(lambda: replace(syn.scaled(syn.VORTEX, 29, 13, 32), drag_law=law), 0, seed=3)
+    lam = rng.standard_normal(E.shape) / scale
+    _, t = o.step_tlm(E, np.zeros_like(E), dt, dstokes=1.0)
+    ref = float((lam * t).sum())
+    _, dst = _gpu_adjoint(R, W, w, E, dt, lam, want_dstokes=True)
+    assert abs(dst - ref) <= 1e-11 * float(np.abs(lam * t).sum()), (dst, ref)
+
+
+def test_adjoint_in_place_and_deterministic(lib):
+    import torch
+    R, W = lib
+    w, o, E, dt, scale, rng = _setup(lambda: syn.scaled(syn.VORTEX, 29, 13, 32), 0, seed=4)
+    lam = rng.standard_normal(E.shape) / scale
+    a, _ = _gpu_adjoint(R, W, w, E, dt, lam)
+    g = W.Grid(w, precision=R.ROSSBI_FP64)
+    s = torch.from_numpy(E).cuda()
+    L = torch.from_numpy(lam).cuda()
+    g.adjoint_step(s, dt, L)  # in place
+    assert np.array_equal(L.cpu().numpy(), a)
+    assert np.array_equal(s.cpu().numpy(), E)  # E^n is read only
+    g.close()
+
+
+def test_adjoint_rejects_perturbation_forms(lib):
+    import torch
+    R, W = lib
+    w = syn.scaled(syn.VORTEX, 16, 12, 16)
+    g = W.Grid(w, precision=R.ROSSBI_FP32_PERT)
+    s = g.initial_state()
+    lam = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+    with pytest.raises(R.RossbiError) as e:
+        g.adjoint_step(s, 1e-4, lam)
+    assert e.value.code == R.ROSSBI_ERR_UNSUPPORTED
+    g.close()
+
+
+# ---------------------------------------------------------------- many steps, autograd, finite differences
+def _objective(W, w, adj, dts, amp=None, stokes=None, drho=None, every=7, grad=True):
+    """J after len(dts) steps from the (modified) initial state; with grad, also
+    dJ/dE^0 and dJ/dSt from the checkpointed adjoint."""
+    import torch
+    R = W.R
+    ww = w if amp is None else replace(w, vortex_amp=amp)
+    ww = ww if stokes is None else replace(ww, stokes=stokes)
+    g = W.Grid(ww, precision=R.ROSSBI_FP64)
+    E0 = g.initial_state()
+    if drho is not None:
+        vel = torch.from_numpy(g.dust_velocity()).cuda()
+        d = torch.from_numpy(drho).cuda()
+        E0[8] += d
+        E0[5:8] += vel * d
+    Wt = adj.vortex_core_weights(g).cuda()
+    if not grad:
+        for dt in dts:
+            g.step(E0, dt=dt)
+        J = float((Wt * E0).sum())
+        g.close()
+        return J
+    x = E0.clone().requires_grad_(True)
+    st = torch.tensor(ww.stokes, dtype=torch.float64, requires_grad=True)
+    EK = adj.run_steps(g, x, dts, stokes=st, every=every)
+    J = (Wt * EK).sum()
+    J.backward()
+    return float(J.detach()), x.grad.detach(), float(st.grad), g
+
+
+def test_adjoint_many_steps_against_oracle_tlm(lib):
+    """Ten checkpointed steps through the autograd driver against ten oracle
+    tangent-linear steps on the same dt sequence: <w, J_10 ... J_1 delta> for
+    a random delta (and d/dSt) equals the gradient the adjoint returns."""
+    import torch
+    R, W = lib
+    from paper_2207_04252_gb300 import adjoint as adj
+    w = syn.scaled(syn.VORTEX, 29, 13, 32)
+    o = oracle.Oracle(w)
+    rng = np.random.default_rng(11)
+    E0 = jitter(oracle.initial_state(o), w.gamma, rng, 1e-3)  # no exact mirror ties
+    _, _, dts = o.run(E0, steps=10)
+    scale = np.abs(E0).mean(axis=(1, 2, 3), keepdims=True)
+    lam = rng.standard_normal(E0.shape) / scale
+    delta = rng.standard_normal(E0.shape) * scale
+    E, t = E0.copy(), delta.copy()
+    for dt in dts:
+        E, t = o.step_tlm(E, t, dt)
+    g = W.Grid(w, precision=R.ROSSBI_FP64)
+    x = torch.from_numpy(E0).cuda().requires_grad_(True)
+    st = torch.tensor(w.stokes, dtype=torch.float64, requires_grad=True)
+    out = adj.run_steps(g, x, dts, stokes=st, every=4)
+    (torch.from_numpy(lam).cuda() * out).sum().backward()
+    lhs, rhs = float((lam * t).sum()), float((x.grad.cpu().numpy() * delta).sum())
+    assert abs(lhs - rhs) <= 1e-10 * float(np.abs(lam * t).sum()), (lhs, rhs)
+    g.close()
+
+
+def test_adjoint_many_steps_stokes_against_oracle_tlm(lib):
+    import torch
+    R, W = lib
+    from paper_2207_04252_gb300 import adjoint as adj
+    w = syn.scaled(syn.VORTEX, 29, 13, 32)
+    o = oracle.Oracle(w)
+    rng = np.random.default_rng(12)
+    E0 = jitter(oracle.initial_state(o), w.gamma, rng, 1e-3)
+    _, _, dts = o.run(E0, steps=8)
+    lam = rng.standard_normal(E0.shape) / np.abs(E0).mean(axis=(1, 2, 3), keepdims=True)
+    # d/dSt of E^8: the Stokes tangent enters every step
+    E, t = E0.copy(), np.zeros_like(E0)
+    for dt in dts:
+        E, t = o.step_tlm(E, t, dt, dstokes=1.0)
+    ref = float((lam * t).sum())
+    g = W.Grid(w, precision=R.ROSSBI_FP64)
+    x = torch.from_numpy(E0).cuda().requires_grad_(True)
+    st = torch.tensor(w.stokes, dtype=torch.float64, requires_grad=True)
+    out = adj.run_steps(g, x, dts, stokes=st, every=3)
+    (torch.from_numpy(lam).cuda() * out).sum().backward()
+    assert abs(float(st.grad) - ref) <= 1e-10 * float(np.abs(lam * t).sum()), (float(st.grad), ref)
+    g.close()
+
+
+def _fd_report(f, x0, hs):
+    """Central differences of f at relative steps hs: {h: value}."""
+    return {h: (f(x0 * (1 + h)) - f(x0 * (1 - h))) / (2 * h * x0) for h in hs}
+
+
+def _gradient_check(lib, w, steps, every, hs_rd=(1e-6, 1e-7, 1e-8)):
+    """Adjoint gradients of J = dust mass in the vortex core after `steps`
+    steps (frozen dts) against central differences of the GPU forward run:
+    vortex amplitude and Stokes number at h = 1e-6 and 1e-4 relative, a random
+    initial dust-density direction at fixed dust velocity at the steps hs_rd.
+    Returns {name: (adjoint, {h: fd})}."""
+    import torch
+    R, W = lib
+    from paper_2207_04252_gb300 import adjoint as adj
+    g0 = W.Grid(w, precision=R.ROSSBI_FP64)
+    dts = adj.cfl_sequence(g0, g0.initial_state(), steps)
+    T_amp = torch.from_numpy(g0.vortex_amp_tangent()).cuda()
+    vel = torch.from_numpy(g0.dust_velocity()).cuda()
+    rho_d = g0.initial_state()[8].double().cpu().numpy()
+    g0.close()
+    J, lam0, dst, g = _objective(W, w, adj, dts, every=every)
+    E = g.initial_state()
+    for dt in dts:
+        g.step(E, dt=dt)
+    assert float((adj.vortex_core_weights(g).cuda() * E).sum()) == J  # the autograd forward is the plain forward
+    g.close()
+    out = {}
+    out["amplitude"] = (float((lam0 * T_amp).sum()),
+                        _fd_report(lambda a: _objective(W, w, adj, dts, amp=a, every=every, grad=False), w.vortex_amp,
+                                   (1e-6, 1e-4)))
+    out["stokes"] = (dst, _fd_report(lambda s: _objective(W, w, adj, dts, stokes=s, every=every, grad=False), w.stokes,
+                                     (1e-6, 1e-4)))
+    rng = np.random.default_rng(7)
+    dr = rng.standard_normal(rho_d.shape) * rho_d
+    dr_t = torch.from_numpy(dr).cuda()
+    grad_rd = float((lam0[8] * dr_t).sum() + (lam0[5:8] * vel * dr_t).sum())
+    fd = {}
+    for h in hs_rd:
+        fd[h] = (_objective(W, w, adj, dts, drho=h * dr, every=every, grad=False) -
+                 _objective(W, w, adj, dts, drho=-h * dr, every=every, grad=False)) / (2 * h)
+    out["dust_density"] = (grad_rd, fd)
+    return out
+
+
+def _assert_fd(report):
+    for name, (a, fds) in report.items():
+        errs = {h: abs(a - v) / abs(v) for h, v in fds.items()}
+        # the best-conditioned difference quotient must agree to 1e-4: small h
+        # loses digits to rounding (d/dSt is ~1e-9 of J), large h crosses
+        # limiter branch boundaries (the dust density carries 1e-3 noise)
+        assert min(errs.values()) <= 1e-4, (name, a, fds, errs)
+
+
+def test_gradients_match_central_differences(lib):
+    rep = _gradient_check(lib, syn.scaled(syn.ADJOINT, 32, 48, 32, steps=20), 20, 7)
+    print("adjoint vs central differences (32x48x32, 20 steps):", rep)
+    _assert_fd(rep)
+
+
+@pytest.mark.parametrize("stokes", [0.01, 0.1, 1.0])
+def test_adjoint_workload_gradients(lib, stokes):
+    """The adjoint workload at full size: 128x256x32, 200 steps, checkpoints
+    every 20; gradients against central differences."""
+    w = replace(syn.ADJOINT, stokes=stokes)
+    rep = _gradient_check(lib, w, w.steps, w.checkpoint_every, hs_rd=(1e-6, 1e-8))
+    print(f"adjoint vs central differences ({w.name}, St = {stokes}):", rep)
+    _assert_fd(rep)

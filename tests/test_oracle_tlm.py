@@ -17,27 +17,7 @@ import pytest
 
 import oracle
 import synthetic as syn
-
-
-def _jitter(E, gamma, rng, a):
-    """Relative noise a on rho, P and rho_d; a * c_s on the velocities."""
-    E = E.copy()
-    rho = E[4]
-    v = E[0:3] / rho
-    P = (gamma - 1.0) * (E[3] - 0.5 * (E[0:3] ** 2).sum(0) / rho)
-    cs = np.sqrt(gamma * P / rho)
-    rho2 = rho * (1.0 + a * rng.standard_normal(rho.shape))
-    P2 = P * (1.0 + a * rng.standard_normal(rho.shape))
-    v2 = v + a * cs * rng.standard_normal(v.shape)
-    E[4] = rho2
-    E[0:3] = rho2 * v2
-    E[3] = P2 / (gamma - 1.0) + 0.5 * rho2 * (v2 ** 2).sum(0)
-    if E.shape[0] > 5:
-        rd = E[8] * (1.0 + a * rng.standard_normal(rho.shape))
-        vd = E[5:8] / E[8] + a * cs * rng.standard_normal(v.shape)
-        E[8] = rd
-        E[5:8] = rd * vd
-    return E
+from tests.parity import jitter as _jitter
 
 
 def _l1(a, b):
