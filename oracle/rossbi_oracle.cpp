@@ -47,6 +47,14 @@
 //      left after that step is far below round-off); PVRS start, floored at
 //      1e-8 min(pL, pR).
 //  R10 CFL uses the frame-relative speed; a dust cell adds cfl V/(|v_d| maxA).
+//
+// Tangent-linear mode (the paper has none; it pins the GPU adjoint).  The
+// numeric core is written for a scalar type T and also instantiated with a
+// dual number (value + one tangent): every branch is taken on the values, so
+// the tangent is the derivative of the branch taken, at a fixed dt.  The
+// star pressure's tangent is not carried through the Newton iterates but set
+// by the implicit function theorem at the converged p*:
+// dp* = -(df_L + df_R + du_R - du_L) / (f_L'(p*) + f_R'(p*)).
 #include <cmath>
 #include <cstdint>
 #include <cstring>

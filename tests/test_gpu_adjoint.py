@@ -177,6 +177,19 @@ def _objective(W, w, adj, dts, amp=None, stokes=None, drho=None, every=7, grad=T
     return float(J.detach()), x.grad.detach(), float(st.grad), g
 
 
+def _gpu_states(g, E0, dts):
+    """The GPU trajectory from E0 (the points the adjoint linearises about);
+    the oracle's tangent-linear steps are taken about the same states, so the
+    comparison does not depend on how two FP64 trajectories drift apart."""
+    import torch
+    s = torch.from_numpy(E0).cuda()
+    out = [E0]
+    for dt in dts:
+        g.step(s, dt=dt)
+        out.append(s.cpu().numpy())
+    return out
+
+
 def test_adjoint_many_steps_against_oracle_tlm(lib):
     """Ten checkpointed steps through the autograd driver against ten oracle
     tangent-linear steps on the same dt sequence: <w, J_10 ... J_1 delta> for
@@ -192,16 +205,16 @@ def test_adjoint_many_steps_against_oracle_tlm(lib):
     scale = np.abs(E0).mean(axis=(1, 2, 3), keepdims=True)
     lam = rng.standard_normal(E0.shape) / scale
     delta = rng.standard_normal(E0.shape) * scale
-    E, t = E0.copy(), delta.copy()
-    for dt in dts:
-        E, t = o.step_tlm(E, t, dt)
     g = W.Grid(w, precision=R.ROSSBI_FP64)
+    t = delta.copy()
+    for n, E in enumerate(_gpu_states(g, E0, dts)[:-1]):
+        _, t = o.step_tlm(E, t, dts[n])
     x = torch.from_numpy(E0).cuda().requires_grad_(True)
     st = torch.tensor(w.stokes, dtype=torch.float64, requires_grad=True)
     out = adj.run_steps(g, x, dts, stokes=st, every=4)
     (torch.from_numpy(lam).cuda() * out).sum().backward()
     lhs, rhs = float((lam * t).sum()), float((x.grad.cpu().numpy() * delta).sum())
-    assert abs(lhs - rhs) <= 1e-10 * float(np.abs(lam * t).sum()), (lhs, rhs)
+    assert abs(lhs - rhs) <= 1e-11 * float(np.abs(lam * t).sum()), (lhs, rhs)
     g.close()
 
 
@@ -216,16 +229,16 @@ def test_adjoint_many_steps_stokes_against_oracle_tlm(lib):
     _, _, dts = o.run(E0, steps=8)
     lam = rng.standard_normal(E0.shape) / np.abs(E0).mean(axis=(1, 2, 3), keepdims=True)
     # d/dSt of E^8: the Stokes tangent enters every step
-    E, t = E0.copy(), np.zeros_like(E0)
-    for dt in dts:
-        E, t = o.step_tlm(E, t, dt, dstokes=1.0)
-    ref = float((lam * t).sum())
     g = W.Grid(w, precision=R.ROSSBI_FP64)
+    t = np.zeros_like(E0)
+    for n, E in enumerate(_gpu_states(g, E0, dts)[:-1]):
+        _, t = o.step_tlm(E, t, dts[n], dstokes=1.0)
+    ref = float((lam * t).sum())
     x = torch.from_numpy(E0).cuda().requires_grad_(True)
     st = torch.tensor(w.stokes, dtype=torch.float64, requires_grad=True)
     out = adj.run_steps(g, x, dts, stokes=st, every=3)
     (torch.from_numpy(lam).cuda() * out).sum().backward()
-    assert abs(float(st.grad) - ref) <= 1e-10 * float(np.abs(lam * t).sum()), (float(st.grad), ref)
+    assert abs(float(st.grad) - ref) <= 1e-11 * float(np.abs(lam * t).sum()), (float(st.grad), ref)
     g.close()
 
 
