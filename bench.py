@@ -46,6 +46,28 @@ def _peaks():
         return HBM_PEAK_FALLBACK, "fallback"
 
 
+def _profile_values(kernel_tag):
+    """Key/value lines of the committed ncu summary of this kernel, if it was
+    taken on the current kernel source, else None."""
+    import glob
+    want = _source_hash(kernel_tag)
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{kernel_tag}__*.txt"))):
+        vals = {}
+        for line in open(path):
+            if "=" in line and not line.startswith("#"):
+                k, v = line.split("=", 1)
+                vals[k.strip()] = v.split("#")[0].strip()
+        if vals.get("source_hash") == want:
+            vals["_file"] = os.path.basename(path)
+            return vals
+    return None
+
+
+# Issue roof of GB300: 4 warp schedulers per SM, one warp instruction each per
+# clock, 152 SMs, at the maximum SM clock (2070 MHz).
+ISSUE_PEAK_WARP_INST_S = 4 * 152 * 2070e6
+
+
 def _traffic(kernel_tag, cells):
     """Per-launch DRAM bytes (read + write) of the stage kernel from a committed
     ncu summary (profiles/<kernel_tag>__<workload>.txt) taken on the current
@@ -372,6 +394,17 @@ def run_ours(args):
     if traffic is not None:
         roofline["traffic"] = traffic
         roofline["traffic_source"] = src
+    # the stage kernels are bound by instruction issue, not by HBM: the same
+    # launches against the issue roof, with the warp instructions per cell of
+    # the committed ncu capture of this kernel source
+    prof = _profile_values(kernel_tag)
+    roofline_issue = None
+    if prof is not None and "warp_instructions_per_cell" in prof:
+        inst = float(prof["warp_instructions_per_cell"]) * w.ncell
+        achieved_i = inst / avg_launch_s
+        roofline_issue = {"bound": "alu", "achieved": achieved_i, "peak": ISSUE_PEAK_WARP_INST_S,
+                          "unit": "warp-instructions/s", "frac": achieved_i / ISSUE_PEAK_WARP_INST_S,
+                          "source": prof["_file"]}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -380,7 +413,8 @@ def run_ours(args):
                 "config": {"workload": w.name, "precision": args.precision, "cells": w.ncell, "fields": g.nf,
                            "state_bytes": state_bytes, "parallelism": f"replicas{world}",
                            "l2": "inputs larger than L2 (no flush needed)"},
-                "roofline": roofline, "e2e": e2e, "gpu_launches": 3 * args.steps, "clocks": clocks,
+                "roofline": roofline, "roofline_issue": roofline_issue, "e2e": e2e,
+                "gpu_launches": 3 * args.steps, "clocks": clocks,
                 "status": R.status_string(status)}
         if args.precision == "fp32" and not args.no_extras:
             fp64 = measure_fp64(R, workloads, w, torch)

@@ -17,14 +17,21 @@
 //
 // Readings of the paper that this file takes (the paper is silent or garbled):
 //  R1  cell centre in r is the geometric mean of its face radii (log mesh).
-//  R2  MinMod limiter (Sect. 2.7 names the limiter only): each face deviation
-//      of the parabola, d = q - E'_i, is limited to minmod(d, s h), where s is
-//      the minmod of the two one-sided slopes and h = +-min(2|x_face - x_i|,
-//      |x_neighbour - x_i|) on that side: the curvature is reduced only where
-//      the parabola would leave the interval of the neighbouring cell values,
-//      the result is flat at an extremum, and it depends continuously on the
-//      data.  If a reconstructed gas face state has rho<=0 or P<=0, all gas
-//      fields of that cell are flattened in that direction.
+//  R2  the parabola acts on the departure of the PRIMITIVE gas variables
+//      (rho, u, v, w, P) from their equilibrium values (Sects. 2.6-2.7 say
+//      "Euler variables"; the exact solver they name works on primitive
+//      states, and conservative departures make the face pressure a
+//      cancellation of O(Mach^2) terms in the rotating frame, whose linearised
+//      step then amplifies perturbations ~6x per step at the disc's outer
+//      edge).  MinMod limiter (Sect. 2.7 names the limiter only): each face
+//      deviation of the parabola, d = q - E'_i, is limited to minmod(d, s h),
+//      where s is the minmod of the two one-sided slopes and
+//      h = +-min(2|x_face - x_i|, |x_neighbour - x_i|) on that side: the
+//      curvature is reduced only where the parabola would leave the interval
+//      of the neighbouring cell values, the result is flat at an extremum, and
+//      it depends continuously on the data.  If a reconstructed gas face state
+//      has rho<=0 or P<=0, all gas deviations of that cell are used flat in
+//      that direction.
 //  R3  the energy flux is (E+P)u_n (App. B prints rho(E+P)u, which is not
 //      dimensionally consistent with the governing equations of Sect. 2.1).
 //  R4  the RK2 update is E + dt*G/V (Sect. 2.5 prints a*V*dt*G; the compact
@@ -300,7 +307,56 @@ static void eq_face(const Oracle& o, int ax, int i, int k, int fc, double e0[5])
   for (int f = 0; f < 5; ++f) e0[f] = s[f];
 }
 
-// Face deviations q- (lower face) and q+ (upper face) of cell `cell` along ax.
+// Primitive gas state (u, v, w, P, rho), in the field slots MU, MV, MW, EN,
+// RHO, of a conservative state, and back.
+template <class T>
+static void prim_of(double g, const T* U, T* W) {
+  for (int q = 0; q < 3; ++q) W[MU + q] = U[MU + q] / U[RHO];
+  W[EN] = pressure(g, U);
+  W[RHO] = U[RHO];
+}
+template <class T>
+static void cons_of(double g, const T* W, T* U) {
+  U[RHO] = W[RHO];
+  for (int q = 0; q < 3; ++q) U[MU + q] = W[RHO] * W[MU + q];
+  U[EN] = W[EN] / (g - 1.0) + 0.5 * W[RHO] * (W[MU] * W[MU] + W[MV] * W[MV] + W[MW] * W[MW]);
+}
+
+// Primitive deviations (u', v', w', P', rho') of cell (i, j, k), stored in the
+// field slots MU, MV, MW, EN, RHO: the cell's primitive state minus the
+// equilibrium primitive state at the cell (reading R2).  Ghost rule of
+// Sect. 2.4 as in dev(): equilibrium ghosts carry zero deviation, periodic
+// ghosts wrap, outflow ghosts copy the nearest interior deviation.
+template <class Acc, class T = typename Acc::value_type>
+static void prim_dev(const Oracle& o, const Acc& E, int i, int j, int k, T d[5]) {
+  int c[3] = {i, j, k};
+  for (int ax = 0; ax < 3; ++ax) {
+    if (c[ax] >= 0 && c[ax] < o.n[ax]) continue;
+    const int bc = c[ax] < 0 ? o.d.bc_lo[ax] : o.d.bc_hi[ax];
+    if (bc == BC_EQUILIBRIUM) {
+      for (int f = 0; f < 5; ++f) d[f] = T(0.0);
+      return;
+    }
+    if (bc == BC_PERIODIC)
+      c[ax] = ((c[ax] % o.n[ax]) + o.n[ax]) % o.n[ax];
+    else
+      c[ax] = c[ax] < 0 ? 0 : o.n[ax] - 1;
+  }
+  const long lin = ((long)c[2] * o.n[1] + c[1]) * o.n[0] + c[0];
+  T U[5];
+  for (int f = 0; f < 5; ++f) U[f] = E.get(f, lin);
+  double W0[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if (o.has_eq) prim_of(o.d.gamma, E0C(o, c[0], c[2]), W0);
+  for (int q = 0; q < 3; ++q) d[MU + q] = U[MU + q] / U[RHO] - W0[MU + q];
+  d[EN] = pressure(o.d.gamma, U) - W0[EN];
+  d[RHO] = U[RHO] - W0[RHO];
+}
+
+// Face deviations q- (lower face) and q+ (upper face) of cell `cell` along ax,
+// as conservative face states minus the conservative face equilibrium.  Gas:
+// parabola + MinMod on the primitive deviations (Sect. 2.7, reading R2), face
+// primitives = face equilibrium primitives + deviation; if either face has
+// rho <= 0 or P <= 0 the cell's gas deviations are used flat.  Dust: reading R5.
 template <class Acc, class T = typename Acc::value_type>
 static void recon(const Oracle& o, const Acc& E, int ax, const int cell[3], T qm[9], T qp[9]) {
   int cm[3] = {cell[0], cell[1], cell[2]}, cp[3] = {cell[0], cell[1], cell[2]};
@@ -309,44 +365,54 @@ static void recon(const Oracle& o, const Acc& E, int ax, const int cell[3], T qm
   const int c = cell[ax];
   const double xm = XC(o, ax, c - 1), x0 = XC(o, ax, c), xp = XC(o, ax, c + 1);
   const double fm = XF(o, ax, c), fp = XF(o, ax, c + 1);
-  T ec[5];
+  T dm[5], d0[5], dp[5], wm[5], wp[5];
+  prim_dev(o, E, cm[0], cm[1], cm[2], dm);
+  prim_dev(o, E, cell[0], cell[1], cell[2], d0);
+  prim_dev(o, E, cp[0], cp[1], cp[2], dp);
   bool gas_shaped = false;
+  for (int f = 0; f < 5; ++f) gas_shaped |= parabola(dm[f], d0[f], dp[f], xm, x0, xp, fm, fp, wm[f], wp[f]);
+  double e0m[5], e0p[5], W0m[5] = {0, 0, 0, 0, 0}, W0p[5] = {0, 0, 0, 0, 0};
+  eq_face(o, ax, cell[0], cell[2], c, e0m);
+  eq_face(o, ax, cell[0], cell[2], c + 1, e0p);
+  if (o.has_eq) {
+    prim_of(o.d.gamma, e0m, W0m);
+    prim_of(o.d.gamma, e0p, W0p);
+  }
+  T Wm[5], Wp[5];
   for (int f = 0; f < 5; ++f) {
-    const T em = dev(o, E, f, cm[0], cm[1], cm[2]);
-    ec[f] = dev(o, E, f, cell[0], cell[1], cell[2]);
-    const T ep = dev(o, E, f, cp[0], cp[1], cp[2]);
-    gas_shaped |= parabola(em, ec[f], ep, xm, x0, xp, fm, fp, qm[f], qp[f]);
+    Wm[f] = W0m[f] + wm[f];
+    Wp[f] = W0p[f] + wp[f];
+  }
+  if (gas_shaped && !(Wm[RHO] > 0.0 && Wp[RHO] > 0.0 && Wm[EN] > 0.0 && Wp[EN] > 0.0)) {
+    for (int f = 0; f < 5; ++f) {  // R2 (iii): positivity of both gas face states
+      Wm[f] = W0m[f] + d0[f];
+      Wp[f] = W0p[f] + d0[f];
+    }
+  }
+  T Um[5], Up[5];
+  cons_of(o.d.gamma, Wm, Um);
+  cons_of(o.d.gamma, Wp, Up);
+  for (int f = 0; f < 5; ++f) {
+    qm[f] = Um[f] - e0m[f];
+    qp[f] = Up[f] - e0p[f];
   }
   if (o.nf > 5) {  // R5: dust in primitive variables (rho_d, u_d, v_d, w_d)
-    T wm[4], w0[4], wp[4], qmw[4], qpw[4];
-    wm[3] = dev(o, E, DRHO, cm[0], cm[1], cm[2]);
-    w0[3] = dev(o, E, DRHO, cell[0], cell[1], cell[2]);
-    wp[3] = dev(o, E, DRHO, cp[0], cp[1], cp[2]);
-    for (int c = 0; c < 3; ++c) {
-      wm[c] = wm[3] > 0.0 ? dev(o, E, DMU + c, cm[0], cm[1], cm[2]) / wm[3] : T(0.0);
-      w0[c] = w0[3] > 0.0 ? dev(o, E, DMU + c, cell[0], cell[1], cell[2]) / w0[3] : T(0.0);
-      wp[c] = wp[3] > 0.0 ? dev(o, E, DMU + c, cp[0], cp[1], cp[2]) / wp[3] : T(0.0);
+    T pm[4], p0[4], pp[4], qmw[4], qpw[4];
+    pm[3] = dev(o, E, DRHO, cm[0], cm[1], cm[2]);
+    p0[3] = dev(o, E, DRHO, cell[0], cell[1], cell[2]);
+    pp[3] = dev(o, E, DRHO, cp[0], cp[1], cp[2]);
+    for (int q = 0; q < 3; ++q) {
+      pm[q] = pm[3] > 0.0 ? dev(o, E, DMU + q, cm[0], cm[1], cm[2]) / pm[3] : T(0.0);
+      p0[q] = p0[3] > 0.0 ? dev(o, E, DMU + q, cell[0], cell[1], cell[2]) / p0[3] : T(0.0);
+      pp[q] = pp[3] > 0.0 ? dev(o, E, DMU + q, cp[0], cp[1], cp[2]) / pp[3] : T(0.0);
     }
-    for (int q = 0; q < 4; ++q) parabola(wm[q], w0[q], wp[q], xm, x0, xp, fm, fp, qmw[q], qpw[q]);
+    for (int q = 0; q < 4; ++q) parabola(pm[q], p0[q], pp[q], xm, x0, xp, fm, fp, qmw[q], qpw[q]);
     qm[DRHO] = qmw[3];
     qp[DRHO] = qpw[3];
-    for (int c = 0; c < 3; ++c) {
-      qm[DMU + c] = qmw[3] * qmw[c];
-      qp[DMU + c] = qpw[3] * qpw[c];
+    for (int q = 0; q < 3; ++q) {
+      qm[DMU + q] = qmw[3] * qmw[q];
+      qp[DMU + q] = qpw[3] * qpw[q];
     }
-  }
-  if (gas_shaped) {  // R2 (iii): positivity of both reconstructed gas face states
-    double e0m[5], e0p[5];
-    T Um[5], Up[5];
-    eq_face(o, ax, cell[0], cell[2], c, e0m);
-    eq_face(o, ax, cell[0], cell[2], c + 1, e0p);
-    for (int f = 0; f < 5; ++f) {
-      Um[f] = e0m[f] + qm[f];
-      Up[f] = e0p[f] + qp[f];
-    }
-    const bool ok = Um[RHO] > 0.0 && Up[RHO] > 0.0 && pressure(o.d.gamma, Um) > 0.0 && pressure(o.d.gamma, Up) > 0.0;
-    if (!ok)
-      for (int f = 0; f < 5; ++f) qm[f] = qp[f] = ec[f];
   }
 }
 

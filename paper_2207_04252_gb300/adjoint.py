@@ -25,26 +25,27 @@ from . import rossbi as R
 
 class _Steps(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, E0, stokes, grid, dts, every):
-        if grid.precision != R.ROSSBI_FP64:
-            raise R.RossbiError(R.ROSSBI_ERR_UNSUPPORTED, "run_steps (the adjoint is FP64 only)")
+    def forward(ctx, E0, stokes, grid, dts, every, agrid):
         law = grid.dust[1] if grid.dust else 0
         grid.dust = (float(stokes), law) if grid.dust else None
+        agrid.dust = grid.dust
         E = E0.detach().clone().contiguous()
         ckpts = []
         for n, dt in enumerate(dts):
             if n % every == 0:
                 ckpts.append(E.clone())
             grid.step(E, dt=dt)
-        ctx.grid, ctx.dts, ctx.every, ctx.ckpts = grid, list(dts), every, ckpts
+        ctx.grid, ctx.agrid, ctx.dts, ctx.every, ctx.ckpts = grid, agrid, list(dts), every, ckpts
+        ctx.in_dtype = E0.dtype
         return E
 
     @staticmethod
     def backward(ctx, lam_out):
-        grid, dts, every = ctx.grid, ctx.dts, ctx.every
+        grid, agrid, dts, every = ctx.grid, ctx.agrid, ctx.dts, ctx.every
         lam = lam_out.detach().to(torch.float64).clone().contiguous()
-        R.rossbi_adjoint_dstokes(grid.h, reset=True)
+        R.rossbi_adjoint_dstokes(agrid.h, reset=True)
         K = len(dts)
+        full = _full_state_fn(grid)
         for s in reversed(range(len(ctx.ckpts))):
             start, end = s * every, min((s + 1) * every, K)
             states = [ctx.ckpts[s]]
@@ -53,19 +54,40 @@ class _Steps(torch.autograd.Function):
                 grid.step(E, dt=dts[n])
                 states.append(E)
             for n in reversed(range(start, end)):
-                grid.adjoint_step(states[n - start], dts[n], lam)
-        dst = R.rossbi_adjoint_dstokes(grid.h, reset=True) if grid.dust else 0.0
+                agrid.adjoint_step(full(states[n - start]), dts[n], lam)
+        dst = R.rossbi_adjoint_dstokes(agrid.h, reset=True) if grid.dust else 0.0
         ctx.ckpts = None
-        return lam, torch.tensor(dst, dtype=torch.float64), None, None, None
+        return lam.to(ctx.in_dtype), torch.tensor(dst, dtype=torch.float64), None, None, None, None
 
 
-def run_steps(grid, E0, dts, stokes=None, every=20):
-    """E^K from E^0 (FP64 tensor (nf, nz, nth, nr) on the device) through the
-    steps dts; differentiable in E0 and in `stokes` (a 0-d float64 tensor;
-    default: the workload's Stokes number, not tracked)."""
+def _full_state_fn(grid):
+    """State of `grid` -> the FP64 full state the adjoint linearises about."""
+    if grid.precision == R.ROSSBI_FP64:
+        return lambda s: s
+    E0 = torch.zeros(grid.shape, dtype=torch.float64, device="cuda")
+    if grid.w.disc is not None:
+        E0[:5] = torch.from_numpy(grid.equilibrium()).cuda()[:, :, None, :]
+
+    def full(s):
+        return (E0 + s.to(torch.float64)).contiguous()
+    return full
+
+
+def run_steps(grid, E0, dts, stokes=None, every=20, adjoint_grid=None):
+    """E^K from E^0 (a state of `grid`, (nf, nz, nth, nr) on the device)
+    through the steps dts; differentiable in E0 and in `stokes` (a 0-d float64
+    tensor; default: the workload's Stokes number, not tracked).
+
+    An FP64 grid is its own adjoint grid.  For a perturbation-form grid (the
+    state is E' = E - E0) the forward run and the checkpoints stay in that
+    form and `adjoint_grid`, an FP64 grid of the same workload, supplies the
+    FP64 adjoint steps, linearised about E0 + E' of the recomputed states."""
     if stokes is None:
         stokes = torch.tensor(grid.w.stokes, dtype=torch.float64)
-    return _Steps.apply(E0, stokes, grid, list(dts), int(every))
+    agrid = grid if grid.precision == R.ROSSBI_FP64 else adjoint_grid
+    if agrid is None or agrid.precision != R.ROSSBI_FP64:
+        raise R.RossbiError(R.ROSSBI_ERR_ARG, "run_steps: a perturbation-form grid needs an FP64 adjoint_grid")
+    return _Steps.apply(E0, stokes, grid, list(dts), int(every), agrid)
 
 
 def cfl_sequence(grid, E0, steps):

@@ -16,7 +16,7 @@
 //   adj_flux_kernel   flux part of G'^T mu' along one axis, accumulated into
 //                     the cotangent of the stage input.
 // A line of L lanes along the axis owns T = L - 4 cells: lane p holds cell
-// c = c0 - 2 + p, reconstructs it, solves the face below it (once per tile),
+// c = c0 - 2 + p, reconstructs it (gas: primitive deviations), solves the face below it (once per tile),
 // back-propagates the face cotangent to both face states, passes the lower
 // one down by a shuffle, back-propagates its own reconstruction and passes
 // the neighbour contributions up and down by shuffles; every sum has a fixed
@@ -254,25 +254,21 @@ __device__ __noinline__ int riemann_jac(double g, double rl, double ul, double p
 }
 
 // ------------------------------------------------------------------ face flux adjoints
-// Cotangents of the conservative face states for a cotangent Fb on the gas
-// flux gas_face_flux<D>(UL, UR).
+// Cotangents of the primitive face states (u, v, w, P, rho in the field
+// slots) for a cotangent Fb on the gas flux gas_face_flux<D>(WL, WR).
 template <int D>
-__device__ __noinline__ void gas_flux_vjp(double g, const double* UL, const double* UR, const double* Fb, double* ULb,
-                                          double* URb, unsigned& status) {
+__device__ __noinline__ void gas_flux_vjp(double g, const double* WL, const double* WR, const double* Fb, double* WLb,
+                                          double* WRb, unsigned& status) {
   constexpr int n = Axes<D>::n, t1 = Axes<D>::t1, t2 = Axes<D>::t2;
 #pragma unroll
-  for (int f = 0; f < 5; ++f) ULb[f] = URb[f] = 0.0;
-  const double rl = UL[RHO], rr = UR[RHO];
-  const double pl = gas_pressure(g, UL[MU], UL[MV], UL[MW], UL[EN], rl);
-  const double pr = gas_pressure(g, UR[MU], UR[MV], UR[MW], UR[EN], rr);
+  for (int f = 0; f < 5; ++f) WLb[f] = WRb[f] = 0.0;
+  const double rl = WL[RHO], rr = WR[RHO], pl = WL[EN], pr = WR[EN];
   if (!(rl > 0.0) || !(rr > 0.0) || !(pl > 0.0) || !(pr > 0.0)) return;  // zero flux
-  const double il = 1.0 / rl, ir = 1.0 / rr;
-  const double unl = UL[n] * il, unr = UR[n] * ir;
   J6 Rs, Us, Ps;
-  const int side = riemann_jac(g, rl, unl, pl, rr, unr, pr, Rs, Us, Ps, status);
+  const int side = riemann_jac(g, rl, WL[n], pl, rr, WR[n], pr, Rs, Us, Ps, status);
   double ut1 = 0.0, ut2 = 0.0;
-  if (side < 0) { ut1 = UL[t1] * il; ut2 = UL[t2] * il; }
-  else if (side > 0) { ut1 = UR[t1] * ir; ut2 = UR[t2] * ir; }
+  if (side < 0) { ut1 = WL[t1]; ut2 = WL[t2]; }
+  else if (side > 0) { ut1 = WR[t1]; ut2 = WR[t2]; }
   const double rho = Rs.v, u = Us.v, p = Ps.v;
   const double m = rho * u;
   const double K = 0.5 * (u * u + ut1 * ut1 + ut2 * ut2);
@@ -288,22 +284,19 @@ __device__ __noinline__ void gas_flux_vjp(double g, const double* UL, const doub
   double w[6];
 #pragma unroll
   for (int q = 0; q < 6; ++q) w[q] = rb * Rs.d[q] + ub * Us.d[q] + pb * Ps.d[q];
-  // primitives (rho, u_n, p) of each side from its conservative state
-  auto prim_back = [&](const double* U, double iv, double un, double rhob, double unb, double presb, double a1,
-                       double a2, double* Ub) {
-    const double gm1 = g - 1.0;
-    const double v0 = U[MU] * iv, v1 = U[MV] * iv, v2 = U[MW] * iv;
-    Ub[EN] = gm1 * presb;
-    Ub[MU] = -gm1 * presb * v0;
-    Ub[MV] = -gm1 * presb * v1;
-    Ub[MW] = -gm1 * presb * v2;
-    Ub[n] += unb * iv;
-    Ub[t1] += a1 * iv;
-    Ub[t2] += a2 * iv;
-    Ub[RHO] = rhob + gm1 * presb * 0.5 * (v0 * v0 + v1 * v1 + v2 * v2) - (unb * un + a1 * U[t1] * iv + a2 * U[t2] * iv) * iv;
-  };
-  prim_back(UL, il, unl, w[0], w[1], w[2], side < 0 ? ut1b : 0.0, side < 0 ? ut2b : 0.0, ULb);
-  prim_back(UR, ir, unr, w[3], w[4], w[5], side > 0 ? ut1b : 0.0, side > 0 ? ut2b : 0.0, URb);
+  WLb[RHO] = w[0];
+  WLb[n] = w[1];
+  WLb[EN] = w[2];
+  WRb[RHO] = w[3];
+  WRb[n] = w[4];
+  WRb[EN] = w[5];
+  if (side < 0) {
+    WLb[t1] = ut1b;
+    WLb[t2] = ut2b;
+  } else if (side > 0) {
+    WRb[t1] = ut1b;
+    WRb[t2] = ut2b;
+  }
 }
 
 // Cotangents of the dust face primitives (u, v, w, rho_d) for a cotangent Fb
@@ -597,12 +590,15 @@ __global__ void __launch_bounds__(L * NL, 1) adj_flux_kernel(const AdjFluxArgs a
       continue;
     }
     const size_t lin = ((size_t)c[2] * g.nth + c[1]) * g.nr + c[0];
+    double U[5], W[5];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      double e = a.E[f][lin];
-      if (f < 5 && g.has_eq) e -= g.e0c[((size_t)f * g.nz + c[2]) * g.nr + c[0]];
-      dst[(size_t)f * PE * NLP] = e;
-    }
+    for (int f = 0; f < 5; ++f) U[f] = a.E[f][lin];
+    gas_prim(g.gamma, U, W);
+#pragma unroll
+    for (int f = 0; f < 5; ++f)
+      dst[(size_t)f * PE * NLP] = g.has_eq ? W[f] - g.w0c[((size_t)f * g.nz + c[2]) * g.nr + c[0]] : W[f];
+#pragma unroll
+    for (int f = 5; f < NF; ++f) dst[(size_t)f * PE * NLP] = a.E[f][lin];
   }
   for (int idx = threadIdx.x; idx < PM * NL; idx += NT) {
     const int pos = D == 0 ? idx % PM : idx / NL;
@@ -644,11 +640,11 @@ __global__ void __launch_bounds__(L * NL, 1) adj_flux_kernel(const AdjFluxArgs a
   unsigned status = 0;
   auto sv = [&](int f, int q) -> double { return sE[((size_t)f * PE + q) * NLP + l]; };
   auto sm = [&](int f, int q) -> double { return sM[((size_t)f * PM + q) * NLP + l]; };
-  auto e0_face = [&](int f, int fd) -> double {
+  auto w0_face = [&](int f, int fd) -> double {
     if (!g.has_eq) return 0.0;
-    if (D == 0) return g.e0r[((size_t)f * g.nz + ck) * (g.nr + 1) + clampi(fd, 0, g.nr)];
-    if (D == 1) return g.e0c[((size_t)f * g.nz + ck) * g.nr + ci];
-    return g.e0z[((size_t)f * (g.nz + 1) + clampi(fd, 0, g.nz)) * g.nr + ci];
+    if (D == 0) return g.w0r[((size_t)f * g.nz + ck) * (g.nr + 1) + clampi(fd, 0, g.nr)];
+    if (D == 1) return g.w0c[((size_t)f * g.nz + ck) * g.nr + ci];
+    return g.w0z[((size_t)f * (g.nz + 1) + clampi(fd, 0, g.nz)) * g.nr + ci];
   };
   double w[9];
   parabola_weights<double, D>(g.rcoef, gi, g.nr, g.dx[D], w);
@@ -660,14 +656,8 @@ __global__ void __launch_bounds__(L * NL, 1) adj_flux_kernel(const AdjFluxArgs a
   for (int f = 0; f < 5; ++f) shaped |= parabola(sv(f, p), sv(f, p + 1), sv(f, p + 2), w, qm[f], qp[f]);
   bool fallback = false;
   if (shaped && line_ok) {
-    double Um[5], Up[5];
-#pragma unroll
-    for (int f = 0; f < 5; ++f) {
-      Um[f] = e0_face(f, c) + qm[f];
-      Up[f] = e0_face(f, c + 1) + qp[f];
-    }
-    fallback = !(Um[RHO] > 0.0 && Up[RHO] > 0.0 && gas_pressure(gam, Um[MU], Um[MV], Um[MW], Um[EN], Um[RHO]) > 0.0 &&
-                 gas_pressure(gam, Up[MU], Up[MV], Up[MW], Up[EN], Up[RHO]) > 0.0);
+    fallback = !(w0_face(RHO, c) + qm[RHO] > 0.0 && w0_face(RHO, c + 1) + qp[RHO] > 0.0 &&
+                 w0_face(EN, c) + qm[EN] > 0.0 && w0_face(EN, c + 1) + qp[EN] > 0.0);
     if (fallback) {
 #pragma unroll
       for (int f = 0; f < 5; ++f) qm[f] = qp[f] = sv(f, p + 1);
@@ -703,9 +693,9 @@ __global__ void __launch_bounds__(L * NL, 1) adj_flux_kernel(const AdjFluxArgs a
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
       const double ql = __shfl_up_sync(FULL, qp[f], 1, L);
-      const double e0 = e0_face(f, c);
-      UL[f] = e0 + ql;
-      UR[f] = e0 + qm[f];
+      const double w0 = w0_face(f, c);
+      UL[f] = w0 + ql;
+      UR[f] = w0 + qm[f];
     }
     if (has_face) {
       gas_flux_vjp<D>(gam, UL, UR, Fb, ULb, URb, status);
@@ -782,8 +772,18 @@ __global__ void __launch_bounds__(L * NL, 1) adj_flux_kernel(const AdjFluxArgs a
   }
   if (line_ok && p >= 2 && p < T + 2 && c < nd) {
     const size_t lin = ((size_t)cc[2] * g.nth + cc[1]) * g.nr + cc[0];
+    // gas: primitive-deviation cotangents back to the conservative fields
+    const double rho = a.E[RHO][lin], ir = 1.0 / rho, gm1 = gam - 1.0;
+    const double v0 = a.E[MU][lin] * ir, v1 = a.E[MV][lin] * ir, v2 = a.E[MW][lin] * ir;
+    const double bP = tot[EN];
+    double lr = tot[RHO] - (tot[MU] * v0 + tot[MV] * v1 + tot[MW] * v2) * ir + gm1 * bP * 0.5 * (v0 * v0 + v1 * v1 + v2 * v2);
+    a.lam[MU][lin] += tot[MU] * ir - gm1 * bP * v0;
+    a.lam[MV][lin] += tot[MV] * ir - gm1 * bP * v1;
+    a.lam[MW][lin] += tot[MW] * ir - gm1 * bP * v2;
+    a.lam[EN][lin] += gm1 * bP;
+    a.lam[RHO][lin] += lr;
 #pragma unroll
-    for (int f = 0; f < NF; ++f) a.lam[f][lin] += tot[f];
+    for (int f = 5; f < NF; ++f) a.lam[f][lin] += tot[f];
   }
   if (status) atomicOr(a.status, status);
 }

@@ -34,6 +34,9 @@ struct DevGrid {
   const double* e0c;     // equilibrium gas state at centres   [5][nz][nr]
   const double* e0r;     // equilibrium gas state at r faces   [5][nz][nr + 1]
   const double* e0z;     // equilibrium gas state at z faces   [5][nz + 1][nr]
+  const double* w0c;     // equilibrium primitive gas state (u, v, w, P, rho in the
+  const double* w0r;     //   field slots MU, MV, MW, EN, RHO) at centres, r faces and
+  const double* w0z;     //   z faces, same layouts as e0c / e0r / e0z
   const double* r0;      // balanced residual G(E0)            [5][nz][nr]
 };
 
@@ -106,19 +109,23 @@ __device__ __forceinline__ int riemann_face(double g, double rl, double ul, doub
   }
   const double pfloor = 1e-8 * fmin(pl, pr);
   double ps = fmax(pfloor, 0.5 * (pl + pr) - 0.125 * (ur - ul) * (rl + rr) * (L.c + R.c));
-  double fl, fdl, fr, fdr;
+  double fl, fdl, fr, fdr, step = 0.0;
   bool conv = false;
   for (int it = 0; it < 100; ++it) {
     pressure_fn(g, L, ps, fl, fdl);
     pressure_fn(g, R, ps, fr, fdr);
     const double pn = fmax(pfloor, ps - (fl + fr + ur - ul) / (fdl + fdr));
     const double change = 2.0 * fabs(pn - ps) / (pn + ps);
+    step = pn - ps;
     ps = pn;
     if (change <= 1e-12) { conv = true; break; }
   }
   if (!conv) status |= STATUS_RIEMANN;
-  pressure_fn(g, L, ps, fl, fdl);
-  pressure_fn(g, R, ps, fr, fdr);
+  // f_K at the converged p* from the last evaluation, one Newton step away:
+  // the neglected second-order term is below rounding once the change is
+  // under 1e-12
+  fl += fdl * step;
+  fr += fdr * step;
   const double us = 0.5 * (ul + ur) + 0.5 * (fr - fl);
   if (0.0 <= us) {  // face lies left of the contact
     if (ps <= pl) {
@@ -160,27 +167,35 @@ __device__ __forceinline__ double gas_pressure(double g, double mu, double mv, d
   return (g - 1.0) * (en - 0.5 * (mu * mu + mv * mv + mw * mw) / rho);
 }
 
+// Primitive gas state (u, v, w, P, rho), in the field slots MU, MV, MW, EN,
+// RHO, of a conservative gas state.
+__device__ __forceinline__ void gas_prim(double g, const double* U, double* W) {
+  const double ir = 1.0 / U[RHO];
+  W[MU] = U[MU] * ir;
+  W[MV] = U[MV] * ir;
+  W[MW] = U[MW] * ir;
+  W[EN] = gas_pressure(g, U[MU], U[MV], U[MW], U[EN], U[RHO]);
+  W[RHO] = U[RHO];
+}
+
 // Gas flux F(E*) through a face normal to axis D from the reconstructed left
-// and right conservative states (App. B flux vector; energy flux (E + P) u_n).
+// and right primitive states (App. B flux vector; energy flux (E + P) u_n).
 template <int D>
-__device__ __forceinline__ void gas_face_flux(double g, const double* UL, const double* UR, double* F,
+__device__ __forceinline__ void gas_face_flux(double g, const double* WL, const double* WR, double* F,
                                               unsigned& status) {
   constexpr int n = Axes<D>::n, t1 = Axes<D>::t1, t2 = Axes<D>::t2;
-  const double rl = UL[RHO], rr = UR[RHO];
-  const double pl = gas_pressure(g, UL[MU], UL[MV], UL[MW], UL[EN], rl);
-  const double pr = gas_pressure(g, UR[MU], UR[MV], UR[MW], UR[EN], rr);
+  const double rl = WL[RHO], rr = WR[RHO], pl = WL[EN], pr = WR[EN];
   if (!(rl > 0.0) || !(rr > 0.0) || !(pl > 0.0) || !(pr > 0.0)) {
     status |= STATUS_NONPHYSICAL;
 #pragma unroll
     for (int f = 0; f < 5; ++f) F[f] = 0.0;
     return;
   }
-  const double il = 1.0 / rl, ir = 1.0 / rr;
   double rho, u, p;
-  const int side = riemann_face(g, rl, UL[n] * il, pl, rr, UR[n] * ir, pr, rho, u, p, status);
+  const int side = riemann_face(g, rl, WL[n], pl, rr, WR[n], pr, rho, u, p, status);
   double ut1 = 0.0, ut2 = 0.0;
-  if (side < 0) { ut1 = UL[t1] * il; ut2 = UL[t2] * il; }
-  else if (side > 0) { ut1 = UR[t1] * ir; ut2 = UR[t2] * ir; }
+  if (side < 0) { ut1 = WL[t1]; ut2 = WL[t2]; }
+  else if (side > 0) { ut1 = WR[t1]; ut2 = WR[t2]; }
   const double m = rho * u;
   F[RHO] = m;
   F[n] = m * u + p;

@@ -40,6 +40,7 @@ struct rossbi_grid {
   double *d_rc = nullptr, *d_rf = nullptr, *d_rcoef = nullptr, *d_vol = nullptr, *d_ivol = nullptr;
   double *d_area_r = nullptr, *d_area_t = nullptr, *d_area_z = nullptr, *d_maxA = nullptr;
   double *d_e0c = nullptr, *d_e0r = nullptr, *d_e0z = nullptr, *d_r0 = nullptr;
+  double* d_w0 = nullptr;              // primitive equilibrium tables (centres, r faces, z faces)
   std::vector<double> h_e0c;
   // reductions and status
   unsigned long long* d_dt = nullptr;  // [3]: step ping-pong slots 0/1, standalone CFL slot 2
@@ -187,6 +188,18 @@ __global__ void cfl_kernel(DevGrid g, StageArgs a, unsigned long long* slot) {
 }
 
 __global__ void set_slot_kernel(unsigned long long* slot, unsigned long long v) { *slot = v; }
+
+// Primitive equilibrium table from a conservative one ([5][n] each), with the
+// conversion the stage kernels apply to the state, so that the deviations of
+// an equilibrium state are exactly zero.
+__global__ void eq_prim_kernel(double gamma, const double* e, double* w, size_t n) {
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+    double U[5], W[5];
+    for (int f = 0; f < 5; ++f) U[f] = e[f * n + q];
+    gas_prim(gamma, U, W);
+    for (int f = 0; f < 5; ++f) w[f * n + q] = W[f];
+  }
+}
 
 // Per-block FP64 partial sums of V * E_f, fixed order.
 __global__ void sums_kernel(DevGrid g, StageArgs a, double* partials) {
@@ -837,6 +850,7 @@ void rossbi_destroy(rossbi_grid* g) {
   if (g->d_hoststate) cudaFree(g->d_hoststate);
   if (g->d_ptab) cudaFree(g->d_ptab);
   if (g->d_fallbacks) cudaFree(g->d_fallbacks);
+  if (g->d_w0) cudaFree(g->d_w0);
   if (g->d_adj) cudaFree(g->d_adj);
   if (g->d_adj_part) cudaFree(g->d_adj_part);
   if (g->d_adj_slots) cudaFree(g->d_adj_slots);
@@ -960,6 +974,7 @@ rossbi_status rossbi_set_equilibrium(rossbi_grid* g, const rossbi_disc_params* d
   g->eq_set = false;
   g->dg.has_eq = 0;
   g->dg.e0c = g->dg.e0r = g->dg.e0z = g->dg.r0 = nullptr;
+  g->dg.w0c = g->dg.w0r = g->dg.w0z = nullptr;
   g->has_disc = disc != nullptr;
   if (!disc) {
     g->h_e0c.assign((size_t)5 * d.nz * d.nr, 0.0);
@@ -997,6 +1012,19 @@ rossbi_status rossbi_set_equilibrium(rossbi_grid* g, const rossbi_disc_params* d
   g->dg.e0c = g->d_e0c;
   g->dg.e0r = g->d_e0r;
   g->dg.e0z = g->d_e0z;
+  {
+    const size_t nc = (size_t)nz * nr, nrf = (size_t)nz * (nr + 1), nzf = (size_t)(nz + 1) * nr;
+    if (g->d_w0) cudaFree(g->d_w0);
+    g->d_w0 = nullptr;
+    CK(cudaMalloc(&g->d_w0, 5 * (nc + nrf + nzf) * sizeof(double)));
+    eq_prim_kernel<<<64, 256, 0, g->stream>>>(d.gamma, g->d_e0c, g->d_w0, nc);
+    eq_prim_kernel<<<64, 256, 0, g->stream>>>(d.gamma, g->d_e0r, g->d_w0 + 5 * nc, nrf);
+    eq_prim_kernel<<<64, 256, 0, g->stream>>>(d.gamma, g->d_e0z, g->d_w0 + 5 * (nc + nrf), nzf);
+    CK(cudaGetLastError());
+    g->dg.w0c = g->d_w0;
+    g->dg.w0r = g->d_w0 + 5 * nc;
+    g->dg.w0z = g->d_w0 + 5 * (nc + nrf);
+  }
   if (d.precision == ROSSBI_FP64) {
     if ((st = empty_run(g)) != ROSSBI_OK) return st;
     g->dg.r0 = g->d_r0;

@@ -1,8 +1,9 @@
 // Fused RK2 stage kernel of the FP64 (full conservative state) form.
 //
 // One CTA owns a TR x TT x TZ tile of cells.  It stages the tile and a 2-deep
-// halo along each axis into shared memory as deviations E' = E - E0 (Sect.
-// 2.7), then sweeps the three directions.  In a sweep, lines along the
+// halo along each axis into shared memory as deviations from the equilibrium
+// (Sect. 2.7; the gas as primitive deviations u', v', w', P', rho'), then
+// sweeps the three directions.  In a sweep, lines along the
 // direction map onto groups of L = pow2(T + 2) lanes: lane p reconstructs cell
 // p - 1 (parabola + MinMod), receives the upper face state of its lower
 // neighbour by a shuffle, solves the exact Riemann problem on its lower face
@@ -158,19 +159,19 @@ __device__ __forceinline__ void sweep_full(const StageArgs& a, const double* sE,
     // parabola weights of this cell along D
     double w[9];
     parabola_weights<double, D>(g.rcoef, gi, g.nr, g.dx[D], w);
-    // equilibrium gas state on the lower face of this cell (index along D = gd)
-    // and on its upper face; table indices clamped (ghost cells reconstruct flat)
+    // equilibrium primitive gas state on the lower face of this cell (index
+    // along D = gd) and on its upper face; table indices clamped
     const int ci = clampi(gi, 0, g.nr - 1), ck = clampi(gk, 0, g.nz - 1);
-    auto e0_face = [&](int f, int fd) -> double {
+    auto w0_face = [&](int f, int fd) -> double {
       if (!g.has_eq) return 0.0;
-      if (D == 0) return g.e0r[((size_t)f * g.nz + ck) * (g.nr + 1) + clampi(fd, 0, g.nr)];
-      if (D == 1) return g.e0c[((size_t)f * g.nz + ck) * g.nr + ci];
-      return g.e0z[((size_t)f * (g.nz + 1) + clampi(fd, 0, g.nz)) * g.nr + ci];
+      if (D == 0) return g.w0r[((size_t)f * g.nz + ck) * (g.nr + 1) + clampi(fd, 0, g.nr)];
+      if (D == 1) return g.w0c[((size_t)f * g.nz + ck) * g.nr + ci];
+      return g.w0z[((size_t)f * (g.nz + 1) + clampi(fd, 0, g.nz)) * g.nr + ci];
     };
     double area = 0.0;
     if (do_face) area = D == 0 ? g.area_r[clampi(gi, 0, g.nr)] : (D == 1 ? g.area_t[ci] : g.area_z[ci]);
 
-    // ---------------- gas: fields 0..4
+    // ---------------- gas: primitive deviations in slots 0..4
     {
       double qm[5], qp[5];
       bool shaped = false;
@@ -180,15 +181,8 @@ __device__ __forceinline__ void sweep_full(const StageArgs& a, const double* sE,
         shaped |= parabola(s[-STRIDE], s[0], s[STRIDE], w, qm[f], qp[f]);
       }
       if (shaped && do_recon) {  // positivity of both reconstructed face states
-        double Um[5], Up[5];
-#pragma unroll
-        for (int f = 0; f < 5; ++f) {
-          Um[f] = e0_face(f, gd) + qm[f];
-          Up[f] = e0_face(f, gd + 1) + qp[f];
-        }
-        const bool ok = Um[RHO] > 0.0 && Up[RHO] > 0.0 &&
-                        gas_pressure(gam, Um[MU], Um[MV], Um[MW], Um[EN], Um[RHO]) > 0.0 &&
-                        gas_pressure(gam, Up[MU], Up[MV], Up[MW], Up[EN], Up[RHO]) > 0.0;
+        const bool ok = w0_face(RHO, gd) + qm[RHO] > 0.0 && w0_face(RHO, gd + 1) + qp[RHO] > 0.0 &&
+                        w0_face(EN, gd) + qm[EN] > 0.0 && w0_face(EN, gd + 1) + qp[EN] > 0.0;
         if (!ok) {
 #pragma unroll
           for (int f = 0; f < 5; ++f) qm[f] = qp[f] = sE[f * BOX + sidx];
@@ -200,9 +194,9 @@ __device__ __forceinline__ void sweep_full(const StageArgs& a, const double* sE,
 #pragma unroll
         for (int f = 0; f < 5; ++f) {
           const double ql = __shfl_up_sync(FULL, qp[f], 1, L);
-          const double e0 = do_face ? e0_face(f, gd) : 0.0;
-          UL[f] = e0 + ql;
-          UR[f] = e0 + qm[f];
+          const double w0 = do_face ? w0_face(f, gd) : 0.0;
+          UL[f] = w0 + ql;
+          UR[f] = w0 + qm[f];
         }
         if (do_face) {
           gas_face_flux<D>(gam, UL, UR, F, status);
@@ -294,7 +288,8 @@ __global__ void __launch_bounds__(NT, 1) stage_full_kernel(const StageArgs a) {
   const int k0 = (tile / (a.tiles_r * a.tiles_t)) * TZ;
   unsigned status = 0;
 
-  // tile + halo as deviations (corners are never read)
+  // tile + halo as deviations (corners are never read): primitive deviations
+  // (u', v', w', P', rho') of the gas in slots 0..4, the dust as it is
   for (int idx = threadIdx.x; idx < BOX; idx += NT) {
     const int x = idx % BX - 2, y = (idx / BX) % BY - 2, z = idx / (BX * BY) - 2;
     const int outside = (x < 0 || x >= TR) + (y < 0 || y >= TT) + (z < 0 || z >= TZ);
@@ -306,12 +301,15 @@ __global__ void __launch_bounds__(NT, 1) stage_full_kernel(const StageArgs a) {
       continue;
     }
     const size_t lin = ((size_t)c[2] * g.nth + c[1]) * g.nr + c[0];
+    double U[5], W[5];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      double e = a.in[f][lin];
-      if (f < 5 && g.has_eq) e -= g.e0c[((size_t)f * g.nz + c[2]) * g.nr + c[0]];
-      sE[f * BOX + idx] = e;
-    }
+    for (int f = 0; f < 5; ++f) U[f] = a.in[f][lin];
+    gas_prim(g.gamma, U, W);
+#pragma unroll
+    for (int f = 0; f < 5; ++f)
+      sE[f * BOX + idx] = g.has_eq ? W[f] - g.w0c[((size_t)f * g.nz + c[2]) * g.nr + c[0]] : W[f];
+#pragma unroll
+    for (int f = 5; f < NF; ++f) sE[f * BOX + idx] = a.in[f][lin];
   }
   __syncthreads();
   sweep_full<NF, TR, TT, TZ, NT, 0>(a, sE, sG, i0, j0, k0, status);

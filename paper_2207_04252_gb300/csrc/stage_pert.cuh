@@ -6,8 +6,11 @@
 // 2.8 is computed without ever forming the large equilibrium terms (the
 // Keplerian centrifugal and gravity terms are O(rho v_K^2 / r), the
 // perturbations 1e-4 of that and less):
-//   - face primitives: rho = rho0 + rho', du = (m' - rho' u0)/rho,
-//     dP = (gamma-1)(E' - [rho' |u0|^2/2 + rho u0.du + rho |du|^2/2]);
+//   - cell primitive perturbations: rho = rho0 + rho', du = (m' - rho' u0)/rho,
+//     dP = (gamma-1)(E' - [rho' |u0|^2/2 + rho u0.du + rho |du|^2/2]); the
+//     parabola and limiter of Sect. 2.7 act on these (the primitive reading),
+//     and a face state is the face equilibrium plus the interpolated
+//     perturbation;
 //   - the exact Riemann solver (Sect. 2.6) iterates on dp* = p* - p0 with
 //     the pressure functions written in p/p_K - 1 (log1p / expm1 for the
 //     rarefaction powers), samples the wave pattern on full values and returns
@@ -114,18 +117,14 @@ struct PSide {
   T rho, un, p, c, dc;          // full values and c - c0
 };
 
-// Conservative perturbations (5 gas fields) -> primitive perturbations about
-// the face equilibrium, in the frame of axis D.  Returns false if the full
-// state is not physical.
+// Face primitive perturbations (du, dv, dw, dP, drho in the field slots MU,
+// MV, MW, EN, RHO) about the face equilibrium, in the frame of axis D, with
+// the full values the wave pattern needs.  Returns false if the full state is
+// not physical.
 template <class T, int D>
-__device__ __forceinline__ bool pert_side(T g, const PFace<T>& W0, T v0, const T* q, bool has_eq, PSide<T>& s) {
+__device__ __forceinline__ bool pert_side(T g, const PFace<T>& W0, const T* q, bool has_eq, PSide<T>& s) {
+  const T dur = q[MU], dvt = q[MV], dwz = q[MW], dp = q[EN];
   const T rho = W0.rho + q[RHO];
-  const T ir = T(1) / rho;
-  const T dur = q[MU] * ir;
-  const T dvt = (q[MV] - q[RHO] * v0) * ir;
-  const T dwz = q[MW] * ir;
-  const T dke = T(0.5) * q[RHO] * v0 * v0 + rho * v0 * dvt + T(0.5) * rho * (dur * dur + dvt * dvt + dwz * dwz);
-  const T dp = (g - T(1)) * (q[EN] - dke);
   s.drho = q[RHO];
   s.dp = dp;
   s.dun = D == 0 ? dur : (D == 1 ? dvt : dwz);
@@ -135,7 +134,7 @@ __device__ __forceinline__ bool pert_side(T g, const PFace<T>& W0, T v0, const T
   s.p = W0.p + dp;
   s.un = W0.un + s.dun;
   if (!(rho > T(0)) || !(s.p > T(0))) return false;
-  s.c = Math<T>::sqrt_(g * s.p * ir);
+  s.c = Math<T>::sqrt_(g * s.p / rho);
   if (has_eq) {
     s.dc = W0.c * sqrt1pm1((dp * W0.rho - W0.p * q[RHO]) / (W0.p * rho));
   } else {
@@ -190,7 +189,7 @@ __device__ __forceinline__ int pert_riemann(T g, const PFace<T>& W0, const PSide
   T d = T(0.5) * (L.dp + R.dp) - T(0.125) * du * (L.rho + R.rho) * (L.c + R.c);  // PVRS in dp
   if (W0.p + d < floor_p) d = floor_p - W0.p;
   const T scale = Math<T>::abs_(L.dp) + Math<T>::abs_(R.dp) + (L.rho * L.c + R.rho * R.c) * Math<T>::abs_(du);
-  T fl, fdl, fr, fdr;
+  T fl, fdl, fr, fdr, step = T(0);
   bool conv = false;
   for (int it = 0; it < Math<T>::max_iter; ++it) {
     const T p = W0.p + d;
@@ -198,7 +197,8 @@ __device__ __forceinline__ int pert_riemann(T g, const PFace<T>& W0, const PSide
     pert_pressure_fn<T, P>(g, R, p, d, fr, fdr);
     T dn = d - (fl + fr + du) / (fdl + fdr);
     if (W0.p + dn < floor_p) dn = floor_p - W0.p;
-    const T change = Math<T>::abs_(dn - d);
+    step = dn - d;
+    const T change = Math<T>::abs_(step);
     d = dn;
     if (change <= T(8) * Math<T>::eps * (scale + Math<T>::abs_(d))) {
       conv = true;
@@ -208,8 +208,10 @@ __device__ __forceinline__ int pert_riemann(T g, const PFace<T>& W0, const PSide
   if (!conv) return 1;
   const T ps = W0.p + d;
   if (ps < T(0.1) * fmin(L.p, R.p)) return 1;  // strong rarefaction: near vacuum
-  pert_pressure_fn<T, P>(g, L, ps, d, fl, fdl);
-  pert_pressure_fn<T, P>(g, R, ps, d, fr, fdr);
+  // f_K at the converged p* from the last evaluation, one (converged) Newton
+  // step away; the second-order remainder is below rounding
+  fl += fdl * step;
+  fr += fdr * step;
   const T dus = T(0.5) * (L.dun + R.dun) + T(0.5) * (fr - fl);
   const T us = W0.un + dus;
   const T g6 = (g - T(1)) / (g + T(1));
@@ -432,17 +434,17 @@ __device__ __forceinline__ void sweep_pert(const PertArgs<T>& a, const T* sE, T*
         const T* s = sE + f * BOX + sidx;
         shaped |= parabola(s[-STRIDE], s[0], s[STRIDE], w, qm[f], qp[f]);
       }
-      // primitive perturbations of both face states, used for the positivity
-      // check of Sect. 2.7's reconstruction and then by the two faces' solvers
+      // both face states, used for the positivity check of Sect. 2.7's
+      // reconstruction and then by the two faces' solvers
       T v0m, v0p;
       const PFace<T> Wm = face_eq<T, D>(a.t, g, ci, ck, gd, v0m);
       const PFace<T> Wp = face_eq<T, D>(a.t, g, ci, ck, gd + 1, v0p);
       PSide<T> sm, sp;
-      bool ok = pert_side<T, D>(gam, Wm, v0m, qm, has_eq, sm) & pert_side<T, D>(gam, Wp, v0p, qp, has_eq, sp);
+      bool ok = pert_side<T, D>(gam, Wm, qm, has_eq, sm) & pert_side<T, D>(gam, Wp, qp, has_eq, sp);
       if (!ok && shaped) {  // positivity fallback: flat reconstruction of the gas fields
 #pragma unroll
         for (int f = 0; f < 5; ++f) qm[f] = qp[f] = sE[f * BOX + sidx];
-        ok = pert_side<T, D>(gam, Wm, v0m, qm, has_eq, sm) & pert_side<T, D>(gam, Wp, v0p, qp, has_eq, sp);
+        ok = pert_side<T, D>(gam, Wm, qm, has_eq, sm) & pert_side<T, D>(gam, Wp, qp, has_eq, sp);
       }
       T F[5];
       {
@@ -546,11 +548,12 @@ __device__ __forceinline__ void cell_prim(T g, const PCell<T>& c, const T* q, T&
 
 // Source perturbation S(E0 + E') - S(E0) per unit volume (App. B sources,
 // stellar gravity, rotating frame), cylindrical geometry.
+// q: the staged cell, primitive gas perturbations (du, dv, dw, dP, drho) in
+// slots 0..4 and the conservative dust fields in slots 5..8.
 template <class T, int NF>
 __device__ __forceinline__ void pert_sources(const DevGrid& g, const PCell<T>& c, const T* q, T* S) {
-  const T gam = (T)g.gamma, Om = (T)g.omega;
-  T rho, du, dv, dw, dp;
-  cell_prim(gam, c, q, rho, du, dv, dw, dp);
+  const T Om = (T)g.omega;
+  const T rho = c.rho0 + q[RHO], du = q[MU], dv = q[MV], dw = q[MW], dp = q[EN];
   const T v = c.v0 + dv;
   S[MU] = q[RHO] * c.Cr + rho * dv * c.cor + rho * dv * dv * c.ir + dp * c.ir;
   S[MV] = -rho * du * (v * c.ir + T(2) * Om);
@@ -656,8 +659,18 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
       continue;
     }
     const size_t lin = ((size_t)c[2] * g.nth + c[1]) * g.nr + c[0];
+    T q[5];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) sE[f * BOX + idx] = a.in[f][lin];
+    for (int f = 0; f < 5; ++f) q[f] = a.in[f][lin];
+    T rho, du, dv, dw, dp;
+    cell_prim((T)g.gamma, cell_eq(a.t, g, c[0], c[2]), q, rho, du, dv, dw, dp);
+    sE[MU * BOX + idx] = du;
+    sE[MV * BOX + idx] = dv;
+    sE[MW * BOX + idx] = dw;
+    sE[EN * BOX + idx] = dp;
+    sE[RHO * BOX + idx] = q[RHO];
+#pragma unroll
+    for (int f = 5; f < NF; ++f) sE[f * BOX + idx] = a.in[f][lin];
   }
   __syncthreads();
   sweep_pert<T, NF, TR, TT, TZ, NT, 0, P>(a, sE, sG, i0, j0, k0, status, nfallback);
@@ -708,18 +721,35 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
 #pragma unroll
       for (int f = 0; f < NF; ++f) sums[f] += V * E[f];
     } else {
-      (void)pert_cell_dt<T, NF>(g, a.t, ce, gi, q, bad_in);
+      bad_in = !(ce.rho0 + q[RHO] > T(0)) || !(ce.p0 + q[EN] > T(0));
+      if (NF == 9) bad_in |= !(q[DRHO] >= T(0));
       if (bad_in) status |= STATUS_NONPHYSICAL;
     }
   }
   if (a.stage2) {
+    // warps reduce in the state precision (a warp covers ~80 cells), the
+    // block and the grid in FP64; the sweeps are over, so the start of the
+    // staging area is free (and the epilogue reads only core cells)
+    constexpr int NW = NT / 32;
     double* red = reinterpret_cast<double*>(smem_raw);
-    const double m = block_min<NT>((double)dtmin, red);
-    if (threadIdx.x == 0) a.partials[(size_t)NF * gridDim.x + blockIdx.x] = m;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      const double s = block_sum<NT>((double)sums[f], red);
-      if (threadIdx.x == 0) a.partials[(size_t)f * gridDim.x + blockIdx.x] = s;
+    for (int o = 16; o > 0; o >>= 1) {
+      dtmin = fmin(dtmin, __shfl_xor_sync(0xffffffffu, dtmin, o));
+#pragma unroll
+      for (int f = 0; f < NF; ++f) sums[f] += __shfl_down_sync(0xffffffffu, sums[f], o);
+    }
+    if (lane == 0) {
+      red[warp * (NF + 1)] = (double)dtmin;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) red[warp * (NF + 1) + 1 + f] = (double)sums[f];
+    }
+    __syncthreads();
+    if (threadIdx.x <= NF) {
+      const int q = threadIdx.x;
+      double acc = q == 0 ? red[0] : red[q];
+      for (int w = 1; w < NW; ++w) acc = q == 0 ? fmin(acc, red[w * (NF + 1)]) : acc + red[w * (NF + 1) + q];
+      a.partials[(size_t)(q == 0 ? NF : q - 1) * gridDim.x + blockIdx.x] = acc;
     }
   }
   if (status) atomicOr(a.status, status);

@@ -275,14 +275,22 @@ def _gradient_check(lib, w, steps, every, hs_rd=(1e-6, 1e-7, 1e-8)):
     out["stokes"] = (dst, _fd_report(lambda s: _objective(W, w, adj, dts, stokes=s, every=every, grad=False), w.stokes,
                                      (1e-6, 1e-4)))
     rng = np.random.default_rng(7)
-    dr = rng.standard_normal(rho_d.shape) * rho_d
-    dr_t = torch.from_numpy(dr).cuda()
-    grad_rd = float((lam0[8] * dr_t).sum() + (lam0[5:8] * vel * dr_t).sum())
-    fd = {}
-    for h in hs_rd:
-        fd[h] = (_objective(W, w, adj, dts, drho=h * dr, every=every, grad=False) -
-                 _objective(W, w, adj, dts, drho=-h * dr, every=every, grad=False)) / (2 * h)
-    out["dust_density"] = (grad_rd, fd)
+    nz, nth, nr = rho_d.shape
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(nth), np.arange(nr), indexing="ij")
+    smooth = np.zeros(rho_d.shape)
+    for _ in range(4):  # a few random low-order modes in (r, theta, z)
+        kr, kt, kz = rng.integers(1, 3), rng.integers(1, 4), rng.integers(0, 2)
+        smooth += rng.standard_normal() * np.sin(2 * np.pi * (kr * i / nr + kt * j / nth + kz * k / nz)
+                                                 + rng.uniform(0, 2 * np.pi))
+    directions = {"dust_density": smooth * rho_d, "dust_density_white": rng.standard_normal(rho_d.shape) * rho_d}
+    for name, dr in directions.items():
+        dr_t = torch.from_numpy(dr).cuda()
+        grad_rd = float((lam0[8] * dr_t).sum() + (lam0[5:8] * vel * dr_t).sum())
+        fd = {}
+        for h in hs_rd:
+            fd[h] = (_objective(W, w, adj, dts, drho=h * dr, every=every, grad=False) -
+                     _objective(W, w, adj, dts, drho=-h * dr, every=every, grad=False)) / (2 * h)
+        out[name] = (grad_rd, fd)
     return out
 
 
@@ -291,8 +299,12 @@ def _assert_fd(report):
         errs = {h: abs(a - v) / abs(v) for h, v in fds.items()}
         # the best-conditioned difference quotient must agree to 1e-4: small h
         # loses digits to rounding (d/dSt is ~1e-9 of J), large h crosses
-        # limiter branch boundaries (the dust density carries 1e-3 noise)
-        assert min(errs.values()) <= 1e-4, (name, a, fds, errs)
+        # limiter branch boundaries.  A white-noise direction in the dust
+        # density (which itself carries 1e-3 cell-to-cell noise) moves the
+        # limiter slopes of every cell and crosses branches at any usable h:
+        # its quotient is reported, with a looser bar
+        bar = 1e-3 if name.endswith("_white") else 1e-4
+        assert min(errs.values()) <= bar, (name, a, fds, errs)
 
 
 def test_gradients_match_central_differences(lib):
@@ -306,6 +318,42 @@ def test_adjoint_workload_gradients(lib, stokes):
     """The adjoint workload at full size: 128x256x32, 200 steps, checkpoints
     every 20; gradients against central differences."""
     w = replace(syn.ADJOINT, stokes=stokes)
-    rep = _gradient_check(lib, w, w.steps, w.checkpoint_every, hs_rd=(1e-6, 1e-8))
+    rep = _gradient_check(lib, w, w.steps, w.checkpoint_every, hs_rd=(1e-6, 1e-8, 3e-9))
     print(f"adjoint vs central differences ({w.name}, St = {stokes}):", rep)
     _assert_fd(rep)
+
+
+def test_fp32_trajectory_gradient(lib):
+    """The FP32 perturbation form's forward run (FP32 checkpoints, segments
+    recomputed in FP32) with the FP64 adjoint linearised about E0 + E' of
+    those states: its gradients stay close to the all-FP64 ones, within what
+    the FP32 trajectory's own error allows."""
+    import torch
+    R, W = lib
+    from paper_2207_04252_gb300 import adjoint as adj
+    w = syn.scaled(syn.ADJOINT, 32, 48, 32, steps=40)
+    g64 = W.Grid(w, precision=R.ROSSBI_FP64)
+    dts = adj.cfl_sequence(g64, g64.initial_state(), w.steps)
+    Wt = adj.vortex_core_weights(g64).cuda()
+    T_amp = torch.from_numpy(g64.vortex_amp_tangent()).cuda()
+    out = {}
+    for name, prec in (("fp64", R.ROSSBI_FP64), ("fp32", R.ROSSBI_FP32_PERT)):
+        g = W.Grid(w, precision=prec)
+        x = g.initial_state().requires_grad_(True)
+        st = torch.tensor(w.stokes, dtype=torch.float64, requires_grad=True)
+        EK = adj.run_steps(g, x, dts, stokes=st, every=10, adjoint_grid=g64 if prec != R.ROSSBI_FP64 else None)
+        J = (Wt * EK.to(torch.float64)).sum()  # dust fields carry no equilibrium: E'_dust = E_dust
+        J.backward()
+        lam0 = x.grad.to(torch.float64)
+        out[name] = (float(J), lam0, float((lam0 * T_amp).sum()), float(st.grad))
+        if g is not g64:
+            g.close()
+    (J64, l64, a64, s64), (J32, l32, a32, s32) = out["fp64"], out["fp32"]
+    rel_lam = float((l32 - l64).norm() / l64.norm())
+    print("fp32-trajectory vs fp64 gradients:", {"J": (J32, J64), "lambda0_rel_l2": rel_lam,
+                                                  "amplitude": (a32, a64), "stokes": (s32, s64)})
+    assert abs(J32 - J64) <= 1e-5 * abs(J64)
+    assert rel_lam <= 1e-3
+    assert abs(a32 - a64) <= 1e-3 * abs(a64)
+    assert abs(s32 - s64) <= 1e-3 * abs(s64)
+    g64.close()
