@@ -310,6 +310,22 @@ def measure_adjoint(R, W, syn, torch, steps=4, warmup=3):
             "gradient_20_steps_over_forward_run": t_grad / t_run, "status": R.status_string(status)}
 
 
+def reduce_max(value, dist, device="cuda"):
+    """Largest of one float per rank (the job's time is its slowest rank's)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(cells_per_rank, steps, world, elapsed_ms):
+    """Whole-job cell-updates/s of `world` replicas that each advanced their
+    own grid of cells_per_rank cells by `steps` steps in elapsed_ms."""
+    return cells_per_rank * steps * world / (elapsed_ms * 1e-3)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -361,12 +377,9 @@ def run_ours(args):
     stage_ms, stage_launches = R.rossbi_profile_read(g.h)
     R.rossbi_profile_enable(g.h, False)
     status |= g.take_status()
-    if dist is not None:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = reduce_max(elapsed_ms, dist)
     clocks = sampler.summary()
-    value = w.ncell * args.steps * world / (elapsed_ms * 1e-3)
+    value = job_throughput(w.ncell, args.steps, world, elapsed_ms)
 
     # end to end through the public API with host buffers (copies inside the timed region)
     e2e_steps = max(1, min(args.steps, 3))
@@ -444,7 +457,18 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64-form and FP32-error side measurements")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="print only the adjoint cost measurement (adjoint workload, FP64)")
     args = ap.parse_args()
+    if args.adjoint_only:
+        import torch
+        import synthetic as syn
+        from paper_2207_04252_gb300 import build as lib_build
+        from paper_2207_04252_gb300 import rossbi as R
+        from paper_2207_04252_gb300 import workloads
+        lib_build.build()
+        print(json.dumps(measure_adjoint(R, workloads, syn, torch)), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
