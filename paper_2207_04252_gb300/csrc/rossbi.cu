@@ -870,9 +870,11 @@ rossbi_status rossbi_init_grid(const rossbi_grid_desc* desc, void* cuda_stream, 
   g->stream = (cudaStream_t)cuda_stream;
   g->nf = desc->n_dust ? 9 : 5;
   g->ncell = (size_t)desc->nr * desc->nth * desc->nz;
-  g->tiles_r = (desc->nr + F64_TR - 1) / F64_TR;
-  g->tiles_t = (desc->nth + F64_TT - 1) / F64_TT;
-  g->tiles_z = (desc->nz + F64_TZ - 1) / F64_TZ;
+  const bool pert = desc->precision != ROSSBI_FP64;  // tile of the form's stage kernel
+  const int tr = pert ? P32_TR : F64_TR, tt = pert ? P32_TT : F64_TT, tz = pert ? P32_TZ : F64_TZ;
+  g->tiles_r = (desc->nr + tr - 1) / tr;
+  g->tiles_t = (desc->nth + tt - 1) / tt;
+  g->tiles_z = (desc->nz + tz - 1) / tz;
   const rossbi_grid_desc& d = *desc;
   const int nr = d.nr;
   const double dy = (d.x1[1] - d.x0[1]) / d.nth;
