@@ -163,6 +163,120 @@ __device__ __forceinline__ int riemann_face(double g, double rl, double ul, doub
   return 1;
 }
 
+// The same solver for gamma = 7/5.  With z_K = (p / p_K)^(1/7) the pressure
+// functions, the star density behind a rarefaction and the fan state are
+// polynomials in z (exponents (gamma-1)/(2 gamma) = 1/7, 1/gamma = 5/7 ... in
+// units of 1/7).  Newton runs on z_L (p = p_L z_L^7, z_R = z_L k with
+// k = (p_L / p_R)^(1/7)), so a face takes two powers instead of two per
+// iteration; the iterates, the stopping test on p and the sampling are those
+// of riemann_face.
+__device__ __forceinline__ void pressure_fn_z(const RSide& K, double p, double z, double& f, double& fd) {
+  if (z <= 1.0) {  // rarefaction: f = 5 c (z - 1), df/dp = 1 / (rho c z^6)
+    const double z3 = z * z * z;
+    f = 5.0 * K.c * (z - 1.0);
+    fd = 1.0 / (K.rho * K.c * z3 * z3);
+  } else {         // shock: A = 2 / ((gamma + 1) rho), B = (gamma - 1) / (gamma + 1) p_K
+    const double A = 1.0 / (1.2 * K.rho);
+    const double B = K.p / 6.0;
+    const double q = sqrt(A / (B + p));
+    f = (p - K.p) * q;
+    fd = (1.0 - 0.5 * (p - K.p) / (B + p)) * q;
+  }
+}
+
+__device__ __forceinline__ void fan_state_g75(const RSide& K, double sgn, double& rho, double& u, double& p) {
+  const double cf = (K.c + sgn * 0.2 * K.u) / 1.2;
+  u = sgn * cf;
+  const double r = cf / K.c, r2 = r * r, r5 = r2 * r2 * r;
+  rho = K.rho * r5;
+  p = K.p * r5 * r2;
+}
+
+__device__ __forceinline__ int riemann_face_g75(double rl, double ul, double pl, double rr, double ur, double pr,
+                                                double& rho, double& u, double& p, unsigned& status) {
+  constexpr double g = 1.4;
+  const RSide L{rl, ul, pl, sqrt(g * pl / rl)};
+  const RSide R{rr, ur, pr, sqrt(g * pr / rr)};
+  if (5.0 * (L.c + R.c) <= ur - ul) {  // the waves open a vacuum
+    const double sl_star = ul + 5.0 * L.c;
+    const double sr_star = ur - 5.0 * R.c;
+    if (0.0 <= sl_star) {
+      if (0.0 <= ul - L.c) { rho = rl; u = ul; p = pl; }
+      else fan_state_g75(L, 1.0, rho, u, p);
+      return -1;
+    }
+    if (0.0 >= sr_star) {
+      if (0.0 >= ur + R.c) { rho = rr; u = ur; p = pr; }
+      else fan_state_g75(R, -1.0, rho, u, p);
+      return 1;
+    }
+    rho = u = p = 0.0;
+    return 0;
+  }
+  const double pfloor = 1e-8 * fmin(pl, pr);
+  double ps = fmax(pfloor, 0.5 * (pl + pr) - 0.125 * (ur - ul) * (rl + rr) * (L.c + R.c));
+  const double k = pow(pl / pr, 1.0 / 7.0);
+  double z = pow(ps / pl, 1.0 / 7.0);
+  double fl, fdl, fr, fdr, step = 0.0;
+  bool conv = false;
+  for (int it = 0; it < 100; ++it) {
+    pressure_fn_z(L, ps, z, fl, fdl);
+    pressure_fn_z(R, ps, z * k, fr, fdr);
+    // Newton on z_L: dp/dz_L = 7 p / z_L
+    double zn = z - (fl + fr + ur - ul) * z / (7.0 * ps * (fdl + fdr));
+    double z2 = zn * zn, z7 = z2 * z2 * z2 * zn;
+    double pn = pl * z7;
+    if (!(pn >= pfloor)) {
+      pn = pfloor;
+      zn = pow(pfloor / pl, 1.0 / 7.0);
+    }
+    const double change = 2.0 * fabs(pn - ps) / (pn + ps);
+    step = pn - ps;
+    ps = pn;
+    z = zn;
+    if (change <= 1e-12) { conv = true; break; }
+  }
+  if (!conv) status |= STATUS_RIEMANN;
+  fl += fdl * step;  // f_K at the converged p*, one Newton step from the last evaluation
+  fr += fdr * step;
+  const double us = 0.5 * (ul + ur) + 0.5 * (fr - fl);
+  if (0.0 <= us) {  // face lies left of the contact
+    if (ps <= pl) {
+      if (0.0 <= ul - L.c) { rho = rl; u = ul; p = pl; return -1; }
+      if (0.0 > us - L.c * z) {
+        const double z2 = z * z;
+        rho = rl * z2 * z2 * z; u = us; p = ps; return -1;
+      }
+      fan_state_g75(L, 1.0, rho, u, p);
+      return -1;
+    }
+    const double ratio = ps / pl;
+    if (0.0 <= ul - L.c * sqrt((g + 1.0) / (2.0 * g) * ratio + (g - 1.0) / (2.0 * g))) {
+      rho = rl; u = ul; p = pl; return -1;
+    }
+    const double g6 = (g - 1.0) / (g + 1.0);
+    rho = rl * (ratio + g6) / (ratio * g6 + 1.0); u = us; p = ps;
+    return -1;
+  }
+  if (ps > pr) {  // right shock
+    const double ratio = ps / pr;
+    if (0.0 >= ur + R.c * sqrt((g + 1.0) / (2.0 * g) * ratio + (g - 1.0) / (2.0 * g))) {
+      rho = rr; u = ur; p = pr; return 1;
+    }
+    const double g6 = (g - 1.0) / (g + 1.0);
+    rho = rr * (ratio + g6) / (ratio * g6 + 1.0); u = us; p = ps;
+    return 1;
+  }
+  if (0.0 >= ur + R.c) { rho = rr; u = ur; p = pr; return 1; }
+  const double zr = z * k;
+  if (0.0 <= us + R.c * zr) {
+    const double z2 = zr * zr;
+    rho = rr * z2 * z2 * zr; u = us; p = ps; return 1;
+  }
+  fan_state_g75(R, -1.0, rho, u, p);
+  return 1;
+}
+
 __device__ __forceinline__ double gas_pressure(double g, double mu, double mv, double mw, double en, double rho) {
   return (g - 1.0) * (en - 0.5 * (mu * mu + mv * mv + mw * mw) / rho);
 }
@@ -192,7 +306,8 @@ __device__ __forceinline__ void gas_face_flux(double g, const double* WL, const 
     return;
   }
   double rho, u, p;
-  const int side = riemann_face(g, rl, WL[n], pl, rr, WR[n], pr, rho, u, p, status);
+  const int side = g == 1.4 ? riemann_face_g75(rl, WL[n], pl, rr, WR[n], pr, rho, u, p, status)
+                            : riemann_face(g, rl, WL[n], pl, rr, WR[n], pr, rho, u, p, status);
   double ut1 = 0.0, ut2 = 0.0;
   if (side < 0) { ut1 = WL[t1]; ut2 = WL[t2]; }
   else if (side > 0) { ut1 = WR[t1]; ut2 = WR[t2]; }
