@@ -130,6 +130,16 @@ __device__ __forceinline__ J6 jpow(const J6& a, double e) {
   return r;
 }
 
+// a^e with its value v given (computed elsewhere, e.g. as a polynomial).
+__device__ __forceinline__ J6 jpow_v(const J6& a, double e, double v) {
+  J6 r;
+  r.v = v;
+  const double s = e * v / a.v;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) r.d[q] = s * a.d[q];
+  return r;
+}
+
 // ------------------------------------------------------------------ Riemann solution and its Jacobian
 struct JSide {
   J6 rho, u, p, c;
@@ -137,10 +147,12 @@ struct JSide {
 
 // f_K(p) at a fixed p (its tangent: the partials in the side's state) and the
 // value of df_K/dp; the value arithmetic is that of pressure_fn.
-__device__ __forceinline__ void pressure_fn_jac(double g, const JSide& K, double p, J6& f, double& fd) {
+// G75 (gamma = 7/5): zK = (p / p_K)^(1/7) is given.
+template <bool G75>
+__device__ __forceinline__ void pressure_fn_jac(double g, const JSide& K, double p, J6& f, double& fd, double zK) {
   if (p <= K.p.v) {
     const J6 prat = jc(p) / K.p;
-    const J6 e = jpow(prat, (g - 1.0) / (2.0 * g));
+    const J6 e = G75 ? jpow_v(prat, 1.0 / 7.0, zK) : jpow(prat, (g - 1.0) / (2.0 * g));
     f = 2.0 * K.c / (g - 1.0) * (e - 1.0);
     fd = e.v / (prat.v * K.rho.v * K.c.v);
   } else {
@@ -152,16 +164,26 @@ __device__ __forceinline__ void pressure_fn_jac(double g, const JSide& K, double
   }
 }
 
+template <bool G75>
 __device__ __forceinline__ void fan_jac(double g, const JSide& K, double sgn, J6& rho, J6& u, J6& p) {
   const J6 cf = 2.0 / (g + 1.0) * (K.c + sgn * 0.5 * (g - 1.0) * K.u);
   u = sgn * cf;
   const J6 ratio = cf / K.c;
-  rho = K.rho * jpow(ratio, 2.0 / (g - 1.0));
-  p = K.p * jpow(ratio, 2.0 * g / (g - 1.0));
+  if (G75) {  // exponents 5 and 7
+    const double r = ratio.v, r2 = r * r, r5 = r2 * r2 * r;
+    rho = K.rho * jpow_v(ratio, 5.0, r5);
+    p = K.p * jpow_v(ratio, 7.0, r5 * r2);
+  } else {
+    rho = K.rho * jpow(ratio, 2.0 / (g - 1.0));
+    p = K.p * jpow(ratio, 2.0 * g / (g - 1.0));
+  }
 }
 
-// The face state of riemann_face together with its Jacobian in the six
-// primitive inputs.  Branch decisions are taken on the same values.
+// The face state of riemann_face (riemann_face_g75 for G75) together with its
+// Jacobian in the six primitive inputs.  Branch decisions are taken on the
+// same values; for gamma = 7/5 the powers come from z = (p/p_L)^(1/7) as in
+// the forward solver.
+template <bool G75>
 __device__ __noinline__ int riemann_jac(double g, double rl, double ul, double pl, double rr, double ur, double pr,
                                         J6& rho, J6& u, J6& p, unsigned& status) {
   const JSide L{jv(rl, 0), jv(ul, 1), jv(pl, 2), jsqrt(g * jv(pl, 2) / jv(rl, 0))};
@@ -172,37 +194,61 @@ __device__ __noinline__ int riemann_jac(double g, double rl, double ul, double p
     const double sr_star = ur - 2.0 * cr / (g - 1.0);
     if (0.0 <= sl_star) {
       if (0.0 <= ul - cl) { rho = L.rho; u = L.u; p = L.p; }
-      else fan_jac(g, L, 1.0, rho, u, p);
+      else fan_jac<G75>(g, L, 1.0, rho, u, p);
       return -1;
     }
     if (0.0 >= sr_star) {
       if (0.0 >= ur + cr) { rho = R.rho; u = R.u; p = R.p; }
-      else fan_jac(g, R, -1.0, rho, u, p);
+      else fan_jac<G75>(g, R, -1.0, rho, u, p);
       return 1;
     }
     rho = u = p = jc(0.0);
     return 0;
   }
-  // Newton on the star pressure, values only (same arithmetic as riemann_face)
+  // Newton on the star pressure, values only (same arithmetic as the forward)
   const RSide Lv{rl, ul, pl, cl}, Rv{rr, ur, pr, cr};
   const double pfloor = 1e-8 * fmin(pl, pr);
   double ps = fmax(pfloor, 0.5 * (pl + pr) - 0.125 * (ur - ul) * (rl + rr) * (cl + cr));
   bool conv = false;
-  for (int it = 0; it < 100; ++it) {
-    double fl, fdl, fr, fdr;
-    pressure_fn(g, Lv, ps, fl, fdl);
-    pressure_fn(g, Rv, ps, fr, fdr);
-    const double pn = fmax(pfloor, ps - (fl + fr + ur - ul) / (fdl + fdr));
-    const double change = 2.0 * fabs(pn - ps) / (pn + ps);
-    ps = pn;
-    if (change <= 1e-12) { conv = true; break; }
+  double zl = 0.0, zr = 0.0;
+  if (G75) {
+    const double k = pow(pl / pr, 1.0 / 7.0);
+    double z = pow(ps / pl, 1.0 / 7.0);
+    for (int it = 0; it < 100; ++it) {
+      double fl, fdl, fr, fdr;
+      pressure_fn_z(Lv, ps, z, fl, fdl);
+      pressure_fn_z(Rv, ps, z * k, fr, fdr);
+      double zn = z - (fl + fr + ur - ul) * z / (7.0 * ps * (fdl + fdr));
+      double z2 = zn * zn, z7 = z2 * z2 * z2 * zn;
+      double pn = pl * z7;
+      if (!(pn >= pfloor)) {
+        pn = pfloor;
+        zn = pow(pfloor / pl, 1.0 / 7.0);
+      }
+      const double change = 2.0 * fabs(pn - ps) / (pn + ps);
+      ps = pn;
+      z = zn;
+      if (change <= 1e-12) { conv = true; break; }
+    }
+    zl = z;
+    zr = z * k;
+  } else {
+    for (int it = 0; it < 100; ++it) {
+      double fl, fdl, fr, fdr;
+      pressure_fn(g, Lv, ps, fl, fdl);
+      pressure_fn(g, Rv, ps, fr, fdr);
+      const double pn = fmax(pfloor, ps - (fl + fr + ur - ul) / (fdl + fdr));
+      const double change = 2.0 * fabs(pn - ps) / (pn + ps);
+      ps = pn;
+      if (change <= 1e-12) { conv = true; break; }
+    }
   }
   if (!conv) status |= STATUS_RIEMANN;
   // implicit function theorem: f_L(p*) + f_R(p*) + u_R - u_L = 0
   J6 FL, FR;
   double dl, dr;
-  pressure_fn_jac(g, L, ps, FL, dl);
-  pressure_fn_jac(g, R, ps, FR, dr);
+  pressure_fn_jac<G75>(g, L, ps, FL, dl, zl);
+  pressure_fn_jac<G75>(g, R, ps, FR, dr, zr);
   J6 PS = jc(ps);
   if (ps == pfloor) {
     PS = 1e-8 * (pl <= pr ? L.p : R.p);
@@ -221,10 +267,16 @@ __device__ __noinline__ int riemann_jac(double g, double rl, double ul, double p
     if (ps <= pl) {
       if (0.0 <= ul - cl) { rho = L.rho; u = L.u; p = L.p; return -1; }
       const J6 ratio = PS / L.p;
-      if (0.0 > US.v - cl * pow(ratio.v, (g - 1.0) / (2.0 * g))) {
-        rho = L.rho * jpow(ratio, 1.0 / g); u = US; p = PS; return -1;
+      if (0.0 > US.v - cl * (G75 ? zl : pow(ratio.v, (g - 1.0) / (2.0 * g)))) {
+        if (G75) {
+          const double z2 = zl * zl;
+          rho = L.rho * jpow_v(ratio, 5.0 / 7.0, z2 * z2 * zl);
+        } else {
+          rho = L.rho * jpow(ratio, 1.0 / g);
+        }
+        u = US; p = PS; return -1;
       }
-      fan_jac(g, L, 1.0, rho, u, p);
+      fan_jac<G75>(g, L, 1.0, rho, u, p);
       return -1;
     }
     const J6 ratio = PS / L.p;
@@ -246,10 +298,16 @@ __device__ __noinline__ int riemann_jac(double g, double rl, double ul, double p
   }
   if (0.0 >= ur + cr) { rho = R.rho; u = R.u; p = R.p; return 1; }
   const J6 ratio = PS / R.p;
-  if (0.0 <= US.v + cr * pow(ratio.v, (g - 1.0) / (2.0 * g))) {
-    rho = R.rho * jpow(ratio, 1.0 / g); u = US; p = PS; return 1;
+  if (0.0 <= US.v + cr * (G75 ? zr : pow(ratio.v, (g - 1.0) / (2.0 * g)))) {
+    if (G75) {
+      const double z2 = zr * zr;
+      rho = R.rho * jpow_v(ratio, 5.0 / 7.0, z2 * z2 * zr);
+    } else {
+      rho = R.rho * jpow(ratio, 1.0 / g);
+    }
+    u = US; p = PS; return 1;
   }
-  fan_jac(g, R, -1.0, rho, u, p);
+  fan_jac<G75>(g, R, -1.0, rho, u, p);
   return 1;
 }
 
@@ -265,7 +323,8 @@ __device__ __noinline__ void gas_flux_vjp(double g, const double* WL, const doub
   const double rl = WL[RHO], rr = WR[RHO], pl = WL[EN], pr = WR[EN];
   if (!(rl > 0.0) || !(rr > 0.0) || !(pl > 0.0) || !(pr > 0.0)) return;  // zero flux
   J6 Rs, Us, Ps;
-  const int side = riemann_jac(g, rl, WL[n], pl, rr, WR[n], pr, Rs, Us, Ps, status);
+  const int side = g == 1.4 ? riemann_jac<true>(g, rl, WL[n], pl, rr, WR[n], pr, Rs, Us, Ps, status)
+                            : riemann_jac<false>(g, rl, WL[n], pl, rr, WR[n], pr, Rs, Us, Ps, status);
   double ut1 = 0.0, ut2 = 0.0;
   if (side < 0) { ut1 = WL[t1]; ut2 = WL[t2]; }
   else if (side > 0) { ut1 = WR[t1]; ut2 = WR[t2]; }

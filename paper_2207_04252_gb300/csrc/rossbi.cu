@@ -744,11 +744,23 @@ rossbi_status adjoint_step(rossbi_grid* g, void* const* state, double dt, const 
   if (st != ROSSBI_OK) return st;
   const size_t nfc = (size_t)g->nf * g->ncell;
   if (!g->d_adj) {
-    g->adj_blocks = (int)std::min<size_t>((g->ncell + ADJ_PT_NT - 1) / ADJ_PT_NT, 2048);
-    CK(cudaMalloc(&g->d_adj, 5 * nfc * sizeof(double)));
-    CK(cudaMalloc(&g->d_adj_part, 2 * (size_t)g->adj_blocks * sizeof(double)));
-    CK(cudaMalloc(&g->d_adj_slots, 2 * sizeof(double)));
-    CK(cudaMemsetAsync(g->d_adj_slots, 0, 2 * sizeof(double), g->stream));
+    // all three buffers or none, so that a failed allocation leaves no half state
+    const int nb = (int)std::min<size_t>((g->ncell + ADJ_PT_NT - 1) / ADJ_PT_NT, 2048);
+    double *adj = nullptr, *part = nullptr, *slots = nullptr;
+    cudaError_t e = cudaMalloc(&adj, 5 * nfc * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&part, 2 * (size_t)nb * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&slots, 2 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemsetAsync(slots, 0, 2 * sizeof(double), g->stream);
+    if (e != cudaSuccess) {
+      cudaFree(adj);
+      cudaFree(part);
+      cudaFree(slots);
+      return e == cudaErrorMemoryAllocation ? ROSSBI_ERR_OOM : ROSSBI_ERR_CUDA;
+    }
+    g->d_adj = adj;
+    g->d_adj_part = part;
+    g->d_adj_slots = slots;
+    g->adj_blocks = nb;
   }
   double *Y1[9], *Es[9], *Y2[9], *Mu[9], *LamS[9];
   for (int f = 0; f < g->nf; ++f) {

@@ -648,29 +648,65 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
   const int k0 = (tile / (a.tiles_r * a.tiles_t)) * TZ;
   unsigned status = 0, nfallback = 0;
 
-  for (int idx = threadIdx.x; idx < BOX; idx += NT) {
-    const int x = idx % BX - 2, y = (idx / BX) % BY - 2, z = idx / (BX * BY) - 2;
-    const int outside = (x < 0 || x >= TR) + (y < 0 || y >= TT) + (z < 0 || z >= TZ);
-    if (outside > 1) continue;
-    int c[3] = {i0 + x, j0 + y, k0 + z};
-    if (!resolve_cell(g, c)) {
+  // staging in batches of CH cells per thread: every load of a batch is
+  // issued before any of them is used (memory-level parallelism)
+  {
+    constexpr int NIT = (BOX + NT - 1) / NT;
+    constexpr int CH = 2;
+    for (int it0 = 0; it0 < NIT; it0 += CH) {
+      T v[CH][NF], e0[CH][3];
+      int st[CH];  // 0: nothing, 1: equilibrium ghost (zero), 2: loaded
 #pragma unroll
-      for (int f = 0; f < NF; ++f) sE[f * BOX + idx] = T(0);
-      continue;
+      for (int u = 0; u < CH; ++u) {
+        const int idx = threadIdx.x + (it0 + u) * NT;
+        st[u] = 0;
+        if (it0 + u < NIT && idx < BOX) {
+          const int x = idx % BX - 2, y = (idx / BX) % BY - 2, z = idx / (BX * BY) - 2;
+          const int outside = (x < 0 || x >= TR) + (y < 0 || y >= TT) + (z < 0 || z >= TZ);
+          if (outside <= 1) {
+            int c[3] = {i0 + x, j0 + y, k0 + z};
+            if (!resolve_cell(g, c)) {
+              st[u] = 1;
+            } else {
+              st[u] = 2;
+              const size_t lin = ((size_t)c[2] * g.nth + c[1]) * g.nr + c[0];
+#pragma unroll
+              for (int f = 0; f < NF; ++f) v[u][f] = a.in[f][lin];
+              if (g.has_eq) {
+                const size_t sz = (size_t)g.nz * g.nr, o = (size_t)c[2] * g.nr + c[0];
+                e0[u][0] = a.t.cen[o];
+                e0[u][1] = a.t.cen[sz + o];
+                e0[u][2] = a.t.cen[2 * sz + o];
+              } else {
+                e0[u][0] = e0[u][1] = e0[u][2] = T(0);
+              }
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        const int idx = threadIdx.x + (it0 + u) * NT;
+        if (st[u] == 1) {
+#pragma unroll
+          for (int f = 0; f < NF; ++f) sE[f * BOX + idx] = T(0);
+        } else if (st[u] == 2) {
+          PCell<T> ce;
+          ce.rho0 = e0[u][0];
+          ce.v0 = e0[u][1];
+          ce.p0 = e0[u][2];
+          T rho, du, dv, dw, dp;
+          cell_prim((T)g.gamma, ce, v[u], rho, du, dv, dw, dp);
+          sE[MU * BOX + idx] = du;
+          sE[MV * BOX + idx] = dv;
+          sE[MW * BOX + idx] = dw;
+          sE[EN * BOX + idx] = dp;
+          sE[RHO * BOX + idx] = v[u][RHO];
+#pragma unroll
+          for (int f = 5; f < NF; ++f) sE[f * BOX + idx] = v[u][f];
+        }
+      }
     }
-    const size_t lin = ((size_t)c[2] * g.nth + c[1]) * g.nr + c[0];
-    T q[5];
-#pragma unroll
-    for (int f = 0; f < 5; ++f) q[f] = a.in[f][lin];
-    T rho, du, dv, dw, dp;
-    cell_prim((T)g.gamma, cell_eq(a.t, g, c[0], c[2]), q, rho, du, dv, dw, dp);
-    sE[MU * BOX + idx] = du;
-    sE[MV * BOX + idx] = dv;
-    sE[MW * BOX + idx] = dw;
-    sE[EN * BOX + idx] = dp;
-    sE[RHO * BOX + idx] = q[RHO];
-#pragma unroll
-    for (int f = 5; f < NF; ++f) sE[f * BOX + idx] = a.in[f][lin];
   }
   __syncthreads();
   sweep_pert<T, NF, TR, TT, TZ, NT, 0, P>(a, sE, sG, i0, j0, k0, status, nfallback);
