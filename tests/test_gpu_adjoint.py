@@ -108,6 +108,35 @@ def test_adjoint_single_cell_columns(lib, name, mk, presteps):
             assert abs(adj[f, k, j, i] - ref) <= 1e-11 * norm, (f, (k, j, i), adj[f, k, j, i], ref)
 
 
+@pytest.mark.parametrize("n,bc", [((27, 13, 5), syn.BC_OUTFLOW), ((5, 3, 7), syn.BC_PERIODIC),
+                                  ((1, 1, 1), syn.BC_PERIODIC)])
+def test_adjoint_box_bifluid(lib, n, bc):
+    """Bi-fluid Box (drag, no sources): zero-gradient and periodic ghosts on
+    ragged and one-cell grids; transpose identity and the columns of the
+    boundary cells."""
+    from tests.test_gpu_parity import _box, _smooth_state
+    R, W = lib
+    w = _box(n, n_dust=1, stokes=0.07, bc=bc)
+    o = oracle.Oracle(w)
+    rng = np.random.default_rng(5)
+    E = jitter(_smooth_state(w, 9), w.gamma, rng, 1e-3)
+    dt = o.cfl_dt(E)
+    scale = np.abs(E).mean(axis=(1, 2, 3), keepdims=True)
+    lam = rng.standard_normal(E.shape) / scale
+    delta = rng.standard_normal(E.shape) * scale
+    _, t = o.step_tlm(E, delta, dt)
+    adj, _ = _gpu_adjoint(R, W, w, E, dt, lam)
+    lhs, rhs = float((lam * t).sum()), float((adj * delta).sum())
+    assert abs(lhs - rhs) <= TOL_DOT * float(np.abs(lam * t).sum()), (lhs, rhs)
+    for (k, j, i) in {(0, 0, 0), (w.nz - 1, w.nth - 1, w.nr - 1), (0, 0, w.nr - 1)}:
+        for f in range(9):
+            d = np.zeros_like(E)
+            d[f, k, j, i] = 1.0
+            _, tc = o.step_tlm(E, d, dt)
+            ref = float((lam * tc).sum())
+            assert abs(adj[f, k, j, i] - ref) <= 1e-11 * (float(np.abs(lam * tc).sum()) + 1e-300), (f, (k, j, i))
+
+
 @pytest.mark.parametrize("law", [0, 1])
 def test_adjoint_stokes_derivative(lib, law):
     R, W = lib
@@ -357,3 +386,27 @@ def test_fp32_trajectory_gradient(lib):
     assert abs(a32 - a64) <= 1e-3 * abs(a64)
     assert abs(s32 - s64) <= 1e-3 * abs(s64)
     g64.close()
+
+
+def test_adjoint_dstokes_total_and_errors(lib):
+    """The running d/dSt total adds every call's value and resets on request;
+    a non-positive or non-finite dt is refused before anything runs."""
+    import torch
+    R, W = lib
+    w, o, E, dt, scale, rng = _setup(lambda: syn.scaled(syn.VORTEX, 16, 12, 16), 0, seed=9)
+    g = W.Grid(w, precision=R.ROSSBI_FP64)
+    s = torch.from_numpy(E).cuda()
+    lam = torch.from_numpy(rng.standard_normal(E.shape) / scale).cuda()
+    R.rossbi_adjoint_dstokes(g.h, reset=True)
+    a = g.adjoint_step(s, dt, lam.clone(), want_dstokes=True)
+    b = g.adjoint_step(s, dt, lam.clone(), want_dstokes=True)
+    assert a == b and a != 0.0
+    assert R.rossbi_adjoint_dstokes(g.h, reset=True) == a + b
+    assert R.rossbi_adjoint_dstokes(g.h) == 0.0
+    before = lam.clone()
+    for bad in (0.0, -dt, float("nan"), float("inf")):
+        with pytest.raises(R.RossbiError) as e:
+            g.adjoint_step(s, bad, lam)
+        assert e.value.code == R.ROSSBI_ERR_ARG
+    assert bool((lam == before).all())
+    g.close()
