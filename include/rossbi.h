@@ -132,7 +132,8 @@ rossbi_status rossbi_cfl_dt(rossbi_grid* g, const void* const* state, double* dt
  * perturbation forms G - R0 is evaluated directly as G(E0 + E') - G(E0).
  *   state   : nfields caller-owned device pointers, read and overwritten.
  *   scratch : nfields device pointers of the same type and size for E*, or
- *             NULL to use a buffer the library allocates on first use.
+ *             NULL to use a buffer the library allocates on first use; none
+ *             may be one of the state pointers (ROSSBI_ERR_ARG).
  *   dt      : > 0 uses this step; 0 uses the device-resident step left by the
  *             previous rossbi_step or rossbi_cfl_dt (no host round trip).
  *   dust    : drag parameters; required when n_dust = 1, ignored otherwise.
@@ -186,7 +187,8 @@ rossbi_status rossbi_step_noalloc(rossbi_grid* g, void* const* state, double dt,
  *   dust    : drag parameters (required when n_dust = 1).
  *   lam_np1 : nfields device pointers, the cotangent of E^{n+1} (FP64).
  *   lam_n   : nfields device pointers receiving the cotangent of E^n; may
- *             be the same buffers as lam_np1 (in place).
+ *             be the same buffers as lam_np1 (in place).  Neither cotangent
+ *             may share a pointer with state_n (ROSSBI_ERR_ARG).
  *   dparam  : if not NULL, receives += lam_np1 . dE^{n+1}/dSt (the Stokes
  *             number of dust), and the call synchronises and reports the
  *             status word.  The same value is always added to a device-side

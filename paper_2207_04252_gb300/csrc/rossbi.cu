@@ -237,16 +237,30 @@ __global__ void __launch_bounds__(RED_NT) reduce_partials_kernel(const double* p
   }
 }
 
+// Raises a kernel's dynamic shared-memory limit once per device (the
+// attribute belongs to the current device's context); `done` is the calling
+// site's own flag word, one bit per device id < 64.
+template <class K>
+rossbi_status set_smem_once(K kern, size_t smem, unsigned long long& done) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+  if (bit && (done & bit)) return ROSSBI_OK;
+  CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  done |= bit;
+  return ROSSBI_OK;
+}
+
 template <int NF>
 rossbi_status launch_stage_f64(rossbi_grid* g, const StageArgs& a, int nblocks) {
   constexpr int BOX = (F64_TR + 4) * (F64_TT + 4) * (F64_TZ + 4);
   constexpr int NCORE = F64_TR * F64_TT * F64_TZ;
   constexpr size_t smem = (size_t)NF * (BOX + NCORE) * sizeof(double);
   auto kern = stage_full_kernel<NF, F64_TR, F64_TT, F64_TZ, F64_NT>;
-  static bool attr = false;
-  if (!attr) {
-    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
+  {
+    static unsigned long long done = 0;
+    const rossbi_status sa = set_smem_once(kern, smem, done);
+    if (sa != ROSSBI_OK) return sa;
   }
   kern<<<nblocks, F64_NT, smem, g->stream>>>(a);
   CK(cudaGetLastError());
@@ -295,10 +309,10 @@ rossbi_status launch_pert_nf(rossbi_grid* g, const PertArgs<T>& a, int nblocks) 
   constexpr int BOX = (TR + 4) * (TT + 4) * (TZ + 4), NCORE = TR * TT * TZ;
   constexpr size_t smem = (size_t)NF * (BOX + NCORE) * sizeof(T);
   auto kern = stage_pert_kernel<T, NF, TR, TT, TZ, NT, MINB, P>;
-  static bool attr = false;
-  if (!attr) {
-    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
+  {
+    static unsigned long long done = 0;
+    const rossbi_status sa = set_smem_once(kern, smem, done);
+    if (sa != ROSSBI_OK) return sa;
   }
   kern<<<nblocks, NT, smem, g->stream>>>(a);
   CK(cudaGetLastError());
@@ -563,6 +577,8 @@ rossbi_status prepare_step(rossbi_grid* g, void* const* state, void* const* scra
   if (scratch) {
     for (int f = 0; f < g->nf; ++f) {
       if (!scratch[f]) return ROSSBI_ERR_ARG;
+      for (int h = 0; h < g->nf; ++h)
+        if (scratch[f] == state[h]) return ROSSBI_ERR_ARG;  // E* must not overwrite E^n
       sc[f] = scratch[f];
     }
   } else {
@@ -661,10 +677,10 @@ rossbi_status launch_adj_flux(rossbi_grid* g, const AdjFluxArgs& a) {
   constexpr size_t smem = adj_flux_smem_doubles<NF, ADJ_L, ADJ_NL>() * sizeof(double);
   constexpr int T = ADJ_L - 4;
   auto kern = adj_flux_kernel<NF, D, ADJ_L, ADJ_NL>;
-  static bool attr = false;
-  if (!attr) {
-    CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
+  {
+    static unsigned long long done = 0;
+    const rossbi_status sa = set_smem_once(kern, smem, done);
+    if (sa != ROSSBI_OK) return sa;
   }
   const rossbi_grid_desc& d = g->desc;
   const long nd = D == 0 ? d.nr : (D == 1 ? d.nth : d.nz);
@@ -736,8 +752,11 @@ rossbi_status adjoint_step(rossbi_grid* g, void* const* state, double dt, const 
   if (!g->eq_set || !state || !lam_np1 || !lam_n) return ROSSBI_ERR_ARG;
   if (g->desc.precision != ROSSBI_FP64) return ROSSBI_ERR_UNSUPPORTED;
   if (!(dt > 0.0) || !std::isfinite(dt)) return ROSSBI_ERR_ARG;
-  for (int f = 0; f < g->nf; ++f)
+  for (int f = 0; f < g->nf; ++f) {
     if (!state[f] || !lam_np1[f] || !lam_n[f]) return ROSSBI_ERR_ARG;
+    for (int h = 0; h < g->nf; ++h)  // the cotangents must not overwrite E^n (lam_n may be lam_np1)
+      if (lam_np1[f] == state[h] || lam_n[f] == state[h]) return ROSSBI_ERR_ARG;
+  }
   if (g->nf == 9 && !dust) return ROSSBI_ERR_ARG;
   DragArgs drag;
   rossbi_status st = drag_args(g, dust, drag);

@@ -409,4 +409,33 @@ def test_adjoint_dstokes_total_and_errors(lib):
             g.adjoint_step(s, bad, lam)
         assert e.value.code == R.ROSSBI_ERR_ARG
     assert bool((lam == before).all())
+    with pytest.raises(R.RossbiError) as e:  # the cotangent must not be the state
+        g.adjoint_step(s, dt, s)
+    assert e.value.code == R.ROSSBI_ERR_ARG
+    g.close()
+
+
+@pytest.mark.parametrize("snapshots", [0, 2, 11])
+def test_revolve_schedule_gives_the_same_gradient(lib, snapshots):
+    """Binomial checkpointing recomputes the same (deterministic) states, so the
+    gradients are bit-identical to the periodic schedule's; the number of
+    recomputed forward steps is the schedule's own."""
+    import torch
+    R, W = lib
+    from paper_2207_04252_gb300 import adjoint as adj
+    w = syn.scaled(syn.VORTEX, 29, 13, 32)
+    g = W.Grid(w, precision=R.ROSSBI_FP64)
+    E0 = g.initial_state()
+    dts = adj.cfl_sequence(g, E0, 12)
+    lam = adj.vortex_core_weights(g).cuda()
+    grads = []
+    for kw in ({"every": 4}, {"snapshots": snapshots}):
+        x = E0.clone().requires_grad_(True)
+        st = torch.tensor(w.stokes, dtype=torch.float64, requires_grad=True)
+        (lam * adj.run_steps(g, x, dts, stokes=st, **kw)).sum().backward()
+        grads.append((x.grad.clone(), float(st.grad), adj._last_backward["forward_steps"]))
+    (g_per, s_per, n_per), (g_rev, s_rev, n_rev) = grads
+    assert bool((g_per == g_rev).all()) and s_per == s_rev
+    assert n_per == 12 - 3
+    assert n_rev == adj.revolve_forward_steps(12, snapshots)
     g.close()

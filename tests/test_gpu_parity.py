@@ -296,3 +296,8 @@ def test_invalid_arguments(lib):
         g.step(s, dt=-1.0)
     with pytest.raises(R.RossbiError):
         R.rossbi_step(g.h, s, None, float("nan"), None, False)
+    before = s.clone()
+    with pytest.raises(R.RossbiError) as e:  # scratch must not be the state
+        R.rossbi_step(g.h, s, s, 1e-4, None, False)
+    assert e.value.code == R.ROSSBI_ERR_ARG
+    assert bool((s == before).all())
