@@ -9,8 +9,9 @@
  *   - cell-centred finite volumes on the conservative variables (Sect. 2.2,
  *     App. B order: rho u, rho v, rho w, E, rho; dust: rho_d u_d, rho_d v_d,
  *     rho_d w_d, rho_d),
- *   - parabolic reconstruction of the deviation from the equilibrium with a
- *     MinMod limiter (Sect. 2.7),
+ *   - parabolic reconstruction of the deviation of the primitive gas
+ *     variables (rho, u, v, w, P) and dust variables from the equilibrium,
+ *     with a MinMod limiter (Sect. 2.7),
  *   - an exact Riemann solver at every gas face (Sect. 2.6) and an upwind
  *     pressureless flux at every dust face (Sect. 2.9),
  *   - geometric, gravity, rotating-frame and drag sources, balanced by the
