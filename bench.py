@@ -91,20 +91,25 @@ def _traffic(kernel_tag, cells):
     return None, None
 
 
-KERNEL_SOURCES = {
-    "stage_fp32": ("device_common.cuh", "stage_pert.cuh"),
-    "stage_fp64pert": ("device_common.cuh", "stage_pert.cuh"),
-    "stage_fp64": ("device_common.cuh", "stage_full.cuh"),
+KERNEL_SOURCES = {  # headers that define the kernel, and the launch-configuration line's token
+    "stage_fp32": (("device_common.cuh", "stage_pert.cuh"), "P32_TR ="),
+    "stage_fp64pert": (("device_common.cuh", "stage_pert.cuh"), "P32_TR ="),
+    "stage_fp64": (("device_common.cuh", "stage_full.cuh"), "F64_TR ="),
 }
 
 
 def _source_hash(kernel_tag):
-    """Hash of the headers that define a kernel (its code, not its callers)."""
+    """Hash of a kernel's code (its headers) and of its launch configuration
+    (the tile / thread-count line of rossbi.cu), not of its callers."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2207_04252_gb300", "csrc")
-    for name in KERNEL_SOURCES[kernel_tag]:
+    headers, token = KERNEL_SOURCES[kernel_tag]
+    for name in headers:
         h.update(open(os.path.join(csrc, name), "rb").read())
+    for line in open(os.path.join(csrc, "rossbi.cu")):
+        if token in line:
+            h.update(line.encode())
     return h.hexdigest()[:16]
 
 

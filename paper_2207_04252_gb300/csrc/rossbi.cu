@@ -22,7 +22,7 @@ namespace {
 
 // Tile of the stage kernels: 14 x 6 x 6 cells, lines of 16 / 8 / 8 lanes.
 constexpr int F64_TR = 14, F64_TT = 6, F64_TZ = 6, F64_NT = 192;
-constexpr int P32_TR = 14, P32_TT = 6, P32_TZ = 6, P32_NT = 192, P32_MINB = 2;
+constexpr int P32_TR = 14, P32_TT = 6, P32_TZ = 6, P32_NT = 256, P32_MINB = 2;
 constexpr int CFL_NT = 256;
 
 }  // namespace
