@@ -79,6 +79,8 @@ def lib():
         L.orc_dust_flux.argtypes = [ctypes.c_int, _D, _D, _D]
         L.orc_drag.argtypes = [ctypes.c_void_p, ctypes.c_int, _D, ctypes.c_double, ctypes.c_double, ctypes.c_int]
         L.orc_status.argtypes = [ctypes.c_void_p]
+        L.orc_set_indirect.argtypes = [ctypes.c_void_p, ctypes.c_double]
+        L.orc_indirect.argtypes = [ctypes.c_void_p, _D, _D]
         _lib = L
     return _lib
 
@@ -124,6 +126,7 @@ class Oracle:
         self.nf = lib().orc_nfields(self.h)
         self.shape = (self.nf, w.nz, w.nth, w.nr)
         self.status = 0
+        self.x_ind = 0.0
         if w.disc is not None:
             disc = np.array(w.disc, dtype=np.float64)
             self.status |= lib().orc_set_equilibrium(self.h, _p(disc))
@@ -160,6 +163,18 @@ class Oracle:
         return E
 
     # ---- the method
+    def set_indirect(self, x_ref):
+        """X_ref of the indirect-gravity term (Sect. 2.10); 0 switches it off."""
+        self.x_ind = float(x_ref)
+        lib().orc_set_indirect(self.h, self.x_ind)
+
+    def indirect(self, E):
+        """X_ref (A_disc, B_disc) of the state E (Sect. 2.10)."""
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        out = np.zeros(2)
+        lib().orc_indirect(self.h, _p(E), _p(out))
+        return out
+
     def rhs(self, E):
         E = np.ascontiguousarray(E, dtype=np.float64)
         G = np.zeros_like(E)
@@ -189,6 +204,8 @@ class Oracle:
         return E, dE
 
     def step_sampled(self, E, dt, cells):
+        if self.x_ind != 0.0:
+            raise ValueError("sampled steps need the whole stage state when indirect gravity is on")
         E = np.ascontiguousarray(E, dtype=np.float64)
         cells = np.ascontiguousarray(cells, dtype=np.int64)
         out = np.zeros((len(cells), self.nf))

@@ -54,6 +54,16 @@
 //      left after that step is far below round-off); PVRS start, floored at
 //      1e-8 min(pL, pR).
 //  R10 CFL uses the frame-relative speed; a dust cell adds cfl V/(|v_d| maxA).
+//  R11 indirect gravity (Sect. 2.10): A_disc and B_disc are sums over the
+//      cells of the stage's input state, each cell a point mass at its
+//      centre; the mass is the gas density's departure from the equilibrium
+//      (an axisymmetric disc exerts no net pull, so its own A and B vanish)
+//      plus the dust density.  As in the paper the vertical component is
+//      dropped, and the constant in front (X_ref) is a parameter (the
+//      gravitational constant in code units, 0 = off).  The force per unit
+//      mass is -grad Phi_ind on gas and dust; the gas energy gains the work
+//      rho (u, v).(-grad Phi_ind).  The equilibrium's residual R0 carries no
+//      indirect term.
 //
 // Tangent-linear mode (the paper has none; it pins the GPU adjoint).  The
 // numeric core is written for a scalar type T and also instantiated with a
@@ -106,6 +116,7 @@ struct Oracle {
   // over the index ranges extended by NG ghosts
   std::vector<double> e0c, e0r, e0z;
   std::vector<double> r0;  // balanced-scheme residual G(E0), nf x ncell
+  double x_ind = 0.0;      // X_ref of the indirect-gravity term (Sect. 2.10), 0 = off
   int status = 0;
   long newton_iters = 0, riemann_calls = 0;
 };
@@ -647,9 +658,10 @@ static void dust_flux(int ax, const T UL[9], const T UR[9], T F[9]) {
 // ---------------------------------------------------------------- sources
 // App. B source vector in cylindrical coordinates, with stellar gravity
 // (Sect. 2.1) and the rotating-frame terms of reading R6; per unit volume,
-// at the cell centre.  The Box has no source terms.
+// at the cell centre.  gind = X_ref (A_disc, B_disc) of Sect. 2.10 (reading
+// R11), or null.  The Box has no source terms.
 template <class T>
-static void sources(const Oracle& o, int i, int k, const T U[9], T S[9]) {
+static void sources(const Oracle& o, int i, int j, int k, const T U[9], const T* gind, T S[9]) {
   for (int f = 0; f < o.nf; ++f) S[f] = T(0.0);
   if (o.d.geometry != GEOM_CYL) return;
   const double r = XC(o, 0, i), z = XC(o, 2, k);
@@ -657,6 +669,13 @@ static void sources(const Oracle& o, int i, int k, const T U[9], T S[9]) {
   const double R3 = R2 * std::sqrt(R2);
   const double fr = -o.d.gm * r / R3, fz = -o.d.gm * z / R3;
   const double Om = o.d.omega_frame;
+  // gradient of the indirect potential, (r, theta) components at this cell
+  T dphi_r(0.0), dphi_t(0.0);
+  if (gind) {
+    const double th = XC(o, 1, j);
+    dphi_r = gind[0] * std::cos(th) + gind[1] * std::sin(th);
+    dphi_t = -gind[0] * std::sin(th) + gind[1] * std::cos(th);
+  }
   {
     const T rho = U[RHO];
     const T u = U[MU] / rho, v = U[MV] / rho, w = U[MW] / rho;
@@ -666,6 +685,11 @@ static void sources(const Oracle& o, int i, int k, const T U[9], T S[9]) {
     S[MW] = rho * fz;
     S[EN] = rho * u * (fr + Om * Om * r) + rho * w * fz;
     S[RHO] = T(0.0);
+    if (gind) {
+      S[MU] -= rho * dphi_r;
+      S[MV] -= rho * dphi_t;
+      S[EN] -= rho * (u * dphi_r + v * dphi_t);
+    }
   }
   if (o.nf > 5 && U[DRHO] > 0.0) {
     const T rho = U[DRHO];
@@ -674,13 +698,42 @@ static void sources(const Oracle& o, int i, int k, const T U[9], T S[9]) {
     S[DMV] = -rho * u * v / r - 2.0 * Om * rho * u;
     S[DMW] = rho * fz;
     S[DRHO] = T(0.0);
+    if (gind) {
+      S[DMU] -= rho * dphi_r;
+      S[DMV] -= rho * dphi_t;
+    }
   }
+}
+
+// Sect. 2.10: X_ref (A_disc, B_disc), the integrals of r' cos(theta') / R'^3
+// and r' sin(theta') / R'^3 over the disc mass, as sums over cells of mass
+// V (rho - rho_0 + rho_d) at the centre (reading R11).  Zero when off.
+template <class Acc, class T = typename Acc::value_type>
+static void indirect_moments(const Oracle& o, const Acc& E, T gind[2]) {
+  gind[0] = gind[1] = T(0.0);
+  if (o.x_ind == 0.0 || o.d.geometry != GEOM_CYL) return;
+  T A(0.0), B(0.0);
+  for (long lin = 0; lin < o.ncell; ++lin) {
+    const int i = (int)(lin % o.n[0]);
+    const int j = (int)((lin / o.n[0]) % o.n[1]);
+    const int k = (int)(lin / ((long)o.n[0] * o.n[1]));
+    const double r = XC(o, 0, i), th = XC(o, 1, j), z = XC(o, 2, k);
+    const double R2 = r * r + z * z;
+    T dm = E.get(RHO, lin);
+    if (o.has_eq) dm = dm - E0C(o, i, k)[RHO];
+    if (o.nf > 5) dm += E.get(DRHO, lin);
+    dm = dm * metric(o, i).V;
+    A += dm * (r * std::cos(th) / (R2 * std::sqrt(R2)));
+    B += dm * (r * std::sin(th) / (R2 * std::sqrt(R2)));
+  }
+  gind[0] = o.x_ind * A;
+  gind[1] = o.x_ind * B;
 }
 
 // ---------------------------------------------------------------- G(E) per cell
 // Sect. 2.2, Eq. (compact form): G = S V - sum_faces A F.n, for one cell.
 template <class Acc, class T = typename Acc::value_type>
-static void G_cell(Oracle& o, const Acc& E, int i, int j, int k, T G[9]) {
+static void G_cell(Oracle& o, const Acc& E, int i, int j, int k, T G[9], const T* gind = nullptr) {
   const Metric m = metric(o, i);
   for (int f = 0; f < o.nf; ++f) G[f] = T(0.0);
   const int cell[3] = {i, j, k};
@@ -714,7 +767,7 @@ static void G_cell(Oracle& o, const Acc& E, int i, int j, int k, T G[9]) {
   for (int f = 0; f < o.nf; ++f) U[f] = E.get(f, lin);
   if (!(U[RHO] > 0.0) || !(pressure(o.d.gamma, U) > 0.0)) o.status |= ST_NONPHYSICAL;
   if (o.nf > 5 && U[DRHO] < 0.0) o.status |= ST_NONPHYSICAL;
-  sources(o, i, k, U, S);
+  sources(o, i, j, k, U, gind, S);
   for (int f = 0; f < o.nf; ++f) G[f] += m.V * S[f];
 }
 
@@ -760,12 +813,12 @@ static void drag(const Oracle& o, int i, T U[9], double tau, const DustParamsT<T
 // One RK stage at one cell: Eout = Ebase + tau G(Ein)/V, then drag (Sect. 2.5).
 template <class Acc, class T = typename Acc::value_type>
 static void stage_cell(Oracle& o, const Acc& Ein, const T* Ebase, long lin, double tau, const DustParamsT<T>& dp,
-                       T out[9]) {
+                       T out[9], const T* gind = nullptr) {
   const int i = (int)(lin % o.n[0]);
   const int j = (int)((lin / o.n[0]) % o.n[1]);
   const int k = (int)(lin / ((long)o.n[0] * o.n[1]));
   T G[9];
-  G_cell(o, Ein, i, j, k, G);
+  G_cell(o, Ein, i, j, k, G, gind);
   if (!o.r0.empty())
     for (int f = 0; f < o.nf; ++f) G[f] -= o.r0[(size_t)f * o.ncell + lin];  // Sect. 2.8 balanced scheme
   const double V = metric(o, i).V;
@@ -776,9 +829,11 @@ static void stage_cell(Oracle& o, const Acc& Ein, const T* Ebase, long lin, doub
 template <class T>
 static void stage_all(Oracle& o, const T* Ein, const T* Ebase, T* Eout, double tau, const DustParamsT<T>& dp) {
   const ArrAccT<T> A{Ein, o.ncell};
-  T out[9];
+  T out[9], gind[2];
+  indirect_moments(o, A, gind);
+  const bool ind = o.x_ind != 0.0 && o.d.geometry == GEOM_CYL;
   for (long lin = 0; lin < o.ncell; ++lin) {
-    stage_cell(o, A, Ebase, lin, tau, dp, out);
+    stage_cell(o, A, Ebase, lin, tau, dp, out, ind ? gind : nullptr);
     for (int f = 0; f < o.nf; ++f) Eout[(size_t)f * o.ncell + lin] = out[f];
   }
 }
@@ -923,12 +978,14 @@ void orc_metric(void* h, int i, double* out /* V, A_lo[3], A_hi[3], maxA */) {
 int orc_rhs(void* h, const double* E, double* G) {
   Oracle& o = *(Oracle*)h;
   const ArrAcc A{E, o.ncell};
-  double g[9];
+  double g[9], gind[2];
+  indirect_moments(o, A, gind);
+  const bool ind = o.x_ind != 0.0 && o.d.geometry == GEOM_CYL;
   for (long lin = 0; lin < o.ncell; ++lin) {
     const int i = (int)(lin % o.n[0]);
     const int j = (int)((lin / o.n[0]) % o.n[1]);
     const int k = (int)(lin / ((long)o.n[0] * o.n[1]));
-    G_cell(o, A, i, j, k, g);
+    G_cell(o, A, i, j, k, g, ind ? gind : nullptr);
     for (int f = 0; f < o.nf; ++f)
       G[(size_t)f * o.ncell + lin] = g[f] - (o.r0.empty() ? 0.0 : o.r0[(size_t)f * o.ncell + lin]);
   }
@@ -984,6 +1041,7 @@ int orc_step_tlm(void* h, double* E, double* dE, double dt, double stokes, doubl
 int orc_step_sampled(void* h, const double* E, double dt, double stokes, int law, const long* cells, long ncells,
                      double* out) {
   Oracle& o = *(Oracle*)h;
+  if (o.x_ind != 0.0) return -1;  // the indirect term needs the whole of E*
   const DustParams dp{stokes, law};
   LazyStageAcc S{&o, E, 0.5 * dt, dp, {}};
   for (long s = 0; s < ncells; ++s) stage_cell(o, S, E, cells[s], dt, dp, out + (size_t)s * o.nf);
@@ -1009,6 +1067,15 @@ void orc_sums(void* h, const double* E, double* sums) {
     for (long lin = 0; lin < o.ncell; ++lin) s += metric(o, (int)(lin % o.n[0])).V * E[(size_t)f * o.ncell + lin];
     sums[f] = s;
   }
+}
+
+// X_ref of the indirect-gravity term of Sect. 2.10 (reading R11); 0 = off.
+void orc_set_indirect(void* h, double x_ref) { ((Oracle*)h)->x_ind = x_ref; }
+
+// X_ref (A_disc, B_disc) of the state E (zero when off or on the Box).
+void orc_indirect(void* h, const double* E, double* out) {
+  const Oracle& o = *(Oracle*)h;
+  indirect_moments(o, ArrAcc{E, o.ncell}, out);
 }
 
 void orc_counters(void* h, long* out) {
