@@ -81,6 +81,7 @@ def lib():
         L.orc_status.argtypes = [ctypes.c_void_p]
         L.orc_set_indirect.argtypes = [ctypes.c_void_p, ctypes.c_double]
         L.orc_indirect.argtypes = [ctypes.c_void_p, _D, _D]
+        L.orc_set_damping.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_double]
         _lib = L
     return _lib
 
@@ -167,6 +168,12 @@ class Oracle:
         """X_ref of the indirect-gravity term (Sect. 2.10); 0 switches it off."""
         self.x_ind = float(x_ref)
         lib().orc_set_indirect(self.h, self.x_ind)
+
+    def set_damping(self, r_ein, r_eout, period_factor=1.0):
+        """Wave-killing zones r < r_ein and r > r_eout (reading R17); a
+        period_factor <= 0 switches them off."""
+        if lib().orc_set_damping(self.h, float(r_ein), float(r_eout), float(period_factor)):
+            raise ValueError("damping zones must lie inside the radial extent of a cylindrical grid")
 
     def indirect(self, E):
         """X_ref (A_disc, B_disc) of the state E (Sect. 2.10)."""

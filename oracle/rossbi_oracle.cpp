@@ -54,7 +54,7 @@
 //      left after that step is far below round-off); PVRS start, floored at
 //      1e-8 min(pL, pR).
 //  R10 CFL uses the frame-relative speed; a dust cell adds cfl V/(|v_d| maxA).
-//  R11 indirect gravity (Sect. 2.10): A_disc and B_disc are sums over the
+//  R16 indirect gravity (Sect. 2.10): A_disc and B_disc are sums over the
 //      cells of the stage's input state, each cell a point mass at its
 //      centre; the mass is the gas density's departure from the equilibrium
 //      (an axisymmetric disc exerts no net pull, so its own A and B vanish)
@@ -64,6 +64,18 @@
 //      mass is -grad Phi_ind on gas and dust; the gas energy gains the work
 //      rho (u, v).(-grad Phi_ind).  The equilibrium's residual R0 carries no
 //      indirect term.
+//  R17 wave-killing zones (Sect. 2.4 names radial wave-killing boundaries
+//      without giving them; the form is that of de Val-Borro et al. 2006,
+//      MNRAS 370, 529): in r < r_ein and r > r_eout the gas departures
+//      relax towards the equilibrium, dE'/dt = -E' R(r) / tau, with R the
+//      parabola that is 1 at the domain boundary and 0 (with zero slope) at
+//      the zone's edge, and tau = f x the Keplerian orbital period at that
+//      boundary.  It is a term of G, so it acts inside every RK stage; the
+//      five conservative gas departures relax at one rate; dust is left
+//      alone.  The edges and f are parameters.  Parity unpinned for the
+//      profile and the constants, which come from the cited work: the pins
+//      check the structure (local, linear, gas-only, the parabola through
+//      its end conditions, the period) and the equilibrium.
 //
 // Tangent-linear mode (the paper has none; it pins the GPU adjoint).  The
 // numeric core is written for a scalar type T and also instantiated with a
@@ -117,6 +129,8 @@ struct Oracle {
   std::vector<double> e0c, e0r, e0z;
   std::vector<double> r0;  // balanced-scheme residual G(E0), nf x ncell
   double x_ind = 0.0;      // X_ref of the indirect-gravity term (Sect. 2.10), 0 = off
+  bool damp = false;       // wave-killing zones of reading R17
+  double damp_ein = 0.0, damp_eout = 0.0, damp_tau_in = 0.0, damp_tau_out = 0.0;
   int status = 0;
   long newton_iters = 0, riemann_calls = 0;
 };
@@ -659,7 +673,7 @@ static void dust_flux(int ax, const T UL[9], const T UR[9], T F[9]) {
 // App. B source vector in cylindrical coordinates, with stellar gravity
 // (Sect. 2.1) and the rotating-frame terms of reading R6; per unit volume,
 // at the cell centre.  gind = X_ref (A_disc, B_disc) of Sect. 2.10 (reading
-// R11), or null.  The Box has no source terms.
+// R16), or null.  The Box has no source terms.
 template <class T>
 static void sources(const Oracle& o, int i, int j, int k, const T U[9], const T* gind, T S[9]) {
   for (int f = 0; f < o.nf; ++f) S[f] = T(0.0);
@@ -707,7 +721,7 @@ static void sources(const Oracle& o, int i, int j, int k, const T U[9], const T*
 
 // Sect. 2.10: X_ref (A_disc, B_disc), the integrals of r' cos(theta') / R'^3
 // and r' sin(theta') / R'^3 over the disc mass, as sums over cells of mass
-// V (rho - rho_0 + rho_d) at the centre (reading R11).  Zero when off.
+// V (rho - rho_0 + rho_d) at the centre (reading R16).  Zero when off.
 template <class Acc, class T = typename Acc::value_type>
 static void indirect_moments(const Oracle& o, const Acc& E, T gind[2]) {
   gind[0] = gind[1] = T(0.0);
@@ -728,6 +742,22 @@ static void indirect_moments(const Oracle& o, const Acc& E, T gind[2]) {
   }
   gind[0] = o.x_ind * A;
   gind[1] = o.x_ind * B;
+}
+
+// Reading R17: relaxation rate R(r) / tau of the wave-killing zones at the
+// centre of radial cell i (0 in the interior).
+static double damping_rate(const Oracle& o, int i) {
+  if (!o.damp) return 0.0;
+  const double r = XC(o, 0, i), rin = o.d.x0[0], rout = o.d.x1[0];
+  if (r < o.damp_ein) {
+    const double x = (o.damp_ein - r) / (o.damp_ein - rin);
+    return x * x / o.damp_tau_in;
+  }
+  if (r > o.damp_eout) {
+    const double x = (r - o.damp_eout) / (rout - o.damp_eout);
+    return x * x / o.damp_tau_out;
+  }
+  return 0.0;
 }
 
 // ---------------------------------------------------------------- G(E) per cell
@@ -769,6 +799,9 @@ static void G_cell(Oracle& o, const Acc& E, int i, int j, int k, T G[9], const T
   if (o.nf > 5 && U[DRHO] < 0.0) o.status |= ST_NONPHYSICAL;
   sources(o, i, j, k, U, gind, S);
   for (int f = 0; f < o.nf; ++f) G[f] += m.V * S[f];
+  const double kd = damping_rate(o, i);  // reading R17
+  if (kd != 0.0)
+    for (int f = 0; f < 5; ++f) G[f] -= m.V * kd * (U[f] - (o.has_eq ? E0C(o, i, k)[f] : 0.0));
 }
 
 // ---------------------------------------------------------------- drag
@@ -1069,13 +1102,30 @@ void orc_sums(void* h, const double* E, double* sums) {
   }
 }
 
-// X_ref of the indirect-gravity term of Sect. 2.10 (reading R11); 0 = off.
+// X_ref of the indirect-gravity term of Sect. 2.10 (reading R16); 0 = off.
 void orc_set_indirect(void* h, double x_ref) { ((Oracle*)h)->x_ind = x_ref; }
 
 // X_ref (A_disc, B_disc) of the state E (zero when off or on the Box).
 void orc_indirect(void* h, const double* E, double* out) {
   const Oracle& o = *(Oracle*)h;
   indirect_moments(o, ArrAcc{E, o.ncell}, out);
+}
+
+// Wave-killing zones of reading R17: edges r_ein (inner zone r < r_ein) and
+// r_eout (outer zone r > r_eout), tau = f x the orbital period 2 pi / Omega_K
+// at each boundary; f <= 0 switches them off.  Cylindrical grids only.
+int orc_set_damping(void* h, double r_ein, double r_eout, double f) {
+  Oracle& o = *(Oracle*)h;
+  o.damp = false;
+  if (!(f > 0.0)) return 0;
+  const double rin = o.d.x0[0], rout = o.d.x1[0];
+  if (o.d.geometry != GEOM_CYL || !(r_ein > rin) || !(r_eout < rout) || !(r_ein <= r_eout)) return 1;
+  o.damp = true;
+  o.damp_ein = r_ein;
+  o.damp_eout = r_eout;
+  o.damp_tau_in = f * 2.0 * M_PI / std::sqrt(o.d.gm / (rin * rin * rin));
+  o.damp_tau_out = f * 2.0 * M_PI / std::sqrt(o.d.gm / (rout * rout * rout));
+  return 0;
 }
 
 void orc_counters(void* h, long* out) {

@@ -1,4 +1,4 @@
-"""Pins of the oracle's indirect-gravity term (Sect. 2.10, reading R11).
+"""Pins of the oracle's indirect-gravity term (Sect. 2.10, reading R16).
 
 The paper gives the gradient of the indirect potential in cylindrical
 components, X_ref (A cos(theta) + B sin(theta), -A sin(theta) + B cos(theta), 0),
@@ -28,15 +28,25 @@ def _grid(o):
     return R, TH, Z, o.volumes()[None, None, :]
 
 
-def _lopsided(o, amp=0.05, th0=1.0, width=0.6):
-    """Initial state plus a gas density bump centred at theta = th0 and, with
-    dust, a dust bump at th0 + 2 (m = 1 asymmetries of both masses)."""
-    E = oracle.initial_state(o)
-    R, TH, Z, _ = _grid(o)
-    for f, c in ((RHO, th0), (DRHO, th0 + 2.0))[:1 if o.nf == 5 else 2]:
-        dth = np.angle(np.exp(1j * (TH - c)))
-        E[f] *= 1.0 + amp * np.exp(-(dth / width) ** 2)
+def bump(E, r, th, z, amp=0.05, th0=1.0, width=0.6):
+    """An m = 1 asymmetry of the disc mass: every gas field scaled by
+    1 + amp exp(-(dtheta/width)^2 - ((r - 1.1)/0.25)^2 - (z/0.08)^2) about
+    theta = th0 and, with dust, every dust field likewise about th0 + 2
+    (velocities and temperature unchanged, so the bump is a mild density and
+    pressure excess, away from the domain's edges and symmetric in z).
+    r, th, z: cell-centre coordinates; E: full conservative state
+    (nf, nz, nth, nr)."""
+    E = E.copy()
+    win = np.exp(-((r[None, None, :] - 1.1) / 0.25) ** 2 - (z[:, None, None] / 0.08) ** 2)
+    groups = ((slice(0, 5), th0), (slice(5, 9), th0 + 2.0))
+    for fs, c in groups[:1 if E.shape[0] == 5 else 2]:
+        dth = np.angle(np.exp(1j * (th[None, :, None] - c)))
+        E[fs] *= (1.0 + amp * win * np.exp(-(dth / width) ** 2))[None]
     return E
+
+
+def _lopsided(o):
+    return bump(oracle.initial_state(o), o.coords(0)[0], o.coords(1)[0], o.coords(2)[0])
 
 
 def _indirect_part(o, E, x_ref):
