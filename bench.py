@@ -264,6 +264,45 @@ def measure_fp64(R, W, w, torch, steps=2, warmup=3):
             "dtype": "f64"}
 
 
+def _timed_steps(g, s, torch, steps, warmup):
+    """ms per step of `steps` device-paced steps after `warmup` untimed ones."""
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        g.step(s, dt=0.0)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        g.step(s, dt=0.0)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1) / steps
+
+
+def measure_indirect(R, g, s, torch, x_ref=0.7, steps=4, warmup=2):
+    """The same step with the indirect gravity of Sect. 2.10 switched on
+    (a moments kernel and its reduction before each stage: 4 more launches
+    per step)."""
+    g.set_indirect(x_ref)
+    ms = _timed_steps(g, s, torch, steps, warmup)
+    ab = g.indirect_moments(s).tolist()
+    status = g.take_status()
+    g.set_indirect(0.0)
+    return {"x_ref": x_ref, "value": g.w.ncell / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "warmup": warmup, "moments_AB": ab, "status": R.status_string(status)}
+
+
+def measure_damping(R, g, s, torch, zones=(0.625, 1.68, 1.0), steps=4, warmup=2):
+    """The same step with the radial wave-killing zones of Sect. 2.4 on
+    (no extra launch: a per-cell relaxation in the stage epilogues)."""
+    g.set_damping(zones)
+    ms = _timed_steps(g, s, torch, steps, warmup)
+    status = g.take_status()
+    g.set_damping(None)
+    return {"zones": list(zones), "value": g.w.ncell / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "steps": steps, "warmup": warmup, "status": R.status_string(status)}
+
+
 def measure_adjoint(R, W, syn, torch, steps=4, warmup=3):
     """Cost of the FP64 discrete adjoint on the adjoint workload (128x256x32,
     bi-fluid): one rossbi_adjoint_step (forward recompute of the step included)
@@ -356,6 +395,8 @@ def run_ours(args):
     g = workloads.Grid(w, precision=prec, stream=stream)
     s = g.initial_state()
     elem = s.element_size()
+    if args.indirect:
+        g.set_indirect(args.indirect)
     g.cfl_dt(s)
     for _ in range(args.warmup):
         g.step(s, dt=0.0)
@@ -430,15 +471,22 @@ def run_ours(args):
                 "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
                 "config": {"workload": w.name, "precision": args.precision, "cells": w.ncell, "fields": g.nf,
                            "state_bytes": state_bytes, "parallelism": f"replicas{world}",
-                           "l2": "inputs larger than L2 (no flush needed)"},
+                           "l2": "inputs larger than L2 (no flush needed)", "indirect_x_ref": args.indirect},
                 "roofline": roofline, "roofline_issue": roofline_issue, "e2e": e2e,
-                "gpu_launches": 3 * args.steps, "clocks": clocks,
+                "gpu_launches": (7 if args.indirect else 3) * args.steps, "clocks": clocks,
                 "status": R.status_string(status)}
         if args.precision == "fp32" and not args.no_extras:
             fp64 = measure_fp64(R, workloads, w, torch)
             line["fp64_form"] = fp64
             line["fp32_over_fp64"] = value / world / fp64["value"]
             line["fp32_error_vs_fp64"] = fp32_error_vs_fp64(R, workloads, syn, torch)
+        if not args.no_extras and not args.indirect:
+            ind = measure_indirect(R, g, s, torch)
+            ind["over_plain_step"] = ind["ms_per_step"] / (elapsed_ms / args.steps)
+            line["indirect"] = ind
+            dmp = measure_damping(R, g, s, torch)
+            dmp["over_plain_step"] = dmp["ms_per_step"] / (elapsed_ms / args.steps)
+            line["damping"] = dmp
         line["adjoint_over_forward"] = None
         if not args.no_extras:
             a = measure_adjoint(R, workloads, syn, torch)
@@ -462,6 +510,8 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64-form and FP32-error side measurements")
+    ap.add_argument("--indirect", type=float, default=0.0,
+                    help="X_ref of the indirect gravity (Sect. 2.10) for the timed steps; 0 = off")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="print only the adjoint cost measurement (adjoint workload, FP64)")
     args = ap.parse_args()

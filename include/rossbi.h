@@ -100,6 +100,14 @@ typedef struct {
   int drag_law;
 } rossbi_dust_params;
 
+/* Radial wave-killing zones (Sect. 2.4 names them; the relaxation is that of
+ * de Val-Borro et al. 2006): r_in <= r < r_edge_in and r_edge_out < r <= r_out.
+ * period_factor scales the relaxation time, tau = period_factor x the
+ * Keplerian orbital period 2 pi / Omega_K at that zone's boundary. */
+typedef struct {
+  double r_edge_in, r_edge_out, period_factor;
+} rossbi_damping_params;
+
 /* Creates a grid: mesh, metrics and device tables (Sects. 2.2-2.4).
  * cuda_stream: a cudaStream_t (NULL = legacy default stream); not owned.
  * On success *out is a new grid to be freed with rossbi_destroy.
@@ -112,6 +120,53 @@ rossbi_status rossbi_init_grid(const rossbi_grid_desc* desc, void* cuda_stream, 
  * R0 = G(E0) used by the FP64 form.  disc == NULL sets E0 = 0 (Box runs).
  * Cylindrical grids require disc != NULL.  Synchronises the stream. */
 rossbi_status rossbi_set_equilibrium(rossbi_grid* g, const rossbi_disc_params* disc);
+
+/* Indirect gravity of Sect. 2.10.  The star, pulled by an asymmetric disc,
+ * accelerates; in its frame gas and dust feel -grad Phi_ind with
+ *   grad Phi_ind = X_ref (A cos(theta) + B sin(theta), -A sin(theta) + B cos(theta), 0)
+ * in (r, theta, z) components, where A and B are the integrals of
+ * r cos(theta) / R^3 and r sin(theta) / R^3 (R^2 = r^2 + z^2) over the disc
+ * mass.  Each RK stage sums them over the cells of its input state in FP64,
+ * taking as mass V (rho - rho_0 + rho_d) at the cell centre: the
+ * axisymmetric equilibrium exerts no net pull, so an undisturbed disc stays
+ * exactly at equilibrium.  As in the paper the vertical component is
+ * dropped.  The gas energy gains the work of the force; the balanced
+ * residual R0 carries no indirect term.
+ *   x_ref : X_ref, the gravitational constant in the code units in which
+ *           density times volume is mass; 0 switches the term off (the
+ *           default).  Finite; non-zero only on cylindrical grids.
+ * The first non-zero call allocates (and synchronises) the device tables;
+ * later calls only change the constant.  While the term is on, each step
+ * launches two extra reductions per stage, rossbi_adjoint_step returns
+ * ROSSBI_ERR_UNSUPPORTED (its global coupling has no adjoint here).
+ * Errors: ROSSBI_ERR_ARG (NULL grid, non-finite x_ref, non-zero x_ref on a
+ * Box), ROSSBI_ERR_OOM, ROSSBI_ERR_CUDA. */
+rossbi_status rossbi_set_indirect(rossbi_grid* g, double x_ref);
+
+/* Wave-killing zones at the radial edges (Sect. 2.4).  Inside a zone the
+ * five conservative gas departures relax towards the equilibrium,
+ *   dE'/dt = -E' R(r) / tau,
+ * with R(r) the parabola that is 1 at the domain boundary and 0, with zero
+ * slope, at the zone's edge (rates tabulated at cell centres).  The term is
+ * part of G, so it acts inside both RK stages and in rossbi_adjoint_step.
+ * Dust is not damped.  p == NULL switches the zones off (the default);
+ * otherwise r_in < r_edge_in <= r_edge_out < r_out and period_factor > 0.
+ * Cylindrical grids with an equilibrium set only.  Allocates an nr-entry
+ * table on first use; synchronises the stream.
+ * Errors: ROSSBI_ERR_ARG, ROSSBI_ERR_OOM, ROSSBI_ERR_CUDA. */
+rossbi_status rossbi_set_damping(rossbi_grid* g, const rossbi_damping_params* p);
+
+/* The disc moments (A_disc, B_disc) of Sect. 2.10 of a state, without the
+ * constant X_ref: the sums over cells of V (rho - rho_0 + rho_d) r cos(theta)
+ * / R^3 and ... r sin(theta) / R^3 at the cell centres, in FP64 and in a
+ * fixed order, exactly as the stage kernels take them.  They measure how far
+ * the disc's mass is off centre; the indirect term need not be on.
+ *   state : nfields device pointers of the grid's precision form.
+ *   ab    : host array of 2 doubles receiving (A_disc, B_disc).
+ * Cylindrical grids with an equilibrium set only.  Allocates the indirect
+ * tables on first use; synchronises the stream.
+ * Errors: ROSSBI_ERR_ARG, ROSSBI_ERR_OOM, ROSSBI_ERR_CUDA. */
+rossbi_status rossbi_indirect_moments(rossbi_grid* g, const void* const* state, double* ab);
 
 /* Copies the equilibrium conservative gas state at cell centres to host
  * memory: host_out[f*nz*nr + k*nr + i], f = 0..4 (App. B order). */
@@ -196,9 +251,9 @@ rossbi_status rossbi_step_noalloc(rossbi_grid* g, void* const* state, double dt,
  *             running total (rossbi_adjoint_dstokes), so callers can leave
  *             dparam NULL and keep the call asynchronous.
  * The library allocates five FP64 states of scratch on the first call.
- * Errors: ROSSBI_ERR_ARG, ROSSBI_ERR_UNSUPPORTED (perturbation forms),
- * ROSSBI_ERR_OOM, ROSSBI_ERR_CUDA, and after a synchronising call
- * ROSSBI_ERR_NONPHYSICAL / ROSSBI_ERR_RIEMANN. */
+ * Errors: ROSSBI_ERR_ARG, ROSSBI_ERR_UNSUPPORTED (perturbation forms, or
+ * indirect gravity switched on), ROSSBI_ERR_OOM, ROSSBI_ERR_CUDA, and after a
+ * synchronising call ROSSBI_ERR_NONPHYSICAL / ROSSBI_ERR_RIEMANN. */
 rossbi_status rossbi_adjoint_step(rossbi_grid* g, const void* const* state_n, double dt,
                                   const rossbi_dust_params* dust, const void* const* lam_np1, void* const* lam_n,
                                   double* dparam);

@@ -38,6 +38,18 @@ struct DevGrid {
   const double* w0r;     //   field slots MU, MV, MW, EN, RHO) at centres, r faces and
   const double* w0z;     //   z faces, same layouts as e0c / e0r / e0z
   const double* r0;      // balanced residual G(E0)            [5][nz][nr]
+  // indirect gravity (Sect. 2.10): X_ref (0 = off); cos / sin of the
+  // axis-1 cell centres [2][nth]; and, for the stage's input state, the
+  // gradient of the indirect potential in (r, theta) components at each
+  // axis-1 index [2][nth], in double and in float
+  double x_ind;
+  const double* ind_cs;
+  const double* ind_g;
+  const float* ind_gf;
+  // wave-killing zones (Sect. 2.4; de Val-Borro et al. 2006 relaxation):
+  // rate R(r) / tau of radial cell i [nr] in double and in float, or null
+  const double* damp_k;
+  const float* damp_kf;
 };
 
 __host__ __device__ constexpr int pow2ceil(int v) {
@@ -337,9 +349,12 @@ __device__ __forceinline__ void dust_kinetic_flux(const T* WL, const T* WR, T* F
 
 // ------------------------------------------------------------------ sources
 // App. B sources per unit volume at the cell centre: geometric terms,
-// stellar gravity (Sect. 2.1) and the rotating-frame Coriolis / centrifugal
-// terms; the Box has none.
-__device__ __forceinline__ void cell_sources(const DevGrid& g, int i, int k, const double* U, double* S) {
+// stellar gravity (Sect. 2.1), the rotating-frame Coriolis / centrifugal
+// terms and, when switched on, the indirect gravity of Sect. 2.10 (force
+// -grad Phi_ind on gas and dust, and its work on the gas); the Box has none.
+// XT = false compiles the optional terms out.
+template <bool XT>
+__device__ __forceinline__ void cell_sources(const DevGrid& g, int i, int j, int k, const double* U, double* S) {
   const double r = g.rc[i + GH];
   const double z = g.x0[2] + (k + 0.5) * g.dx[2];
   const double R2 = r * r + z * z;
@@ -369,6 +384,18 @@ __device__ __forceinline__ void cell_sources(const DevGrid& g, int i, int k, con
       S[DMU] = S[DMV] = S[DMW] = 0.0;
     }
     S[DRHO] = 0.0;
+  }
+  if (XT && g.x_ind != 0.0) {
+    const double gr = g.ind_g[j], gt = g.ind_g[g.nth + j];  // grad Phi_ind, (r, theta)
+    const double rho = U[RHO];
+    const double ir = 1.0 / rho;
+    S[MU] -= rho * gr;
+    S[MV] -= rho * gt;
+    S[EN] -= rho * (U[MU] * ir * gr + U[MV] * ir * gt);
+    if (g.nf > 5 && U[DRHO] > 0.0) {
+      S[DMU] -= U[DRHO] * gr;
+      S[DMV] -= U[DRHO] * gt;
+    }
   }
 }
 

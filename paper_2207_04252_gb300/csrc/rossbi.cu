@@ -65,6 +65,10 @@ struct rossbi_grid {
   double* d_adj = nullptr;
   double* d_adj_part = nullptr;
   double* d_adj_slots = nullptr;       // [0] this call's d/dSt, [1] running total
+  // indirect gravity: [2] disc moments A, B; [2][nth] cos / sin of the
+  // azimuthal centres; [nz][nr] V r / R^3; [2][IND_BLOCKS] block partials
+  double* d_ind = nullptr;
+  double* d_damp = nullptr;            // wave-killing rates R(r) / tau per radial cell [nr]
   int adj_blocks = 0;
   // stage-kernel timing (rossbi_profile_*)
   bool profiling = false;
@@ -237,6 +241,85 @@ __global__ void __launch_bounds__(RED_NT) reduce_partials_kernel(const double* p
   }
 }
 
+// Disc moments of the indirect gravity (Sect. 2.10): per-block FP64 partial
+// sums of w (rho - rho_0 + rho_d) cos(theta) and ... sin(theta), with
+// w = V r / R^3 of the cell centre; `full` states carry rho itself, the
+// perturbation forms rho' already.  A warp takes one azimuthal row (nr cells)
+// at a time; each lane sums its cells of the row in the state's precision
+// (FP32: against a float copy of w, so that GB300's narrow FP64 pipe sees
+// three operations per lane and row instead of several per cell), then the
+// row sums are weighted by cos / sin and accumulated in FP64.  Rows go to
+// warps in a fixed order, so the sums are reproducible.
+constexpr int IND_NT = 256, IND_BLOCKS = 152 * 4;
+template <class T>
+__global__ void __launch_bounds__(IND_NT) indirect_moments_kernel(DevGrid g, const T* rho, const T* drho, int full,
+                                                                  const double* w, const float* wf,
+                                                                  double* partials) {
+  __shared__ double red[IND_NT / 32];
+  constexpr int NW = IND_NT / 32;
+  const int lane = threadIdx.x & 31;
+  double A = 0.0, B = 0.0;
+  const int rows = g.nth * g.nz;
+  for (int row = blockIdx.x * NW + (threadIdx.x >> 5); row < rows; row += gridDim.x * NW) {
+    const int j = row % g.nth, k = row / g.nth;
+    const size_t base = (size_t)row * g.nr;
+    T m = T(0);
+    if constexpr (sizeof(T) == 4) {
+      const float* wk = wf + (size_t)k * g.nr;
+      for (int i = lane; i < g.nr; i += 32) m += (rho[base + i] + (drho ? drho[base + i] : 0.0f)) * wk[i];
+    } else {
+      const double* wk = w + (size_t)k * g.nr;
+      const double* e0 = full && g.has_eq ? g.e0c + ((size_t)RHO * g.nz + k) * g.nr : nullptr;
+      for (int i = lane; i < g.nr; i += 32) {
+        double dm = rho[base + i];
+        if (e0) dm -= e0[i];
+        if (drho) dm += drho[base + i];
+        m += dm * wk[i];
+      }
+    }
+    A += (double)m * g.ind_cs[j];
+    B += (double)m * g.ind_cs[g.nth + j];
+  }
+  A = block_sum<IND_NT>(A, red);
+  B = block_sum<IND_NT>(B, red);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = A;
+    partials[gridDim.x + blockIdx.x] = B;
+  }
+}
+
+// Fixed-order reduction of the moment partials into (A_disc, B_disc), as
+// reduce_partials_kernel does it, then the gradient of the indirect
+// potential at every axis-1 index, X_ref (A cos + B sin, -A sin + B cos), in
+// double and in float (the stage epilogues read it per cell).
+__global__ void __launch_bounds__(RED_NT) indirect_reduce_kernel(const double* partials, int nblocks, int nth,
+                                                                 double x_ref, const double* cs, double* ab,
+                                                                 double* gtab, float* gtabf) {
+  __shared__ double red[RED_NT / 32];
+  __shared__ double AB[2];
+  for (int row = 0; row < 2; ++row) {
+    const double* p = partials + (size_t)row * nblocks;
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += RED_NT) v += p[b];
+    v = block_sum<RED_NT>(v, red);
+    if (threadIdx.x == 0) AB[row] = v;
+  }
+  __syncthreads();
+  const double A = AB[0], B = AB[1];
+  if (threadIdx.x == 0) {
+    ab[0] = A;
+    ab[1] = B;
+  }
+  for (int j = threadIdx.x; j < nth; j += RED_NT) {
+    const double c = cs[j], s = cs[nth + j];
+    const double gr = x_ref * (A * c + B * s), gt = x_ref * (-A * s + B * c);
+    gtab[j] = gr;
+    gtab[nth + j] = gt;
+    gtabf[j] = (float)gr;
+    gtabf[nth + j] = (float)gt;
+  }
+}
+
 // Raises a kernel's dynamic shared-memory limit once per device (the
 // attribute belongs to the current device's context); `done` is the calling
 // site's own flag word, one bit per device id < 64.
@@ -251,12 +334,12 @@ rossbi_status set_smem_once(K kern, size_t smem, unsigned long long& done) {
   return ROSSBI_OK;
 }
 
-template <int NF>
+template <int NF, bool XT>
 rossbi_status launch_stage_f64(rossbi_grid* g, const StageArgs& a, int nblocks) {
   constexpr int BOX = (F64_TR + 4) * (F64_TT + 4) * (F64_TZ + 4);
   constexpr int NCORE = F64_TR * F64_TT * F64_TZ;
   constexpr size_t smem = (size_t)NF * (BOX + NCORE) * sizeof(double);
-  auto kern = stage_full_kernel<NF, F64_TR, F64_TT, F64_TZ, F64_NT>;
+  auto kern = stage_full_kernel<NF, F64_TR, F64_TT, F64_TZ, F64_NT, XT>;
   {
     static unsigned long long done = 0;
     const rossbi_status sa = set_smem_once(kern, smem, done);
@@ -293,7 +376,9 @@ rossbi_status launch_stage(rossbi_grid* g, const StageArgs& a, int nblocks) {
     e1 = g->ev[2 * g->ev_used + 1];
     CK(cudaEventRecord(e0, g->stream));
   }
-  rossbi_status st = g->nf == 9 ? launch_stage_f64<9>(g, a, nblocks) : launch_stage_f64<5>(g, a, nblocks);
+  const bool xt = a.g.x_ind != 0.0 || a.g.damp_k != nullptr;  // optional terms on
+  rossbi_status st = g->nf == 9 ? (xt ? launch_stage_f64<9, true>(g, a, nblocks) : launch_stage_f64<9, false>(g, a, nblocks))
+                                : (xt ? launch_stage_f64<5, true>(g, a, nblocks) : launch_stage_f64<5, false>(g, a, nblocks));
   if (st != ROSSBI_OK) return st;
   if (e0) {
     CK(cudaEventRecord(e1, g->stream));
@@ -302,13 +387,13 @@ rossbi_status launch_stage(rossbi_grid* g, const StageArgs& a, int nblocks) {
   return ROSSBI_OK;
 }
 
-template <class T, int NF, class P>
-rossbi_status launch_pert_nf(rossbi_grid* g, const PertArgs<T>& a, int nblocks) {
+template <class T, int NF, class P, bool XT>
+rossbi_status launch_pert_nf_x(rossbi_grid* g, const PertArgs<T>& a, int nblocks) {
   constexpr bool F32 = sizeof(T) == 4;
   constexpr int TR = P32_TR, TT = P32_TT, TZ = P32_TZ, NT = P32_NT, MINB = F32 ? P32_MINB : 1;
   constexpr int BOX = (TR + 4) * (TT + 4) * (TZ + 4), NCORE = TR * TT * TZ;
   constexpr size_t smem = (size_t)NF * (BOX + NCORE) * sizeof(T);
-  auto kern = stage_pert_kernel<T, NF, TR, TT, TZ, NT, MINB, P>;
+  auto kern = stage_pert_kernel<T, NF, TR, TT, TZ, NT, MINB, P, XT>;
   {
     static unsigned long long done = 0;
     const rossbi_status sa = set_smem_once(kern, smem, done);
@@ -317,6 +402,12 @@ rossbi_status launch_pert_nf(rossbi_grid* g, const PertArgs<T>& a, int nblocks) 
   kern<<<nblocks, NT, smem, g->stream>>>(a);
   CK(cudaGetLastError());
   return ROSSBI_OK;
+}
+
+template <class T, int NF, class P>
+rossbi_status launch_pert_nf(rossbi_grid* g, const PertArgs<T>& a, int nblocks) {
+  const bool xt = a.g.x_ind != 0.0 || a.g.damp_k != nullptr;  // optional terms on
+  return xt ? launch_pert_nf_x<T, NF, P, true>(g, a, nblocks) : launch_pert_nf_x<T, NF, P, false>(g, a, nblocks);
 }
 
 template <class T>
@@ -395,6 +486,8 @@ rossbi_status empty_run(rossbi_grid* g) {
     StageArgs a = base_args(g);
     a.g.nth = nth_s;
     a.g.r0 = nullptr;
+    a.g.x_ind = 0.0;  // the equilibrium's residual carries no indirect term
+    a.g.damp_k = nullptr;  // nor a relaxation (E' = 0 there)
     for (int f = 0; f < g->nf; ++f) a.in[f] = dE + f * nslab;
     a.gout = dG;
     a.mode = 1;
@@ -591,6 +684,88 @@ rossbi_status prepare_step(rossbi_grid* g, void* const* state, void* const* scra
   return drag_args(g, dust, drag);
 }
 
+// Layout of the indirect-gravity tables, offsets in doubles: [2] the moments
+// A, B; [2][nth] cos / sin of the azimuthal centres; [nz][nr] the weights
+// V r / R^3 of the cell centres; [2][IND_BLOCKS] block partials; [2][nth]
+// the gradient of the indirect potential; the same as floats; the weights as
+// floats (for the FP32 form).
+struct IndLayout {
+  size_t cs, w, part, g, gf, wf, total;
+};
+IndLayout ind_layout(const rossbi_grid_desc& d) {
+  const size_t nw = (size_t)d.nz * d.nr, nth = d.nth;
+  IndLayout L;
+  L.cs = 2;
+  L.w = L.cs + 2 * nth;
+  L.part = L.w + nw;
+  L.g = L.part + 2 * (size_t)IND_BLOCKS;
+  L.gf = L.g + 2 * nth;
+  L.wf = L.gf + nth;  // 2 nth floats
+  L.total = L.wf + (nw + 1) / 2;
+  return L;
+}
+
+// Device tables of the indirect gravity (allocated once, layout above).
+rossbi_status ensure_ind_tables(rossbi_grid* g) {
+  if (g->d_ind) return ROSSBI_OK;
+  const rossbi_grid_desc& d = g->desc;
+  const double dy = (d.x1[1] - d.x0[1]) / d.nth, dz = (d.x1[2] - d.x0[2]) / d.nz;
+  const IndLayout L = ind_layout(d);
+  const size_t nw = (size_t)d.nz * d.nr, wf_at = L.wf;
+  std::vector<double> h(L.total, 0.0);
+  for (int j = 0; j < d.nth; ++j) {
+    const double th = d.x0[1] + (j + 0.5) * dy;
+    h[2 + j] = std::cos(th);
+    h[2 + d.nth + j] = std::sin(th);
+  }
+  double* w = h.data() + 2 + 2 * (size_t)d.nth;
+  for (int k = 0; k < d.nz; ++k) {
+    const double z = d.x0[2] + (k + 0.5) * dz;
+    for (int i = 0; i < d.nr; ++i) {
+      const double r = axis0_centre(d, i), rm = axis0_face(d, i), rp = axis0_face(d, i + 1);
+      const double V = 0.5 * (rp * rp - rm * rm) * dy * dz, R2 = r * r + z * z;
+      w[(size_t)k * d.nr + i] = V * r / (R2 * std::sqrt(R2));
+    }
+  }
+  std::vector<float> wf(nw);
+  for (size_t q = 0; q < nw; ++q) wf[q] = (float)w[q];
+  std::memcpy(h.data() + wf_at, wf.data(), nw * sizeof(float));
+  rossbi_status st = upload(&g->d_ind, h, g->stream);
+  if (st == ROSSBI_OK && cudaStreamSynchronize(g->stream) != cudaSuccess) st = ROSSBI_ERR_CUDA;
+  if (st != ROSSBI_OK) {
+    if (g->d_ind) cudaFree(g->d_ind);
+    g->d_ind = nullptr;
+    return st;
+  }
+  g->dg.ind_cs = g->d_ind + L.cs;
+  g->dg.ind_g = g->d_ind + L.g;
+  g->dg.ind_gf = reinterpret_cast<const float*>(g->d_ind + L.gf);
+  return ROSSBI_OK;
+}
+
+// X_ref-free disc moments (A_disc, B_disc) of a state into d_ind[0..1].
+rossbi_status indirect_moments(rossbi_grid* g, void* const* state) {
+  const rossbi_grid_desc& d = g->desc;
+  const IndLayout L = ind_layout(d);
+  const double* w = g->d_ind + L.w;
+  double* part = g->d_ind + L.part;
+  const float* wf = reinterpret_cast<const float*>(g->d_ind + L.wf);
+  const bool has_dust = g->nf == 9;
+  if (d.precision == ROSSBI_FP32_PERT)
+    indirect_moments_kernel<float><<<IND_BLOCKS, IND_NT, 0, g->stream>>>(
+        g->dg, (const float*)state[RHO], has_dust ? (const float*)state[DRHO] : nullptr, 0, w, wf, part);
+  else
+    indirect_moments_kernel<double><<<IND_BLOCKS, IND_NT, 0, g->stream>>>(
+        g->dg, (const double*)state[RHO], has_dust ? (const double*)state[DRHO] : nullptr,
+        d.precision == ROSSBI_FP64, w, wf, part);
+  CK(cudaGetLastError());
+  indirect_reduce_kernel<<<1, RED_NT, 0, g->stream>>>(part, IND_BLOCKS, d.nth, g->dg.x_ind, g->d_ind + L.cs,
+                                                      g->d_ind, g->d_ind + L.g,
+                                                      reinterpret_cast<float*>(g->d_ind + L.gf));
+  CK(cudaGetLastError());
+  return ROSSBI_OK;
+}
+
 rossbi_status finish_step(rossbi_grid* g, int nxt, double* next_dt) {
   reduce_partials_kernel<<<g->nf + 1, RED_NT, 0, g->stream>>>(g->d_partials, n_tiles(g), g->nf, g->d_sums,
                                                                g->d_dt + nxt);
@@ -622,8 +797,10 @@ rossbi_status step_full(rossbi_grid* g, void* const* state, void* const* sc, dou
   }
   a.tau_frac = 0.5;
   a.stage2 = 0;
-  rossbi_status st = launch_stage(g, a, nblocks);
+  rossbi_status st = g->dg.x_ind != 0.0 ? indirect_moments(g, state) : ROSSBI_OK;
+  if (st == ROSSBI_OK) st = launch_stage(g, a, nblocks);
   if (st != ROSSBI_OK) return st;
+  if (g->dg.x_ind != 0.0 && (st = indirect_moments(g, sc)) != ROSSBI_OK) return st;
   // stage 2: E^{n+1} = E^n + dt (G(E*) - R0)/V, then drag; fused CFL and sums
   for (int f = 0; f < g->nf; ++f) {
     a.in[f] = (const double*)sc[f];
@@ -654,8 +831,10 @@ rossbi_status step_pert(rossbi_grid* g, void* const* state, void* const* sc, dou
   }
   a.tau_frac = 0.5;
   a.stage2 = 0;
-  rossbi_status st = launch_pert<T>(g, a, nblocks);
+  rossbi_status st = g->dg.x_ind != 0.0 ? indirect_moments(g, state) : ROSSBI_OK;
+  if (st == ROSSBI_OK) st = launch_pert<T>(g, a, nblocks);
   if (st != ROSSBI_OK) return st;
+  if (g->dg.x_ind != 0.0 && (st = indirect_moments(g, sc)) != ROSSBI_OK) return st;
   for (int f = 0; f < g->nf; ++f) {
     a.in[f] = (const T*)sc[f];
     a.base[f] = (const T*)state[f];
@@ -885,6 +1064,8 @@ void rossbi_destroy(rossbi_grid* g) {
   if (g->d_adj) cudaFree(g->d_adj);
   if (g->d_adj_part) cudaFree(g->d_adj_part);
   if (g->d_adj_slots) cudaFree(g->d_adj_slots);
+  if (g->d_ind) cudaFree(g->d_ind);
+  if (g->d_damp) cudaFree(g->d_damp);
   if (g->h_pinned) cudaFreeHost(g->h_pinned);
   for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
   delete g;
@@ -1200,10 +1381,73 @@ rossbi_status rossbi_profile_read(rossbi_grid* g, double* stage_ms, int* stage_l
   return ROSSBI_OK;
 }
 
+rossbi_status rossbi_set_indirect(rossbi_grid* g, double x_ref) {
+  if (!g || !std::isfinite(x_ref)) return ROSSBI_ERR_ARG;
+  if (x_ref != 0.0 && g->desc.geometry != ROSSBI_GEOM_CYL) return ROSSBI_ERR_ARG;
+  if (x_ref != 0.0) {
+    const rossbi_status st = ensure_ind_tables(g);
+    if (st != ROSSBI_OK) return st;
+  }
+  g->dg.x_ind = x_ref;
+  return ROSSBI_OK;
+}
+
+rossbi_status rossbi_set_damping(rossbi_grid* g, const rossbi_damping_params* p) {
+  if (!g) return ROSSBI_ERR_ARG;
+  if (!p) {
+    g->dg.damp_k = nullptr;
+    return ROSSBI_OK;
+  }
+  const rossbi_grid_desc& d = g->desc;
+  const double rin = d.x0[0], rout = d.x1[0];
+  if (d.geometry != ROSSBI_GEOM_CYL || !g->eq_set) return ROSSBI_ERR_ARG;
+  if (!(p->r_edge_in > rin) || !(p->r_edge_out < rout) || !(p->r_edge_in <= p->r_edge_out)) return ROSSBI_ERR_ARG;
+  if (!(p->period_factor > 0.0) || !std::isfinite(p->period_factor)) return ROSSBI_ERR_ARG;
+  const double pi = 3.14159265358979323846;
+  const double tau_in = p->period_factor * 2.0 * pi / std::sqrt(d.gm / (rin * rin * rin));
+  const double tau_out = p->period_factor * 2.0 * pi / std::sqrt(d.gm / (rout * rout * rout));
+  std::vector<double> k(d.nr + (d.nr + 1) / 2, 0.0);  // rates, then the same as floats
+  for (int i = 0; i < d.nr; ++i) {  // parabola: 1 at the boundary, 0 with zero slope at the zone edge
+    const double r = axis0_centre(d, i);
+    if (r < p->r_edge_in) {
+      const double x = (p->r_edge_in - r) / (p->r_edge_in - rin);
+      k[i] = x * x / tau_in;
+    } else if (r > p->r_edge_out) {
+      const double x = (r - p->r_edge_out) / (rout - p->r_edge_out);
+      k[i] = x * x / tau_out;
+    }
+  }
+  std::vector<float> kf(d.nr);
+  for (int i = 0; i < d.nr; ++i) kf[i] = (float)k[i];
+  std::memcpy(k.data() + d.nr, kf.data(), d.nr * sizeof(float));
+  g->dg.damp_k = nullptr;
+  g->dg.damp_kf = nullptr;
+  rossbi_status st = upload(&g->d_damp, k, g->stream);
+  if (st == ROSSBI_OK && cudaStreamSynchronize(g->stream) != cudaSuccess) st = ROSSBI_ERR_CUDA;
+  if (st != ROSSBI_OK) return st;
+  g->dg.damp_k = g->d_damp;
+  g->dg.damp_kf = reinterpret_cast<const float*>(g->d_damp + d.nr);
+  return ROSSBI_OK;
+}
+
+rossbi_status rossbi_indirect_moments(rossbi_grid* g, const void* const* state, double* ab) {
+  if (!g || !state || !ab || !g->eq_set || g->desc.geometry != ROSSBI_GEOM_CYL) return ROSSBI_ERR_ARG;
+  if (!state[RHO] || (g->nf == 9 && !state[DRHO])) return ROSSBI_ERR_ARG;
+  rossbi_status st = ensure_ind_tables(g);
+  if (st == ROSSBI_OK) st = indirect_moments(g, (void* const*)state);
+  if (st != ROSSBI_OK) return st;
+  CK(cudaMemcpyAsync(g->h_pinned, g->d_ind, 2 * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+  st = sync_and_status(g);
+  ab[0] = g->h_pinned[0];
+  ab[1] = g->h_pinned[1];
+  return st;
+}
+
 rossbi_status rossbi_adjoint_step(rossbi_grid* g, const void* const* state_n, double dt,
                                   const rossbi_dust_params* dust, const void* const* lam_np1, void* const* lam_n,
                                   double* dparam) {
   if (!g) return ROSSBI_ERR_ARG;
+  if (g->dg.x_ind != 0.0) return ROSSBI_ERR_UNSUPPORTED;  // the global indirect term has no adjoint here
   return adjoint_step(g, (void* const*)state_n, dt, dust, lam_np1, lam_n, dparam);
 }
 

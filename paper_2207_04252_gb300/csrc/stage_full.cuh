@@ -275,7 +275,9 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
-template <int NF, int TR, int TT, int TZ, int NT>
+// XT: the optional terms (indirect gravity, wave-killing zones) are compiled
+// in; the plain instantiation carries none of their code.
+template <int NF, int TR, int TT, int TZ, int NT, bool XT>
 __global__ void __launch_bounds__(NT, 1) stage_full_kernel(const StageArgs a) {
   constexpr int BX = TR + 4, BY = TT + 4, BZ = TZ + 4, BOX = BX * BY * BZ, NCORE = TR * TT * TZ;
   extern __shared__ double smem[];
@@ -339,7 +341,7 @@ __global__ void __launch_bounds__(NT, 1) stage_full_kernel(const StageArgs a) {
     if (cell_nonphysical(g, U)) status |= STATUS_NONPHYSICAL;
     if (g.geom == GEOM_CYL) {
       double S[NF];
-      cell_sources(g, gi, gk, U, S);
+      cell_sources<XT>(g, gi, gj, gk, U, S);
       const double V = g.vol[gi];
 #pragma unroll
       for (int f = 0; f < NF; ++f) G[f] += V * S[f];
@@ -347,6 +349,14 @@ __global__ void __launch_bounds__(NT, 1) stage_full_kernel(const StageArgs a) {
     if (g.r0) {
 #pragma unroll
       for (int f = 0; f < 5; ++f) G[f] -= g.r0[((size_t)f * g.nz + gk) * g.nr + gi];
+    }
+    if (XT && g.damp_k) {  // wave-killing zones: the gas departures relax towards E0
+      const double kd = g.damp_k[gi];
+      if (kd != 0.0) {
+        const double V = g.vol[gi];
+#pragma unroll
+        for (int f = 0; f < 5; ++f) G[f] -= V * kd * (U[f] - g.e0c[((size_t)f * g.nz + gk) * g.nr + gi]);
+      }
     }
     if (a.mode == 1) {
 #pragma unroll

@@ -547,11 +547,13 @@ __device__ __forceinline__ void cell_prim(T g, const PCell<T>& c, const T* q, T&
 }
 
 // Source perturbation S(E0 + E') - S(E0) per unit volume (App. B sources,
-// stellar gravity, rotating frame), cylindrical geometry.
+// stellar gravity, rotating frame), cylindrical geometry, plus the whole
+// indirect-gravity source of Sect. 2.10 when it is on (the equilibrium's
+// residual carries none).
 // q: the staged cell, primitive gas perturbations (du, dv, dw, dP, drho) in
 // slots 0..4 and the conservative dust fields in slots 5..8.
-template <class T, int NF>
-__device__ __forceinline__ void pert_sources(const DevGrid& g, const PCell<T>& c, const T* q, T* S) {
+template <class T, int NF, bool XT>
+__device__ __forceinline__ void pert_sources(const DevGrid& g, const PCell<T>& c, int j, const T* q, T* S) {
   const T Om = (T)g.omega;
   const T rho = c.rho0 + q[RHO], du = q[MU], dv = q[MV], dw = q[MW], dp = q[EN];
   const T v = c.v0 + dv;
@@ -573,6 +575,23 @@ __device__ __forceinline__ void pert_sources(const DevGrid& g, const PCell<T>& c
       S[DMU] = S[DMV] = S[DMW] = T(0);
     }
     S[DRHO] = T(0);
+  }
+  if (XT && g.x_ind != 0.0) {
+    T gr, gt;  // grad Phi_ind, (r, theta), tabulated per axis-1 index in the state precision
+    if constexpr (sizeof(T) == 4) {
+      gr = g.ind_gf[j];
+      gt = g.ind_gf[g.nth + j];
+    } else {
+      gr = g.ind_g[j];
+      gt = g.ind_g[g.nth + j];
+    }
+    S[MU] -= rho * gr;
+    S[MV] -= rho * gt;
+    S[EN] -= rho * (du * gr + v * gt);
+    if (NF == 9 && q[DRHO] > T(0)) {
+      S[DMU] -= q[DRHO] * gr;
+      S[DMV] -= q[DRHO] * gt;
+    }
   }
 }
 
@@ -635,7 +654,9 @@ __device__ __forceinline__ T pert_cell_dt(const DevGrid& g, const PertTables<T>&
   return dt;
 }
 
-template <class T, int NF, int TR, int TT, int TZ, int NT, int MINB, class P>
+// XT: the optional terms (indirect gravity, wave-killing zones) are compiled
+// in; the plain instantiation carries none of their code.
+template <class T, int NF, int TR, int TT, int TZ, int NT, int MINB, class P, bool XT>
 __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> a) {
   constexpr int BX = TR + 4, BY = TT + 4, BZ = TZ + 4, BOX = BX * BY * BZ, NCORE = TR * TT * TZ;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -736,10 +757,20 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
     }
     if (g.geom == GEOM_CYL) {
       T S[NF];
-      pert_sources<T, NF>(g, ce, q, S);
+      pert_sources<T, NF, XT>(g, ce, gj, q, S);
       const T V = a.t.vol[gi];
 #pragma unroll
       for (int f = 0; f < NF; ++f) G[f] += V * S[f];
+    }
+    if (XT && g.damp_k) {  // wave-killing zones: the gas departures E' relax towards 0
+      T kd;
+      if constexpr (sizeof(T) == 4) kd = g.damp_kf[gi];
+      else kd = g.damp_k[gi];
+      if (kd != T(0)) {
+        const T V = a.t.vol[gi];
+#pragma unroll
+        for (int f = 0; f < 5; ++f) G[f] -= V * kd * a.in[f][lin];
+      }
     }
     const T iv = a.t.ivol[gi];
     T E[NF];

@@ -25,7 +25,7 @@ ROSSBI_FP64, ROSSBI_FP32_PERT, ROSSBI_FP64_PERT = 0, 1, 2
 
 # every function declared in include/rossbi.h
 EXPORTS = (
-    "rossbi_init_grid", "rossbi_set_equilibrium", "rossbi_get_equilibrium", "rossbi_cfl_dt", "rossbi_step",
+    "rossbi_init_grid", "rossbi_set_equilibrium", "rossbi_set_indirect", "rossbi_indirect_moments", "rossbi_set_damping", "rossbi_get_equilibrium", "rossbi_cfl_dt", "rossbi_step",
     "rossbi_step_host", "rossbi_step_noalloc", "rossbi_adjoint_step", "rossbi_adjoint_dstokes",
     "rossbi_conservation_sums", "rossbi_fallback_count", "rossbi_take_status", "rossbi_profile_enable",
     "rossbi_profile_read", "rossbi_nfields", "rossbi_precision", "rossbi_destroy", "rossbi_status_string",
@@ -47,6 +47,10 @@ class rossbi_disc_params(ctypes.Structure):
 
 class rossbi_dust_params(ctypes.Structure):
     _fields_ = [("stokes", ctypes.c_double), ("drag_law", ctypes.c_int)]
+
+
+class rossbi_damping_params(ctypes.Structure):
+    _fields_ = [("r_edge_in", ctypes.c_double), ("r_edge_out", ctypes.c_double), ("period_factor", ctypes.c_double)]
 
 
 class RossbiError(RuntimeError):
@@ -71,6 +75,9 @@ def load(path: str = LIB_PATH):
     L = ctypes.CDLL(path)
     L.rossbi_init_grid.argtypes = [ctypes.POINTER(rossbi_grid_desc), _VP, ctypes.POINTER(_VP)]
     L.rossbi_set_equilibrium.argtypes = [_VP, ctypes.POINTER(rossbi_disc_params)]
+    L.rossbi_set_indirect.argtypes = [_VP, ctypes.c_double]
+    L.rossbi_indirect_moments.argtypes = [_VP, _PP, _DP]
+    L.rossbi_set_damping.argtypes = [_VP, ctypes.POINTER(rossbi_damping_params)]
     L.rossbi_get_equilibrium.argtypes = [_VP, _DP]
     L.rossbi_cfl_dt.argtypes = [_VP, _PP, _DP]
     L.rossbi_step.argtypes = [_VP, _PP, _PP, ctypes.c_double, ctypes.POINTER(rossbi_dust_params), _DP]
@@ -197,6 +204,25 @@ def rossbi_adjoint_step(grid, state, dt, dust, lam_np1, lam_n, want_dstokes=Fals
                                       _fields(lam_n, nf), ctypes.byref(v) if want_dstokes else None),
            "rossbi_adjoint_step")
     return v.value if want_dstokes else None
+
+
+def rossbi_set_indirect(grid, x_ref):
+    """Indirect gravity of Sect. 2.10 with constant X_ref (0 switches it off)."""
+    _check(load().rossbi_set_indirect(grid, float(x_ref)), "rossbi_set_indirect")
+
+
+def rossbi_set_damping(grid, zones):
+    """Wave-killing zones (r_edge_in, r_edge_out, period_factor), or None for off."""
+    p = None if zones is None else ctypes.byref(rossbi_damping_params(*map(float, zones)))
+    _check(load().rossbi_set_damping(grid, p), "rossbi_set_damping")
+
+
+def rossbi_indirect_moments(grid, state) -> np.ndarray:
+    """(A_disc, B_disc) of Sect. 2.10 of a state (without X_ref)."""
+    out = np.zeros(2)
+    _check(load().rossbi_indirect_moments(grid, _fields(state, rossbi_nfields(grid)), out.ctypes.data_as(_DP)),
+           "rossbi_indirect_moments")
+    return out
 
 
 def rossbi_adjoint_dstokes(grid, reset=False) -> float:

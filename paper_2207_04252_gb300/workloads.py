@@ -67,6 +67,18 @@ class Grid:
     def cfl_dt(self, state):
         return R.rossbi_cfl_dt(self.h, state)
 
+    def set_indirect(self, x_ref):
+        """Indirect gravity of Sect. 2.10 with constant X_ref (0 = off)."""
+        R.rossbi_set_indirect(self.h, x_ref)
+
+    def set_damping(self, zones):
+        """Wave-killing zones (r_edge_in, r_edge_out, period_factor), or None."""
+        R.rossbi_set_damping(self.h, zones)
+
+    def indirect_moments(self, state):
+        """(A_disc, B_disc) of Sect. 2.10 of a state, FP64."""
+        return R.rossbi_indirect_moments(self.h, state)
+
     def sums(self, state):
         return R.rossbi_conservation_sums(self.h, state)
 

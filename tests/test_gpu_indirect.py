@@ -1,0 +1,151 @@
+"""Parity of the indirect gravity (Sect. 2.10) on the GPU with the oracle.
+
+A lopsided disc (the vortex workload plus an m = 1 gas bump and a dust bump,
+tests/test_oracle_indirect.py) pulls the star; every RK stage sums the disc
+moments A, B over its input state (FP64 block partials, fixed-order
+reduction) and adds -grad Phi_ind to gas and dust.  The GPU follows the
+oracle's dt sequence; bars as for the forms without the term: FP64 and the
+FP64 perturbation form <= 1e-12, the FP32 perturbation form <= 1e-5.  The
+grid 20 x 18 x 16 spans several 14 x 6 x 6 tiles with ragged tails.
+"""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as syn
+from tests.parity import rel_l1
+from tests.test_oracle_indirect import _lopsided, bump
+
+pytestmark = pytest.mark.gpu
+
+X_REF = 0.7
+STEPS = 30
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    from paper_2207_04252_gb300 import build
+    build.build()
+    from paper_2207_04252_gb300 import rossbi, workloads
+    torch.cuda.init()
+    return rossbi, workloads
+
+
+def _gpu_state(g, E_full):
+    """A full conservative state in the grid's precision form, on the device."""
+    import torch
+    E = E_full.copy()
+    if g.perturbation:
+        E[:5] -= g.equilibrium()[:, :, None, :]
+    return torch.from_numpy(E).to("cuda", g.dtype).contiguous()
+
+
+def _lopsided_gpu(g):
+    return _gpu_state(g, bump(g.full_state(g.initial_state("cuda")), g.centres(0), g.centres(1), g.centres(2)))
+
+
+@pytest.fixture(scope="module")
+def reference():
+    """Oracle runs of the lopsided vortex with and without the term."""
+    w = syn.scaled(syn.VORTEX, 20, 18, 16)
+    o = oracle.Oracle(w)
+    E0 = _lopsided(o)
+    o.set_indirect(X_REF)
+    E, _, dts = o.run(E0.copy(), steps=STEPS)
+    assert o.take_status() == 0
+    o.set_indirect(0.0)
+    E_off, _, _ = o.run(E0.copy(), dts=dts)
+    return w, o, E0, E, E_off, dts
+
+
+@pytest.mark.parametrize("form", ["fp64", "fp64_pert", "fp32_pert"])
+def test_indirect_parity(lib, reference, form):
+    R, W = lib
+    w, o, E0, E_ref, E_off, dts = reference
+    prec = {"fp64": R.ROSSBI_FP64, "fp64_pert": R.ROSSBI_FP64_PERT, "fp32_pert": R.ROSSBI_FP32_PERT}[form]
+    tol = 1e-5 if form == "fp32_pert" else 1e-12
+    g = W.Grid(w, precision=prec)
+    g.set_indirect(X_REF)
+    s = _lopsided_gpu(g)
+    for dt in dts:
+        g.step(s, dt=dt)
+    assert g.take_status() == 0
+    V = o.volumes()
+    errs = rel_l1(g.full_state(s), E_ref, V)
+    assert all(e <= tol for e in errs.values()), errs
+    # the term is far above the bar: without it the runs part by much more
+    off = rel_l1(E_off, E_ref, V)
+    assert off["momentum"] > 100 * max(tol, errs["momentum"]), (off, errs)
+    g.close()
+
+
+def test_moments_match_oracle(lib):
+    """The library's moments of a state against the oracle's, on the
+    lopsided vortex at 64 x 128 x 32 (262,144 cells), all three forms.  The
+    FP32 form sums each lane's cells of a row in float before the FP64
+    accumulation, hence its looser bar."""
+    R, W = lib
+    w = syn.scaled(syn.VORTEX, 64, 128, 32)
+    o = oracle.Oracle(w)
+    o.set_indirect(1.0)
+    for prec, tol in ((R.ROSSBI_FP64, 1e-12), (R.ROSSBI_FP64_PERT, 1e-12), (R.ROSSBI_FP32_PERT, 1e-5)):
+        g = W.Grid(w, precision=prec)
+        s = _lopsided_gpu(g)
+        ab = g.indirect_moments(s)
+        ref = o.indirect(g.full_state(s))
+        assert np.hypot(*ref) > 0
+        assert np.abs(ab - ref).max() <= tol * np.hypot(*ref), (prec, ab, ref)
+        g.close()
+
+
+def test_undisturbed_disc_feels_nothing(lib):
+    """An undisturbed disc has A = B = 0 exactly, so runs with and without
+    the term agree bit for bit; the FP64 form also keeps E = E0 exactly
+    (balanced scheme, Sect. 2.8)."""
+    R, W = lib
+    w = replace(syn.scaled(syn.DISC_NOISE, 20, 18, 16), noise_amp=0.0)
+    for prec in (R.ROSSBI_FP64, R.ROSSBI_FP32_PERT):
+        runs = []
+        for x_ref in (1.0, 0.0):
+            g = W.Grid(w, precision=prec)
+            g.set_indirect(x_ref)
+            s = g.initial_state("cuda")
+            s0 = s.clone()
+            assert not g.indirect_moments(s).any()
+            dt = g.cfl_dt(s)
+            for _ in range(5):
+                g.step(s, dt=dt)
+            assert g.take_status() == 0
+            if prec == R.ROSSBI_FP64:
+                assert bool((s == s0).all())
+            runs.append(s.cpu())
+            g.close()
+        assert bool((runs[0] == runs[1]).all())
+
+
+def test_argument_errors(lib):
+    import torch
+    R, W = lib
+    box = W.Grid(syn.scaled(syn.SOD, 16, 2, 2))
+    with pytest.raises(R.RossbiError) as e:
+        box.set_indirect(1.0)
+    assert e.value.code == R.ROSSBI_ERR_ARG
+    box.set_indirect(0.0)  # off is always accepted
+    box.close()
+    g = W.Grid(syn.scaled(syn.VORTEX, 20, 18, 16))
+    for bad in (float("nan"), float("inf")):
+        with pytest.raises(R.RossbiError):
+            g.set_indirect(bad)
+    s = g.initial_state("cuda")
+    lam = torch.ones_like(s)
+    g.set_indirect(X_REF)
+    with pytest.raises(R.RossbiError) as e:
+        g.adjoint_step(s, 1e-3, lam)
+    assert e.value.code == R.ROSSBI_ERR_UNSUPPORTED
+    g.set_indirect(0.0)
+    g.adjoint_step(s, 1e-3, lam)  # back to the plain step: the adjoint runs
+    assert g.take_status() == 0
+    g.close()
