@@ -137,8 +137,10 @@ rossbi_status rossbi_set_equilibrium(rossbi_grid* g, const rossbi_disc_params* d
  *           default).  Finite; non-zero only on cylindrical grids.
  * The first non-zero call allocates (and synchronises) the device tables;
  * later calls only change the constant.  While the term is on, each step
- * launches two extra reductions per stage, rossbi_adjoint_step returns
- * ROSSBI_ERR_UNSUPPORTED (its global coupling has no adjoint here).
+ * launches a moments kernel and its reduction before each stage, and
+ * rossbi_adjoint_step carries the term too: its local part, and the
+ * cotangent that reaches every cell's rho and rho_d through A and B (one
+ * more reduction and broadcast per stage).
  * Errors: ROSSBI_ERR_ARG (NULL grid, non-finite x_ref, non-zero x_ref on a
  * Box), ROSSBI_ERR_OOM, ROSSBI_ERR_CUDA. */
 rossbi_status rossbi_set_indirect(rossbi_grid* g, double x_ref);
@@ -251,9 +253,9 @@ rossbi_status rossbi_step_noalloc(rossbi_grid* g, void* const* state, double dt,
  *             running total (rossbi_adjoint_dstokes), so callers can leave
  *             dparam NULL and keep the call asynchronous.
  * The library allocates five FP64 states of scratch on the first call.
- * Errors: ROSSBI_ERR_ARG, ROSSBI_ERR_UNSUPPORTED (perturbation forms, or
- * indirect gravity switched on), ROSSBI_ERR_OOM, ROSSBI_ERR_CUDA, and after a
- * synchronising call ROSSBI_ERR_NONPHYSICAL / ROSSBI_ERR_RIEMANN. */
+ * Errors: ROSSBI_ERR_ARG, ROSSBI_ERR_UNSUPPORTED (perturbation forms),
+ * ROSSBI_ERR_OOM, ROSSBI_ERR_CUDA, and after a synchronising call
+ * ROSSBI_ERR_NONPHYSICAL / ROSSBI_ERR_RIEMANN. */
 rossbi_status rossbi_adjoint_step(rossbi_grid* g, const void* const* state_n, double dt,
                                   const rossbi_dust_params* dust, const void* const* lam_np1, void* const* lam_n,
                                   double* dparam);

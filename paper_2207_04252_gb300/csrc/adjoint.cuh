@@ -540,6 +540,7 @@ struct AdjPointArgs {
   DragArgs drag;
   int stage2;
   double* partials;        // [gridDim.x] block sums of lambda_out . dD/dSt
+  double* ind_partials;    // indirect gravity on: [2][gridDim.x] block sums of dJ/dA, dJ/dB (without X_ref)
 };
 
 constexpr int ADJ_PT_NT = 256;
@@ -550,6 +551,7 @@ __global__ void __launch_bounds__(ADJ_PT_NT) adj_point_kernel(const AdjPointArgs
   const DevGrid& g = a.g;
   const size_t ncell = (size_t)g.nr * g.nth * g.nz;
   double dst = 0.0;
+  double pa = 0.0, pb = 0.0;  // indirect gravity: cotangents of A_disc, B_disc (over X_ref)
   for (size_t lin = blockIdx.x * (size_t)ADJ_PT_NT + threadIdx.x; lin < ncell; lin += (size_t)gridDim.x * ADJ_PT_NT) {
     const int gi = (int)(lin % g.nr);
     const int gk = (int)(lin / ((size_t)g.nr * g.nth));
@@ -584,6 +586,27 @@ __global__ void __launch_bounds__(ADJ_PT_NT) adj_point_kernel(const AdjPointArgs
 #pragma unroll
         for (int f = 0; f < 5; ++f) src[f] -= kd * s[f];
       }
+      if (g.x_ind != 0.0) {
+        // indirect gravity, S = -(rho gr, rho gt, 0, m_u gr + m_v gt) and
+        // -(rho_d gr, rho_d gt, 0) for dust: its local part at fixed
+        // (gr, gt), and P = dJ/dgr, Q = dJ/dgt, which reach A and B through
+        // gr = X (A c + B s), gt = X (-A s + B c)
+        const int gj = (int)((lin / g.nr) % g.nth);
+        const double gr = g.ind_g[gj], gt = g.ind_g[g.nth + gj];
+        src[RHO] -= s[MU] * gr + s[MV] * gt;
+        src[MU] -= s[EN] * gr;
+        src[MV] -= s[EN] * gt;
+        double P = -(s[MU] * E[RHO] + s[EN] * E[MU]);
+        double Q = -(s[MV] * E[RHO] + s[EN] * E[MV]);
+        if (NF == 9 && E[DRHO] > 0.0) {
+          src[DRHO] -= s[DMU] * gr + s[DMV] * gt;
+          P -= s[DMU] * E[DRHO];
+          Q -= s[DMV] * E[DRHO];
+        }
+        const double c = g.ind_cs[gj], sn = g.ind_cs[g.nth + gj];
+        pa += P * c - Q * sn;
+        pb += P * sn + Q * c;
+      }
     }
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
@@ -598,6 +621,33 @@ __global__ void __launch_bounds__(ADJ_PT_NT) adj_point_kernel(const AdjPointArgs
   }
   const double t = block_sum<ADJ_PT_NT>(dst, red);
   if (threadIdx.x == 0) a.partials[blockIdx.x] = t;
+  if (g.x_ind != 0.0) {
+    const double ta = block_sum<ADJ_PT_NT>(pa, red);
+    const double tb = block_sum<ADJ_PT_NT>(pb, red);
+    if (threadIdx.x == 0) {
+      a.ind_partials[blockIdx.x] = ta;
+      a.ind_partials[gridDim.x + blockIdx.x] = tb;
+    }
+  }
+}
+
+// The cotangent that reaches the stage input through the disc moments:
+// A = sum w (rho - rho_0 + rho_d) cos(theta), B likewise with sin, so
+// lam[RHO] and lam[DRHO] gain X_ref w (dA cos(theta_j) + dB sin(theta_j)),
+// (dA, dB) the reduced point-kernel partials; w = V r / R^3 [nz][nr].
+__global__ void __launch_bounds__(ADJ_PT_NT) adj_indirect_bcast_kernel(const DevGrid g, const double* w,
+                                                                       const double* dAB, double* lam_rho,
+                                                                       double* lam_drho) {
+  const size_t ncell = (size_t)g.nr * g.nth * g.nz;
+  const double dA = g.x_ind * dAB[0], dB = g.x_ind * dAB[1];
+  for (size_t lin = blockIdx.x * (size_t)ADJ_PT_NT + threadIdx.x; lin < ncell; lin += (size_t)gridDim.x * ADJ_PT_NT) {
+    const int i = (int)(lin % g.nr);
+    const size_t jk = lin / g.nr;
+    const int j = (int)(jk % g.nth), k = (int)(jk / g.nth);
+    const double v = w[(size_t)k * g.nr + i] * (dA * g.ind_cs[j] + dB * g.ind_cs[g.nth + j]);
+    lam_rho[lin] += v;
+    if (lam_drho) lam_drho[lin] += v;
+  }
 }
 
 struct AdjFluxArgs {

@@ -68,6 +68,8 @@ struct rossbi_grid {
   // indirect gravity: [2] disc moments A, B; [2][nth] cos / sin of the
   // azimuthal centres; [nz][nr] V r / R^3; [2][IND_BLOCKS] block partials
   double* d_ind = nullptr;
+  double* d_adj_ind = nullptr;         // adjoint of the indirect term: [2 stages][2][adj_blocks] partials,
+                                       // [2 stages][2] reduced, [2][nth] stage-1 gradient table
   double* d_damp = nullptr;            // wave-killing rates R(r) / tau per radial cell [nr]
   int adj_blocks = 0;
   // stage-kernel timing (rossbi_profile_*)
@@ -898,8 +900,25 @@ rossbi_status adjoint_reverse(rossbi_grid* g, void* const* state, double dt, con
   p.tau = dt;
   p.stage2 = 1;
   p.partials = g->d_adj_part;
+  // indirect gravity: the stage's gradient tables (stage 2: those of E*, left
+  // in the grid's tables by the recompute; stage 1: the saved copy), block
+  // partials of dJ/dA, dJ/dB, their reduction, and the broadcast through the
+  // moments into the cotangent of the stage input
+  const bool ind = g->dg.x_ind != 0.0;
+  const IndLayout L = ind_layout(g->desc);
+  double* ind_part = g->d_adj_ind;
+  double* ind_dab = g->d_adj_ind + 4 * (size_t)nb;
+  const double* ind_g1 = g->d_adj_ind + 4 * (size_t)nb + 4;
+  p.ind_partials = ind_part;
   adj_point_kernel<NF><<<nb, ADJ_PT_NT, 0, g->stream>>>(p);
   CK(cudaGetLastError());
+  if (ind) {
+    reduce_partials_kernel<<<2, RED_NT, 0, g->stream>>>(ind_part, nb, 2, ind_dab, nullptr);
+    CK(cudaGetLastError());
+    adj_indirect_bcast_kernel<<<nb, ADJ_PT_NT, 0, g->stream>>>(g->dg, g->d_ind + L.w, ind_dab, LamS[RHO],
+                                                                NF == 9 ? LamS[DRHO] : nullptr);
+    CK(cudaGetLastError());
+  }
   rossbi_status st = launch_adj_flux<NF, 0>(g, fa);
   if (st == ROSSBI_OK) st = launch_adj_flux<NF, 1>(g, fa);
   if (st == ROSSBI_OK) st = launch_adj_flux<NF, 2>(g, fa);
@@ -915,8 +934,20 @@ rossbi_status adjoint_reverse(rossbi_grid* g, void* const* state, double dt, con
   p.tau = 0.5 * dt;
   p.stage2 = 0;
   p.partials = g->d_adj_part + nb;
+  if (ind) {
+    p.g.ind_g = ind_g1;
+    p.ind_partials = ind_part + 2 * (size_t)nb;
+  }
   adj_point_kernel<NF><<<nb, ADJ_PT_NT, 0, g->stream>>>(p);
   CK(cudaGetLastError());
+  if (ind) {
+    reduce_partials_kernel<<<2, RED_NT, 0, g->stream>>>(ind_part + 2 * (size_t)nb, nb, 2, ind_dab + 2, nullptr);
+    CK(cudaGetLastError());
+    adj_indirect_bcast_kernel<<<nb, ADJ_PT_NT, 0, g->stream>>>(g->dg, g->d_ind + L.w, ind_dab + 2,
+                                                                (double*)lam_n[RHO],
+                                                                NF == 9 ? (double*)lam_n[DRHO] : nullptr);
+    CK(cudaGetLastError());
+  }
   st = launch_adj_flux<NF, 0>(g, fa);
   if (st == ROSSBI_OK) st = launch_adj_flux<NF, 1>(g, fa);
   if (st == ROSSBI_OK) st = launch_adj_flux<NF, 2>(g, fa);
@@ -960,6 +991,11 @@ rossbi_status adjoint_step(rossbi_grid* g, void* const* state, double dt, const 
     g->d_adj_slots = slots;
     g->adj_blocks = nb;
   }
+  const bool ind = g->dg.x_ind != 0.0;
+  if (ind && !g->d_adj_ind) {
+    const size_t n = 4 * (size_t)g->adj_blocks + 4 + 2 * (size_t)g->desc.nth;
+    CK(cudaMalloc(&g->d_adj_ind, n * sizeof(double)));
+  }
   double *Y1[9], *Es[9], *Y2[9], *Mu[9], *LamS[9];
   for (int f = 0; f < g->nf; ++f) {
     Y1[f] = g->d_adj + f * g->ncell;
@@ -982,6 +1018,13 @@ rossbi_status adjoint_step(rossbi_grid* g, void* const* state, double dt, const 
     a.out[f] = Y1[f];
   }
   a.tau_frac = 0.5;
+  if (ind) {  // the moments of E^n; stage 1's gradient table is kept for the reverse sweep
+    st = indirect_moments(g, state);
+    if (st != ROSSBI_OK) return st;
+    const IndLayout L = ind_layout(g->desc);
+    CK(cudaMemcpyAsync(g->d_adj_ind + 4 * (size_t)g->adj_blocks + 4, g->d_ind + L.g,
+                       2 * (size_t)g->desc.nth * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+  }
   st = launch_stage(g, a, nblocks);
   if (st != ROSSBI_OK) return st;
   double* const* Estar = Y1;
@@ -1001,6 +1044,7 @@ rossbi_status adjoint_step(rossbi_grid* g, void* const* state, double dt, const 
     a.out[f] = Y2[f];
   }
   a.tau_frac = 1.0;
+  if (ind && (st = indirect_moments(g, (void* const*)Estar)) != ROSSBI_OK) return st;
   st = launch_stage(g, a, nblocks);
   if (st != ROSSBI_OK) return st;
   st = g->nf == 9 ? adjoint_reverse<9>(g, state, dt, drag, lam_np1, lam_n, Y1, Estar, Y2, Mu, LamS)
@@ -1065,6 +1109,7 @@ void rossbi_destroy(rossbi_grid* g) {
   if (g->d_adj_part) cudaFree(g->d_adj_part);
   if (g->d_adj_slots) cudaFree(g->d_adj_slots);
   if (g->d_ind) cudaFree(g->d_ind);
+  if (g->d_adj_ind) cudaFree(g->d_adj_ind);
   if (g->d_damp) cudaFree(g->d_damp);
   if (g->h_pinned) cudaFreeHost(g->h_pinned);
   for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
@@ -1447,7 +1492,6 @@ rossbi_status rossbi_adjoint_step(rossbi_grid* g, const void* const* state_n, do
                                   const rossbi_dust_params* dust, const void* const* lam_np1, void* const* lam_n,
                                   double* dparam) {
   if (!g) return ROSSBI_ERR_ARG;
-  if (g->dg.x_ind != 0.0) return ROSSBI_ERR_UNSUPPORTED;  // the global indirect term has no adjoint here
   return adjoint_step(g, (void* const*)state_n, dt, dust, lam_np1, lam_n, dparam);
 }
 
