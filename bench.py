@@ -303,6 +303,23 @@ def measure_damping(R, g, s, torch, zones=(0.625, 1.68, 1.0), steps=4, warmup=2)
             "steps": steps, "warmup": warmup, "status": R.status_string(status)}
 
 
+def measure_explosion(R, W, syn, torch, steps=2, warmup=1):
+    """The cylindrical explosion of Sect. 4.1 at the paper's 1600 x 3200 polar
+    resolution (one z cell), FP64 form, device-paced steps."""
+    w = syn.EXPLOSION
+    g = W.Grid(w, precision=R.ROSSBI_FP64, stream=torch.cuda.current_stream())
+    s = g.initial_state()
+    g.cfl_dt(s)
+    ms = _timed_steps(g, s, torch, steps, warmup)
+    status = g.take_status()
+    g.close()
+    del s
+    torch.cuda.empty_cache()
+    return {"workload": w.name, "value": w.ncell / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "warmup": warmup, "dtype": "f64", "status": R.status_string(status),
+            "note": "one z cell: the 14x6x6 tile computes six z planes per cell"}
+
+
 def measure_adjoint(R, W, syn, torch, steps=4, warmup=3):
     """Cost of the FP64 discrete adjoint on the adjoint workload (128x256x32,
     bi-fluid): one rossbi_adjoint_step (forward recompute of the step included)
@@ -480,6 +497,7 @@ def run_ours(args):
             line["fp64_form"] = fp64
             line["fp32_over_fp64"] = value / world / fp64["value"]
             line["fp32_error_vs_fp64"] = fp32_error_vs_fp64(R, workloads, syn, torch)
+            line["explosion"] = measure_explosion(R, workloads, syn, torch)
         if not args.no_extras and not args.indirect:
             ind = measure_indirect(R, g, s, torch)
             ind["over_plain_step"] = ind["ms_per_step"] / (elapsed_ms / args.steps)

@@ -69,9 +69,11 @@ typedef struct rossbi_grid rossbi_grid; /* opaque, library-owned */
  *   nr,nth,nz: cells along r (x), theta (y), z.  Each >= 1.
  *   bc_lo/hi : per axis; ROSSBI_BC_EQUILIBRIUM ghosts carry E' = 0,
  *              PERIODIC wraps, OUTFLOW copies the nearest interior E'.
- *              A cylindrical grid needs periodic theta and non-periodic r, z.
+ *              A cylindrical grid needs periodic theta and non-periodic r.
  *   gamma    : ratio of specific heats (> 1).
- *   gm       : G M of the central star (cylindrical only).
+ *   gm       : G M of the central star (cylindrical only; >= 0, and > 0 for a
+ *              disc equilibrium or the constant-Stokes drag law, which use
+ *              the Keplerian frequency).
  *   omega_frame : angular speed of the rotating frame (cylindrical only).
  *   cfl      : N_CFL of the CFL condition (Sect. 2.5; the paper uses 1/2).
  *   n_dust   : 0 (gas only, 5 fields) or 1 (gas + one dust fluid, 9 fields).
@@ -117,8 +119,10 @@ rossbi_status rossbi_init_grid(const rossbi_grid_desc* desc, void* cuda_stream, 
 
 /* Sets the disc equilibrium E0 (App. A) at cell centres and faces, and runs
  * the "empty run" of Sect. 2.8 once to store the balanced residual
- * R0 = G(E0) used by the FP64 form.  disc == NULL sets E0 = 0 (Box runs).
- * Cylindrical grids require disc != NULL.  Synchronises the stream. */
+ * R0 = G(E0) used by the FP64 form.  disc == NULL sets E0 = 0: Box runs, and
+ * cylindrical runs without a disc such as the explosion test of Sect. 4.1
+ * (FP64 form only: the perturbation forms return ROSSBI_ERR_UNSUPPORTED for a
+ * cylindrical grid without a disc).  Synchronises the stream. */
 rossbi_status rossbi_set_equilibrium(rossbi_grid* g, const rossbi_disc_params* disc);
 
 /* Indirect gravity of Sect. 2.10.  The star, pulled by an asymmetric disc,
@@ -153,7 +157,7 @@ rossbi_status rossbi_set_indirect(rossbi_grid* g, double x_ref);
  * part of G, so it acts inside both RK stages and in rossbi_adjoint_step.
  * Dust is not damped.  p == NULL switches the zones off (the default);
  * otherwise r_in < r_edge_in <= r_edge_out < r_out and period_factor > 0.
- * Cylindrical grids with an equilibrium set only.  Allocates an nr-entry
+ * Cylindrical grids with a disc equilibrium only.  Allocates an nr-entry
  * table on first use; synchronises the stream.
  * Errors: ROSSBI_ERR_ARG, ROSSBI_ERR_OOM, ROSSBI_ERR_CUDA. */
 rossbi_status rossbi_set_damping(rossbi_grid* g, const rossbi_damping_params* p);

@@ -295,6 +295,12 @@ def initial_state(o: Oracle) -> np.ndarray:
         E[syn.F_RHO] = rho[None, None, :]
         E[syn.F_EN] = (p / (g - 1.0))[None, None, :]
         return E
+    if w.ic == "explosion":  # Sect. 4.1: (rho, P) = (1, 1) for r <= 0.4, (0.125, 0.1) outside, at rest
+        rc, _ = o.coords(0)
+        inside = rc <= 0.4
+        E[syn.F_RHO] = np.where(inside, 1.0, 0.125)[None, None, :]
+        E[syn.F_EN] = (np.where(inside, 1.0, 0.1) / (g - 1.0))[None, None, :]
+        return E
     E0 = o.equilibrium_state()
     rho0 = E0[syn.F_RHO]
     v0 = E0[syn.F_MV] / rho0

@@ -151,9 +151,9 @@ rossbi_status check_desc(const rossbi_grid_desc& d) {
     if ((d.bc_lo[a] == ROSSBI_BC_PERIODIC) != (d.bc_hi[a] == ROSSBI_BC_PERIODIC)) return ROSSBI_ERR_ARG;
   }
   if (d.geometry == ROSSBI_GEOM_CYL) {
-    if (!(d.x0[0] > 0.0) || !(d.gm > 0.0)) return ROSSBI_ERR_ARG;
+    if (!(d.x0[0] > 0.0) || !(d.gm >= 0.0) || !std::isfinite(d.gm)) return ROSSBI_ERR_ARG;
     if (d.bc_lo[1] != ROSSBI_BC_PERIODIC) return ROSSBI_ERR_ARG;
-    if (d.bc_lo[0] == ROSSBI_BC_PERIODIC || d.bc_lo[2] == ROSSBI_BC_PERIODIC) return ROSSBI_ERR_ARG;
+    if (d.bc_lo[0] == ROSSBI_BC_PERIODIC) return ROSSBI_ERR_ARG;
   }
   if (d.precision != ROSSBI_FP64 && d.precision != ROSSBI_FP32_PERT && d.precision != ROSSBI_FP64_PERT)
     return ROSSBI_ERR_ARG;
@@ -648,6 +648,8 @@ rossbi_status drag_args(rossbi_grid* g, const rossbi_dust_params* dust, DragArgs
     drag.stokes = dust->stokes;
     drag.law = dust->drag_law;
     if (!(dust->stokes > 0.0)) return ROSSBI_ERR_ARG;
+    if (dust->drag_law == 0 && g->desc.geometry == ROSSBI_GEOM_CYL && !(g->desc.gm > 0.0))
+      return ROSSBI_ERR_ARG;  // t_s = St / Omega_K needs a star
     if (dust->drag_law == 1) {
       if (!g->has_disc) return ROSSBI_ERR_ARG;
       double rho1, vth1, p1;
@@ -1229,7 +1231,11 @@ rossbi_status rossbi_init_grid(const rossbi_grid_desc* desc, void* cuda_stream, 
 rossbi_status rossbi_set_equilibrium(rossbi_grid* g, const rossbi_disc_params* disc) {
   if (!g) return ROSSBI_ERR_ARG;
   const rossbi_grid_desc& d = g->desc;
-  if (d.geometry == ROSSBI_GEOM_CYL && !disc) return ROSSBI_ERR_ARG;
+  // a cylindrical grid without a disc (E0 = 0, e.g. the explosion test of
+  // Sect. 4.1) runs in the FP64 form; the perturbation forms' source
+  // coefficients are tabulated from a disc equilibrium
+  if (d.geometry == ROSSBI_GEOM_CYL && !disc && d.precision != ROSSBI_FP64) return ROSSBI_ERR_UNSUPPORTED;
+  if (d.geometry == ROSSBI_GEOM_CYL && disc && !(d.gm > 0.0)) return ROSSBI_ERR_ARG;  // Keplerian disc
   g->eq_set = false;
   g->dg.has_eq = 0;
   g->dg.e0c = g->dg.e0r = g->dg.e0z = g->dg.r0 = nullptr;
@@ -1445,7 +1451,7 @@ rossbi_status rossbi_set_damping(rossbi_grid* g, const rossbi_damping_params* p)
   }
   const rossbi_grid_desc& d = g->desc;
   const double rin = d.x0[0], rout = d.x1[0];
-  if (d.geometry != ROSSBI_GEOM_CYL || !g->eq_set) return ROSSBI_ERR_ARG;
+  if (d.geometry != ROSSBI_GEOM_CYL || !g->eq_set || !g->has_disc) return ROSSBI_ERR_ARG;
   if (!(p->r_edge_in > rin) || !(p->r_edge_out < rout) || !(p->r_edge_in <= p->r_edge_out)) return ROSSBI_ERR_ARG;
   if (!(p->period_factor > 0.0) || !std::isfinite(p->period_factor)) return ROSSBI_ERR_ARG;
   const double pi = 3.14159265358979323846;

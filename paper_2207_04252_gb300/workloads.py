@@ -159,6 +159,11 @@ class Grid:
             Ep[syn.F_RHO] = np.where(left, 1.0, 0.125)[None, None, :]
             Ep[syn.F_EN] = (np.where(left, 1.0, 0.1) / (g - 1.0))[None, None, :]
             return Ep
+        if w.ic == "explosion":  # at rest; (rho, P) = (1, 1) inside r = 0.4, (0.125, 0.1) outside
+            high = self.centres(0) <= 0.4
+            Ep[syn.F_RHO] = np.where(high, 1.0, 0.125)[None, None, :]
+            Ep[syn.F_EN] = (np.where(high, 1.0, 0.1) / (g - 1.0))[None, None, :]
+            return Ep
         E0 = self.equilibrium()
         rho0 = E0[syn.F_RHO][:, None, :]
         v0 = (E0[syn.F_MV] / E0[syn.F_RHO])[:, None, :]

@@ -2,7 +2,7 @@
 
 The paper's own workloads (Sect. 4: cylindrical explosion, equilibrium disc,
 Rossby-wave vortices, dust trapping; the "column Gaussian vortex" of its
-scaling runs) use no public dataset.  These five describe the sizes, extents,
+scaling runs) use no public dataset.  These six describe the sizes, extents,
 parameters and seeds of the synthetic inputs; the initial-condition recipe is
 written out independently by each side.
 
@@ -41,7 +41,7 @@ class Workload:
     x1: tuple
     bc_lo: tuple
     bc_hi: tuple
-    ic: str                      # "sod", "noise", "vortex"
+    ic: str                      # "sod", "noise", "vortex", "explosion"
     steps: int
     gamma: float = 1.4
     gm: float = 1.0
@@ -114,7 +114,21 @@ THROUGHPUT = _disc("bifluid_two_vortices_512x1024x128", 512, 1024, 128, 50, ic="
                    seed=4252, vortices=((0.8, 0.0), (1.3, math.pi)), dust_ratio=0.01, dust_noise=1e-3,
                    stokes=0.05)
 
-ALL = (SOD, DISC_NOISE, VORTEX, ADJOINT, THROUGHPUT)
+# Cylindrical explosion (Sect. 4.1; Toro ch. 17): a 2-D Riemann problem on the
+# polar mesh, (rho, P) = (1, 1) for r <= 0.4 and (0.125, 0.1) outside, at rest;
+# no gravity, no rotation, no equilibrium, gamma = 1.4; N_r x N_theta =
+# 1600 x 3200 with one z cell.  The paper gives no radial extent: r in
+# [e^-pi, 1] makes every cell of the logarithmic mesh square at this
+# resolution (dr / r = dtheta).  The single z cell is thick (dz = 1) so that
+# the CFL step is set by the r and theta faces.  Run to t = 0.25, the time of
+# Toro's reference solution (the paper prints t = 2.5).
+EXPLOSION = Workload(
+    name="explosion_polar_1600x3200x1", geometry=GEOM_CYL, nr=1600, nth=3200, nz=1,
+    x0=(math.exp(-math.pi), 0.0, -0.5), x1=(1.0, 2.0 * math.pi, 0.5),
+    bc_lo=(BC_OUTFLOW, BC_PERIODIC, BC_PERIODIC), bc_hi=(BC_OUTFLOW, BC_PERIODIC, BC_PERIODIC),
+    ic="explosion", steps=0, gm=0.0, omega_frame=0.0, t_end=0.25)
+
+ALL = (SOD, DISC_NOISE, VORTEX, ADJOINT, THROUGHPUT, EXPLOSION)
 
 
 def by_name(name: str) -> Workload:
