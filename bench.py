@@ -466,6 +466,11 @@ def run_ours(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": None, "peak_kind": peak_kind, "kernel": kernel_tag,
                 "avg_launch_ms": avg_launch_s * 1e3}
+    # secondary figure: against the 2F field accesses per cell-step that a
+    # temporally fused two-stage tile (4-deep halo) would need
+    achieved_2f = 1.0 * g.nf * elem * w.ncell / avg_launch_s / 1e9
+    roofline["secondary_2f"] = {"achieved": achieved_2f, "frac": achieved_2f / peak,
+                                "bytes_per_cell_step": 2 * g.nf * elem}
     traffic, src = _traffic(kernel_tag, w.ncell)
     if traffic is not None:
         roofline["traffic"] = traffic
