@@ -168,9 +168,10 @@ def _gpu_smi_id(torch):
         return os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
 
 
-def cpu_baseline(w, steps=3, shape=(64, 128, 32)):
+def cpu_baseline(w, steps=7, shape=(64, 128, 32)):
     """Times the CPU oracle, as it stands, on a bounded sample of the workload:
-    the same workload on a reduced grid (same extents and physics)."""
+    the same workload on a reduced grid (same extents and physics), about ten
+    seconds of single-thread work."""
     import oracle
     import synthetic as syn
     ws = syn.scaled(w, *shape, steps=steps)
