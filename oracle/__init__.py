@@ -82,6 +82,7 @@ def lib():
         L.orc_set_indirect.argtypes = [ctypes.c_void_p, ctypes.c_double]
         L.orc_indirect.argtypes = [ctypes.c_void_p, _D, _D]
         L.orc_set_damping.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        L.orc_set_stokes_regime.argtypes = [ctypes.c_void_p, ctypes.c_double]
         _lib = L
     return _lib
 
@@ -174,6 +175,10 @@ class Oracle:
         period_factor <= 0 switches them off."""
         if lib().orc_set_damping(self.h, float(r_ein), float(r_eout), float(period_factor)):
             raise ValueError("damping zones must lie inside the radial extent of a cylindrical grid")
+
+    def set_stokes_regime(self, kappa):
+        """kappa = r_p / lambda_0 of drag law 2 (reading R19); <= 0: Epstein only."""
+        lib().orc_set_stokes_regime(self.h, float(kappa))
 
     def indirect(self, E):
         """X_ref (A_disc, B_disc) of the state E (Sect. 2.10)."""

@@ -76,6 +76,12 @@
 //      profile and the constants, which come from the cited work: the pins
 //      check the structure (local, linear, gas-only, the parabola through
 //      its end conditions, the period) and the equilibrium.
+//  R19 Stokes regime (Sect. 2.9, drag law 2): the Epstein stopping time of
+//      law 1 applies while r_p <= 9 lambda / 4; above, t_s = (4/9)(r_p/lambda)
+//      t_E (continuous at the switch).  The mean free path is lambda =
+//      lambda_0 / rho_g (Sect. 2.9: mu m_u / (sigma_eff rho)), and
+//      kappa = r_p / lambda_0 is a parameter; rho_s r_p is fixed, as for
+//      law 1, so that the Epstein stopping time gives St at r = 1, z = 0.
 //
 // Parity unpinned (readings checked only for their properties and for
 // self-consistency, since the paper gives no formula or value to test them
@@ -140,6 +146,7 @@ struct Oracle {
   double x_ind = 0.0;      // X_ref of the indirect-gravity term (Sect. 2.10), 0 = off
   bool damp = false;       // wave-killing zones of reading R17
   double damp_ein = 0.0, damp_eout = 0.0, damp_tau_in = 0.0, damp_tau_out = 0.0;
+  double kappa = 0.0;      // r_p / lambda_0 of the Stokes regime (reading R19)
   int status = 0;
   long newton_iters = 0, riemann_calls = 0;
 };
@@ -817,7 +824,8 @@ static void G_cell(Oracle& o, const Acc& E, int i, int j, int k, T G[9], const T
 template <class T>
 struct DustParamsT {
   T stokes;
-  int drag_law;  // 0: constant Stokes number St = t_s Omega_K(r); 1: Epstein, St fixed at (r=1, z=0)
+  int drag_law;  // 0: constant Stokes number St = t_s Omega_K(r); 1: Epstein, St fixed at (r=1, z=0);
+                 // 2: Epstein with the Stokes regime above r_p = 9 lambda / 4 (reading R19)
 };
 using DustParams = DustParamsT<double>;
 // Sect. 2.9 drag law with the semi-implicit integration of reading R7.
@@ -836,6 +844,8 @@ static void drag(const Oracle& o, int i, T U[9], double tau, const DustParamsT<T
     const T rhos_rp = dp.stokes * rho1 * std::sqrt(o.d.gamma * p1 / rho1) / std::sqrt(o.d.gm);
     const T cs = sqrt(o.d.gamma * pressure(o.d.gamma, U) / rg);
     ts = rhos_rp / (rg * cs);
+    // r_p / lambda = kappa rho_g; the Stokes regime lengthens t_s by (4/9) r_p / lambda
+    if (dp.drag_law == 2 && o.kappa * rg > 2.25) ts = ts * ((4.0 / 9.0) * (o.kappa * rg));
   }
   const T eps = rd / rg;
   const T kk = tau * (1.0 + eps) / ts;
@@ -1136,6 +1146,10 @@ int orc_set_damping(void* h, double r_ein, double r_eout, double f) {
   o.damp_tau_out = f * 2.0 * M_PI / std::sqrt(o.d.gm / (rout * rout * rout));
   return 0;
 }
+
+// kappa = r_p / lambda_0 of the Stokes regime of drag law 2 (reading R19);
+// kappa <= 0 keeps every cell in the Epstein regime.
+void orc_set_stokes_regime(void* h, double kappa) { ((Oracle*)h)->kappa = kappa; }
 
 void orc_counters(void* h, long* out) {
   const Oracle& o = *(Oracle*)h;
