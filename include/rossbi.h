@@ -96,10 +96,16 @@ typedef struct {
 
 /* Drag (Sect. 2.9).  drag_law 0: t_s = stokes / Omega_K(r) (Box: t_s = stokes);
  * drag_law 1: Epstein t_s = rho_s r_p / (rho_g c_s) with rho_s r_p fixed so
- * that the Stokes number equals `stokes` at r = 1, z = 0 of the equilibrium. */
+ * that the Stokes number equals `stokes` at r = 1, z = 0 of the equilibrium;
+ * drag_law 2: law 1 plus the Stokes regime, t_s = (4/9)(r_p / lambda) t_E
+ * where r_p > 9 lambda / 4, with the mean free path lambda = lambda_0 / rho_g
+ * and kappa = r_p / lambda_0 (>= 0; ignored by laws 0 and 1).  Law 2 is not
+ * available to rossbi_adjoint_step (ROSSBI_ERR_UNSUPPORTED) nor to
+ * rossbi_step_noalloc (ROSSBI_ERR_ARG). */
 typedef struct {
   double stokes;
   int drag_law;
+  double kappa;
 } rossbi_dust_params;
 
 /* Radial wave-killing zones (Sect. 2.4 names them; the relaxation is that of

@@ -129,6 +129,8 @@ class Oracle:
         self.shape = (self.nf, w.nz, w.nth, w.nr)
         self.status = 0
         self.x_ind = 0.0
+        if w.drag_kappa:
+            lib().orc_set_stokes_regime(self.h, float(w.drag_kappa))
         if w.disc is not None:
             disc = np.array(w.disc, dtype=np.float64)
             self.status |= lib().orc_set_equilibrium(self.h, _p(disc))

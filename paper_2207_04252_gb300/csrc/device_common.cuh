@@ -402,13 +402,17 @@ __device__ __forceinline__ void cell_sources(const DevGrid& g, int i, int j, int
 // ------------------------------------------------------------------ drag
 struct DragArgs {
   double stokes;
-  double rhos_rp;  // Epstein constant rho_s r_p (drag_law 1)
+  double rhos_rp;  // Epstein constant rho_s r_p (drag laws 1 and 2)
   int law;
+  double kappa;    // drag law 2: r_p / lambda_0, the mean free path being lambda_0 / rho_g
 };
 
 // Semi-implicit drag over a stage of length tau (Sect. 2.9 drag law): the
 // relative gas-dust velocity relaxes by 1 / (1 + tau (1 + eps) / t_s) at
 // fixed barycentric velocity; the gas energy gains the work done on the gas.
+// Drag law 2 (compiled in with XT) adds the Stokes regime of Sect. 2.9:
+// above r_p = 9 lambda / 4 the Epstein time grows by (4/9) r_p / lambda.
+template <bool XT = false>
 __device__ __forceinline__ void apply_drag(const DevGrid& g, int i, double* U, double tau, const DragArgs& d) {
   const double rg = U[RHO], rd = U[DRHO];
   if (!(rd > 0.0) || !(rg > 0.0)) return;
@@ -423,6 +427,7 @@ __device__ __forceinline__ void apply_drag(const DevGrid& g, int i, double* U, d
   } else {
     const double cs = sqrt(g.gamma * gas_pressure(g.gamma, U[MU], U[MV], U[MW], U[EN], rg) / rg);
     ts = d.rhos_rp / (rg * cs);
+    if (XT && d.law == 2 && d.kappa * rg > 2.25) ts = ts * ((4.0 / 9.0) * (d.kappa * rg));
   }
   const double kk = tau * (1.0 + rd / rg) / ts;
   const double mu = rg * rd / (rg + rd);

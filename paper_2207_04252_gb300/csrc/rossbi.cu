@@ -378,7 +378,7 @@ rossbi_status launch_stage(rossbi_grid* g, const StageArgs& a, int nblocks) {
     e1 = g->ev[2 * g->ev_used + 1];
     CK(cudaEventRecord(e0, g->stream));
   }
-  const bool xt = a.g.x_ind != 0.0 || a.g.damp_k != nullptr;  // optional terms on
+  const bool xt = a.g.x_ind != 0.0 || a.g.damp_k != nullptr || a.drag.law == 2;  // optional terms on
   rossbi_status st = g->nf == 9 ? (xt ? launch_stage_f64<9, true>(g, a, nblocks) : launch_stage_f64<9, false>(g, a, nblocks))
                                 : (xt ? launch_stage_f64<5, true>(g, a, nblocks) : launch_stage_f64<5, false>(g, a, nblocks));
   if (st != ROSSBI_OK) return st;
@@ -408,7 +408,7 @@ rossbi_status launch_pert_nf_x(rossbi_grid* g, const PertArgs<T>& a, int nblocks
 
 template <class T, int NF, class P>
 rossbi_status launch_pert_nf(rossbi_grid* g, const PertArgs<T>& a, int nblocks) {
-  const bool xt = a.g.x_ind != 0.0 || a.g.damp_k != nullptr;  // optional terms on
+  const bool xt = a.g.x_ind != 0.0 || a.g.damp_k != nullptr || a.drag.law == 2;  // optional terms on
   return xt ? launch_pert_nf_x<T, NF, P, true>(g, a, nblocks) : launch_pert_nf_x<T, NF, P, false>(g, a, nblocks);
 }
 
@@ -643,14 +643,18 @@ PertArgs<T> pert_args(rossbi_grid* g) {
 // Drag parameters of a step (Sect. 2.9 drag law; Epstein constant fixed so
 // that the Stokes number holds at r = 1, z = 0).
 rossbi_status drag_args(rossbi_grid* g, const rossbi_dust_params* dust, DragArgs& drag) {
-  drag = DragArgs{0.0, 0.0, 0};
+  drag = DragArgs{0.0, 0.0, 0, 0.0};
   if (g->nf == 9) {
     drag.stokes = dust->stokes;
     drag.law = dust->drag_law;
     if (!(dust->stokes > 0.0)) return ROSSBI_ERR_ARG;
     if (dust->drag_law == 0 && g->desc.geometry == ROSSBI_GEOM_CYL && !(g->desc.gm > 0.0))
       return ROSSBI_ERR_ARG;  // t_s = St / Omega_K needs a star
-    if (dust->drag_law == 1) {
+    if (dust->drag_law == 2) {  // Epstein constant as for law 1, plus the Stokes regime
+      if (!(dust->kappa >= 0.0) || !std::isfinite(dust->kappa)) return ROSSBI_ERR_ARG;
+      drag.kappa = dust->kappa;
+    }
+    if (dust->drag_law == 1 || dust->drag_law == 2) {
       if (!g->has_disc) return ROSSBI_ERR_ARG;
       double rho1, vth1, p1;
       equilibrium_prim(g->desc, g->disc, 1.0, 0.0, rho1, vth1, p1);
@@ -970,6 +974,7 @@ rossbi_status adjoint_step(rossbi_grid* g, void* const* state, double dt, const 
       if (lam_np1[f] == state[h] || lam_n[f] == state[h]) return ROSSBI_ERR_ARG;
   }
   if (g->nf == 9 && !dust) return ROSSBI_ERR_ARG;
+  if (g->nf == 9 && dust->drag_law == 2) return ROSSBI_ERR_UNSUPPORTED;  // no adjoint of the Stokes regime yet
   DragArgs drag;
   rossbi_status st = drag_args(g, dust, drag);
   if (st != ROSSBI_OK) return st;
@@ -1589,7 +1594,7 @@ extern "C" rossbi_status rossbi_step_noalloc(rossbi_grid* g, void* const* state,
   void* sc[9];
   for (int f = 0; f < g->nf; ++f) sc[f] = (char*)base + (size_t)f * field_bytes;
   double* partials = (double*)((char*)base + (size_t)g->nf * field_bytes);
-  DragArgs drag{0.0, 0.0, 0};
+  DragArgs drag{0.0, 0.0, 0, 0.0};
   if (g->nf == 9) {
     if (!(dust->stokes > 0.0) || (dust->drag_law != 0 && dust->drag_law != 1)) return ROSSBI_ERR_ARG;
     drag.stokes = dust->stokes;

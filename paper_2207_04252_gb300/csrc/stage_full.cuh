@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(NT, 1) stage_full_kernel(const StageArgs a) {
     double E[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) E[f] = a.base[f][lin] + tau * G[f] * iv;
-    if (NF == 9) apply_drag(g, gi, E, tau, a.drag);
+    if (NF == 9) apply_drag<XT>(g, gi, E, tau, a.drag);
 #pragma unroll
     for (int f = 0; f < NF; ++f) a.out[f][lin] = E[f];
     if (a.stage2) {

@@ -597,7 +597,7 @@ __device__ __forceinline__ void pert_sources(const DevGrid& g, const PCell<T>& c
 
 // Semi-implicit drag on a perturbation-form cell state (same closed form as the
 // full-state kernel; the gas velocity is u0 + du).
-template <class T>
+template <class T, bool XT>
 __device__ __forceinline__ void pert_drag(const DevGrid& g, const PertTables<T>& t, const PCell<T>& c, int i, T* q,
                                           T tau, const DragArgs& d) {
   const T gam = (T)g.gamma;
@@ -611,6 +611,10 @@ __device__ __forceinline__ void pert_drag(const DevGrid& g, const PertTables<T>&
   } else {
     const T cs = Math<T>::sqrt_(gam * (c.p0 + dp) / rg);
     ts = (T)d.rhos_rp / (rg * cs);
+    if (XT && d.law == 2) {  // Stokes regime of Sect. 2.9 above r_p = 9 lambda / 4
+      const T x = (T)d.kappa * rg;
+      if (x > T(2.25)) ts = ts * (T(4.0 / 9.0) * x);
+    }
   }
   const T kk = tau * (T(1) + rd / rg) / ts;
   const T mu = rg * rd / (rg + rd);
@@ -776,7 +780,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
     T E[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) E[f] = a.base[f][lin] + tau * G[f] * iv;
-    if (NF == 9) pert_drag(g, a.t, ce, gi, E, tau, a.drag);
+    if (NF == 9) pert_drag<T, XT>(g, a.t, ce, gi, E, tau, a.drag);
 #pragma unroll
     for (int f = 0; f < NF; ++f) a.out[f][lin] = E[f];
     bool bad_in = false;

@@ -46,7 +46,7 @@ class rossbi_disc_params(ctypes.Structure):
 
 
 class rossbi_dust_params(ctypes.Structure):
-    _fields_ = [("stokes", ctypes.c_double), ("drag_law", ctypes.c_int)]
+    _fields_ = [("stokes", ctypes.c_double), ("drag_law", ctypes.c_int), ("kappa", ctypes.c_double)]
 
 
 class rossbi_damping_params(ctypes.Structure):

@@ -41,7 +41,7 @@ class Grid:
         self.nf = R.rossbi_nfields(self.h)
         self.dtype = torch.float32 if precision == R.ROSSBI_FP32_PERT else torch.float64
         self.perturbation = precision in (R.ROSSBI_FP32_PERT, R.ROSSBI_FP64_PERT)
-        self.dust = (w.stokes, w.drag_law) if w.n_dust else None
+        self.dust = (w.stokes, w.drag_law, w.drag_kappa) if w.n_dust else None
         self.shape = (self.nf, w.nz, w.nth, w.nr)
 
     def close(self):

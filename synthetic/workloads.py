@@ -59,6 +59,7 @@ class Workload:
     dust_noise: float = 0.0
     stokes: float = 0.0
     drag_law: int = 0
+    drag_kappa: float = 0.0      # drag law 2: r_p / lambda_0 of the Stokes regime
     t_end: float = 0.0           # >0: run to this time, clipping the last step
     checkpoint_every: int = 0
 
