@@ -54,3 +54,39 @@ def test_invalid_descriptions_rejected_without_gpu():
     zero = rossbi.make_desc(rossbi.ROSSBI_GEOM_BOX, (0, 4, 4), (0, 0, 0), (1, 1, 1), (0, 0, 0), (0, 0, 0))
     with pytest.raises(rossbi.RossbiError):
         rossbi.rossbi_init_grid(zero)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structures have the sizes and field offsets that a C
+    compiler gives the header's structs (gcc, this machine's ABI)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    structs = {
+        "rossbi_grid_desc": rossbi.rossbi_grid_desc,
+        "rossbi_disc_params": rossbi.rossbi_disc_params,
+        "rossbi_dust_params": rossbi.rossbi_dust_params,
+        "rossbi_damping_params": rossbi.rossbi_damping_params,
+    }
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rossbi.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    c = {}
+    for line in out:
+        if line:
+            name, key, val = line.split()
+            c[(name, key)] = int(val)
+    for name, cls in structs.items():
+        assert ctypes.sizeof(cls) == c[(name, "size")], name
+        for field, _ in cls._fields_:
+            assert getattr(cls, field).offset == c[(name, field)], (name, field)
