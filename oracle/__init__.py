@@ -83,6 +83,7 @@ def lib():
         L.orc_indirect.argtypes = [ctypes.c_void_p, _D, _D]
         L.orc_set_damping.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_double]
         L.orc_set_stokes_regime.argtypes = [ctypes.c_void_p, ctypes.c_double]
+        L.orc_sources.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]
         _lib = L
     return _lib
 
@@ -177,6 +178,13 @@ class Oracle:
         period_factor <= 0 switches them off."""
         if lib().orc_set_damping(self.h, float(r_ein), float(r_eout), float(period_factor)):
             raise ValueError("damping zones must lie inside the radial extent of a cylindrical grid")
+
+    def sources(self, i, j, k, U):
+        """App. B source vector per unit volume of the state U at cell (i, j, k)."""
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        S = np.zeros(self.nf)
+        lib().orc_sources(self.h, i, j, k, _p(U), _p(S))
+        return S
 
     def set_stokes_regime(self, kappa):
         """kappa = r_p / lambda_0 of drag law 2 (reading R19); <= 0: Epstein only."""

@@ -1147,6 +1147,16 @@ int orc_set_damping(void* h, double r_ein, double r_eout, double f) {
   return 0;
 }
 
+// App. B source vector per unit volume of the state U (nf values) at the
+// centre of cell (i, j, k), without the indirect term.
+void orc_sources(void* h, int i, int j, int k, const double* U, double* S) {
+  const Oracle& o = *(Oracle*)h;
+  double u[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, s[9];
+  for (int f = 0; f < o.nf; ++f) u[f] = U[f];
+  sources(o, i, j, k, u, (const double*)nullptr, s);
+  for (int f = 0; f < o.nf; ++f) S[f] = s[f];
+}
+
 // kappa = r_p / lambda_0 of the Stokes regime of drag law 2 (reading R19);
 // kappa <= 0 keeps every cell in the Epstein regime.
 void orc_set_stokes_regime(void* h, double kappa) { ((Oracle*)h)->kappa = kappa; }
