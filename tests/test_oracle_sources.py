@@ -72,3 +72,32 @@ def test_sources_follow_the_effective_potential(omega):
             U2[MV] += rho * 0.2
             U2[EN] += 0.5 * rho * ((v + 0.2) ** 2 - v * v)
             assert o.sources(i, 2, k, U2)[EN] == S[EN]
+
+
+def test_rotating_frame_sources_are_the_inertial_ones():
+    """The same gas seen from a frame rotating at Omega_f: with v_in = v +
+    Omega_f r, the radial momentum source is the inertial one (centrifugal
+    and Coriolis terms are exactly the expansion of rho v_in^2 / r), and the
+    azimuthal one is the inertial one less rho Omega_f u (along a parcel's
+    path, d v / dt = d v_in / dt - Omega_f dr / dt).  A sign error in either
+    Coriolis term or in the centrifugal term fails this."""
+    from dataclasses import replace
+    base = syn.scaled(syn.VORTEX, 12, 8, 16)
+    rng = np.random.default_rng(12)
+    for omega in (1.0, 0.63):
+        o_rot = oracle.Oracle(replace(base, omega_frame=omega))
+        o_in = oracle.Oracle(replace(base, omega_frame=0.0))
+        rc, _ = o_rot.coords(0)
+        for i, k in ((0, 0), (6, 9), (11, 15)):
+            r = rc[i]
+            U, (rho, u, v, ww, P, rd, ud, vd, wd) = _state(rng, base.gamma)
+            Ui = U.copy()
+            Ui[MV] = rho * (v + omega * r)
+            Ui[EN] = P / (base.gamma - 1) + 0.5 * rho * (u * u + (v + omega * r) ** 2 + ww * ww)
+            Ui[DMV] = rd * (vd + omega * r)
+            Sr, Si = o_rot.sources(i, 1, k, U), o_in.sources(i, 1, k, Ui)
+            scale = rho * (v + omega * r) ** 2 / r + P / r
+            assert Sr[MU] == pytest.approx(Si[MU], abs=1e-12 * scale)
+            assert Sr[MV] == pytest.approx(Si[MV] - rho * omega * u, abs=1e-12 * scale)
+            assert Sr[DMU] == pytest.approx(Si[DMU], abs=1e-12 * scale)
+            assert Sr[DMV] == pytest.approx(Si[DMV] - rd * omega * ud, abs=1e-12 * scale)
