@@ -84,6 +84,7 @@ def lib():
         L.orc_set_damping.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_double]
         L.orc_set_stokes_regime.argtypes = [ctypes.c_void_p, ctypes.c_double]
         L.orc_sources.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]
+        L.orc_set_species_stokes.argtypes = [ctypes.c_void_p, _D, ctypes.c_int]
         _lib = L
     return _lib
 
@@ -185,6 +186,11 @@ class Oracle:
         S = np.zeros(self.nf)
         lib().orc_sources(self.h, i, j, k, _p(U), _p(S))
         return S
+
+    def set_species_stokes(self, factors):
+        """Stokes-number factors of the dust species (species 0 keeps St)."""
+        f = np.ascontiguousarray(factors, dtype=np.float64)
+        lib().orc_set_species_stokes(self.h, _p(f), len(f))
 
     def set_stokes_regime(self, kappa):
         """kappa = r_p / lambda_0 of drag law 2 (reading R19); <= 0: Epstein only."""
@@ -345,13 +351,15 @@ def initial_state(o: Oracle) -> np.ndarray:
         E[syn.F_MU] = rho0 * up
         E[syn.F_MV] += rho0 * vp
         E[syn.F_EN] += 0.5 * rho0 * (up * up + 2.0 * v0 * vp + vp * vp)
-        if nf > 5:
-            xi = syn.uniform_pm1(w.seed, syn.F_DRHO, w.ncell).reshape(w.nz, w.nth, w.nr)
-            rd = w.dust_ratio * rho0 * (1.0 + w.dust_noise * xi)
-            E[syn.F_DRHO] = rd
-            E[syn.F_DMU] = rd * up
-            E[syn.F_DMV] = rd * (v0 + vp)
-            E[syn.F_DMW] = 0.0
+        nd = (nf - 5) // 4
+        for s in range(nd):  # each species: its share of the dust, its own noise, moving with the gas
+            b = 5 + 4 * s
+            xi = syn.uniform_pm1(w.seed, syn.F_DRHO + 4 * s, w.ncell).reshape(w.nz, w.nth, w.nr)
+            rd = w.dust_ratio / nd * rho0 * (1.0 + w.dust_noise * xi)
+            E[b + 3] = rd
+            E[b] = rd * up
+            E[b + 1] = rd * (v0 + vp)
+            E[b + 2] = 0.0
     else:
         raise ValueError(w.ic)
     return E

@@ -82,6 +82,12 @@
 //      lambda_0 / rho_g (Sect. 2.9: mu m_u / (sigma_eff rho)), and
 //      kappa = r_p / lambda_0 is a parameter; rho_s r_p is fixed, as for
 //      law 1, so that the Epstein stopping time gives St at r = 1, z = 0.
+//  R20 several dust species (Sect. 5.4 names the multi-fluid approach): N
+//      pressureless dust fluids, species s in fields 5 + 4 s .. 8 + 4 s, each
+//      reconstructed, fluxed and sourced as the single dust fluid (R5) and
+//      coupled to the gas only, by its own drag (Stokes number St x f_s); the
+//      semi-implicit drag solves the coupled backward-Euler system in closed
+//      form (one species keeps the closed form of R7).
 //
 // Parity unpinned (readings checked only for their properties and for
 // self-consistency, since the paper gives no formula or value to test them
@@ -120,6 +126,9 @@ enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_EQUILIBRIUM = 2 };
 // followed by the dust fluid (rho_d u_d, rho_d v_d, rho_d w_d, rho_d).
 enum { MU = 0, MV = 1, MW = 2, EN = 3, RHO = 4, DMU = 5, DMV = 6, DMW = 7, DRHO = 8 };
 enum { ST_NONPHYSICAL = 1, ST_RIEMANN = 2 };
+// Dust species s occupies fields 5 + 4 s .. 8 + 4 s (rho_d u_d, rho_d v_d,
+// rho_d w_d, rho_d); species 0 is the single dust fluid above.
+static const int ND_MAX = 4, NFMAX = 5 + 4 * ND_MAX;
 
 struct Desc {
   int geometry, nr, nth, nz;
@@ -147,6 +156,8 @@ struct Oracle {
   bool damp = false;       // wave-killing zones of reading R17
   double damp_ein = 0.0, damp_eout = 0.0, damp_tau_in = 0.0, damp_tau_out = 0.0;
   double kappa = 0.0;      // r_p / lambda_0 of the Stokes regime (reading R19)
+  int nd = 0;              // dust species
+  double st_factor[ND_MAX] = {1.0, 1.0, 1.0, 1.0};  // St_k = St x st_factor[k] (reading R20)
   int status = 0;
   long newton_iters = 0, riemann_calls = 0;
 };
@@ -399,7 +410,7 @@ static void prim_dev(const Oracle& o, const Acc& E, int i, int j, int k, T d[5])
 // primitives = face equilibrium primitives + deviation; if either face has
 // rho <= 0 or P <= 0 the cell's gas deviations are used flat.  Dust: reading R5.
 template <class Acc, class T = typename Acc::value_type>
-static void recon(const Oracle& o, const Acc& E, int ax, const int cell[3], T qm[9], T qp[9]) {
+static void recon(const Oracle& o, const Acc& E, int ax, const int cell[3], T qm[NFMAX], T qp[NFMAX]) {
   int cm[3] = {cell[0], cell[1], cell[2]}, cp[3] = {cell[0], cell[1], cell[2]};
   cm[ax] -= 1;
   cp[ax] += 1;
@@ -437,22 +448,23 @@ static void recon(const Oracle& o, const Acc& E, int ax, const int cell[3], T qm
     qm[f] = Um[f] - e0m[f];
     qp[f] = Up[f] - e0p[f];
   }
-  if (o.nf > 5) {  // R5: dust in primitive variables (rho_d, u_d, v_d, w_d)
+  for (int s = 0; s < o.nd; ++s) {  // R5: dust in primitive variables (rho_d, u_d, v_d, w_d), per species
+    const int b = 5 + 4 * s;
     T pm[4], p0[4], pp[4], qmw[4], qpw[4];
-    pm[3] = dev(o, E, DRHO, cm[0], cm[1], cm[2]);
-    p0[3] = dev(o, E, DRHO, cell[0], cell[1], cell[2]);
-    pp[3] = dev(o, E, DRHO, cp[0], cp[1], cp[2]);
+    pm[3] = dev(o, E, b + 3, cm[0], cm[1], cm[2]);
+    p0[3] = dev(o, E, b + 3, cell[0], cell[1], cell[2]);
+    pp[3] = dev(o, E, b + 3, cp[0], cp[1], cp[2]);
     for (int q = 0; q < 3; ++q) {
-      pm[q] = pm[3] > 0.0 ? dev(o, E, DMU + q, cm[0], cm[1], cm[2]) / pm[3] : T(0.0);
-      p0[q] = p0[3] > 0.0 ? dev(o, E, DMU + q, cell[0], cell[1], cell[2]) / p0[3] : T(0.0);
-      pp[q] = pp[3] > 0.0 ? dev(o, E, DMU + q, cp[0], cp[1], cp[2]) / pp[3] : T(0.0);
+      pm[q] = pm[3] > 0.0 ? dev(o, E, b + q, cm[0], cm[1], cm[2]) / pm[3] : T(0.0);
+      p0[q] = p0[3] > 0.0 ? dev(o, E, b + q, cell[0], cell[1], cell[2]) / p0[3] : T(0.0);
+      pp[q] = pp[3] > 0.0 ? dev(o, E, b + q, cp[0], cp[1], cp[2]) / pp[3] : T(0.0);
     }
     for (int q = 0; q < 4; ++q) parabola(pm[q], p0[q], pp[q], xm, x0, xp, fm, fp, qmw[q], qpw[q]);
-    qm[DRHO] = qmw[3];
-    qp[DRHO] = qpw[3];
+    qm[b + 3] = qmw[3];
+    qp[b + 3] = qpw[3];
     for (int q = 0; q < 3; ++q) {
-      qm[DMU + q] = qmw[3] * qmw[q];
-      qp[DMU + q] = qpw[3] * qpw[q];
+      qm[b + q] = qmw[3] * qmw[q];
+      qp[b + q] = qpw[3] * qpw[q];
     }
   }
 }
@@ -663,11 +675,12 @@ static void gas_flux(Oracle& o, int ax, const T UL[5], const T UR[5], T F[5]) {
 // dust fluid: what moves right leaves the left state, what moves left leaves
 // the right state.
 template <class T>
-static void dust_flux(int ax, const T UL[9], const T UR[9], T F[9]) {
+static void dust_flux(int ax, const T* UL, const T* UR, T* F, int b = 5) {  // b: the species' first field
   int n, t1, t2;
   axes(ax, n, t1, t2);
-  n += 5; t1 += 5; t2 += 5;
-  const T rl = UL[DRHO], rr = UR[DRHO];
+  n += b; t1 += b; t2 += b;
+  const int drho = b + 3;
+  const T rl = UL[drho], rr = UR[drho];
   T Fs[4] = {T(0.0), T(0.0), T(0.0), T(0.0)};
   if (rl > 0.0) {
     const T ul = UL[n] / rl;
@@ -679,7 +692,7 @@ static void dust_flux(int ax, const T UL[9], const T UR[9], T F[9]) {
     const T m = rr * (ur < 0.0 ? ur : T(0.0));
     Fs[0] += m; Fs[1] += m * ur; Fs[2] += m * (UR[t1] / rr); Fs[3] += m * (UR[t2] / rr);
   }
-  F[DRHO] = Fs[0];
+  F[drho] = Fs[0];
   F[n] = Fs[1];
   F[t1] = Fs[2];
   F[t2] = Fs[3];
@@ -691,7 +704,7 @@ static void dust_flux(int ax, const T UL[9], const T UR[9], T F[9]) {
 // at the cell centre.  gind = X_ref (A_disc, B_disc) of Sect. 2.10 (reading
 // R16), or null.  The Box has no source terms.
 template <class T>
-static void sources(const Oracle& o, int i, int j, int k, const T U[9], const T* gind, T S[9]) {
+static void sources(const Oracle& o, int i, int j, int k, const T* U, const T* gind, T* S) {
   for (int f = 0; f < o.nf; ++f) S[f] = T(0.0);
   if (o.d.geometry != GEOM_CYL) return;
   const double r = XC(o, 0, i), z = XC(o, 2, k);
@@ -721,16 +734,18 @@ static void sources(const Oracle& o, int i, int j, int k, const T U[9], const T*
       S[EN] -= rho * (u * dphi_r + v * dphi_t);
     }
   }
-  if (o.nf > 5 && U[DRHO] > 0.0) {
-    const T rho = U[DRHO];
-    const T u = U[DMU] / rho, v = U[DMV] / rho;
-    S[DMU] = rho * v * v / r + rho * fr + 2.0 * Om * rho * v + rho * Om * Om * r;
-    S[DMV] = -rho * u * v / r - 2.0 * Om * rho * u;
-    S[DMW] = rho * fz;
-    S[DRHO] = T(0.0);
+  for (int sp = 0; sp < o.nd; ++sp) {
+    const int b = 5 + 4 * sp;
+    if (!(U[b + 3] > 0.0)) continue;
+    const T rho = U[b + 3];
+    const T u = U[b] / rho, v = U[b + 1] / rho;
+    S[b] = rho * v * v / r + rho * fr + 2.0 * Om * rho * v + rho * Om * Om * r;
+    S[b + 1] = -rho * u * v / r - 2.0 * Om * rho * u;
+    S[b + 2] = rho * fz;
+    S[b + 3] = T(0.0);
     if (gind) {
-      S[DMU] -= rho * dphi_r;
-      S[DMV] -= rho * dphi_t;
+      S[b] -= rho * dphi_r;
+      S[b + 1] -= rho * dphi_t;
     }
   }
 }
@@ -751,7 +766,7 @@ static void indirect_moments(const Oracle& o, const Acc& E, T gind[2]) {
     const double R2 = r * r + z * z;
     T dm = E.get(RHO, lin);
     if (o.has_eq) dm = dm - E0C(o, i, k)[RHO];
-    if (o.nf > 5) dm += E.get(DRHO, lin);
+    for (int sp = 0; sp < o.nd; ++sp) dm += E.get(5 + 4 * sp + 3, lin);
     dm = dm * metric(o, i).V;
     A += dm * (r * std::cos(th) / (R2 * std::sqrt(R2)));
     B += dm * (r * std::sin(th) / (R2 * std::sqrt(R2)));
@@ -779,12 +794,12 @@ static double damping_rate(const Oracle& o, int i) {
 // ---------------------------------------------------------------- G(E) per cell
 // Sect. 2.2, Eq. (compact form): G = S V - sum_faces A F.n, for one cell.
 template <class Acc, class T = typename Acc::value_type>
-static void G_cell(Oracle& o, const Acc& E, int i, int j, int k, T G[9], const T* gind = nullptr) {
+static void G_cell(Oracle& o, const Acc& E, int i, int j, int k, T G[NFMAX], const T* gind = nullptr) {
   const Metric m = metric(o, i);
   for (int f = 0; f < o.nf; ++f) G[f] = T(0.0);
   const int cell[3] = {i, j, k};
   for (int ax = 0; ax < 3; ++ax) {
-    T qm_c[9], qp_c[9], qm_m[9], qp_m[9], qm_p[9], qp_p[9];
+    T qm_c[NFMAX], qp_c[NFMAX], qm_m[NFMAX], qp_m[NFMAX], qm_p[NFMAX], qp_p[NFMAX];
     int cm[3] = {i, j, k}, cp[3] = {i, j, k};
     cm[ax] -= 1;
     cp[ax] += 1;
@@ -797,22 +812,23 @@ static void G_cell(Oracle& o, const Acc& E, int i, int j, int k, T G[9], const T
       const T* ql = side == 0 ? qp_m : qp_c;       // left state of the face
       const T* qr = side == 0 ? qm_c : qm_p;       // right state of the face
       double e0[5];
-      T UL[9], UR[9], F[9];
+      T UL[NFMAX], UR[NFMAX], F[NFMAX];
       eq_face(o, ax, i, k, fc, e0);
       for (int f = 0; f < 5; ++f) { UL[f] = e0[f] + ql[f]; UR[f] = e0[f] + qr[f]; }
       for (int f = 5; f < o.nf; ++f) { UL[f] = ql[f]; UR[f] = qr[f]; }
       gas_flux(o, ax, UL, UR, F);
-      if (o.nf > 5) dust_flux(ax, UL, UR, F);
+      for (int sp = 0; sp < o.nd; ++sp) dust_flux(ax, UL, UR, F, 5 + 4 * sp);
       const double A = side == 0 ? m.A_lo[ax] : m.A_hi[ax];
       for (int f = 0; f < o.nf; ++f) G[f] += side == 0 ? A * F[f] : -A * F[f];
     }
   }
-  T U[9], S[9];
-  for (int f = 0; f < 9; ++f) U[f] = T(0.0);
+  T U[NFMAX], S[NFMAX];
+  for (int f = 0; f < NFMAX; ++f) U[f] = T(0.0);
   const long lin = ((long)k * o.n[1] + j) * o.n[0] + i;
   for (int f = 0; f < o.nf; ++f) U[f] = E.get(f, lin);
   if (!(U[RHO] > 0.0) || !(pressure(o.d.gamma, U) > 0.0)) o.status |= ST_NONPHYSICAL;
-  if (o.nf > 5 && U[DRHO] < 0.0) o.status |= ST_NONPHYSICAL;
+  for (int sp = 0; sp < o.nd; ++sp)
+    if (U[5 + 4 * sp + 3] < 0.0) o.status |= ST_NONPHYSICAL;
   sources(o, i, j, k, U, gind, S);
   for (int f = 0; f < o.nf; ++f) G[f] += m.V * S[f];
   const double kd = damping_rate(o, i);  // reading R17
@@ -828,25 +844,67 @@ struct DustParamsT {
                  // 2: Epstein with the Stokes regime above r_p = 9 lambda / 4 (reading R19)
 };
 using DustParams = DustParamsT<double>;
-// Sect. 2.9 drag law with the semi-implicit integration of reading R7.
+// Sect. 2.9 stopping time of dust species `sp` (Stokes number St x
+// st_factor[sp]) in a cell of radial index i with gas state U.
 template <class T>
-static void drag(const Oracle& o, int i, T U[9], double tau, const DustParamsT<T>& dp) {
-  if (o.nf < 9) return;
-  const T rg = U[RHO], rd = U[DRHO];
-  if (!(rd > 0.0) || !(rg > 0.0)) return;
-  T ts;
-  if (dp.drag_law == 0) {
-    ts = o.d.geometry == GEOM_CYL ? dp.stokes / std::sqrt(o.d.gm / std::pow(XC(o, 0, i), 3)) : dp.stokes;
-  } else {
-    // Epstein t_s = rho_s r_p / (rho_g c_s), with rho_s r_p fixed so that St holds at r = 1, z = 0
-    double rho1, vth1, p1;
-    eq_prim(o, 1.0, 0.0, rho1, vth1, p1);
-    const T rhos_rp = dp.stokes * rho1 * std::sqrt(o.d.gamma * p1 / rho1) / std::sqrt(o.d.gm);
-    const T cs = sqrt(o.d.gamma * pressure(o.d.gamma, U) / rg);
-    ts = rhos_rp / (rg * cs);
-    // r_p / lambda = kappa rho_g; the Stokes regime lengthens t_s by (4/9) r_p / lambda
-    if (dp.drag_law == 2 && o.kappa * rg > 2.25) ts = ts * ((4.0 / 9.0) * (o.kappa * rg));
+static T stopping_time(const Oracle& o, int i, const T* U, const DustParamsT<T>& dp, int sp) {
+  const T st = sp == 0 ? dp.stokes : dp.stokes * o.st_factor[sp];
+  const T rg = U[RHO];
+  if (dp.drag_law == 0)
+    return o.d.geometry == GEOM_CYL ? st / std::sqrt(o.d.gm / std::pow(XC(o, 0, i), 3)) : st;
+  // Epstein t_s = rho_s r_p / (rho_g c_s), with rho_s r_p fixed so that St holds at r = 1, z = 0
+  double rho1, vth1, p1;
+  eq_prim(o, 1.0, 0.0, rho1, vth1, p1);
+  const T rhos_rp = st * rho1 * std::sqrt(o.d.gamma * p1 / rho1) / std::sqrt(o.d.gm);
+  const T cs = sqrt(o.d.gamma * pressure(o.d.gamma, U) / rg);
+  T ts = rhos_rp / (rg * cs);
+  // r_p / lambda = kappa rho_g; the Stokes regime lengthens t_s by (4/9) r_p / lambda
+  if (dp.drag_law == 2 && o.kappa * rg > 2.25) ts = ts * ((4.0 / 9.0) * (o.kappa * rg));
+  return ts;
+}
+
+// Sect. 2.9 drag law with the semi-implicit integration of reading R7.  One
+// species: the relative velocity relaxes in closed form at a fixed
+// barycentric velocity.  Several (reading R20): the backward-Euler system
+// rho_g v_g' = rho_g v_g + sum_k rho_k (v_k' - v_g') a_k,
+// v_k' = v_k - (v_k' - v_g') a_k (a_k = tau / t_k, no dust-dust exchange) is
+// solved in closed form, v_k' - v_g' = (v_k - v_g') / (1 + a_k); the gas
+// energy gains the work of the drag on the gas in both.
+template <class T>
+static void drag(const Oracle& o, int i, T* U, double tau, const DustParamsT<T>& dp) {
+  if (o.nd == 0) return;
+  const T rg = U[RHO];
+  if (o.nd > 1) {
+    if (!(rg > 0.0)) return;
+    T a[ND_MAX], num[3], den = rg;
+    for (int c = 0; c < 3; ++c) num[c] = U[MU + c];
+    for (int sp = 0; sp < o.nd; ++sp) {
+      const int b = 5 + 4 * sp;
+      a[sp] = T(0.0);
+      if (!(U[b + 3] > 0.0)) continue;
+      a[sp] = tau / stopping_time(o, i, U, dp, sp);
+      const T w = a[sp] / (1.0 + a[sp]);
+      den += U[b + 3] * w;
+      for (int c = 0; c < 3; ++c) num[c] += U[b + c] * w;  // rho_k v_k a_k / (1 + a_k)
+    }
+    T dE = T(0.0);
+    for (int c = 0; c < 3; ++c) {
+      const T vg_ex = U[MU + c] / rg;
+      const T vg = num[c] / den;
+      for (int sp = 0; sp < o.nd; ++sp) {
+        const int b = 5 + 4 * sp;
+        if (!(U[b + 3] > 0.0)) continue;
+        U[b + c] = U[b + 3] * ((U[b + c] / U[b + 3] + a[sp] * vg) / (1.0 + a[sp]));
+      }
+      U[MU + c] = rg * vg;
+      dE += 0.5 * rg * (vg * vg - vg_ex * vg_ex);
+    }
+    U[EN] += dE;
+    return;
   }
+  const T rd = U[DRHO];
+  if (!(rd > 0.0) || !(rg > 0.0)) return;
+  const T ts = stopping_time(o, i, U, dp, 0);
   const T eps = rd / rg;
   const T kk = tau * (1.0 + eps) / ts;
   const T mu = rg * rd / (rg + rd);
@@ -865,11 +923,11 @@ static void drag(const Oracle& o, int i, T U[9], double tau, const DustParamsT<T
 // One RK stage at one cell: Eout = Ebase + tau G(Ein)/V, then drag (Sect. 2.5).
 template <class Acc, class T = typename Acc::value_type>
 static void stage_cell(Oracle& o, const Acc& Ein, const T* Ebase, long lin, double tau, const DustParamsT<T>& dp,
-                       T out[9], const T* gind = nullptr) {
+                       T out[NFMAX], const T* gind = nullptr) {
   const int i = (int)(lin % o.n[0]);
   const int j = (int)((lin / o.n[0]) % o.n[1]);
   const int k = (int)(lin / ((long)o.n[0] * o.n[1]));
-  T G[9];
+  T G[NFMAX];
   G_cell(o, Ein, i, j, k, G, gind);
   if (!o.r0.empty())
     for (int f = 0; f < o.nf; ++f) G[f] -= o.r0[(size_t)f * o.ncell + lin];  // Sect. 2.8 balanced scheme
@@ -881,7 +939,7 @@ static void stage_cell(Oracle& o, const Acc& Ein, const T* Ebase, long lin, doub
 template <class T>
 static void stage_all(Oracle& o, const T* Ein, const T* Ebase, T* Eout, double tau, const DustParamsT<T>& dp) {
   const ArrAccT<T> A{Ein, o.ncell};
-  T out[9], gind[2];
+  T out[NFMAX], gind[2];
   indirect_moments(o, A, gind);
   const bool ind = o.x_ind != 0.0 && o.d.geometry == GEOM_CYL;
   for (long lin = 0; lin < o.ncell; ++lin) {
@@ -897,11 +955,11 @@ struct LazyStageAcc {
   const double* En;
   double tau;
   DustParams dp;
-  mutable std::unordered_map<long, std::array<double, 9>> cache;
+  mutable std::unordered_map<long, std::array<double, NFMAX>> cache;
   double get(int f, long lin) const {
     auto it = cache.find(lin);
     if (it == cache.end()) {
-      std::array<double, 9> v{};
+      std::array<double, NFMAX> v{};
       const ArrAcc A{En, o->ncell};
       stage_cell(*o, A, En, lin, tau, dp, v.data());
       it = cache.emplace(lin, v).first;
@@ -910,14 +968,16 @@ struct LazyStageAcc {
   }
 };
 
-static double cell_dt(const Oracle& o, const double U[9], int i) {
+static double cell_dt(const Oracle& o, const double* U, int i) {
   const Metric m = metric(o, i);
   const double rho = U[RHO];
   const double vel = sqrt(U[MU] * U[MU] + U[MV] * U[MV] + U[MW] * U[MW]) / rho;
   const double cs = sqrt(o.d.gamma * pressure(o.d.gamma, U) / rho);
   double dt = o.d.cfl * m.V / ((vel + cs) * m.maxA);  // Sect. 2.5, Eq. (cfl condition)
-  if (o.nf > 5 && U[DRHO] > 0.0) {
-    const double vd = sqrt(U[DMU] * U[DMU] + U[DMV] * U[DMV] + U[DMW] * U[DMW]) / U[DRHO];
+  for (int sp = 0; sp < o.nd; ++sp) {
+    const int b = 5 + 4 * sp;
+    if (!(U[b + 3] > 0.0)) continue;
+    const double vd = sqrt(U[b] * U[b] + U[b + 1] * U[b + 1] + U[b + 2] * U[b + 2]) / U[b + 3];
     if (vd > 0.0) dt = std::min(dt, o.d.cfl * m.V / (vd * m.maxA));
   }
   return dt;
@@ -960,7 +1020,8 @@ void* orc_create(const Desc* d) {
   o->n[0] = d->nr;
   o->n[1] = d->nth;
   o->n[2] = d->nz;
-  o->nf = 5 + (d->n_dust > 0 ? 4 : 0);
+  o->nd = std::max(0, std::min(d->n_dust, ND_MAX));
+  o->nf = 5 + 4 * o->nd;
   o->ncell = (long)d->nr * d->nth * d->nz;
   for (int ax = 0; ax < 3; ++ax) {
     o->xc[ax].resize(o->n[ax] + 2 * NG);
@@ -993,7 +1054,7 @@ int orc_set_equilibrium(void* h, const double* disc) {
   std::vector<double> E0((size_t)o.nf * o.ncell), R((size_t)o.nf * o.ncell);
   equilibrium_state(o, E0.data());
   const ArrAcc A{E0.data(), o.ncell};
-  double G[9];
+  double G[NFMAX];
   for (long lin = 0; lin < o.ncell; ++lin) {
     const int i = (int)(lin % o.n[0]);
     const int j = (int)((lin / o.n[0]) % o.n[1]);
@@ -1030,7 +1091,7 @@ void orc_metric(void* h, int i, double* out /* V, A_lo[3], A_hi[3], maxA */) {
 int orc_rhs(void* h, const double* E, double* G) {
   Oracle& o = *(Oracle*)h;
   const ArrAcc A{E, o.ncell};
-  double g[9], gind[2];
+  double g[NFMAX], gind[2];
   indirect_moments(o, A, gind);
   const bool ind = o.x_ind != 0.0 && o.d.geometry == GEOM_CYL;
   for (long lin = 0; lin < o.ncell; ++lin) {
@@ -1104,7 +1165,7 @@ int orc_step_sampled(void* h, const double* E, double dt, double stokes, int law
 
 double orc_cfl_dt(void* h, const double* E) {
   const Oracle& o = *(Oracle*)h;
-  double dt = INFINITY, U[9];
+  double dt = INFINITY, U[NFMAX];
   for (long lin = 0; lin < o.ncell; ++lin) {
     for (int f = 0; f < o.nf; ++f) U[f] = E[(size_t)f * o.ncell + lin];
     dt = std::min(dt, cell_dt(o, U, (int)(lin % o.n[0])));
@@ -1151,10 +1212,17 @@ int orc_set_damping(void* h, double r_ein, double r_eout, double f) {
 // centre of cell (i, j, k), without the indirect term.
 void orc_sources(void* h, int i, int j, int k, const double* U, double* S) {
   const Oracle& o = *(Oracle*)h;
-  double u[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, s[9];
+  double u[NFMAX] = {0}, s[NFMAX];
   for (int f = 0; f < o.nf; ++f) u[f] = U[f];
   sources(o, i, j, k, u, (const double*)nullptr, s);
   for (int f = 0; f < o.nf; ++f) S[f] = s[f];
+}
+
+// Stokes-number factors of the dust species (reading R20): species k has
+// St x f[k]; species 0 always has St itself.
+void orc_set_species_stokes(void* h, const double* f, int n) {
+  Oracle& o = *(Oracle*)h;
+  for (int k = 1; k < n && k < ND_MAX; ++k) o.st_factor[k] = f[k];
 }
 
 // kappa = r_p / lambda_0 of the Stokes regime of drag law 2 (reading R19);
@@ -1192,7 +1260,7 @@ void orc_gas_flux(void* h, int ax, const double* UL, const double* UR, double* F
 
 // UL, UR, F: the four dust fields (rho_d u_d, rho_d v_d, rho_d w_d, rho_d).
 void orc_dust_flux(int ax, const double* UL, const double* UR, double* F) {
-  double F9[9] = {0}, L9[9] = {0}, R9[9] = {0};
+  double F9[NFMAX] = {0}, L9[NFMAX] = {0}, R9[NFMAX] = {0};
   for (int f = 0; f < 4; ++f) { L9[5 + f] = UL[f]; R9[5 + f] = UR[f]; }
   dust_flux(ax, L9, R9, F9);
   for (int f = 5; f < 9; ++f) F[f - 5] = F9[f];

@@ -69,7 +69,7 @@ class Workload:
 
     @property
     def nfields(self) -> int:
-        return 5 + (4 if self.n_dust > 0 else 0)
+        return 5 + 4 * self.n_dust
 
     @property
     def shape(self) -> tuple:
