@@ -85,6 +85,9 @@ def lib():
         L.orc_set_stokes_regime.argtypes = [ctypes.c_void_p, ctypes.c_double]
         L.orc_sources.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]
         L.orc_set_species_stokes.argtypes = [ctypes.c_void_p, _D, ctypes.c_int]
+        L.orc_set_recon.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.orc_recon_faces.argtypes = [ctypes.c_void_p, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      _D, _D]
         _lib = L
     return _lib
 
@@ -131,6 +134,8 @@ class Oracle:
         self.shape = (self.nf, w.nz, w.nth, w.nr)
         self.status = 0
         self.x_ind = 0.0
+        if lib().orc_set_recon(self.h, int(w.recon)):
+            raise ValueError(f"unknown reconstruction mode {w.recon}")
         if w.drag_kappa:
             lib().orc_set_stokes_regime(self.h, float(w.drag_kappa))
         if w.disc is not None:
@@ -202,6 +207,15 @@ class Oracle:
         out = np.zeros(2)
         lib().orc_indirect(self.h, _p(E), _p(out))
         return out
+
+    def recon_faces(self, E, ax, i, j, k):
+        """Full reconstructed states (E0 + q) on the lower and upper faces of
+        cell (i, j, k) along axis ax (Sect. 2.7): (Um, Up), nf values each."""
+        E = np.ascontiguousarray(E, dtype=np.float64)
+        Um = np.zeros(self.nf)
+        Up = np.zeros(self.nf)
+        lib().orc_recon_faces(self.h, _p(E), ax, i, j, k, _p(Um), _p(Up))
+        return Um, Up
 
     def rhs(self, E):
         E = np.ascontiguousarray(E, dtype=np.float64)

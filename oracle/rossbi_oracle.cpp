@@ -17,29 +17,37 @@
 //
 // Readings of the paper that this file takes (the paper is silent or garbled):
 //  R1  cell centre in r is the geometric mean of its face radii (log mesh).
-//  R2  the parabola acts on the departure of the PRIMITIVE gas variables
-//      (rho, u, v, w, P) from their equilibrium values (Sects. 2.6-2.7 say
-//      "Euler variables"; the exact solver they name works on primitive
-//      states, and conservative departures make the face pressure a
-//      cancellation of O(Mach^2) terms in the rotating frame, whose linearised
-//      step then amplifies perturbations ~6x per step at the disc's outer
-//      edge).  MinMod limiter (Sect. 2.7 names the limiter only): each face
-//      deviation of the parabola, d = q - E'_i, is limited to minmod(d, s h),
-//      where s is the minmod of the two one-sided slopes and
+//  R2  reconstruction (Sect. 2.7 on the conservative vector E of App. B): the
+//      parabola acts component-wise on the departures E'_p = E_p - E0_p of the
+//      five conservative gas variables (rho u, rho v, rho w, E, rho); a face
+//      state is the face equilibrium E0 plus the interpolated departure.  This
+//      is the default.  The MinMod limiter (Sect. 2.7 names the limiter only):
+//      each face deviation of the parabola, d = q - E'_i, is limited to
+//      minmod(d, s h), where s is the minmod of the two one-sided slopes and
 //      h = +-min(2|x_face - x_i|, |x_neighbour - x_i|) on that side: the
 //      curvature is reduced only where the parabola would leave the interval
 //      of the neighbouring cell values, the result is flat at an extremum, and
 //      it depends continuously on the data.  If a reconstructed gas face state
-//      has rho<=0 or P<=0, all gas deviations of that cell are used flat in
+//      has rho<=0 or P<=0, all gas departures of that cell are used flat in
 //      that direction.
+//      Option (a departure from the paper, kept for comparison): the same
+//      parabola and limiter on the departures of the PRIMITIVE gas variables
+//      (rho, u, v, w, P) from the equilibrium primitives, the face state being
+//      the face equilibrium primitives plus the interpolated departure.  In a
+//      fast rotating frame the conservative face pressure P = (gamma - 1)
+//      (E - |m|^2 / 2 rho) is a difference of terms O(Mach^2) larger than P,
+//      so the conservative form is sensitive there; the primitive form is not.
 //  R3  the energy flux is (E+P)u_n (App. B prints rho(E+P)u, which is not
 //      dimensionally consistent with the governing equations of Sect. 2.1).
 //  R4  the RK2 update is E + dt*G/V (Sect. 2.5 prints a*V*dt*G; the compact
 //      form V dE/dt = G of Sect. 2.2 fixes the 1/V).
 //  R5  the dust ("adapted" solver, Sect. 2.9) is reconstructed in primitive
-//      variables (rho_d and the velocity, same limiter) and its face flux is
-//      the kinetic flux-vector splitting of pressureless gas dynamics
-//      (Bouchut, Jin & Li 2003): rho_L max(u_L,0)(1,u_L,...) +
+//      variables (rho_d and the velocity, same limiter) in both gas modes, a
+//      departure from the component-wise E'_p of Sect. 2.7: the dust has no
+//      pressure to keep rho_d away from zero, and the dust velocity of
+//      interpolated momentum and density is unbounded near dust vacuum.  Its
+//      face flux is the kinetic flux-vector splitting of pressureless gas
+//      dynamics (Bouchut, Jin & Li 2003): rho_L max(u_L,0)(1,u_L,...) +
 //      rho_R min(u_R,0)(1,u_R,...), which carries delta shocks by
 //      accumulating mass.
 //  R6  rotating frame of angular speed Omega_f: Coriolis 2 Omega_f rho v e_r -
@@ -126,6 +134,9 @@ enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_EQUILIBRIUM = 2 };
 // followed by the dust fluid (rho_d u_d, rho_d v_d, rho_d w_d, rho_d).
 enum { MU = 0, MV = 1, MW = 2, EN = 3, RHO = 4, DMU = 5, DMV = 6, DMW = 7, DRHO = 8 };
 enum { ST_NONPHYSICAL = 1, ST_RIEMANN = 2 };
+// Reconstruction of the gas (reading R2): conservative departures (Sect. 2.7
+// on App. B's E, the default) or primitive departures (option).
+enum { RECON_CONSERVATIVE = 0, RECON_PRIMITIVE = 1 };
 // Dust species s occupies fields 5 + 4 s .. 8 + 4 s (rho_d u_d, rho_d v_d,
 // rho_d w_d, rho_d); species 0 is the single dust fluid above.
 static const int ND_MAX = 4, NFMAX = 5 + 4 * ND_MAX;
@@ -157,6 +168,7 @@ struct Oracle {
   double damp_ein = 0.0, damp_eout = 0.0, damp_tau_in = 0.0, damp_tau_out = 0.0;
   double kappa = 0.0;      // r_p / lambda_0 of the Stokes regime (reading R19)
   int nd = 0;              // dust species
+  int recon = RECON_CONSERVATIVE;  // gas reconstruction (reading R2)
   double st_factor[ND_MAX] = {1.0, 1.0, 1.0, 1.0};  // St_k = St x st_factor[k] (reading R20)
   int status = 0;
   long newton_iters = 0, riemann_calls = 0;
@@ -405,10 +417,12 @@ static void prim_dev(const Oracle& o, const Acc& E, int i, int j, int k, T d[5])
 }
 
 // Face deviations q- (lower face) and q+ (upper face) of cell `cell` along ax,
-// as conservative face states minus the conservative face equilibrium.  Gas:
-// parabola + MinMod on the primitive deviations (Sect. 2.7, reading R2), face
-// primitives = face equilibrium primitives + deviation; if either face has
-// rho <= 0 or P <= 0 the cell's gas deviations are used flat.  Dust: reading R5.
+// as conservative face states minus the conservative face equilibrium.  Gas
+// (Sect. 2.7, reading R2): by default the parabola + MinMod on each of the
+// five conservative departures E'_p; with the primitive option, on the
+// primitive departures, face primitives = face equilibrium primitives +
+// deviation.  In both, if either face has rho <= 0 or P <= 0 the cell's gas
+// departures are used flat.  Dust: reading R5.
 template <class Acc, class T = typename Acc::value_type>
 static void recon(const Oracle& o, const Acc& E, int ax, const int cell[3], T qm[NFMAX], T qp[NFMAX]) {
   int cm[3] = {cell[0], cell[1], cell[2]}, cp[3] = {cell[0], cell[1], cell[2]};
@@ -417,36 +431,57 @@ static void recon(const Oracle& o, const Acc& E, int ax, const int cell[3], T qm
   const int c = cell[ax];
   const double xm = XC(o, ax, c - 1), x0 = XC(o, ax, c), xp = XC(o, ax, c + 1);
   const double fm = XF(o, ax, c), fp = XF(o, ax, c + 1);
-  T dm[5], d0[5], dp[5], wm[5], wp[5];
-  prim_dev(o, E, cm[0], cm[1], cm[2], dm);
-  prim_dev(o, E, cell[0], cell[1], cell[2], d0);
-  prim_dev(o, E, cp[0], cp[1], cp[2], dp);
-  bool gas_shaped = false;
-  for (int f = 0; f < 5; ++f) gas_shaped |= parabola(dm[f], d0[f], dp[f], xm, x0, xp, fm, fp, wm[f], wp[f]);
-  double e0m[5], e0p[5], W0m[5] = {0, 0, 0, 0, 0}, W0p[5] = {0, 0, 0, 0, 0};
+  double e0m[5], e0p[5];
   eq_face(o, ax, cell[0], cell[2], c, e0m);
   eq_face(o, ax, cell[0], cell[2], c + 1, e0p);
-  if (o.has_eq) {
-    prim_of(o.d.gamma, e0m, W0m);
-    prim_of(o.d.gamma, e0p, W0p);
-  }
-  T Wm[5], Wp[5];
-  for (int f = 0; f < 5; ++f) {
-    Wm[f] = W0m[f] + wm[f];
-    Wp[f] = W0p[f] + wp[f];
-  }
-  if (gas_shaped && !(Wm[RHO] > 0.0 && Wp[RHO] > 0.0 && Wm[EN] > 0.0 && Wp[EN] > 0.0)) {
-    for (int f = 0; f < 5; ++f) {  // R2 (iii): positivity of both gas face states
-      Wm[f] = W0m[f] + d0[f];
-      Wp[f] = W0p[f] + d0[f];
+  if (o.recon == RECON_CONSERVATIVE) {
+    T em[5], ec[5], ep[5];
+    bool gas_shaped = false;
+    for (int f = 0; f < 5; ++f) {
+      em[f] = dev(o, E, f, cm[0], cm[1], cm[2]);
+      ec[f] = dev(o, E, f, cell[0], cell[1], cell[2]);
+      ep[f] = dev(o, E, f, cp[0], cp[1], cp[2]);
+      gas_shaped |= parabola(em[f], ec[f], ep[f], xm, x0, xp, fm, fp, qm[f], qp[f]);
     }
-  }
-  T Um[5], Up[5];
-  cons_of(o.d.gamma, Wm, Um);
-  cons_of(o.d.gamma, Wp, Up);
-  for (int f = 0; f < 5; ++f) {
-    qm[f] = Um[f] - e0m[f];
-    qp[f] = Up[f] - e0p[f];
+    if (gas_shaped) {  // positivity of both gas face states
+      T Um[5], Up[5];
+      for (int f = 0; f < 5; ++f) {
+        Um[f] = e0m[f] + qm[f];
+        Up[f] = e0p[f] + qp[f];
+      }
+      if (!(Um[RHO] > 0.0 && Up[RHO] > 0.0 && pressure(o.d.gamma, Um) > 0.0 && pressure(o.d.gamma, Up) > 0.0))
+        for (int f = 0; f < 5; ++f) qm[f] = qp[f] = ec[f];
+    }
+  } else {
+    T dm[5], d0[5], dp[5], wm[5], wp[5];
+    prim_dev(o, E, cm[0], cm[1], cm[2], dm);
+    prim_dev(o, E, cell[0], cell[1], cell[2], d0);
+    prim_dev(o, E, cp[0], cp[1], cp[2], dp);
+    bool gas_shaped = false;
+    for (int f = 0; f < 5; ++f) gas_shaped |= parabola(dm[f], d0[f], dp[f], xm, x0, xp, fm, fp, wm[f], wp[f]);
+    double W0m[5] = {0, 0, 0, 0, 0}, W0p[5] = {0, 0, 0, 0, 0};
+    if (o.has_eq) {
+      prim_of(o.d.gamma, e0m, W0m);
+      prim_of(o.d.gamma, e0p, W0p);
+    }
+    T Wm[5], Wp[5];
+    for (int f = 0; f < 5; ++f) {
+      Wm[f] = W0m[f] + wm[f];
+      Wp[f] = W0p[f] + wp[f];
+    }
+    if (gas_shaped && !(Wm[RHO] > 0.0 && Wp[RHO] > 0.0 && Wm[EN] > 0.0 && Wp[EN] > 0.0)) {
+      for (int f = 0; f < 5; ++f) {  // positivity of both gas face states
+        Wm[f] = W0m[f] + d0[f];
+        Wp[f] = W0p[f] + d0[f];
+      }
+    }
+    T Um[5], Up[5];
+    cons_of(o.d.gamma, Wm, Um);
+    cons_of(o.d.gamma, Wp, Up);
+    for (int f = 0; f < 5; ++f) {
+      qm[f] = Um[f] - e0m[f];
+      qp[f] = Up[f] - e0p[f];
+    }
   }
   for (int s = 0; s < o.nd; ++s) {  // R5: dust in primitive variables (rho_d, u_d, v_d, w_d), per species
     const int b = 5 + 4 * s;
@@ -1223,6 +1258,31 @@ void orc_sources(void* h, int i, int j, int k, const double* U, double* S) {
 void orc_set_species_stokes(void* h, const double* f, int n) {
   Oracle& o = *(Oracle*)h;
   for (int k = 1; k < n && k < ND_MAX; ++k) o.st_factor[k] = f[k];
+}
+
+// Gas reconstruction of reading R2: 0 = conservative departures (Sect. 2.7
+// on App. B's E; the default), 1 = primitive departures.
+int orc_set_recon(void* h, int mode) {
+  if (mode != RECON_CONSERVATIVE && mode != RECON_PRIMITIVE) return 1;
+  ((Oracle*)h)->recon = mode;
+  return 0;
+}
+
+// Reconstructed face states of cell (i, j, k) along axis ax: the full
+// conservative states (E0 + q) on its lower (Um) and upper (Up) faces, nf
+// values each (dust: the reconstructed dust fields).
+void orc_recon_faces(void* h, const double* E, int ax, int i, int j, int k, double* Um, double* Up) {
+  const Oracle& o = *(Oracle*)h;
+  const ArrAcc A{E, o.ncell};
+  const int cell[3] = {i, j, k};
+  double qm[NFMAX], qp[NFMAX], e0m[5], e0p[5];
+  recon(o, A, ax, cell, qm, qp);
+  eq_face(o, ax, i, k, cell[ax], e0m);
+  eq_face(o, ax, i, k, cell[ax] + 1, e0p);
+  for (int f = 0; f < o.nf; ++f) {
+    Um[f] = f < 5 ? e0m[f] + qm[f] : qm[f];
+    Up[f] = f < 5 ? e0p[f] + qp[f] : qp[f];
+  }
 }
 
 // kappa = r_p / lambda_0 of the Stokes regime of drag law 2 (reading R19);

@@ -24,6 +24,9 @@ import math
 GEOM_BOX, GEOM_CYL = 0, 1
 BC_PERIODIC, BC_OUTFLOW, BC_EQUILIBRIUM = 0, 1, 2
 F_MU, F_MV, F_MW, F_EN, F_RHO, F_DMU, F_DMV, F_DMW, F_DRHO = range(9)
+# Gas reconstruction: the paper's component-wise parabola on the conservative
+# departures (Sect. 2.7 on App. B's E), or the primitive-departure option.
+RECON_CONSERVATIVE, RECON_PRIMITIVE = 0, 1
 
 H_ASPECT = 0.05
 DISC_PARAMS = (1.0, -0.5, H_ASPECT * H_ASPECT / 2.0, -1.0)  # sigma0, beta_sigma, T0, beta_T
@@ -62,6 +65,7 @@ class Workload:
     drag_kappa: float = 0.0      # drag law 2: r_p / lambda_0 of the Stokes regime
     t_end: float = 0.0           # >0: run to this time, clipping the last step
     checkpoint_every: int = 0
+    recon: int = RECON_CONSERVATIVE
 
     @property
     def ncell(self) -> int:

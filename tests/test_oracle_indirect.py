@@ -82,7 +82,7 @@ def _cartesian_brute_force(o, E, x_ref):
 
 @pytest.mark.parametrize("dust", [True, False])
 def test_indirect_matches_cartesian_newtonian_pull(dust):
-    w = syn.scaled(syn.VORTEX if dust else syn.DISC_NOISE, 10, 12, 8)
+    w = syn.scaled(syn.VORTEX if dust else syn.DISC_NOISE, 16, 12, 16)
     o = oracle.Oracle(w)
     E = _lopsided(o)
     D = _indirect_part(o, E, 0.7)
@@ -101,7 +101,7 @@ def test_indirect_matches_cartesian_newtonian_pull(dust):
 
 
 def test_axisymmetric_disc_exerts_no_pull():
-    w = syn.scaled(syn.VORTEX, 10, 12, 8)
+    w = syn.scaled(syn.VORTEX, 16, 12, 16)
     o = oracle.Oracle(w)
     E = o.equilibrium_state()
     R, TH, Z, _ = _grid(o)
@@ -118,7 +118,7 @@ def test_turning_the_disc_turns_the_force(shift):
     """Rolling every field by whole cells in theta rolls the indirect source
     with it: its local (r, theta) components are those of a rotated vector.
     A sign or a cos/sin swap in the cylindrical formula breaks this."""
-    w = syn.scaled(syn.VORTEX, 10, 12, 8)
+    w = syn.scaled(syn.VORTEX, 16, 12, 16)
     o = oracle.Oracle(w)
     E = _lopsided(o)
     D = _indirect_part(o, E, 0.7)
@@ -128,7 +128,7 @@ def test_turning_the_disc_turns_the_force(shift):
 
 
 def test_equilibrium_stays_bit_exact_with_indirect_gravity():
-    w = syn.scaled(syn.DISC_NOISE, 10, 12, 8)
+    w = syn.scaled(syn.DISC_NOISE, 16, 12, 16)
     o = oracle.Oracle(w)
     o.set_indirect(1.0)
     E = o.equilibrium_state()
@@ -149,7 +149,7 @@ def test_box_has_no_indirect_term():
 
 
 def test_sampled_steps_refuse_the_global_term():
-    w = syn.scaled(syn.VORTEX, 10, 12, 8)
+    w = syn.scaled(syn.VORTEX, 16, 12, 16)
     o = oracle.Oracle(w)
     o.set_indirect(1.0)
     E = oracle.initial_state(o)
@@ -160,7 +160,7 @@ def test_sampled_steps_refuse_the_global_term():
 def test_tlm_carries_the_indirect_term():
     """Tangent-linear step with the global A, B against central differences
     of the step, along a density direction that moves A and B."""
-    w = syn.scaled(syn.VORTEX, 10, 12, 16)
+    w = syn.scaled(syn.VORTEX, 16, 12, 32)
     o = oracle.Oracle(w)
     o.set_indirect(0.7)
     rng = np.random.default_rng(5)

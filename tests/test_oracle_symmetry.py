@@ -22,7 +22,7 @@ MU, MV, MW, EN, RHO, DMU, DMV, DMW, DRHO = range(9)
 
 
 def _state():
-    w = syn.scaled(syn.VORTEX, 12, 10, 16)
+    w = syn.scaled(syn.VORTEX, 12, 10, 32)
     o = oracle.Oracle(w)
     E = jitter(oracle.initial_state(o), w.gamma, np.random.default_rng(9), 1e-3)
     return w, o, E
