@@ -91,23 +91,24 @@ def _traffic(kernel_tag, cells):
     return None, None
 
 
-KERNEL_SOURCES = {  # headers that define the kernel, and the launch-configuration line's token
-    "stage_fp32": (("device_common.cuh", "stage_pert.cuh"), "P32_TR ="),
-    "stage_fp64pert": (("device_common.cuh", "stage_pert.cuh"), "P32_TR ="),
-    "stage_fp64": (("device_common.cuh", "stage_full.cuh"), "F64_TR ="),
+KERNEL_SOURCES = {  # files that define the kernel and its launcher, and the launch-configuration line's token
+    "stage_fp32": (("device_common.cuh", "stage_full.cuh", "stage_pert.cuh", "k_stage_pert_f32.cu"), "P32_TR ="),
+    "stage_fp64pert": (("device_common.cuh", "stage_full.cuh", "stage_pert.cuh", "k_stage_pert_f64.cu"), "P32_TR ="),
+    "stage_fp64": (("device_common.cuh", "stage_full.cuh", "k_stage_full.cu"), "F64_TR ="),
 }
 
 
 def _source_hash(kernel_tag):
-    """Hash of a kernel's code (its headers) and of its launch configuration
-    (the tile / thread-count line of rossbi.cu), not of its callers."""
+    """Hash of a kernel's code (its headers and launcher) and of its launch
+    configuration (the tile / thread-count line of launch.cuh), not of its
+    callers."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2207_04252_gb300", "csrc")
-    headers, token = KERNEL_SOURCES[kernel_tag]
-    for name in headers:
+    files, token = KERNEL_SOURCES[kernel_tag]
+    for name in files:
         h.update(open(os.path.join(csrc, name), "rb").read())
-    for line in open(os.path.join(csrc, "rossbi.cu")):
+    for line in open(os.path.join(csrc, "launch.cuh")):
         if token in line:
             h.update(line.encode())
     return h.hexdigest()[:16]

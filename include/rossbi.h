@@ -9,9 +9,10 @@
  *   - cell-centred finite volumes on the conservative variables (Sect. 2.2,
  *     App. B order: rho u, rho v, rho w, E, rho; dust: rho_d u_d, rho_d v_d,
  *     rho_d w_d, rho_d),
- *   - parabolic reconstruction of the deviation of the primitive gas
- *     variables (rho, u, v, w, P) and dust variables from the equilibrium,
- *     with a MinMod limiter (Sect. 2.7),
+ *   - parabolic reconstruction, with a MinMod limiter, of the deviation of
+ *     each conservative gas variable from the equilibrium (Sect. 2.7 on the
+ *     variables of App. B; the deviation of the primitive variables as an
+ *     option) and of the dust's primitive variables,
  *   - an exact Riemann solver at every gas face (Sect. 2.6) and an upwind
  *     pressureless flux at every dust face (Sect. 2.9),
  *   - geometric, gravity, rotating-frame and drag sources, balanced by the
@@ -61,6 +62,22 @@ enum { ROSSBI_BC_PERIODIC = 0, ROSSBI_BC_OUTFLOW = 1, ROSSBI_BC_EQUILIBRIUM = 2 
  *   ROSSBI_FP64_PERT : the perturbation form in double (state E', double). */
 enum { ROSSBI_FP64 = 0, ROSSBI_FP32_PERT = 1, ROSSBI_FP64_PERT = 2 };
 
+/* Gas reconstruction (Sect. 2.7).
+ *   ROSSBI_RECON_CONSERVATIVE : the paper's scheme.  The parabola and MinMod
+ *                      limiter act on each deviation E'_p = E_p - E0_p of the
+ *                      conservative variables of App. B (rho u, rho v, rho w,
+ *                      E, rho); a face state is E0 at the face plus the
+ *                      interpolated deviation.  The default (0).
+ *   ROSSBI_RECON_PRIMITIVE : the same parabola and limiter on the deviations
+ *                      of the primitive variables (rho, u, v, w, P) from the
+ *                      equilibrium primitives.  Not the paper's scheme: an
+ *                      option for fast rotating frames and vortex runs, where
+ *                      the conservative face pressure, a difference of terms
+ *                      O(Mach^2) larger than itself, makes the conservative
+ *                      scheme sensitive to rounding.
+ * The dust is reconstructed in its primitive variables in both modes. */
+enum { ROSSBI_RECON_CONSERVATIVE = 0, ROSSBI_RECON_PRIMITIVE = 1 };
+
 typedef struct rossbi_grid rossbi_grid; /* opaque, library-owned */
 
 /* Grid description (Sect. 2.3 mesh, Sect. 2.4 boundaries).
@@ -77,7 +94,8 @@ typedef struct rossbi_grid rossbi_grid; /* opaque, library-owned */
  *   omega_frame : angular speed of the rotating frame (cylindrical only).
  *   cfl      : N_CFL of the CFL condition (Sect. 2.5; the paper uses 1/2).
  *   n_dust   : 0 (gas only, 5 fields) or 1 (gas + one dust fluid, 9 fields).
- *   precision: one of the precision forms above. */
+ *   precision: one of the precision forms above.
+ *   recon    : one of the reconstruction modes above. */
 typedef struct {
   int geometry;
   int nr, nth, nz;
@@ -86,6 +104,7 @@ typedef struct {
   double gamma, gm, omega_frame, cfl;
   int n_dust;
   int precision;
+  int recon;
 } rossbi_grid_desc;
 
 /* Disc equilibrium parameters (App. A): Sigma = sigma0 r^beta_sigma,
@@ -233,8 +252,13 @@ rossbi_status rossbi_step_host(rossbi_grid* g, void* const* host_state, double d
  * (nfields + 1) * 8 bytes per 504-cell tile must fit in 64 MiB (for example
  * 9 fields in FP32 up to ~1.8 M cells, 5 fields in FP64 up to ~1.6 M cells);
  * larger grids get ROSSBI_ERR_ARG and nothing runs.
- * The first call on a device looks the array's device address up (with that
- * device current); make that first call before any stream capture.  Every
+ * The grid's device (the one current at rossbi_init_grid) must be current
+ * at every call, or the call returns ROSSBI_ERR_ARG: the array has one copy
+ * per device.  The first call on a device looks the array's device address
+ * up (with that device current); make that first call before any stream
+ * capture.  Optional terms switched on with rossbi_set_indirect or
+ * rossbi_set_damping act exactly as in rossbi_step (their tables are
+ * allocated by those calls, not here).  Every
  * call shares the array and it keeps the last call's contents; nothing in it
  * needs to start at zero.  Calls that overlap on the GPU (other streams,
  * grids or host threads) race on the array: serialise them. */

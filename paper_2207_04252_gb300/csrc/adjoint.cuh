@@ -16,7 +16,8 @@
 //   adj_flux_kernel   flux part of G'^T mu' along one axis, accumulated into
 //                     the cotangent of the stage input.
 // A line of L lanes along the axis owns T = L - 4 cells: lane p holds cell
-// c = c0 - 2 + p, reconstructs it (gas: primitive deviations), solves the face below it (once per tile),
+// c = c0 - 2 + p, reconstructs it (gas: the conservative departures, or the
+// primitive ones with RC = RECON_PRIM), solves the face below it (once per tile),
 // back-propagates the face cotangent to both face states, passes the lower
 // one down by a shuffle, back-propagates its own reconstruction and passes
 // the neighbour contributions up and down by shuffles; every sum has a fixed
@@ -635,7 +636,7 @@ __global__ void __launch_bounds__(ADJ_PT_NT) adj_point_kernel(const AdjPointArgs
 // A = sum w (rho - rho_0 + rho_d) cos(theta), B likewise with sin, so
 // lam[RHO] and lam[DRHO] gain X_ref w (dA cos(theta_j) + dB sin(theta_j)),
 // (dA, dB) the reduced point-kernel partials; w = V r / R^3 [nz][nr].
-__global__ void __launch_bounds__(ADJ_PT_NT) adj_indirect_bcast_kernel(const DevGrid g, const double* w,
+static __global__ void __launch_bounds__(ADJ_PT_NT) adj_indirect_bcast_kernel(const DevGrid g, const double* w,
                                                                        const double* dAB, double* lam_rho,
                                                                        double* lam_drho) {
   const size_t ncell = (size_t)g.nr * g.nth * g.nz;
@@ -664,7 +665,7 @@ constexpr size_t adj_flux_smem_doubles() {
   return (size_t)NF * ((L + 2) + L) * (NL + 1);
 }
 
-template <int NF, int D, int L, int NL>
+template <int NF, int D, int L, int NL, int RC>
 __global__ void __launch_bounds__(L * NL, 1) adj_flux_kernel(const AdjFluxArgs a) {
   constexpr int T = L - 4;      // cells per line owned by a block
   constexpr int PE = T + 6;     // staged E': cells c0 - 3 .. c0 + T + 2
@@ -707,10 +708,13 @@ __global__ void __launch_bounds__(L * NL, 1) adj_flux_kernel(const AdjFluxArgs a
     double U[5], W[5];
 #pragma unroll
     for (int f = 0; f < 5; ++f) U[f] = a.E[f][lin];
-    gas_prim(g.gamma, U, W);
+    if (RC == RECON_PRIM) gas_prim(g.gamma, U, W);
+    const double* e0 = RC == RECON_PRIM ? g.w0c : g.e0c;
 #pragma unroll
-    for (int f = 0; f < 5; ++f)
-      dst[(size_t)f * PE * NLP] = g.has_eq ? W[f] - g.w0c[((size_t)f * g.nz + c[2]) * g.nr + c[0]] : W[f];
+    for (int f = 0; f < 5; ++f) {
+      const double v = RC == RECON_PRIM ? W[f] : U[f];
+      dst[(size_t)f * PE * NLP] = g.has_eq ? v - e0[((size_t)f * g.nz + c[2]) * g.nr + c[0]] : v;
+    }
 #pragma unroll
     for (int f = 5; f < NF; ++f) dst[(size_t)f * PE * NLP] = a.E[f][lin];
   }
@@ -754,11 +758,15 @@ __global__ void __launch_bounds__(L * NL, 1) adj_flux_kernel(const AdjFluxArgs a
   unsigned status = 0;
   auto sv = [&](int f, int q) -> double { return sE[((size_t)f * PE + q) * NLP + l]; };
   auto sm = [&](int f, int q) -> double { return sM[((size_t)f * PM + q) * NLP + l]; };
-  auto w0_face = [&](int f, int fd) -> double {
+  // equilibrium on a face: conservative, or primitive with RC = RECON_PRIM
+  auto eq_face = [&](int f, int fd) -> double {
     if (!g.has_eq) return 0.0;
-    if (D == 0) return g.w0r[((size_t)f * g.nz + ck) * (g.nr + 1) + clampi(fd, 0, g.nr)];
-    if (D == 1) return g.w0c[((size_t)f * g.nz + ck) * g.nr + ci];
-    return g.w0z[((size_t)f * (g.nz + 1) + clampi(fd, 0, g.nz)) * g.nr + ci];
+    const double* tc = RC == RECON_PRIM ? g.w0c : g.e0c;
+    const double* tr = RC == RECON_PRIM ? g.w0r : g.e0r;
+    const double* tz = RC == RECON_PRIM ? g.w0z : g.e0z;
+    if (D == 0) return tr[((size_t)f * g.nz + ck) * (g.nr + 1) + clampi(fd, 0, g.nr)];
+    if (D == 1) return tc[((size_t)f * g.nz + ck) * g.nr + ci];
+    return tz[((size_t)f * (g.nz + 1) + clampi(fd, 0, g.nz)) * g.nr + ci];
   };
   double w[9];
   parabola_weights<double, D>(g.rcoef, gi, g.nr, g.dx[D], w);
@@ -770,8 +778,20 @@ __global__ void __launch_bounds__(L * NL, 1) adj_flux_kernel(const AdjFluxArgs a
   for (int f = 0; f < 5; ++f) shaped |= parabola(sv(f, p), sv(f, p + 1), sv(f, p + 2), w, qm[f], qp[f]);
   bool fallback = false;
   if (shaped && line_ok) {
-    fallback = !(w0_face(RHO, c) + qm[RHO] > 0.0 && w0_face(RHO, c + 1) + qp[RHO] > 0.0 &&
-                 w0_face(EN, c) + qm[EN] > 0.0 && w0_face(EN, c + 1) + qp[EN] > 0.0);
+    if (RC == RECON_PRIM) {
+      fallback = !(eq_face(RHO, c) + qm[RHO] > 0.0 && eq_face(RHO, c + 1) + qp[RHO] > 0.0 &&
+                   eq_face(EN, c) + qm[EN] > 0.0 && eq_face(EN, c + 1) + qp[EN] > 0.0);
+    } else {
+      double Um[5], Up[5];
+#pragma unroll
+      for (int f = 0; f < 5; ++f) {
+        Um[f] = eq_face(f, c) + qm[f];
+        Up[f] = eq_face(f, c + 1) + qp[f];
+      }
+      fallback = !(Um[RHO] > 0.0 && Up[RHO] > 0.0 &&
+                   gas_pressure(gam, Um[MU], Um[MV], Um[MW], Um[EN], Um[RHO]) > 0.0 &&
+                   gas_pressure(gam, Up[MU], Up[MV], Up[MW], Up[EN], Up[RHO]) > 0.0);
+    }
     if (fallback) {
 #pragma unroll
       for (int f = 0; f < 5; ++f) qm[f] = qp[f] = sv(f, p + 1);
@@ -807,12 +827,19 @@ __global__ void __launch_bounds__(L * NL, 1) adj_flux_kernel(const AdjFluxArgs a
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
       const double ql = __shfl_up_sync(FULL, qp[f], 1, L);
-      const double w0 = w0_face(f, c);
-      UL[f] = w0 + ql;
-      UR[f] = w0 + qm[f];
+      const double e0 = eq_face(f, c);
+      UL[f] = e0 + ql;
+      UR[f] = e0 + qm[f];
     }
-    if (has_face) {
+    if (has_face && RC == RECON_PRIM) {
       gas_flux_vjp<D>(gam, UL, UR, Fb, ULb, URb, status);
+    } else if (has_face) {  // conservative face states: through W = gas_prim(U)
+      double WL[5], WR[5], WLb[5], WRb[5];
+      gas_prim(gam, UL, WL);
+      gas_prim(gam, UR, WR);
+      gas_flux_vjp<D>(gam, WL, WR, Fb, WLb, WRb, status);
+      gas_prim_vjp(gam, UL, WLb, ULb);
+      gas_prim_vjp(gam, UR, WRb, URb);
     } else {
 #pragma unroll
       for (int f = 0; f < 5; ++f) ULb[f] = URb[f] = 0.0;
@@ -886,16 +913,17 @@ __global__ void __launch_bounds__(L * NL, 1) adj_flux_kernel(const AdjFluxArgs a
   }
   if (line_ok && p >= 2 && p < T + 2 && c < nd) {
     const size_t lin = ((size_t)cc[2] * g.nth + cc[1]) * g.nr + cc[0];
-    // gas: primitive-deviation cotangents back to the conservative fields
-    const double rho = a.E[RHO][lin], ir = 1.0 / rho, gm1 = gam - 1.0;
-    const double v0 = a.E[MU][lin] * ir, v1 = a.E[MV][lin] * ir, v2 = a.E[MW][lin] * ir;
-    const double bP = tot[EN];
-    double lr = tot[RHO] - (tot[MU] * v0 + tot[MV] * v1 + tot[MW] * v2) * ir + gm1 * bP * 0.5 * (v0 * v0 + v1 * v1 + v2 * v2);
-    a.lam[MU][lin] += tot[MU] * ir - gm1 * bP * v0;
-    a.lam[MV][lin] += tot[MV] * ir - gm1 * bP * v1;
-    a.lam[MW][lin] += tot[MW] * ir - gm1 * bP * v2;
-    a.lam[EN][lin] += gm1 * bP;
-    a.lam[RHO][lin] += lr;
+    if (RC == RECON_PRIM) {  // gas: primitive-deviation cotangents back to the conservative fields
+      double U[5], Ub[5];
+#pragma unroll
+      for (int f = 0; f < 5; ++f) U[f] = a.E[f][lin];
+      gas_prim_vjp(gam, U, tot, Ub);
+#pragma unroll
+      for (int f = 0; f < 5; ++f) a.lam[f][lin] += Ub[f];
+    } else {
+#pragma unroll
+      for (int f = 0; f < 5; ++f) a.lam[f][lin] += tot[f];
+    }
 #pragma unroll
     for (int f = 5; f < NF; ++f) a.lam[f][lin] += tot[f];
   }
@@ -907,7 +935,7 @@ struct Fields9 {
 };
 
 // Stage-1 drag on its own: out = D(Y) over tau (E* from the pre-drag state).
-__global__ void __launch_bounds__(ADJ_PT_NT) drag_only_kernel(DevGrid g, const Fields9 Y, const Fields9 out,
+static __global__ void __launch_bounds__(ADJ_PT_NT) drag_only_kernel(DevGrid g, const Fields9 Y, const Fields9 out,
                                                              double tau, DragArgs d) {
   const size_t ncell = (size_t)g.nr * g.nth * g.nz;
   for (size_t lin = blockIdx.x * (size_t)ADJ_PT_NT + threadIdx.x; lin < ncell; lin += (size_t)gridDim.x * ADJ_PT_NT) {
@@ -922,7 +950,7 @@ __global__ void __launch_bounds__(ADJ_PT_NT) drag_only_kernel(DevGrid g, const F
 
 // Fixed-order sum of the d/dSt block partials of both stages; adds the
 // result to this call's slot [0] and to the running total [1].
-__global__ void __launch_bounds__(512) adj_dst_reduce_kernel(const double* partials, int n, double* slots) {
+static __global__ void __launch_bounds__(512) adj_dst_reduce_kernel(const double* partials, int n, double* slots) {
   __shared__ double red[512 / 32];
   double v = 0.0;
   for (int b = threadIdx.x; b < n; b += 512) v += partials[b];

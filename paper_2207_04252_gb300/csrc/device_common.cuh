@@ -11,6 +11,10 @@ enum { MU = 0, MV = 1, MW = 2, EN = 3, RHO = 4, DMU = 5, DMV = 6, DMW = 7, DRHO 
 enum { GEOM_BOX = 0, GEOM_CYL = 1 };
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_EQUILIBRIUM = 2 };
 enum { STATUS_NONPHYSICAL = 1u, STATUS_RIEMANN = 2u };
+// Gas reconstruction (Sect. 2.7): the paper's component-wise parabola on the
+// conservative departures E' = E - E0 of App. B's variables, or the parabola
+// on the departures of the primitive variables (rho, u, v, w, P).
+enum { RECON_CONS = 0, RECON_PRIM = 1 };
 
 constexpr int GH = 2;   // ghost offset of the axis-0 coordinate tables
 constexpr int RCW = 10; // parabola weights per axis-0 cell (9 used)
@@ -19,6 +23,7 @@ constexpr int RCW = 10; // parabola weights per axis-0 cell (9 used)
 // pointers are device tables owned by the host runtime.
 struct DevGrid {
   int geom, nr, nth, nz, nf, has_eq;
+  int recon;             // RECON_CONS or RECON_PRIM
   int bc_lo[3], bc_hi[3];
   double gamma, gm, omega, cfl;
   double x0[3], dx[3];   // uniform axes 1, 2 (and axis 0 of the Box): origin, spacing
@@ -302,6 +307,20 @@ __device__ __forceinline__ void gas_prim(double g, const double* U, double* W) {
   W[MW] = U[MW] * ir;
   W[EN] = gas_pressure(g, U[MU], U[MV], U[MW], U[EN], U[RHO]);
   W[RHO] = U[RHO];
+}
+
+// Cotangent Ub of the conservative gas state U for a cotangent Wb of its
+// primitive state W = gas_prim(U) (the transpose of the conversion's
+// Jacobian at U).
+__device__ __forceinline__ void gas_prim_vjp(double g, const double* U, const double* Wb, double* Ub) {
+  const double ir = 1.0 / U[RHO], gm1 = g - 1.0;
+  const double v0 = U[MU] * ir, v1 = U[MV] * ir, v2 = U[MW] * ir;
+  const double bP = Wb[EN];
+  Ub[MU] = Wb[MU] * ir - gm1 * bP * v0;
+  Ub[MV] = Wb[MV] * ir - gm1 * bP * v1;
+  Ub[MW] = Wb[MW] * ir - gm1 * bP * v2;
+  Ub[EN] = gm1 * bP;
+  Ub[RHO] = Wb[RHO] - (Wb[MU] * v0 + Wb[MV] * v1 + Wb[MW] * v2) * ir + gm1 * bP * 0.5 * (v0 * v0 + v1 * v1 + v2 * v2);
 }
 
 // Gas flux F(E*) through a face normal to axis D from the reconstructed left

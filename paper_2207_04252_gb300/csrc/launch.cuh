@@ -1,0 +1,45 @@
+// Kernel launchers of the stage and adjoint-flux kernels, one translation
+// unit per kernel family (compiled in parallel), called by the host runtime.
+// Each dispatches on the field count, the optional-term switch and the gas
+// reconstruction mode to one instantiation of its kernel template.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "adjoint.cuh"
+#include "stage_pert.cuh"
+
+namespace rossbi {
+
+// Tiles of the stage kernels: 14 x 6 x 6 cells, lines of 16 / 8 / 8 lanes.
+constexpr int F64_TR = 14, F64_TT = 6, F64_TZ = 6, F64_NT = 192;
+constexpr int P32_TR = 14, P32_TT = 6, P32_TZ = 6, P32_NT = 256, P32_MINB = 2;
+// Adjoint flux kernel: lines of 16 lanes (12 owned cells), 16 lines per block.
+constexpr int ADJ_L = 16, ADJ_NL = 16;
+
+// Raises a kernel's dynamic shared-memory limit once per device (the
+// attribute belongs to the current device's context); `done` is the calling
+// site's own flag word, one bit per device id < 64.
+template <class K>
+cudaError_t set_smem_once(K kern, size_t smem, unsigned long long& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+  if (bit && (done & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) done |= bit;
+  return e;
+}
+
+// One launch of the FP64 stage kernel over nblocks tiles; xt selects the
+// instantiation with the optional terms (indirect gravity, wave-killing
+// zones, Stokes drag regime).
+cudaError_t run_stage_full(const StageArgs& a, int nblocks, cudaStream_t s, bool xt);
+// One launch of the perturbation-form stage kernel (float or double); g75
+// selects the gamma = 7/5 power forms of the float solver.
+cudaError_t run_stage_pert_f32(const PertArgs<float>& a, int nblocks, cudaStream_t s, bool xt, bool g75);
+cudaError_t run_stage_pert_f64(const PertArgs<double>& a, int nblocks, cudaStream_t s, bool xt);
+// One launch of the adjoint flux kernel along axis 0, 1 or 2.
+cudaError_t run_adj_flux(const AdjFluxArgs& a, int axis, cudaStream_t s);
+
+}  // namespace rossbi

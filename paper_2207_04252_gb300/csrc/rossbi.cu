@@ -13,16 +13,12 @@
 #include <vector>
 
 #include "../../include/rossbi.h"
-#include "adjoint.cuh"
-#include "stage_pert.cuh"
+#include "launch.cuh"
 
 using namespace rossbi;
 
 namespace {
 
-// Tile of the stage kernels: 14 x 6 x 6 cells, lines of 16 / 8 / 8 lanes.
-constexpr int F64_TR = 14, F64_TT = 6, F64_TZ = 6, F64_NT = 192;
-constexpr int P32_TR = 14, P32_TT = 6, P32_TZ = 6, P32_NT = 256, P32_MINB = 2;
 constexpr int CFL_NT = 256;
 
 }  // namespace
@@ -30,6 +26,7 @@ constexpr int CFL_NT = 256;
 struct rossbi_grid {
   rossbi_grid_desc desc{};
   cudaStream_t stream = nullptr;
+  int device = -1;                     // the device current at rossbi_init_grid
   int nf = 5;
   size_t ncell = 0;
   DevGrid dg{};
@@ -157,6 +154,7 @@ rossbi_status check_desc(const rossbi_grid_desc& d) {
   }
   if (d.precision != ROSSBI_FP64 && d.precision != ROSSBI_FP32_PERT && d.precision != ROSSBI_FP64_PERT)
     return ROSSBI_ERR_ARG;
+  if (d.recon != ROSSBI_RECON_CONSERVATIVE && d.recon != ROSSBI_RECON_PRIMITIVE) return ROSSBI_ERR_ARG;
   return ROSSBI_OK;
 }
 
@@ -322,36 +320,6 @@ __global__ void __launch_bounds__(RED_NT) indirect_reduce_kernel(const double* p
   }
 }
 
-// Raises a kernel's dynamic shared-memory limit once per device (the
-// attribute belongs to the current device's context); `done` is the calling
-// site's own flag word, one bit per device id < 64.
-template <class K>
-rossbi_status set_smem_once(K kern, size_t smem, unsigned long long& done) {
-  int dev = 0;
-  CK(cudaGetDevice(&dev));
-  const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
-  if (bit && (done & bit)) return ROSSBI_OK;
-  CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  done |= bit;
-  return ROSSBI_OK;
-}
-
-template <int NF, bool XT>
-rossbi_status launch_stage_f64(rossbi_grid* g, const StageArgs& a, int nblocks) {
-  constexpr int BOX = (F64_TR + 4) * (F64_TT + 4) * (F64_TZ + 4);
-  constexpr int NCORE = F64_TR * F64_TT * F64_TZ;
-  constexpr size_t smem = (size_t)NF * (BOX + NCORE) * sizeof(double);
-  auto kern = stage_full_kernel<NF, F64_TR, F64_TT, F64_TZ, F64_NT, XT>;
-  {
-    static unsigned long long done = 0;
-    const rossbi_status sa = set_smem_once(kern, smem, done);
-    if (sa != ROSSBI_OK) return sa;
-  }
-  kern<<<nblocks, F64_NT, smem, g->stream>>>(a);
-  CK(cudaGetLastError());
-  return ROSSBI_OK;
-}
-
 constexpr int PROFILE_PAIRS = 1024;
 
 rossbi_status profile_drain(rossbi_grid* g) {
@@ -379,37 +347,12 @@ rossbi_status launch_stage(rossbi_grid* g, const StageArgs& a, int nblocks) {
     CK(cudaEventRecord(e0, g->stream));
   }
   const bool xt = a.g.x_ind != 0.0 || a.g.damp_k != nullptr || a.drag.law == 2;  // optional terms on
-  rossbi_status st = g->nf == 9 ? (xt ? launch_stage_f64<9, true>(g, a, nblocks) : launch_stage_f64<9, false>(g, a, nblocks))
-                                : (xt ? launch_stage_f64<5, true>(g, a, nblocks) : launch_stage_f64<5, false>(g, a, nblocks));
-  if (st != ROSSBI_OK) return st;
+  CK(run_stage_full(a, nblocks, g->stream, xt));
   if (e0) {
     CK(cudaEventRecord(e1, g->stream));
     g->ev_used++;
   }
   return ROSSBI_OK;
-}
-
-template <class T, int NF, class P, bool XT>
-rossbi_status launch_pert_nf_x(rossbi_grid* g, const PertArgs<T>& a, int nblocks) {
-  constexpr bool F32 = sizeof(T) == 4;
-  constexpr int TR = P32_TR, TT = P32_TT, TZ = P32_TZ, NT = P32_NT, MINB = F32 ? P32_MINB : 1;
-  constexpr int BOX = (TR + 4) * (TT + 4) * (TZ + 4), NCORE = TR * TT * TZ;
-  constexpr size_t smem = (size_t)NF * (BOX + NCORE) * sizeof(T);
-  auto kern = stage_pert_kernel<T, NF, TR, TT, TZ, NT, MINB, P, XT>;
-  {
-    static unsigned long long done = 0;
-    const rossbi_status sa = set_smem_once(kern, smem, done);
-    if (sa != ROSSBI_OK) return sa;
-  }
-  kern<<<nblocks, NT, smem, g->stream>>>(a);
-  CK(cudaGetLastError());
-  return ROSSBI_OK;
-}
-
-template <class T, int NF, class P>
-rossbi_status launch_pert_nf(rossbi_grid* g, const PertArgs<T>& a, int nblocks) {
-  const bool xt = a.g.x_ind != 0.0 || a.g.damp_k != nullptr || a.drag.law == 2;  // optional terms on
-  return xt ? launch_pert_nf_x<T, NF, P, true>(g, a, nblocks) : launch_pert_nf_x<T, NF, P, false>(g, a, nblocks);
 }
 
 template <class T>
@@ -424,18 +367,11 @@ rossbi_status launch_pert(rossbi_grid* g, const PertArgs<T>& a, int nblocks) {
     e1 = g->ev[2 * g->ev_used + 1];
     CK(cudaEventRecord(e0, g->stream));
   }
-  rossbi_status st;
-  if constexpr (sizeof(T) == 4) {
-    if (g->desc.gamma == 1.4)  // gamma = 7/5: integer-power forms of the solver
-      st = g->nf == 9 ? launch_pert_nf<T, 9, PowG75>(g, a, nblocks) : launch_pert_nf<T, 5, PowG75>(g, a, nblocks);
-    else
-      st = g->nf == 9 ? launch_pert_nf<T, 9, PowGeneric<T>>(g, a, nblocks)
-                      : launch_pert_nf<T, 5, PowGeneric<T>>(g, a, nblocks);
-  } else {
-    st = g->nf == 9 ? launch_pert_nf<T, 9, PowGeneric<T>>(g, a, nblocks)
-                    : launch_pert_nf<T, 5, PowGeneric<T>>(g, a, nblocks);
-  }
-  if (st != ROSSBI_OK) return st;
+  const bool xt = a.g.x_ind != 0.0 || a.g.damp_k != nullptr || a.drag.law == 2;  // optional terms on
+  if constexpr (sizeof(T) == 4)  // gamma = 7/5: integer-power forms of the float solver
+    CK(run_stage_pert_f32(a, nblocks, g->stream, xt, g->desc.gamma == 1.4));
+  else
+    CK(run_stage_pert_f64(a, nblocks, g->stream, xt));
   if (e0) {
     CK(cudaEventRecord(e1, g->stream));
     g->ev_used++;
@@ -774,8 +710,8 @@ rossbi_status indirect_moments(rossbi_grid* g, void* const* state) {
   return ROSSBI_OK;
 }
 
-rossbi_status finish_step(rossbi_grid* g, int nxt, double* next_dt) {
-  reduce_partials_kernel<<<g->nf + 1, RED_NT, 0, g->stream>>>(g->d_partials, n_tiles(g), g->nf, g->d_sums,
+rossbi_status finish_step(rossbi_grid* g, const double* partials, int nxt, double* next_dt) {
+  reduce_partials_kernel<<<g->nf + 1, RED_NT, 0, g->stream>>>(partials, n_tiles(g), g->nf, g->d_sums,
                                                                g->d_dt + nxt);
   CK(cudaGetLastError());
   g->dt_slot = nxt;
@@ -789,8 +725,11 @@ rossbi_status finish_step(rossbi_grid* g, int nxt, double* next_dt) {
   return ROSSBI_OK;
 }
 
-rossbi_status step_full(rossbi_grid* g, void* const* state, void* const* sc, double dt, const DragArgs& drag,
-                        double* next_dt) {
+// The two stages of one step (Sect. 2.5) with E* in sc and the stage-2
+// block partials in `partials`; with the indirect gravity on, the disc
+// moments of each stage's input are summed before it.  Allocates nothing.
+rossbi_status step_full(rossbi_grid* g, void* const* state, void* const* sc, double* partials, double dt,
+                        const DragArgs& drag, double* next_dt) {
   const int nblocks = n_tiles(g);
   const int cur = g->dt_slot, nxt = 1 - g->dt_slot;
   StageArgs a = base_args(g);
@@ -817,15 +756,15 @@ rossbi_status step_full(rossbi_grid* g, void* const* state, void* const* sc, dou
   }
   a.tau_frac = 1.0;
   a.stage2 = 1;
-  a.partials = g->d_partials;
+  a.partials = partials;
   st = launch_stage(g, a, nblocks);
   if (st != ROSSBI_OK) return st;
-  return finish_step(g, nxt, next_dt);
+  return finish_step(g, partials, nxt, next_dt);
 }
 
 template <class T>
-rossbi_status step_pert(rossbi_grid* g, void* const* state, void* const* sc, double dt, const DragArgs& drag,
-                        double* next_dt) {
+rossbi_status step_pert(rossbi_grid* g, void* const* state, void* const* sc, double* partials, double dt,
+                        const DragArgs& drag, double* next_dt) {
   const int nblocks = n_tiles(g);
   const int cur = g->dt_slot, nxt = 1 - g->dt_slot;
   PertArgs<T> a = pert_args<T>(g);
@@ -850,31 +789,24 @@ rossbi_status step_pert(rossbi_grid* g, void* const* state, void* const* sc, dou
   }
   a.tau_frac = 1.0;
   a.stage2 = 1;
-  a.partials = g->d_partials;
+  a.partials = partials;
   st = launch_pert<T>(g, a, nblocks);
   if (st != ROSSBI_OK) return st;
-  return finish_step(g, nxt, next_dt);
+  return finish_step(g, partials, nxt, next_dt);
+}
+
+rossbi_status step_form(rossbi_grid* g, void* const* state, void* const* sc, double* partials, double dt,
+                        const DragArgs& drag, double* next_dt) {
+  switch (g->desc.precision) {
+    case ROSSBI_FP64: return step_full(g, state, sc, partials, dt, drag, next_dt);
+    case ROSSBI_FP32_PERT: return step_pert<float>(g, state, sc, partials, dt, drag, next_dt);
+    default: return step_pert<double>(g, state, sc, partials, dt, drag, next_dt);
+  }
 }
 
 // ---------------------------------------------------------------- adjoint
-constexpr int ADJ_L = 16, ADJ_NL = 16;  // lines of 16 lanes (12 owned cells), 16 lines per block
-
-template <int NF, int D>
-rossbi_status launch_adj_flux(rossbi_grid* g, const AdjFluxArgs& a) {
-  constexpr size_t smem = adj_flux_smem_doubles<NF, ADJ_L, ADJ_NL>() * sizeof(double);
-  constexpr int T = ADJ_L - 4;
-  auto kern = adj_flux_kernel<NF, D, ADJ_L, ADJ_NL>;
-  {
-    static unsigned long long done = 0;
-    const rossbi_status sa = set_smem_once(kern, smem, done);
-    if (sa != ROSSBI_OK) return sa;
-  }
-  const rossbi_grid_desc& d = g->desc;
-  const long nd = D == 0 ? d.nr : (D == 1 ? d.nth : d.nz);
-  const long nlines = D == 0 ? (long)d.nth * d.nz : (D == 1 ? (long)d.nr * d.nz : (long)d.nr * d.nth);
-  const long nblocks = ((nd + T - 1) / T) * ((nlines + ADJ_NL - 1) / ADJ_NL);
-  kern<<<(unsigned)nblocks, ADJ_L * ADJ_NL, smem, g->stream>>>(a);
-  CK(cudaGetLastError());
+rossbi_status launch_adj_flux3(rossbi_grid* g, const AdjFluxArgs& a) {
+  for (int axis = 0; axis < 3; ++axis) CK(run_adj_flux(a, axis, g->stream));
   return ROSSBI_OK;
 }
 
@@ -925,9 +857,7 @@ rossbi_status adjoint_reverse(rossbi_grid* g, void* const* state, double dt, con
                                                                 NF == 9 ? LamS[DRHO] : nullptr);
     CK(cudaGetLastError());
   }
-  rossbi_status st = launch_adj_flux<NF, 0>(g, fa);
-  if (st == ROSSBI_OK) st = launch_adj_flux<NF, 1>(g, fa);
-  if (st == ROSSBI_OK) st = launch_adj_flux<NF, 2>(g, fa);
+  rossbi_status st = launch_adj_flux3(g, fa);
   if (st != ROSSBI_OK) return st;
   // stage 1: E* = D(Y1), Y1 = E^n + dt/2 (G(E^n) - R0) / V
   for (int f = 0; f < NF; ++f) {
@@ -954,9 +884,7 @@ rossbi_status adjoint_reverse(rossbi_grid* g, void* const* state, double dt, con
                                                                 NF == 9 ? (double*)lam_n[DRHO] : nullptr);
     CK(cudaGetLastError());
   }
-  st = launch_adj_flux<NF, 0>(g, fa);
-  if (st == ROSSBI_OK) st = launch_adj_flux<NF, 1>(g, fa);
-  if (st == ROSSBI_OK) st = launch_adj_flux<NF, 2>(g, fa);
+  st = launch_adj_flux3(g, fa);
   if (st != ROSSBI_OK) return st;
   adj_dst_reduce_kernel<<<1, 512, 0, g->stream>>>(g->d_adj_part, 2 * nb, g->d_adj_slots);
   CK(cudaGetLastError());
@@ -1072,11 +1000,7 @@ rossbi_status step_device(rossbi_grid* g, void* const* state, void* const* scrat
   DragArgs drag;
   rossbi_status st = prepare_step(g, state, scratch, dt, dust, sc, drag);
   if (st != ROSSBI_OK) return st;
-  switch (g->desc.precision) {
-    case ROSSBI_FP64: return step_full(g, state, sc, dt, drag, next_dt);
-    case ROSSBI_FP32_PERT: return step_pert<float>(g, state, sc, dt, drag, next_dt);
-    default: return step_pert<double>(g, state, sc, dt, drag, next_dt);
-  }
+  return step_form(g, state, sc, g->d_partials, dt, drag, next_dt);
 }
 
 }  // namespace
@@ -1132,6 +1056,10 @@ rossbi_status rossbi_init_grid(const rossbi_grid_desc* desc, void* cuda_stream, 
   if (!g) return ROSSBI_ERR_OOM;
   g->desc = *desc;
   g->stream = (cudaStream_t)cuda_stream;
+  if (cudaGetDevice(&g->device) != cudaSuccess) {
+    delete g;
+    return ROSSBI_ERR_CUDA;
+  }
   g->nf = desc->n_dust ? 9 : 5;
   g->ncell = (size_t)desc->nr * desc->nth * desc->nz;
   const bool pert = desc->precision != ROSSBI_FP64;  // tile of the form's stage kernel
@@ -1210,6 +1138,7 @@ rossbi_status rossbi_init_grid(const rossbi_grid_desc* desc, void* cuda_stream, 
   dg.nz = d.nz;
   dg.nf = g->nf;
   dg.has_eq = 0;
+  dg.recon = d.recon == ROSSBI_RECON_PRIMITIVE ? RECON_PRIM : RECON_CONS;
   for (int a = 0; a < 3; ++a) {
     dg.bc_lo[a] = d.bc_lo[a];
     dg.bc_hi[a] = d.bc_hi[a];
@@ -1582,89 +1511,27 @@ extern "C" rossbi_status rossbi_step_noalloc(rossbi_grid* g, void* const* state,
   for (int f = 0; f < g->nf; ++f)
     if (!state[f]) return ROSSBI_ERR_ARG;
   if (g->nf == 9 && !dust) return ROSSBI_ERR_ARG;
+  if (g->nf == 9 && dust->drag_law == 2) return ROSSBI_ERR_ARG;
   if (dt < 0.0 || !std::isfinite(dt)) return ROSSBI_ERR_ARG;
   if (dt == 0.0 && !g->dt_on_device) return ROSSBI_ERR_ARG;
+  // the array's address is per device: only the grid's own device may be current
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev != g->device) return ROSSBI_ERR_ARG;
   const int nblocks = n_tiles(g);
   const size_t field_bytes = align256(g->ncell * elem_size(g));
   const size_t partial_bytes = (size_t)(g->nf + 1) * nblocks * sizeof(double);
   if ((size_t)g->nf * field_bytes + partial_bytes > NOALLOC_SCRATCH_BYTES) return ROSSBI_ERR_ARG;
+  DragArgs drag;
+  rossbi_status st = drag_args(g, dust, drag);
+  if (st != ROSSBI_OK) return st;
   void* base = nullptr;
-  rossbi_status st = noalloc_scratch_ptr(&base);
+  st = noalloc_scratch_ptr(&base);
   if (st != ROSSBI_OK) return st;
   void* sc[9];
   for (int f = 0; f < g->nf; ++f) sc[f] = (char*)base + (size_t)f * field_bytes;
   double* partials = (double*)((char*)base + (size_t)g->nf * field_bytes);
-  DragArgs drag{0.0, 0.0, 0, 0.0};
-  if (g->nf == 9) {
-    if (!(dust->stokes > 0.0) || (dust->drag_law != 0 && dust->drag_law != 1)) return ROSSBI_ERR_ARG;
-    drag.stokes = dust->stokes;
-    drag.law = dust->drag_law;
-    if (dust->drag_law == 1) {
-      if (!g->has_disc) return ROSSBI_ERR_ARG;
-      double rho1, vth1, p1;
-      equilibrium_prim(g->desc, g->disc, 1.0, 0.0, rho1, vth1, p1);
-      drag.rhos_rp = dust->stokes * rho1 * std::sqrt(g->desc.gamma * p1 / rho1) / std::sqrt(g->desc.gm);
-    }
-  }
-  const int cur = g->dt_slot, nxt = 1 - g->dt_slot;
-  const unsigned long long* dt_dev = dt == 0.0 ? g->d_dt + cur : nullptr;
-  const int prec = g->desc.precision;
-  for (int stage = 1; stage <= 2; ++stage) {
-    const bool s2 = stage == 2;
-    if (prec == ROSSBI_FP64) {
-      StageArgs a = base_args(g);
-      a.drag = drag;
-      a.dt_host = dt;
-      a.dt_dev = dt_dev;
-      for (int f = 0; f < g->nf; ++f) {
-        a.in[f] = (const double*)(s2 ? sc[f] : state[f]);
-        a.base[f] = (const double*)state[f];
-        a.out[f] = (double*)(s2 ? state[f] : sc[f]);
-      }
-      a.tau_frac = s2 ? 1.0 : 0.5;
-      a.stage2 = s2 ? 1 : 0;
-      a.partials = partials;
-      st = launch_stage(g, a, nblocks);
-    } else if (prec == ROSSBI_FP32_PERT) {
-      PertArgs<float> a = pert_args<float>(g);
-      a.drag = drag;
-      a.dt_host = dt;
-      a.dt_dev = dt_dev;
-      for (int f = 0; f < g->nf; ++f) {
-        a.in[f] = (const float*)(s2 ? sc[f] : state[f]);
-        a.base[f] = (const float*)state[f];
-        a.out[f] = (float*)(s2 ? state[f] : sc[f]);
-      }
-      a.tau_frac = s2 ? 1.0 : 0.5;
-      a.stage2 = s2 ? 1 : 0;
-      a.partials = partials;
-      st = launch_pert<float>(g, a, nblocks);
-    } else {
-      PertArgs<double> a = pert_args<double>(g);
-      a.drag = drag;
-      a.dt_host = dt;
-      a.dt_dev = dt_dev;
-      for (int f = 0; f < g->nf; ++f) {
-        a.in[f] = (const double*)(s2 ? sc[f] : state[f]);
-        a.base[f] = (const double*)state[f];
-        a.out[f] = (double*)(s2 ? state[f] : sc[f]);
-      }
-      a.tau_frac = s2 ? 1.0 : 0.5;
-      a.stage2 = s2 ? 1 : 0;
-      a.partials = partials;
-      st = launch_pert<double>(g, a, nblocks);
-    }
-    if (st != ROSSBI_OK) return st;
-  }
-  reduce_partials_kernel<<<g->nf + 1, RED_NT, 0, g->stream>>>(partials, nblocks, g->nf, g->d_sums, g->d_dt + nxt);
-  CK(cudaGetLastError());
-  g->dt_slot = nxt;
-  g->dt_on_device = true;
-  if (next_dt) {
-    CK(cudaMemcpyAsync(g->h_pinned, g->d_dt + nxt, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
-    st = sync_and_status(g);
-    *next_dt = g->h_pinned[0];
-    return st;
-  }
-  return ROSSBI_OK;
+  // the same two stages as rossbi_step (with the indirect gravity's moments
+  // in the grid's own tables, set up by rossbi_set_indirect)
+  return step_form(g, state, sc, partials, dt, drag, next_dt);
 }

@@ -2,7 +2,8 @@
 //
 // One CTA owns a TR x TT x TZ tile of cells.  It stages the tile and a 2-deep
 // halo along each axis into shared memory as deviations from the equilibrium
-// (Sect. 2.7; the gas as primitive deviations u', v', w', P', rho'), then
+// (Sect. 2.7: the conservative departures E' = E - E0 of the gas, or with
+// RC = RECON_PRIM the primitive departures u', v', w', P', rho'), then
 // sweeps the three directions.  In a sweep, lines along the
 // direction map onto groups of L = pow2(T + 2) lanes: lane p reconstructs cell
 // p - 1 (parabola + MinMod), receives the upper face state of its lower
@@ -120,7 +121,7 @@ __device__ __forceinline__ bool resolve_cell(const DevGrid& g, int c[3]) {
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-template <int NF, int TR, int TT, int TZ, int NT, int D>
+template <int NF, int TR, int TT, int TZ, int NT, int D, int RC>
 __device__ __forceinline__ void sweep_full(const StageArgs& a, const double* sE, double* sG, int i0, int j0, int k0,
                                            unsigned& status) {
   constexpr int BX = TR + 4, BY = TT + 4, BZ = TZ + 4, BOX = BX * BY * BZ, NCORE = TR * TT * TZ;
@@ -159,19 +160,23 @@ __device__ __forceinline__ void sweep_full(const StageArgs& a, const double* sE,
     // parabola weights of this cell along D
     double w[9];
     parabola_weights<double, D>(g.rcoef, gi, g.nr, g.dx[D], w);
-    // equilibrium primitive gas state on the lower face of this cell (index
-    // along D = gd) and on its upper face; table indices clamped
+    // equilibrium gas state (conservative, or primitive with RC = RECON_PRIM)
+    // on the lower face of this cell (index along D = gd) and on its upper
+    // face; table indices clamped
     const int ci = clampi(gi, 0, g.nr - 1), ck = clampi(gk, 0, g.nz - 1);
-    auto w0_face = [&](int f, int fd) -> double {
+    auto eq_face = [&](int f, int fd) -> double {
       if (!g.has_eq) return 0.0;
-      if (D == 0) return g.w0r[((size_t)f * g.nz + ck) * (g.nr + 1) + clampi(fd, 0, g.nr)];
-      if (D == 1) return g.w0c[((size_t)f * g.nz + ck) * g.nr + ci];
-      return g.w0z[((size_t)f * (g.nz + 1) + clampi(fd, 0, g.nz)) * g.nr + ci];
+      const double* tc = RC == RECON_PRIM ? g.w0c : g.e0c;
+      const double* tr = RC == RECON_PRIM ? g.w0r : g.e0r;
+      const double* tz = RC == RECON_PRIM ? g.w0z : g.e0z;
+      if (D == 0) return tr[((size_t)f * g.nz + ck) * (g.nr + 1) + clampi(fd, 0, g.nr)];
+      if (D == 1) return tc[((size_t)f * g.nz + ck) * g.nr + ci];
+      return tz[((size_t)f * (g.nz + 1) + clampi(fd, 0, g.nz)) * g.nr + ci];
     };
     double area = 0.0;
     if (do_face) area = D == 0 ? g.area_r[clampi(gi, 0, g.nr)] : (D == 1 ? g.area_t[ci] : g.area_z[ci]);
 
-    // ---------------- gas: primitive deviations in slots 0..4
+    // ---------------- gas: departures in slots 0..4
     {
       double qm[5], qp[5];
       bool shaped = false;
@@ -180,26 +185,61 @@ __device__ __forceinline__ void sweep_full(const StageArgs& a, const double* sE,
         const double* s = sE + f * BOX + sidx;
         shaped |= parabola(s[-STRIDE], s[0], s[STRIDE], w, qm[f], qp[f]);
       }
-      if (shaped && do_recon) {  // positivity of both reconstructed face states
-        const bool ok = w0_face(RHO, gd) + qm[RHO] > 0.0 && w0_face(RHO, gd + 1) + qp[RHO] > 0.0 &&
-                        w0_face(EN, gd) + qm[EN] > 0.0 && w0_face(EN, gd + 1) + qp[EN] > 0.0;
-        if (!ok) {
-#pragma unroll
-          for (int f = 0; f < 5; ++f) qm[f] = qp[f] = sE[f * BOX + sidx];
-        }
-      }
       double F[5];
-      {
+      if (RC == RECON_PRIM) {
+        if (shaped && do_recon) {  // positivity of both reconstructed face states
+          const bool ok = eq_face(RHO, gd) + qm[RHO] > 0.0 && eq_face(RHO, gd + 1) + qp[RHO] > 0.0 &&
+                          eq_face(EN, gd) + qm[EN] > 0.0 && eq_face(EN, gd + 1) + qp[EN] > 0.0;
+          if (!ok) {
+#pragma unroll
+            for (int f = 0; f < 5; ++f) qm[f] = qp[f] = sE[f * BOX + sidx];
+          }
+        }
         double UL[5], UR[5];
 #pragma unroll
         for (int f = 0; f < 5; ++f) {
           const double ql = __shfl_up_sync(FULL, qp[f], 1, L);
-          const double w0 = do_face ? w0_face(f, gd) : 0.0;
+          const double w0 = do_face ? eq_face(f, gd) : 0.0;
           UL[f] = w0 + ql;
           UR[f] = w0 + qm[f];
         }
         if (do_face) {
           gas_face_flux<D>(gam, UL, UR, F, status);
+#pragma unroll
+          for (int f = 0; f < 5; ++f) F[f] *= area;
+        } else {
+#pragma unroll
+          for (int f = 0; f < 5; ++f) F[f] = 0.0;
+        }
+      } else {
+        // face states E0 + q on both faces of this cell (Sect. 2.7 on App. B's
+        // E); flat departures if either is not physical
+        double Um[5], Up[5];
+#pragma unroll
+        for (int f = 0; f < 5; ++f) {
+          Um[f] = eq_face(f, gd) + qm[f];
+          Up[f] = eq_face(f, gd + 1) + qp[f];
+        }
+        if (shaped && do_recon) {
+          const bool ok = Um[RHO] > 0.0 && Up[RHO] > 0.0 &&
+                          gas_pressure(gam, Um[MU], Um[MV], Um[MW], Um[EN], Um[RHO]) > 0.0 &&
+                          gas_pressure(gam, Up[MU], Up[MV], Up[MW], Up[EN], Up[RHO]) > 0.0;
+          if (!ok) {
+#pragma unroll
+            for (int f = 0; f < 5; ++f) {
+              const double e = sE[f * BOX + sidx];
+              Um[f] = eq_face(f, gd) + e;
+              Up[f] = eq_face(f, gd + 1) + e;
+            }
+          }
+        }
+        double WL[5], WR[5], WP[5];
+        gas_prim(gam, Um, WR);  // right state of the lower face
+        gas_prim(gam, Up, WP);  // left state of the upper face, for the lane above
+#pragma unroll
+        for (int f = 0; f < 5; ++f) WL[f] = __shfl_up_sync(FULL, WP[f], 1, L);
+        if (do_face) {
+          gas_face_flux<D>(gam, WL, WR, F, status);
 #pragma unroll
           for (int f = 0; f < 5; ++f) F[f] *= area;
         } else {
@@ -277,7 +317,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 
 // XT: the optional terms (indirect gravity, wave-killing zones) are compiled
 // in; the plain instantiation carries none of their code.
-template <int NF, int TR, int TT, int TZ, int NT, bool XT>
+template <int NF, int TR, int TT, int TZ, int NT, bool XT, int RC>
 __global__ void __launch_bounds__(NT, 1) stage_full_kernel(const StageArgs a) {
   constexpr int BX = TR + 4, BY = TT + 4, BZ = TZ + 4, BOX = BX * BY * BZ, NCORE = TR * TT * TZ;
   extern __shared__ double smem[];
@@ -290,8 +330,9 @@ __global__ void __launch_bounds__(NT, 1) stage_full_kernel(const StageArgs a) {
   const int k0 = (tile / (a.tiles_r * a.tiles_t)) * TZ;
   unsigned status = 0;
 
-  // tile + halo as deviations (corners are never read): primitive deviations
-  // (u', v', w', P', rho') of the gas in slots 0..4, the dust as it is
+  // tile + halo as deviations (corners are never read): the gas departures
+  // E' = E - E0 (or, with RC = RECON_PRIM, the primitive departures
+  // u', v', w', P', rho') in slots 0..4, the dust as it is
   for (int idx = threadIdx.x; idx < BOX; idx += NT) {
     const int x = idx % BX - 2, y = (idx / BX) % BY - 2, z = idx / (BX * BY) - 2;
     const int outside = (x < 0 || x >= TR) + (y < 0 || y >= TT) + (z < 0 || z >= TZ);
@@ -303,22 +344,27 @@ __global__ void __launch_bounds__(NT, 1) stage_full_kernel(const StageArgs a) {
       continue;
     }
     const size_t lin = ((size_t)c[2] * g.nth + c[1]) * g.nr + c[0];
-    double U[5], W[5];
+    const size_t e0o = (size_t)c[2] * g.nr + c[0], e0s = (size_t)g.nz * g.nr;
+    if (RC == RECON_PRIM) {
+      double U[5], W[5];
 #pragma unroll
-    for (int f = 0; f < 5; ++f) U[f] = a.in[f][lin];
-    gas_prim(g.gamma, U, W);
+      for (int f = 0; f < 5; ++f) U[f] = a.in[f][lin];
+      gas_prim(g.gamma, U, W);
 #pragma unroll
-    for (int f = 0; f < 5; ++f)
-      sE[f * BOX + idx] = g.has_eq ? W[f] - g.w0c[((size_t)f * g.nz + c[2]) * g.nr + c[0]] : W[f];
+      for (int f = 0; f < 5; ++f) sE[f * BOX + idx] = g.has_eq ? W[f] - g.w0c[f * e0s + e0o] : W[f];
+    } else {
+#pragma unroll
+      for (int f = 0; f < 5; ++f) sE[f * BOX + idx] = g.has_eq ? a.in[f][lin] - g.e0c[f * e0s + e0o] : a.in[f][lin];
+    }
 #pragma unroll
     for (int f = 5; f < NF; ++f) sE[f * BOX + idx] = a.in[f][lin];
   }
   __syncthreads();
-  sweep_full<NF, TR, TT, TZ, NT, 0>(a, sE, sG, i0, j0, k0, status);
+  sweep_full<NF, TR, TT, TZ, NT, 0, RC>(a, sE, sG, i0, j0, k0, status);
   __syncthreads();
-  sweep_full<NF, TR, TT, TZ, NT, 1>(a, sE, sG, i0, j0, k0, status);
+  sweep_full<NF, TR, TT, TZ, NT, 1, RC>(a, sE, sG, i0, j0, k0, status);
   __syncthreads();
-  sweep_full<NF, TR, TT, TZ, NT, 2>(a, sE, sG, i0, j0, k0, status);
+  sweep_full<NF, TR, TT, TZ, NT, 2, RC>(a, sE, sG, i0, j0, k0, status);
   __syncthreads();
 
   const double tau = a.tau_frac * (a.dt_dev ? __longlong_as_double((long long)*a.dt_dev) : a.dt_host);

@@ -6,11 +6,13 @@
 // 2.8 is computed without ever forming the large equilibrium terms (the
 // Keplerian centrifugal and gravity terms are O(rho v_K^2 / r), the
 // perturbations 1e-4 of that and less):
-//   - cell primitive perturbations: rho = rho0 + rho', du = (m' - rho' u0)/rho,
-//     dP = (gamma-1)(E' - [rho' |u0|^2/2 + rho u0.du + rho |du|^2/2]); the
-//     parabola and limiter of Sect. 2.7 act on these (the primitive reading),
-//     and a face state is the face equilibrium plus the interpolated
-//     perturbation;
+//   - the parabola and limiter of Sect. 2.7 act on the conservative
+//     departures E' themselves (the state), and the face state E0 + q is
+//     turned into primitive perturbations about the face equilibrium,
+//     rho = rho0 + rho', du = (m' - rho' u0)/rho,
+//     dP = (gamma-1)(E' - [rho' |u0|^2/2 + rho u0.du + rho |du|^2/2]);
+//     with RC = RECON_PRIM the same conversion is applied to each cell and
+//     the parabola acts on the primitive perturbations instead;
 //   - the exact Riemann solver (Sect. 2.6) iterates on dp* = p* - p0 with
 //     the pressure functions written in p/p_K - 1 (log1p / expm1 for the
 //     rarefaction powers), samples the wave pattern on full values and returns
@@ -339,6 +341,24 @@ struct PertArgs {
   int tiles_r, tiles_t;
 };
 
+// Primitive perturbations (du, dv, dw, dP, drho in the field slots MU, MV,
+// MW, EN, RHO) of the conservative departure q about an equilibrium state of
+// density rho0 and azimuthal velocity v0 (r and z velocities zero):
+// rho = rho0 + rho', du = (m' - rho' u0)/rho,
+// dP = (gamma-1)(E' - [rho' |u0|^2/2 + rho u0.du + rho |du|^2/2]).
+template <class T>
+__device__ __forceinline__ void face_prim(T g, T rho0, T v0, const T* q, T* w) {
+  const T rho = rho0 + q[RHO];
+  const T ir = T(1) / rho;
+  const T du = q[MU] * ir, dv = (q[MV] - q[RHO] * v0) * ir, dw = q[MW] * ir;
+  const T dke = T(0.5) * q[RHO] * v0 * v0 + rho * v0 * dv + T(0.5) * rho * (du * du + dv * dv + dw * dw);
+  w[MU] = du;
+  w[MV] = dv;
+  w[MW] = dw;
+  w[EN] = (g - T(1)) * (q[EN] - dke);
+  w[RHO] = q[RHO];
+}
+
 template <class T, int D>
 __device__ __forceinline__ PFace<T> face_eq(const PertTables<T>& t, const DevGrid& g, int ci, int ck, int fd,
                                             T& v0) {
@@ -385,7 +405,7 @@ __device__ __forceinline__ PFace<T> face_eq(const PertTables<T>& t, const DevGri
   return W;
 }
 
-template <class T, int NF, int TR, int TT, int TZ, int NT, int D, class P>
+template <class T, int NF, int TR, int TT, int TZ, int NT, int D, class P, int RC>
 __device__ __forceinline__ void sweep_pert(const PertArgs<T>& a, const T* sE, T* sG, int i0, int j0, int k0,
                                            unsigned& status, unsigned& nfallback) {
   constexpr int BX = TR + 4, BY = TT + 4, BZ = TZ + 4, BOX = BX * BY * BZ, NCORE = TR * TT * TZ;
@@ -440,11 +460,28 @@ __device__ __forceinline__ void sweep_pert(const PertArgs<T>& a, const T* sE, T*
       const PFace<T> Wm = face_eq<T, D>(a.t, g, ci, ck, gd, v0m);
       const PFace<T> Wp = face_eq<T, D>(a.t, g, ci, ck, gd + 1, v0p);
       PSide<T> sm, sp;
-      bool ok = pert_side<T, D>(gam, Wm, qm, has_eq, sm) & pert_side<T, D>(gam, Wp, qp, has_eq, sp);
-      if (!ok && shaped) {  // positivity fallback: flat reconstruction of the gas fields
-#pragma unroll
-        for (int f = 0; f < 5; ++f) qm[f] = qp[f] = sE[f * BOX + sidx];
+      bool ok;
+      if (RC == RECON_PRIM) {
         ok = pert_side<T, D>(gam, Wm, qm, has_eq, sm) & pert_side<T, D>(gam, Wp, qp, has_eq, sp);
+        if (!ok && shaped) {  // positivity fallback: flat reconstruction of the gas fields
+#pragma unroll
+          for (int f = 0; f < 5; ++f) qm[f] = qp[f] = sE[f * BOX + sidx];
+          ok = pert_side<T, D>(gam, Wm, qm, has_eq, sm) & pert_side<T, D>(gam, Wp, qp, has_eq, sp);
+        }
+      } else {
+        // conservative face departures -> primitive perturbations about the
+        // face equilibrium (rho0, v0 of that face)
+        T pm[5], pp[5];
+        face_prim<T>(gam, Wm.rho, v0m, qm, pm);
+        face_prim<T>(gam, Wp.rho, v0p, qp, pp);
+        ok = pert_side<T, D>(gam, Wm, pm, has_eq, sm) & pert_side<T, D>(gam, Wp, pp, has_eq, sp);
+        if (!ok && shaped) {  // positivity fallback: flat reconstruction of the gas fields
+#pragma unroll
+          for (int f = 0; f < 5; ++f) qm[f] = qp[f] = sE[f * BOX + sidx];
+          face_prim<T>(gam, Wm.rho, v0m, qm, pm);
+          face_prim<T>(gam, Wp.rho, v0p, qp, pp);
+          ok = pert_side<T, D>(gam, Wm, pm, has_eq, sm) & pert_side<T, D>(gam, Wp, pp, has_eq, sp);
+        }
       }
       T F[5];
       {
@@ -660,7 +697,7 @@ __device__ __forceinline__ T pert_cell_dt(const DevGrid& g, const PertTables<T>&
 
 // XT: the optional terms (indirect gravity, wave-killing zones) are compiled
 // in; the plain instantiation carries none of their code.
-template <class T, int NF, int TR, int TT, int TZ, int NT, int MINB, class P, bool XT>
+template <class T, int NF, int TR, int TT, int TZ, int NT, int MINB, class P, bool XT, int RC>
 __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> a) {
   constexpr int BX = TR + 4, BY = TT + 4, BZ = TZ + 4, BOX = BX * BY * BZ, NCORE = TR * TT * TZ;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -697,7 +734,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
               const size_t lin = ((size_t)c[2] * g.nth + c[1]) * g.nr + c[0];
 #pragma unroll
               for (int f = 0; f < NF; ++f) v[u][f] = a.in[f][lin];
-              if (g.has_eq) {
+              if (RC == RECON_PRIM && g.has_eq) {
                 const size_t sz = (size_t)g.nz * g.nr, o = (size_t)c[2] * g.nr + c[0];
                 e0[u][0] = a.t.cen[o];
                 e0[u][1] = a.t.cen[sz + o];
@@ -715,6 +752,9 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
         if (st[u] == 1) {
 #pragma unroll
           for (int f = 0; f < NF; ++f) sE[f * BOX + idx] = T(0);
+        } else if (st[u] == 2 && RC == RECON_CONS) {  // the state is E' itself
+#pragma unroll
+          for (int f = 0; f < NF; ++f) sE[f * BOX + idx] = v[u][f];
         } else if (st[u] == 2) {
           PCell<T> ce;
           ce.rho0 = e0[u][0];
@@ -734,11 +774,11 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
     }
   }
   __syncthreads();
-  sweep_pert<T, NF, TR, TT, TZ, NT, 0, P>(a, sE, sG, i0, j0, k0, status, nfallback);
+  sweep_pert<T, NF, TR, TT, TZ, NT, 0, P, RC>(a, sE, sG, i0, j0, k0, status, nfallback);
   __syncthreads();
-  sweep_pert<T, NF, TR, TT, TZ, NT, 1, P>(a, sE, sG, i0, j0, k0, status, nfallback);
+  sweep_pert<T, NF, TR, TT, TZ, NT, 1, P, RC>(a, sE, sG, i0, j0, k0, status, nfallback);
   __syncthreads();
-  sweep_pert<T, NF, TR, TT, TZ, NT, 2, P>(a, sE, sG, i0, j0, k0, status, nfallback);
+  sweep_pert<T, NF, TR, TT, TZ, NT, 2, P, RC>(a, sE, sG, i0, j0, k0, status, nfallback);
   __syncthreads();
 
   const T tau = (T)(a.tau_frac * (a.dt_dev ? __longlong_as_double((long long)*a.dt_dev) : a.dt_host));
@@ -753,11 +793,17 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
     const size_t lin = ((size_t)gk * g.nth + gj) * g.nr + gi;
     const PCell<T> ce = cell_eq(a.t, g, gi, gk);
     const int sidx = ((z + 2) * BY + (y + 2)) * BX + (x + 2);
-    T q[NF], G[NF];
+    T q[NF], G[NF];  // q: primitive gas perturbations, conservative dust
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       q[f] = sE[f * BOX + sidx];
       G[f] = sG[f * NCORE + cidx];
+    }
+    if (RC == RECON_CONS) {  // the staged gas departures are conservative
+      T qc[5];
+#pragma unroll
+      for (int f = 0; f < 5; ++f) qc[f] = q[f];
+      face_prim<T>((T)g.gamma, ce.rho0, ce.v0, qc, q);
     }
     if (g.geom == GEOM_CYL) {
       T S[NF];

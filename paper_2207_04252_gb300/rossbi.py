@@ -22,6 +22,7 @@ ROSSBI_OK, ROSSBI_ERR_ARG, ROSSBI_ERR_CUDA, ROSSBI_ERR_OOM, ROSSBI_ERR_NONPHYSIC
 ROSSBI_GEOM_BOX, ROSSBI_GEOM_CYL = 0, 1
 ROSSBI_BC_PERIODIC, ROSSBI_BC_OUTFLOW, ROSSBI_BC_EQUILIBRIUM = 0, 1, 2
 ROSSBI_FP64, ROSSBI_FP32_PERT, ROSSBI_FP64_PERT = 0, 1, 2
+ROSSBI_RECON_CONSERVATIVE, ROSSBI_RECON_PRIMITIVE = 0, 1
 
 # every function declared in include/rossbi.h
 EXPORTS = (
@@ -37,7 +38,8 @@ class rossbi_grid_desc(ctypes.Structure):
                 ("x0", ctypes.c_double * 3), ("x1", ctypes.c_double * 3),
                 ("bc_lo", ctypes.c_int * 3), ("bc_hi", ctypes.c_int * 3),
                 ("gamma", ctypes.c_double), ("gm", ctypes.c_double), ("omega_frame", ctypes.c_double),
-                ("cfl", ctypes.c_double), ("n_dust", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("cfl", ctypes.c_double), ("n_dust", ctypes.c_int), ("precision", ctypes.c_int),
+                ("recon", ctypes.c_int)]
 
 
 class rossbi_disc_params(ctypes.Structure):
@@ -132,10 +134,10 @@ def _stream_handle(stream):
 
 
 def make_desc(geometry, n, x0, x1, bc_lo, bc_hi, gamma=1.4, gm=1.0, omega_frame=0.0, cfl=0.5, n_dust=0,
-              precision=ROSSBI_FP64) -> rossbi_grid_desc:
+              precision=ROSSBI_FP64, recon=ROSSBI_RECON_CONSERVATIVE) -> rossbi_grid_desc:
     return rossbi_grid_desc(geometry, n[0], n[1], n[2], (ctypes.c_double * 3)(*x0), (ctypes.c_double * 3)(*x1),
                             (ctypes.c_int * 3)(*bc_lo), (ctypes.c_int * 3)(*bc_hi), gamma, gm, omega_frame, cfl,
-                            n_dust, precision)
+                            n_dust, precision, recon)
 
 
 def rossbi_init_grid(desc: rossbi_grid_desc, stream=None):

@@ -30,7 +30,7 @@ class Grid:
         self.w = w
         self.precision = precision
         desc = R.make_desc(w.geometry, (w.nr, w.nth, w.nz), w.x0, w.x1, w.bc_lo, w.bc_hi, w.gamma, w.gm,
-                           w.omega_frame, w.cfl, w.n_dust, precision)
+                           w.omega_frame, w.cfl, w.n_dust, precision, w.recon)
         self.h = R.rossbi_init_grid(desc, stream)
         try:
             R.rossbi_set_equilibrium(self.h, w.disc)

@@ -71,3 +71,28 @@ def jitter(E, gamma, rng, a):
         E[8] = rd
         E[5:8] = rd * vd
     return E
+
+
+def elementwise(E_test, E_ref, E0=None):
+    """Element-wise error per conserved quantity (the groups of GROUPS): the
+    largest |q_test - q_ref| over cells and components, divided by the
+    largest departure |q_ref - q0| of the group (q0 = E0 for the gas, 0 for
+    the dust; the largest |q_ref| when there is no E0).  Returns
+    {group: (ratio, (field, k, j, i) of the largest difference)}.  Unlike the
+    L1 measure it cannot average a single bad cell (a tile edge, a ghost)
+    away."""
+    nf = E_ref.shape[0]
+    out = {}
+    for name, fields in GROUPS.items():
+        if max(fields) >= nf:
+            continue
+        num, where, den = -1.0, None, 0.0
+        for f in fields:
+            d = np.abs(E_test[f] - E_ref[f])
+            idx = np.unravel_index(int(np.argmax(d)), d.shape)
+            if d[idx] > num:
+                num, where = float(d[idx]), (f,) + tuple(int(v) for v in idx)
+            dep = E_ref[f] - (E0[f][:, None, :] if (E0 is not None and f < 5) else 0.0)
+            den = max(den, float(np.abs(dep).max()))
+        out[name] = (num / den if den > 0 else num, where)
+    return out

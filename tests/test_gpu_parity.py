@@ -1,17 +1,29 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
 Both sides build their own initial state from the shared seeded inputs and are
-compared by the relative L1 error per conserved field (tests/parity.py); the
-GPU follows the oracle's dt sequence, and its own CFL sequence is checked
-against the oracle's separately.  Bar for the FP64 form: <= 1e-12.
+compared by the relative L1 error per conserved field (tests/parity.py) and,
+beside it, element-wise (the largest difference over the largest departure
+from equilibrium of that quantity, with its location); the GPU follows the
+oracle's dt sequence, and its own CFL sequence is checked against the
+oracle's separately.  Bar for the FP64 form: <= 1e-12 (L1).
+
+The scheme is the paper's by default: the parabola of Sect. 2.7 on the
+conservative departures of App. B's variables.  The primitive-departure
+option is checked beside it.
 
 Horizons.  Two correct FP64 implementations differ by rounding order, so a
 multi-step comparison is only as good as the trajectory's own conditioning.
 Measured on the oracle against itself with a 1e-15 relative input
-perturbation: the 1-D Sod tube stays <= 1e-15 over all 224 steps; the noisy
-disc (24x32x32) stays <= 6e-14 for 100 steps; the bi-fluid vortex (24x32x32)
-<= 2.1e-13 for 100 steps, and the adjoint workload's vortex (32x48x32)
-<= 2.9e-13 for 200 steps.  The tests run the disc and the vortex 100 steps.
+perturbation (largest relative L1 over the conserved quantities):
+  - the 1-D Sod tube: <= 1e-15 over all 224 steps;
+  - the noisy disc, conservative (24x32x32): 1.3e-13 after 100 steps;
+    (15x7x33): 4.3e-14 after 20;
+  - the bi-fluid vortex, conservative: (20x36x32) 1.1e-13 after 15 steps,
+    2.8e-12 after 20, 5e-9 after 40; (29x13x32) 6.3e-13 after 20 -- the
+    conservative face pressure is a difference of terms O(Mach^2) larger
+    than itself, and a rounding-level difference grows ~1.2x per step; the
+    vortex is compared over those 15 and 20 steps;
+  - the bi-fluid vortex, primitive option (20x36x32): 2.1e-13 after 100.
 Small grids span several 14x6x6 kernel tiles and ragged tails; the full-size
 workloads are checked on sampled cells after one step.
 """
@@ -20,7 +32,7 @@ import pytest
 
 import oracle
 import synthetic as syn
-from tests.parity import rel_l1, rel_l1_components
+from tests.parity import elementwise, rel_l1, rel_l1_components
 
 pytestmark = pytest.mark.gpu
 
@@ -58,12 +70,21 @@ def _run_gpu(grid, state, steps=None, t_end=None):
     return state, t, dts
 
 
-def _compare(grid, o, state_gpu, E_ref, tol=TOL64):
+EL64 = 1e-9  # element-wise bar of the FP64 form, relative to the largest departure
+
+
+def _compare(grid, o, state_gpu, E_ref, tol=TOL64, el_tol=EL64):
     E = grid.full_state(state_gpu)
     V = o.volumes()
     errs = rel_l1(E, E_ref, V)
     for name, e in errs.items():
         assert e <= tol, (name, e, errs, rel_l1_components(E, E_ref, V))
+    E0 = grid.equilibrium() if grid.w.disc is not None else None
+    el = elementwise(E, E_ref, E0)
+    print("L1", {k: f"{v:.1e}" for k, v in errs.items()}, "element-wise",
+          {k: (f"{r:.1e}", at) for k, (r, at) in el.items()})
+    for name, (r, at) in el.items():
+        assert r <= el_tol, (name, r, at, el)
     return errs
 
 
@@ -127,9 +148,16 @@ def test_disc_noise(lib, n, steps):
     _parity_run(lib, syn.scaled(syn.DISC_NOISE, *n, steps=steps), steps)
 
 
-@pytest.mark.parametrize("n,steps", [((20, 36, 32), 100), ((29, 13, 32), 40)])
+@pytest.mark.parametrize("n,steps", [((20, 36, 32), 15), ((29, 13, 32), 20)])
 def test_vortex_bifluid(lib, n, steps):
     _parity_run(lib, syn.scaled(syn.VORTEX, *n, steps=steps), steps)
+
+
+@pytest.mark.parametrize("wl,n,steps", [(syn.VORTEX, (20, 36, 32), 100), (syn.DISC_NOISE, (24, 32, 32), 100)])
+def test_primitive_option(lib, wl, n, steps):
+    """The primitive-departure option (not the paper's scheme) over the long
+    horizon its conditioning allows."""
+    _parity_run(lib, syn.scaled(wl, *n, steps=steps, recon=syn.RECON_PRIMITIVE), steps)
 
 
 def test_equilibrium_bit_exact(lib):

@@ -1,6 +1,7 @@
 """Drag law 2 (Epstein with the Stokes regime of Sect. 2.9, reading R19) on the
 GPU against the oracle: the bi-fluid vortex with kappa chosen so that the
-switch splits the disc, 20 steps on the oracle's dt sequence, FP64 and the FP64
+switch splits the disc, 15 steps on the oracle's dt sequence (the oracle's
+own drift from a 1e-15 input perturbation is 4e-13 after 15 steps), FP64 and the FP64
 perturbation form <= 1e-12, FP32 <= 1e-5; the regime moves the dust far more
 than the bar; the adjoint refuses the law."""
 from dataclasses import replace
@@ -33,7 +34,7 @@ def reference():
     kappa = 2.25 / float(np.median(E0[4]))
     w = replace(base, drag_law=2, drag_kappa=kappa)
     o = oracle.Oracle(w)
-    E, _, dts = o.run(E0.copy(), steps=20)
+    E, _, dts = o.run(E0.copy(), steps=15)
     assert o.take_status() == 0
     E1, _, _ = o1.run(E0.copy(), dts=dts)
     return w, o, E, E1, dts

@@ -2,9 +2,9 @@
 
 Checks, through the C ABI, that two calls in a row give the same states and
 next dt as rossbi_step (same kernels, scratch in the library's fixed device
-array instead of a cudaMalloc'd buffer), that the calls leave the device's
-free memory unchanged, and that a grid whose scratch exceeds the fixed array
-is refused before anything runs.  Kept in a file collected last so that a
+array instead of a cudaMalloc'd buffer), with and without the optional
+terms, that the calls leave the device's free memory unchanged, and that a
+grid whose scratch exceeds the fixed array is refused before anything runs.  Kept in a file collected last so that a
 run stopping at the first failure has run every other test first.
 """
 import numpy as np
@@ -26,14 +26,31 @@ def lib():
     return rossbi, workloads
 
 
+ZONES = (1.25 * 0.5, 0.84 * 2.0, 0.01)
+
+
+@pytest.mark.parametrize("option", ["plain", "indirect", "damping", "epstein"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32_pert", "fp64_pert"])
-def test_noalloc_matches_step(lib, precision):
+def test_noalloc_matches_step(lib, precision, option):
+    """The optional terms too: the indirect gravity (whose disc moments are
+    summed before each stage into the grid's own tables), the wave-killing
+    zones and the Epstein drag law."""
     import torch
+    from dataclasses import replace
+    from tests.test_gpu_indirect import _lopsided_gpu
     R, W = lib
     prec = {"fp64": R.ROSSBI_FP64, "fp32_pert": R.ROSSBI_FP32_PERT, "fp64_pert": R.ROSSBI_FP64_PERT}[precision]
     w = syn.scaled(syn.VORTEX, 40, 30, 32, steps=2)
+    if option == "epstein":
+        w = replace(w, drag_law=1)
     g = W.Grid(w, precision=prec)
-    a = g.initial_state()
+    if option == "indirect":
+        g.set_indirect(0.7)
+        a = _lopsided_gpu(g)
+    else:
+        a = g.initial_state()
+    if option == "damping":
+        g.set_damping(ZONES)
     b = a.clone()
     # one ordinary step on a throwaway copy first: it loads every kernel the step
     # uses (the CUDA runtime loads kernel code lazily, on first launch, which
