@@ -93,7 +93,13 @@ typedef struct rossbi_grid rossbi_grid; /* opaque, library-owned */
  *              the Keplerian frequency).
  *   omega_frame : angular speed of the rotating frame (cylindrical only).
  *   cfl      : N_CFL of the CFL condition (Sect. 2.5; the paper uses 1/2).
- *   n_dust   : 0 (gas only, 5 fields) or 1 (gas + one dust fluid, 9 fields).
+ *   n_dust   : number of pressureless dust fluids (species), 0 .. 4; the
+ *              state has 5 + 4 n_dust fields, species s in fields 5 + 4 s ..
+ *              8 + 4 s (rho_d u_d, rho_d v_d, rho_d w_d, rho_d).  Several
+ *              species (the multi-fluid approach Sect. 5.4 names) each couple
+ *              to the gas by their own drag, St x their factor
+ *              (rossbi_set_dust_species); rossbi_adjoint_step takes at most
+ *              one (ROSSBI_ERR_UNSUPPORTED).
  *   precision: one of the precision forms above.
  *   recon    : one of the reconstruction modes above. */
 typedef struct {
@@ -119,8 +125,7 @@ typedef struct {
  * drag_law 2: law 1 plus the Stokes regime, t_s = (4/9)(r_p / lambda) t_E
  * where r_p > 9 lambda / 4, with the mean free path lambda = lambda_0 / rho_g
  * and kappa = r_p / lambda_0 (>= 0; ignored by laws 0 and 1).  Law 2 is not
- * available to rossbi_adjoint_step (ROSSBI_ERR_UNSUPPORTED) nor to
- * rossbi_step_noalloc (ROSSBI_ERR_ARG). */
+ * available to rossbi_step_noalloc (ROSSBI_ERR_ARG). */
 typedef struct {
   double stokes;
   int drag_law;
@@ -186,6 +191,39 @@ rossbi_status rossbi_set_indirect(rossbi_grid* g, double x_ref);
  * table on first use; synchronises the stream.
  * Errors: ROSSBI_ERR_ARG, ROSSBI_ERR_OOM, ROSSBI_ERR_CUDA. */
 rossbi_status rossbi_set_damping(rossbi_grid* g, const rossbi_damping_params* p);
+
+/* Halo exchange of a decomposition in theta.  Sect. 3.1 splits the grid
+ * into blocks that exchange ghost cells with their neighbours; a sub-domain
+ * here is a grid of its own whose theta extent is its owned rows plus four
+ * halo rows on each side (two per RK stage: the step's E* must be right two
+ * rows beyond the owned ones), with the same dtheta as the whole grid, and
+ * every step is followed by an exchange of those halo rows.  These two calls
+ * move the rows: pack copies rows j0 .. j0 + rows - 1 of every field of the
+ * state into buf, unpack copies buf into those rows.
+ *   state : nfields device pointers of the grid's precision form.
+ *   buf   : device buffer of nfields * nz * rows * nr elements of the state's
+ *           type, laid out [field][k][row][i] (contiguous; on several GPUs it
+ *           is what a neighbour sends or receives).
+ *   0 <= j0, j0 + rows <= nth, rows >= 1.
+ * One kernel launch on the grid's stream; asynchronous.
+ * Errors: ROSSBI_ERR_ARG, ROSSBI_ERR_CUDA. */
+rossbi_status rossbi_pack_theta_rows(rossbi_grid* g, const void* const* state, int j0, int rows, void* buf);
+rossbi_status rossbi_unpack_theta_rows(rossbi_grid* g, void* const* state, int j0, int rows, const void* buf);
+
+/* Stokes numbers of several dust species (Sect. 5.4's multi-fluid approach;
+ * the drag law of Sect. 2.9 applies to each species).  Species s has the
+ * Stokes number St x stokes_factor[s], St that of rossbi_dust_params; under
+ * the Epstein laws its rho_s r_p scales the same way.
+ *   stokes_factor : host array of n = n_dust doubles; stokes_factor[0] must be
+ *                   1 (species 0 has St itself), the others > 0 and finite.
+ * The drag of n_dust > 1 species is the closed-form solution of the
+ * backward-Euler system that couples the gas to every species (no
+ * dust-dust exchange): v_g' = (rho_g v_g + sum rho_k w_k v_k) /
+ * (rho_g + sum rho_k w_k), v_k' = (v_k + a_k v_g') / (1 + a_k), a_k = tau /
+ * t_k, w_k = a_k / (1 + a_k); the gas energy gains the drag's work.
+ * Default: every factor 1.  Takes effect from the next step.
+ * Errors: ROSSBI_ERR_ARG (NULL, n != n_dust, n_dust = 0, a bad factor). */
+rossbi_status rossbi_set_dust_species(rossbi_grid* g, const double* stokes_factor, int n);
 
 /* The disc moments (A_disc, B_disc) of Sect. 2.10 of a state, without the
  * constant X_ref: the sums over cells of V (rho - rho_0 + rho_d) r cos(theta)
@@ -287,7 +325,8 @@ rossbi_status rossbi_step_noalloc(rossbi_grid* g, void* const* state, double dt,
  *             running total (rossbi_adjoint_dstokes), so callers can leave
  *             dparam NULL and keep the call asynchronous.
  * The library allocates five FP64 states of scratch on the first call.
- * Errors: ROSSBI_ERR_ARG, ROSSBI_ERR_UNSUPPORTED (perturbation forms),
+ * Errors: ROSSBI_ERR_ARG, ROSSBI_ERR_UNSUPPORTED (perturbation forms, more
+ * than one dust species),
  * ROSSBI_ERR_OOM, ROSSBI_ERR_CUDA, and after a synchronising call
  * ROSSBI_ERR_NONPHYSICAL / ROSSBI_ERR_RIEMANN. */
 rossbi_status rossbi_adjoint_step(rossbi_grid* g, const void* const* state_n, double dt,
@@ -319,7 +358,7 @@ rossbi_status rossbi_take_status(rossbi_grid* g);
 rossbi_status rossbi_profile_enable(rossbi_grid* g, int enable);
 rossbi_status rossbi_profile_read(rossbi_grid* g, double* stage_ms, int* stage_launches);
 
-/* Number of conservative fields (5 or 9) and the precision form. */
+/* Number of conservative fields (5 + 4 n_dust) and the precision form. */
 int rossbi_nfields(const rossbi_grid* g);
 int rossbi_precision(const rossbi_grid* g);
 

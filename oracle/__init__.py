@@ -138,6 +138,8 @@ class Oracle:
             raise ValueError(f"unknown reconstruction mode {w.recon}")
         if w.drag_kappa:
             lib().orc_set_stokes_regime(self.h, float(w.drag_kappa))
+        if w.dust_stokes_factors:
+            self.set_species_stokes(w.dust_stokes_factors)
         if w.disc is not None:
             disc = np.array(w.disc, dtype=np.float64)
             self.status |= lib().orc_set_equilibrium(self.h, _p(disc))

@@ -434,6 +434,7 @@ __device__ __forceinline__ double drag_vjp(const DevGrid& g, int i, const double
   const double rg = U[RHO], rd = U[DRHO];
   if (!(rd > 0.0) || !(rg > 0.0)) return 0.0;
   double ts, cs = 0.0;
+  bool stokes_regime = false;  // drag law 2 above r_p = 9 lambda / 4 (the forward's branch)
   if (d.law == 0) {
     if (g.geom == GEOM_CYL) {
       const double r = g.rc[i + GH];
@@ -444,6 +445,8 @@ __device__ __forceinline__ double drag_vjp(const DevGrid& g, int i, const double
   } else {
     cs = sqrt(g.gamma * gas_pressure(g.gamma, U[MU], U[MV], U[MW], U[EN], rg) / rg);
     ts = d.rhos_rp / (rg * cs);
+    stokes_regime = d.law == 2 && d.kappa * rg > 2.25;
+    if (stokes_regime) ts = ts * ((4.0 / 9.0) * (d.kappa * rg));
   }
   const double kk = tau * (1.0 + rd / rg) / ts;
   const double mu = rg * rd / (rg + rd);
@@ -478,8 +481,10 @@ __device__ __forceinline__ double drag_vjp(const DevGrid& g, int i, const double
   rdb += kkb * tau / (rg * ts);
   rgb -= kkb * tau * rd / (rg * rg * ts);
   const double tsb = -kkb * kk / ts;
-  if (d.law == 1) {  // t_s = rhos_rp / (rho_g c_s), c_s = sqrt(gamma P / rho_g)
-    rgb -= tsb * ts / rg;
+  if (d.law == 1 || d.law == 2) {
+    // t_s = rhos_rp / (rho_g c_s), c_s = sqrt(gamma P / rho_g); in the Stokes
+    // regime t_s = (4/9) kappa rhos_rp / c_s, with no explicit rho_g
+    if (!stokes_regime) rgb -= tsb * ts / rg;
     const double csb = -tsb * ts / cs;
     const double Pb = csb * g.gamma / (2.0 * cs * rg);
     rgb -= csb * cs / (2.0 * rg);
@@ -496,7 +501,7 @@ __device__ __forceinline__ double drag_vjp(const DevGrid& g, int i, const double
   }
   li[RHO] += rgb;
   li[DRHO] += rdb;
-  return tsb * ts / d.stokes;  // t_s is proportional to St in both laws
+  return tsb * ts / d.stokes;  // t_s is proportional to St in every law
 }
 
 // out += s S'(U)^T for the App. B sources at a cell (cylindrical only).
@@ -942,7 +947,7 @@ static __global__ void __launch_bounds__(ADJ_PT_NT) drag_only_kernel(DevGrid g, 
     double U[9];
 #pragma unroll
     for (int f = 0; f < 9; ++f) U[f] = Y.p[f][lin];
-    apply_drag(g, (int)(lin % g.nr), U, tau, d);
+    apply_drag<true, 1>(g, (int)(lin % g.nr), U, tau, d);
 #pragma unroll
     for (int f = 0; f < 9; ++f) out.p[f][lin] = U[f];
   }

@@ -6,8 +6,12 @@
 
 namespace rossbi {
 
-// Conservative variables in App. B order, then the dust fluid.
+// Conservative variables in App. B order, then the dust fluid; dust species
+// s occupies fields 5 + 4 s .. 8 + 4 s in the same order (species 0 is DMU ..
+// DRHO).
 enum { MU = 0, MV = 1, MW = 2, EN = 3, RHO = 4, DMU = 5, DMV = 6, DMW = 7, DRHO = 8 };
+constexpr int ND_MAX = 4;                 // dust species
+constexpr int NF_MAX = 5 + 4 * ND_MAX;    // conservative fields
 enum { GEOM_BOX = 0, GEOM_CYL = 1 };
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_EQUILIBRIUM = 2 };
 enum { STATUS_NONPHYSICAL = 1u, STATUS_RIEMANN = 2u };
@@ -55,6 +59,8 @@ struct DevGrid {
   // rate R(r) / tau of radial cell i [nr] in double and in float, or null
   const double* damp_k;
   const float* damp_kf;
+  // dust species s has the Stokes number St x st_factor[s] (st_factor[0] = 1)
+  double st_factor[ND_MAX];
 };
 
 __host__ __device__ constexpr int pow2ceil(int v) {
@@ -391,18 +397,18 @@ __device__ __forceinline__ void cell_sources(const DevGrid& g, int i, int j, int
     S[EN] = rho * u * (fr + Om * Om * r) + rho * w * fz;
     S[RHO] = 0.0;
   }
-  if (g.nf > 5) {
-    const double rho = U[DRHO];
+  for (int b = 5; b < g.nf; b += 4) {  // each dust species
+    const double rho = U[b + 3];
     if (rho > 0.0) {
       const double ir = 1.0 / rho;
-      const double u = U[DMU] * ir, v = U[DMV] * ir;
-      S[DMU] = rho * v * v / r + rho * fr + 2.0 * Om * rho * v + rho * Om * Om * r;
-      S[DMV] = -rho * u * v / r - 2.0 * Om * rho * u;
-      S[DMW] = rho * fz;
+      const double u = U[b] * ir, v = U[b + 1] * ir;
+      S[b] = rho * v * v / r + rho * fr + 2.0 * Om * rho * v + rho * Om * Om * r;
+      S[b + 1] = -rho * u * v / r - 2.0 * Om * rho * u;
+      S[b + 2] = rho * fz;
     } else {
-      S[DMU] = S[DMV] = S[DMW] = 0.0;
+      S[b] = S[b + 1] = S[b + 2] = 0.0;
     }
-    S[DRHO] = 0.0;
+    S[b + 3] = 0.0;
   }
   if (XT && g.x_ind != 0.0) {
     const double gr = g.ind_g[j], gt = g.ind_g[g.nth + j];  // grad Phi_ind, (r, theta)
@@ -411,9 +417,11 @@ __device__ __forceinline__ void cell_sources(const DevGrid& g, int i, int j, int
     S[MU] -= rho * gr;
     S[MV] -= rho * gt;
     S[EN] -= rho * (U[MU] * ir * gr + U[MV] * ir * gt);
-    if (g.nf > 5 && U[DRHO] > 0.0) {
-      S[DMU] -= U[DRHO] * gr;
-      S[DMV] -= U[DRHO] * gt;
+    for (int b = 5; b < g.nf; b += 4) {
+      if (U[b + 3] > 0.0) {
+        S[b] -= U[b + 3] * gr;
+        S[b + 1] -= U[b + 3] * gt;
+      }
     }
   }
 }
@@ -426,41 +434,89 @@ struct DragArgs {
   double kappa;    // drag law 2: r_p / lambda_0, the mean free path being lambda_0 / rho_g
 };
 
-// Semi-implicit drag over a stage of length tau (Sect. 2.9 drag law): the
-// relative gas-dust velocity relaxes by 1 / (1 + tau (1 + eps) / t_s) at
-// fixed barycentric velocity; the gas energy gains the work done on the gas.
-// Drag law 2 (compiled in with XT) adds the Stokes regime of Sect. 2.9:
-// above r_p = 9 lambda / 4 the Epstein time grows by (4/9) r_p / lambda.
-template <bool XT = false>
-__device__ __forceinline__ void apply_drag(const DevGrid& g, int i, double* U, double tau, const DragArgs& d) {
-  const double rg = U[RHO], rd = U[DRHO];
-  if (!(rd > 0.0) || !(rg > 0.0)) return;
-  double ts;
+// Stopping time of dust species s (Stokes number St x st_factor[s]) in a cell
+// of radial index i with gas state U (Sect. 2.9): drag law 0 t_s = St /
+// Omega_K(r) (the Box: St); laws 1 and 2 Epstein t_s = rho_s r_p /
+// (rho_g c_s), rho_s r_p proportional to St; law 2 (compiled in with XT) adds
+// the Stokes regime of Sect. 2.9: above r_p = 9 lambda / 4 the Epstein time
+// grows by (4/9) r_p / lambda.
+template <bool XT>
+__device__ __forceinline__ double stopping_time(const DevGrid& g, int i, const double* U, const DragArgs& d, int s) {
+  const double rg = U[RHO];
   if (d.law == 0) {
+    const double st = d.stokes * g.st_factor[s];
     if (g.geom == GEOM_CYL) {
       const double r = g.rc[i + GH];
-      ts = d.stokes / sqrt(g.gm / (r * r * r));
-    } else {
-      ts = d.stokes;
+      return st / sqrt(g.gm / (r * r * r));
     }
-  } else {
-    const double cs = sqrt(g.gamma * gas_pressure(g.gamma, U[MU], U[MV], U[MW], U[EN], rg) / rg);
-    ts = d.rhos_rp / (rg * cs);
-    if (XT && d.law == 2 && d.kappa * rg > 2.25) ts = ts * ((4.0 / 9.0) * (d.kappa * rg));
+    return st;
   }
-  const double kk = tau * (1.0 + rd / rg) / ts;
-  const double mu = rg * rd / (rg + rd);
-  const double relax = kk / (1.0 + kk);
+  const double cs = sqrt(g.gamma * gas_pressure(g.gamma, U[MU], U[MV], U[MW], U[EN], rg) / rg);
+  double ts = d.rhos_rp * g.st_factor[s] / (rg * cs);
+  if (XT && d.law == 2 && d.kappa * rg > 2.25) ts = ts * ((4.0 / 9.0) * (d.kappa * rg));
+  return ts;
+}
+
+// Semi-implicit drag over a stage of length tau (Sect. 2.9 drag law).  One
+// dust species: the relative gas-dust velocity relaxes by
+// 1 / (1 + tau (1 + eps) / t_s) at fixed barycentric velocity.  ND > 1
+// species: the backward-Euler system of the gas coupled to each species
+// (no dust-dust exchange) in closed form, v_g' = (rho_g v_g + sum rho_k w_k
+// v_k) / (rho_g + sum rho_k w_k), v_k' = (v_k + a_k v_g') / (1 + a_k), with
+// a_k = tau / t_k and w_k = a_k / (1 + a_k).  The gas energy gains the work
+// done on the gas in both.
+template <bool XT, int ND>
+__device__ __forceinline__ void apply_drag(const DevGrid& g, int i, double* U, double tau, const DragArgs& d) {
+  const double rg = U[RHO];
+  if constexpr (ND == 1) {
+    const double rd = U[DRHO];
+    if (!(rd > 0.0) || !(rg > 0.0)) return;
+    const double ts = stopping_time<XT>(g, i, U, d, 0);
+    const double kk = tau * (1.0 + rd / rg) / ts;
+    const double mu = rg * rd / (rg + rd);
+    const double relax = kk / (1.0 + kk);
+    double dE = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double vg = U[MU + c] / rg;
+      const double X = mu * (U[DMU + c] / rd - vg) * relax;
+      U[MU + c] += X;
+      U[DMU + c] -= X;
+      dE += 0.5 * X * (U[MU + c] / rg + vg);
+    }
+    U[EN] += dE;
+  } else {
+  if (!(rg > 0.0)) return;
+  double a[ND], num[3], den = rg;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) num[c] = U[MU + c];
+#pragma unroll
+  for (int s = 0; s < ND; ++s) {
+    const int b = 5 + 4 * s;
+    a[s] = 0.0;
+    if (!(U[b + 3] > 0.0)) continue;
+    a[s] = tau / stopping_time<XT>(g, i, U, d, s);
+    const double w = a[s] / (1.0 + a[s]);
+    den += U[b + 3] * w;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) num[c] += U[b + c] * w;
+  }
   double dE = 0.0;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const double vg = U[MU + c] / rg;
-    const double X = mu * (U[DMU + c] / rd - vg) * relax;
-    U[MU + c] += X;
-    U[DMU + c] -= X;
-    dE += 0.5 * X * (U[MU + c] / rg + vg);
+    const double vg_ex = U[MU + c] / rg;
+    const double vg = num[c] / den;
+#pragma unroll
+    for (int s = 0; s < ND; ++s) {
+      const int b = 5 + 4 * s;
+      if (!(U[b + 3] > 0.0)) continue;
+      U[b + c] = U[b + 3] * ((U[b + c] / U[b + 3] + a[s] * vg) / (1.0 + a[s]));
+    }
+    U[MU + c] = rg * vg;
+    dE += 0.5 * rg * (vg * vg - vg_ex * vg_ex);
   }
   U[EN] += dE;
+  }
 }
 
 // ------------------------------------------------------------------ CFL
@@ -471,8 +527,9 @@ __device__ __forceinline__ double cell_dt(const DevGrid& g, int i, const double*
   const double cs = sqrt(g.gamma * gas_pressure(g.gamma, U[MU], U[MV], U[MW], U[EN], rho) / rho);
   const double V = g.vol[i], A = g.maxA[i];
   double dt = g.cfl * V / ((vel + cs) * A);
-  if (g.nf > 5 && U[DRHO] > 0.0) {
-    const double vd = sqrt(U[DMU] * U[DMU] + U[DMV] * U[DMV] + U[DMW] * U[DMW]) / U[DRHO];
+  for (int b = 5; b < g.nf; b += 4) {
+    if (!(U[b + 3] > 0.0)) continue;
+    const double vd = sqrt(U[b] * U[b] + U[b + 1] * U[b + 1] + U[b + 2] * U[b + 2]) / U[b + 3];
     if (vd > 0.0) dt = fmin(dt, g.cfl * V / (vd * A));
   }
   return dt;
@@ -481,7 +538,7 @@ __device__ __forceinline__ double cell_dt(const DevGrid& g, int i, const double*
 __device__ __forceinline__ bool cell_nonphysical(const DevGrid& g, const double* U) {
   const double P = gas_pressure(g.gamma, U[MU], U[MV], U[MW], U[EN], U[RHO]);
   bool bad = !(U[RHO] > 0.0) || !(P > 0.0);
-  if (g.nf > 5) bad |= !(U[DRHO] >= 0.0);
+  for (int b = 5; b < g.nf; b += 4) bad |= !(U[b + 3] >= 0.0);
   return bad;
 }
 

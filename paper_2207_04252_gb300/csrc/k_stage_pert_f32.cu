@@ -1,4 +1,5 @@
-// Launcher of the FP32 perturbation-form stage kernel (stage_pert.cuh).
+// Launcher of the FP32 perturbation-form stage kernel (stage_pert.cuh) for
+// gamma = 7/5 (the integer-power forms of the solver).
 #include "launch.cuh"
 
 namespace rossbi {
@@ -16,24 +17,22 @@ cudaError_t launch(const PertArgs<float>& a, int nblocks, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int NF, class P, int RC>
-cudaError_t launch_x(const PertArgs<float>& a, int nblocks, cudaStream_t s, bool xt) {
-  return xt ? launch<NF, P, true, RC>(a, nblocks, s) : launch<NF, P, false, RC>(a, nblocks, s);
-}
-
-template <class P, int RC>
-cudaError_t launch_nf(const PertArgs<float>& a, int nblocks, cudaStream_t s, bool xt) {
-  return a.g.nf == 9 ? launch_x<9, P, RC>(a, nblocks, s, xt) : launch_x<5, P, RC>(a, nblocks, s, xt);
-}
-
 }  // namespace
 
-cudaError_t run_stage_pert_f32(const PertArgs<float>& a, int nblocks, cudaStream_t s, bool xt, bool g75) {
-  if (a.g.recon == RECON_PRIM)
-    return g75 ? launch_nf<PowG75, RECON_PRIM>(a, nblocks, s, xt)
-               : launch_nf<PowGeneric<float>, RECON_PRIM>(a, nblocks, s, xt);
-  return g75 ? launch_nf<PowG75, RECON_CONS>(a, nblocks, s, xt)
-             : launch_nf<PowGeneric<float>, RECON_CONS>(a, nblocks, s, xt);
+template <class P>
+cudaError_t run_stage_pert_f32_p(const PertArgs<float>& a, int nblocks, cudaStream_t s, bool xt) {
+  return by_nf(a.g.nf, [&](auto nf) {
+    constexpr int NF = decltype(nf)::value;
+    if (a.g.recon == RECON_PRIM)
+      return xt ? launch<NF, P, true, RECON_PRIM>(a, nblocks, s) : launch<NF, P, false, RECON_PRIM>(a, nblocks, s);
+    return xt ? launch<NF, P, true, RECON_CONS>(a, nblocks, s) : launch<NF, P, false, RECON_CONS>(a, nblocks, s);
+  });
 }
+
+#ifndef ROSSBI_F32_GENERIC_GAMMA
+template cudaError_t run_stage_pert_f32_p<PowG75>(const PertArgs<float>&, int, cudaStream_t, bool);
+#else
+template cudaError_t run_stage_pert_f32_p<PowGeneric<float>>(const PertArgs<float>&, int, cudaStream_t, bool);
+#endif
 
 }  // namespace rossbi

@@ -5,6 +5,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "adjoint.cuh"
 #include "stage_pert.cuh"
 
@@ -13,6 +15,25 @@ namespace rossbi {
 // Tiles of the stage kernels: 14 x 6 x 6 cells, lines of 16 / 8 / 8 lanes.
 constexpr int F64_TR = 14, F64_TT = 6, F64_TZ = 6, F64_NT = 192;
 constexpr int P32_TR = 14, P32_TT = 6, P32_TZ = 6, P32_NT = 256, P32_MINB = 2;
+// With more than two dust species the FP64-state kernels' staged tile and
+// halo of 14 x 6 x 6 cells no longer fit in shared memory (17 fields:
+// 248 KB): they take tiles two z cells thick (lines of 4 lanes in z).
+constexpr int THIN_TZ = 2;
+constexpr int tile_z(bool fp64_state, int nf) { return fp64_state && nf > 13 ? THIN_TZ : 6; }
+
+// Calls f(std::integral_constant<int, NF>) for the field count nf (5 + 4 x
+// the number of dust species, 0 .. 4).
+template <class F>
+cudaError_t by_nf(int nf, F&& f) {
+  switch (nf) {
+    case 5: return f(std::integral_constant<int, 5>{});
+    case 9: return f(std::integral_constant<int, 9>{});
+    case 13: return f(std::integral_constant<int, 13>{});
+    case 17: return f(std::integral_constant<int, 17>{});
+    case 21: return f(std::integral_constant<int, 21>{});
+  }
+  return cudaErrorInvalidValue;
+}
 // Adjoint flux kernel: lines of 16 lanes (12 owned cells), 16 lines per block.
 constexpr int ADJ_L = 16, ADJ_NL = 16;
 
@@ -37,7 +58,12 @@ cudaError_t set_smem_once(K kern, size_t smem, unsigned long long& done) {
 cudaError_t run_stage_full(const StageArgs& a, int nblocks, cudaStream_t s, bool xt);
 // One launch of the perturbation-form stage kernel (float or double); g75
 // selects the gamma = 7/5 power forms of the float solver.
-cudaError_t run_stage_pert_f32(const PertArgs<float>& a, int nblocks, cudaStream_t s, bool xt, bool g75);
+template <class P>
+cudaError_t run_stage_pert_f32_p(const PertArgs<float>& a, int nblocks, cudaStream_t s, bool xt);
+inline cudaError_t run_stage_pert_f32(const PertArgs<float>& a, int nblocks, cudaStream_t s, bool xt, bool g75) {
+  return g75 ? run_stage_pert_f32_p<PowG75>(a, nblocks, s, xt)
+             : run_stage_pert_f32_p<PowGeneric<float>>(a, nblocks, s, xt);
+}
 cudaError_t run_stage_pert_f64(const PertArgs<double>& a, int nblocks, cudaStream_t s, bool xt);
 // One launch of the adjoint flux kernel along axis 0, 1 or 2.
 cudaError_t run_adj_flux(const AdjFluxArgs& a, int axis, cudaStream_t s);

@@ -47,7 +47,7 @@ struct rossbi_grid {
   size_t partials_cap = 0;
   double* d_sums = nullptr;
   unsigned* d_status = nullptr;
-  double* h_pinned = nullptr;          // [16] readback area: [0..8] values, [12] status word
+  double* h_pinned = nullptr;          // [32] readback area: [0..20] values, [28] status word
   // library-owned buffers
   void* d_scratch = nullptr;           // E* when the caller passes none
   void* d_hoststate = nullptr;         // device copy for rossbi_step_host
@@ -140,7 +140,7 @@ rossbi_status check_desc(const rossbi_grid_desc& d) {
   if (d.nr < 1 || d.nth < 1 || d.nz < 1) return ROSSBI_ERR_ARG;
   if (d.geometry != ROSSBI_GEOM_BOX && d.geometry != ROSSBI_GEOM_CYL) return ROSSBI_ERR_ARG;
   if (!(d.gamma > 1.0) || !(d.cfl > 0.0)) return ROSSBI_ERR_ARG;
-  if (d.n_dust != 0 && d.n_dust != 1) return ROSSBI_ERR_UNSUPPORTED;
+  if (d.n_dust < 0 || d.n_dust > ND_MAX) return ROSSBI_ERR_UNSUPPORTED;
   for (int a = 0; a < 3; ++a) {
     if (!(d.x1[a] > d.x0[a])) return ROSSBI_ERR_ARG;
     for (int bc : {d.bc_lo[a], d.bc_hi[a]})
@@ -165,11 +165,11 @@ rossbi_status status_from_word(unsigned w) {
 }
 
 rossbi_status sync_and_status(rossbi_grid* g) {
-  CK(cudaMemcpyAsync(g->h_pinned + 12, g->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, g->stream));
+  CK(cudaMemcpyAsync(g->h_pinned + 28, g->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, g->stream));
   CK(cudaMemsetAsync(g->d_status, 0, sizeof(unsigned), g->stream));
   CK(cudaStreamSynchronize(g->stream));
   unsigned w;
-  std::memcpy(&w, g->h_pinned + 12, sizeof(unsigned));
+  std::memcpy(&w, g->h_pinned + 28, sizeof(unsigned));
   return status_from_word(w);
 }
 
@@ -180,7 +180,7 @@ __global__ void cfl_kernel(DevGrid g, StageArgs a, unsigned long long* slot) {
   double m = INFINITY;
   unsigned status = 0;
   for (size_t lin = blockIdx.x * (size_t)CFL_NT + threadIdx.x; lin < ncell; lin += (size_t)gridDim.x * CFL_NT) {
-    double U[9];
+    double U[NF_MAX];
     for (int f = 0; f < g.nf; ++f) U[f] = a.in[f][lin];
     const int i = (int)(lin % g.nr);
     if (cell_nonphysical(g, U)) status |= STATUS_NONPHYSICAL;
@@ -209,7 +209,7 @@ __global__ void eq_prim_kernel(double gamma, const double* e, double* w, size_t 
 __global__ void sums_kernel(DevGrid g, StageArgs a, double* partials) {
   __shared__ double red[CFL_NT / 32];
   const size_t ncell = (size_t)g.nr * g.nth * g.nz;
-  double s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  double s[NF_MAX] = {};
   for (size_t lin = blockIdx.x * (size_t)CFL_NT + threadIdx.x; lin < ncell; lin += (size_t)gridDim.x * CFL_NT) {
     const double V = g.vol[lin % g.nr];
     for (int f = 0; f < g.nf; ++f) s[f] += V * a.in[f][lin];
@@ -241,8 +241,15 @@ __global__ void __launch_bounds__(RED_NT) reduce_partials_kernel(const double* p
   }
 }
 
+// Dust densities of every species (null beyond n).
+template <class T>
+struct DustRho {
+  const T* p[ND_MAX];
+  int n;
+};
+
 // Disc moments of the indirect gravity (Sect. 2.10): per-block FP64 partial
-// sums of w (rho - rho_0 + rho_d) cos(theta) and ... sin(theta), with
+// sums of w (rho - rho_0 + sum rho_d) cos(theta) and ... sin(theta), with
 // w = V r / R^3 of the cell centre; `full` states carry rho itself, the
 // perturbation forms rho' already.  A warp takes one azimuthal row (nr cells)
 // at a time; each lane sums its cells of the row in the state's precision
@@ -252,8 +259,8 @@ __global__ void __launch_bounds__(RED_NT) reduce_partials_kernel(const double* p
 // warps in a fixed order, so the sums are reproducible.
 constexpr int IND_NT = 256, IND_BLOCKS = 152 * 4;
 template <class T>
-__global__ void __launch_bounds__(IND_NT) indirect_moments_kernel(DevGrid g, const T* rho, const T* drho, int full,
-                                                                  const double* w, const float* wf,
+__global__ void __launch_bounds__(IND_NT) indirect_moments_kernel(DevGrid g, const T* rho, const DustRho<T> dr,
+                                                                  int full, const double* w, const float* wf,
                                                                   double* partials) {
   __shared__ double red[IND_NT / 32];
   constexpr int NW = IND_NT / 32;
@@ -266,14 +273,18 @@ __global__ void __launch_bounds__(IND_NT) indirect_moments_kernel(DevGrid g, con
     T m = T(0);
     if constexpr (sizeof(T) == 4) {
       const float* wk = wf + (size_t)k * g.nr;
-      for (int i = lane; i < g.nr; i += 32) m += (rho[base + i] + (drho ? drho[base + i] : 0.0f)) * wk[i];
+      for (int i = lane; i < g.nr; i += 32) {
+        float x = rho[base + i];
+        for (int s = 0; s < dr.n; ++s) x += dr.p[s][base + i];
+        m += x * wk[i];
+      }
     } else {
       const double* wk = w + (size_t)k * g.nr;
       const double* e0 = full && g.has_eq ? g.e0c + ((size_t)RHO * g.nz + k) * g.nr : nullptr;
       for (int i = lane; i < g.nr; i += 32) {
         double dm = rho[base + i];
         if (e0) dm -= e0[i];
-        if (drho) dm += drho[base + i];
+        for (int s = 0; s < dr.n; ++s) dm += dr.p[s][base + i];
         m += dm * wk[i];
       }
     }
@@ -317,6 +328,31 @@ __global__ void __launch_bounds__(RED_NT) indirect_reduce_kernel(const double* p
     gtab[nth + j] = gt;
     gtabf[j] = (float)gr;
     gtabf[nth + j] = (float)gt;
+  }
+}
+
+// Halo rows of a decomposition in theta (Sect. 3.1 splits the grid into
+// blocks of cells): copies rows j0 .. j0 + rows - 1 of every field between
+// the state (SoA, index (k nth + j) nr + i) and a contiguous buffer laid out
+// [f][k][jj][i].  One thread per element, consecutive threads along r, so
+// both sides are read and written in coalesced runs of nr elements.
+template <class T>
+struct FieldPtrs {
+  T* p[NF_MAX];
+};
+template <class T>
+__global__ void theta_rows_kernel(FieldPtrs<T> st, T* buf, int nr, int nth, int nz, int nf, int j0, int rows,
+                                  int unpack) {
+  const size_t per_field = (size_t)nz * rows * nr, n = per_field * nf;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+    const int f = (int)(q / per_field);
+    const size_t r = q - (size_t)f * per_field;
+    const int i = (int)(r % nr);
+    const size_t kj = r / nr;
+    const int jj = (int)(kj % rows), k = (int)(kj / rows);
+    const size_t lin = ((size_t)k * nth + (j0 + jj)) * nr + i;
+    if (unpack) st.p[f][lin] = buf[q];
+    else buf[q] = st.p[f][lin];
   }
 }
 
@@ -386,7 +422,7 @@ rossbi_status ensure_partials(rossbi_grid* g, size_t nblocks) {
   if (g->d_partials) cudaFree(g->d_partials);
   g->d_partials = nullptr;
   g->partials_cap = 0;
-  CK(cudaMalloc(&g->d_partials, nblocks * 10 * sizeof(double)));
+  CK(cudaMalloc(&g->d_partials, nblocks * (NF_MAX + 1) * sizeof(double)));
   g->partials_cap = nblocks;
   return ROSSBI_OK;
 }
@@ -573,14 +609,29 @@ PertArgs<T> pert_args(rossbi_grid* g) {
   a.status = g->d_status;
   a.tiles_r = g->tiles_r;
   a.tiles_t = g->tiles_t;
+  a.gam = (T)g->dg.gamma;
+  a.om = (T)g->dg.omega;
+  a.cfl = (T)g->dg.cfl;
+  a.dx1 = (T)g->dg.dx[1];
+  a.dx2 = (T)g->dg.dx[2];
+  for (int sp = 0; sp < ND_MAX; ++sp) a.st_factor[sp] = (T)g->dg.st_factor[sp];
   return a;
+}
+
+// The drag parameters of a step in the state precision.
+template <class T>
+void set_pert_drag(PertArgs<T>& a, const DragArgs& drag) {
+  a.drag = drag;
+  a.stokes = (T)drag.stokes;
+  a.rhos_rp = (T)drag.rhos_rp;
+  a.kappa = (T)drag.kappa;
 }
 
 // Drag parameters of a step (Sect. 2.9 drag law; Epstein constant fixed so
 // that the Stokes number holds at r = 1, z = 0).
 rossbi_status drag_args(rossbi_grid* g, const rossbi_dust_params* dust, DragArgs& drag) {
   drag = DragArgs{0.0, 0.0, 0, 0.0};
-  if (g->nf == 9) {
+  if (g->nf > 5) {
     drag.stokes = dust->stokes;
     drag.law = dust->drag_law;
     if (!(dust->stokes > 0.0)) return ROSSBI_ERR_ARG;
@@ -608,7 +659,7 @@ rossbi_status prepare_step(rossbi_grid* g, void* const* state, void* const* scra
   if (!state) return ROSSBI_ERR_ARG;
   for (int f = 0; f < g->nf; ++f)
     if (!state[f]) return ROSSBI_ERR_ARG;
-  if (g->nf == 9 && !dust) return ROSSBI_ERR_ARG;
+  if (g->nf > 5 && !dust) return ROSSBI_ERR_ARG;
   if (dt < 0.0 || !std::isfinite(dt)) return ROSSBI_ERR_ARG;
   if (dt == 0.0 && !g->dt_on_device) return ROSSBI_ERR_ARG;
   if (scratch) {
@@ -694,14 +745,17 @@ rossbi_status indirect_moments(rossbi_grid* g, void* const* state) {
   const double* w = g->d_ind + L.w;
   double* part = g->d_ind + L.part;
   const float* wf = reinterpret_cast<const float*>(g->d_ind + L.wf);
-  const bool has_dust = g->nf == 9;
-  if (d.precision == ROSSBI_FP32_PERT)
-    indirect_moments_kernel<float><<<IND_BLOCKS, IND_NT, 0, g->stream>>>(
-        g->dg, (const float*)state[RHO], has_dust ? (const float*)state[DRHO] : nullptr, 0, w, wf, part);
-  else
+  if (d.precision == ROSSBI_FP32_PERT) {
+    DustRho<float> dr{};
+    for (int b = 5; b < g->nf; b += 4) dr.p[dr.n++] = (const float*)state[b + 3];
+    indirect_moments_kernel<float><<<IND_BLOCKS, IND_NT, 0, g->stream>>>(g->dg, (const float*)state[RHO], dr, 0, w,
+                                                                         wf, part);
+  } else {
+    DustRho<double> dr{};
+    for (int b = 5; b < g->nf; b += 4) dr.p[dr.n++] = (const double*)state[b + 3];
     indirect_moments_kernel<double><<<IND_BLOCKS, IND_NT, 0, g->stream>>>(
-        g->dg, (const double*)state[RHO], has_dust ? (const double*)state[DRHO] : nullptr,
-        d.precision == ROSSBI_FP64, w, wf, part);
+        g->dg, (const double*)state[RHO], dr, d.precision == ROSSBI_FP64, w, wf, part);
+  }
   CK(cudaGetLastError());
   indirect_reduce_kernel<<<1, RED_NT, 0, g->stream>>>(part, IND_BLOCKS, d.nth, g->dg.x_ind, g->d_ind + L.cs,
                                                       g->d_ind, g->d_ind + L.g,
@@ -768,7 +822,7 @@ rossbi_status step_pert(rossbi_grid* g, void* const* state, void* const* sc, dou
   const int nblocks = n_tiles(g);
   const int cur = g->dt_slot, nxt = 1 - g->dt_slot;
   PertArgs<T> a = pert_args<T>(g);
-  a.drag = drag;
+  set_pert_drag(a, drag);
   a.dt_host = dt;
   a.dt_dev = dt == 0.0 ? g->d_dt + cur : nullptr;
   for (int f = 0; f < g->nf; ++f) {
@@ -901,8 +955,8 @@ rossbi_status adjoint_step(rossbi_grid* g, void* const* state, double dt, const 
     for (int h = 0; h < g->nf; ++h)  // the cotangents must not overwrite E^n (lam_n may be lam_np1)
       if (lam_np1[f] == state[h] || lam_n[f] == state[h]) return ROSSBI_ERR_ARG;
   }
+  if (g->nf > 9) return ROSSBI_ERR_UNSUPPORTED;  // the adjoint carries one dust species
   if (g->nf == 9 && !dust) return ROSSBI_ERR_ARG;
-  if (g->nf == 9 && dust->drag_law == 2) return ROSSBI_ERR_UNSUPPORTED;  // no adjoint of the Stokes regime yet
   DragArgs drag;
   rossbi_status st = drag_args(g, dust, drag);
   if (st != ROSSBI_OK) return st;
@@ -996,7 +1050,7 @@ rossbi_status adjoint_step(rossbi_grid* g, void* const* state, double dt, const 
 
 rossbi_status step_device(rossbi_grid* g, void* const* state, void* const* scratch, double dt,
                           const rossbi_dust_params* dust, double* next_dt) {
-  void* sc[9];
+  void* sc[NF_MAX];
   DragArgs drag;
   rossbi_status st = prepare_step(g, state, scratch, dt, dust, sc, drag);
   if (st != ROSSBI_OK) return st;
@@ -1060,10 +1114,11 @@ rossbi_status rossbi_init_grid(const rossbi_grid_desc* desc, void* cuda_stream, 
     delete g;
     return ROSSBI_ERR_CUDA;
   }
-  g->nf = desc->n_dust ? 9 : 5;
+  g->nf = 5 + 4 * desc->n_dust;
   g->ncell = (size_t)desc->nr * desc->nth * desc->nz;
   const bool pert = desc->precision != ROSSBI_FP64;  // tile of the form's stage kernel
-  const int tr = pert ? P32_TR : F64_TR, tt = pert ? P32_TT : F64_TT, tz = pert ? P32_TZ : F64_TZ;
+  const int tr = pert ? P32_TR : F64_TR, tt = pert ? P32_TT : F64_TT;
+  const int tz = tile_z(desc->precision != ROSSBI_FP32_PERT, g->nf);
   g->tiles_r = (desc->nr + tr - 1) / tr;
   g->tiles_t = (desc->nth + tt - 1) / tt;
   g->tiles_z = (desc->nz + tz - 1) / tz;
@@ -1121,10 +1176,10 @@ rossbi_status rossbi_init_grid(const rossbi_grid_desc* desc, void* cuda_stream, 
     if ((st = upload(&g->d_area_z, az, g->stream)) != ROSSBI_OK) break;
     if ((st = upload(&g->d_maxA, maxA, g->stream)) != ROSSBI_OK) break;
     if (cudaMalloc(&g->d_dt, 3 * sizeof(unsigned long long)) != cudaSuccess) { st = ROSSBI_ERR_OOM; break; }
-    if (cudaMalloc(&g->d_sums, 9 * sizeof(double)) != cudaSuccess) { st = ROSSBI_ERR_OOM; break; }
+    if (cudaMalloc(&g->d_sums, NF_MAX * sizeof(double)) != cudaSuccess) { st = ROSSBI_ERR_OOM; break; }
     if (cudaMalloc(&g->d_status, sizeof(unsigned)) != cudaSuccess) { st = ROSSBI_ERR_OOM; break; }
     if (cudaMemsetAsync(g->d_status, 0, sizeof(unsigned), g->stream) != cudaSuccess) { st = ROSSBI_ERR_CUDA; break; }
-    if (cudaMallocHost(&g->h_pinned, 16 * sizeof(double)) != cudaSuccess) { st = ROSSBI_ERR_OOM; break; }
+    if (cudaMallocHost(&g->h_pinned, 32 * sizeof(double)) != cudaSuccess) { st = ROSSBI_ERR_OOM; break; }
     if (cudaStreamSynchronize(g->stream) != cudaSuccess) { st = ROSSBI_ERR_CUDA; break; }
   } while (false);
   if (st != ROSSBI_OK) {
@@ -1139,6 +1194,7 @@ rossbi_status rossbi_init_grid(const rossbi_grid_desc* desc, void* cuda_stream, 
   dg.nf = g->nf;
   dg.has_eq = 0;
   dg.recon = d.recon == ROSSBI_RECON_PRIMITIVE ? RECON_PRIM : RECON_CONS;
+  for (int sp = 0; sp < ND_MAX; ++sp) dg.st_factor[sp] = 1.0;
   for (int a = 0; a < 3; ++a) {
     dg.bc_lo[a] = d.bc_lo[a];
     dg.bc_hi[a] = d.bc_hi[a];
@@ -1258,13 +1314,17 @@ rossbi_status rossbi_cfl_dt(rossbi_grid* g, const void* const* state, double* dt
   } else if (prec == ROSSBI_FP32_PERT) {
     PertArgs<float> a = pert_args<float>(g);
     for (int f = 0; f < g->nf; ++f) a.in[f] = (const float*)state[f];
-    if (g->nf == 9) pert_cfl_kernel<float, 9><<<blocks, 256, 0, g->stream>>>(a, slot);
-    else pert_cfl_kernel<float, 5><<<blocks, 256, 0, g->stream>>>(a, slot);
+    CK(by_nf(g->nf, [&](auto nf) {
+      pert_cfl_kernel<float, decltype(nf)::value><<<blocks, 256, 0, g->stream>>>(a, slot);
+      return cudaGetLastError();
+    }));
   } else {
     PertArgs<double> a = pert_args<double>(g);
     for (int f = 0; f < g->nf; ++f) a.in[f] = (const double*)state[f];
-    if (g->nf == 9) pert_cfl_kernel<double, 9><<<blocks, 256, 0, g->stream>>>(a, slot);
-    else pert_cfl_kernel<double, 5><<<blocks, 256, 0, g->stream>>>(a, slot);
+    CK(by_nf(g->nf, [&](auto nf) {
+      pert_cfl_kernel<double, decltype(nf)::value><<<blocks, 256, 0, g->stream>>>(a, slot);
+      return cudaGetLastError();
+    }));
   }
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(g->h_pinned, slot, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
@@ -1288,7 +1348,7 @@ rossbi_status rossbi_step_host(rossbi_grid* g, void* const* host_state, double d
   rossbi_status st = ensure_scratch(g, &g->d_hoststate);
   if (st != ROSSBI_OK) return st;
   const size_t bytes = g->ncell * elem_size(g);
-  void* dev[9];
+  void* dev[NF_MAX];
   for (int f = 0; f < g->nf; ++f) {
     dev[f] = (char*)g->d_hoststate + (size_t)f * bytes;
     CK(cudaMemcpyAsync(dev[f], host_state[f], bytes, cudaMemcpyHostToDevice, g->stream));
@@ -1317,13 +1377,17 @@ rossbi_status rossbi_conservation_sums(rossbi_grid* g, const void* const* state,
   } else if (prec == ROSSBI_FP32_PERT) {
     PertArgs<float> a = pert_args<float>(g);
     for (int f = 0; f < g->nf; ++f) a.in[f] = (const float*)state[f];
-    if (g->nf == 9) pert_sums_kernel<float, 9><<<blocks, 256, 0, g->stream>>>(a, g->d_partials);
-    else pert_sums_kernel<float, 5><<<blocks, 256, 0, g->stream>>>(a, g->d_partials);
+    CK(by_nf(g->nf, [&](auto nf) {
+      pert_sums_kernel<float, decltype(nf)::value><<<blocks, 256, 0, g->stream>>>(a, g->d_partials);
+      return cudaGetLastError();
+    }));
   } else {
     PertArgs<double> a = pert_args<double>(g);
     for (int f = 0; f < g->nf; ++f) a.in[f] = (const double*)state[f];
-    if (g->nf == 9) pert_sums_kernel<double, 9><<<blocks, 256, 0, g->stream>>>(a, g->d_partials);
-    else pert_sums_kernel<double, 5><<<blocks, 256, 0, g->stream>>>(a, g->d_partials);
+    CK(by_nf(g->nf, [&](auto nf) {
+      pert_sums_kernel<double, decltype(nf)::value><<<blocks, 256, 0, g->stream>>>(a, g->d_partials);
+      return cudaGetLastError();
+    }));
   }
   CK(cudaGetLastError());
   reduce_partials_kernel<<<g->nf, RED_NT, 0, g->stream>>>(g->d_partials, blocks, g->nf, g->d_sums, nullptr);
@@ -1415,9 +1479,52 @@ rossbi_status rossbi_set_damping(rossbi_grid* g, const rossbi_damping_params* p)
   return ROSSBI_OK;
 }
 
+rossbi_status theta_rows(rossbi_grid* g, void* const* state, int j0, int rows, void* buf, int unpack) {
+  if (!g || !state || !buf || rows < 1 || j0 < 0 || j0 + rows > g->desc.nth) return ROSSBI_ERR_ARG;
+  for (int f = 0; f < g->nf; ++f)
+    if (!state[f]) return ROSSBI_ERR_ARG;
+  const rossbi_grid_desc& d = g->desc;
+  const size_t n = (size_t)g->nf * d.nz * rows * d.nr;
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 8);
+  if (d.precision == ROSSBI_FP32_PERT) {
+    FieldPtrs<float> p{};
+    for (int f = 0; f < g->nf; ++f) p.p[f] = (float*)state[f];
+    theta_rows_kernel<float><<<blocks, 256, 0, g->stream>>>(p, (float*)buf, d.nr, d.nth, d.nz, g->nf, j0, rows,
+                                                             unpack);
+  } else {
+    FieldPtrs<double> p{};
+    for (int f = 0; f < g->nf; ++f) p.p[f] = (double*)state[f];
+    theta_rows_kernel<double><<<blocks, 256, 0, g->stream>>>(p, (double*)buf, d.nr, d.nth, d.nz, g->nf, j0, rows,
+                                                              unpack);
+  }
+  CK(cudaGetLastError());
+  return ROSSBI_OK;
+}
+
+rossbi_status rossbi_pack_theta_rows(rossbi_grid* g, const void* const* state, int j0, int rows, void* buf) {
+  return theta_rows(g, (void* const*)state, j0, rows, buf, 0);
+}
+
+rossbi_status rossbi_unpack_theta_rows(rossbi_grid* g, void* const* state, int j0, int rows, const void* buf) {
+  return theta_rows(g, state, j0, rows, (void*)buf, 1);
+}
+
+rossbi_status rossbi_set_dust_species(rossbi_grid* g, const double* stokes_factor, int n) {
+  if (!g || !stokes_factor) return ROSSBI_ERR_ARG;
+  const int nd = (g->nf - 5) / 4;
+  if (n != nd || nd < 1) return ROSSBI_ERR_ARG;
+  if (stokes_factor[0] != 1.0) return ROSSBI_ERR_ARG;  // species 0 has the Stokes number itself
+  for (int sp = 1; sp < n; ++sp)
+    if (!(stokes_factor[sp] > 0.0) || !std::isfinite(stokes_factor[sp])) return ROSSBI_ERR_ARG;
+  for (int sp = 0; sp < n; ++sp) g->dg.st_factor[sp] = stokes_factor[sp];
+  return ROSSBI_OK;
+}
+
 rossbi_status rossbi_indirect_moments(rossbi_grid* g, const void* const* state, double* ab) {
   if (!g || !state || !ab || !g->eq_set || g->desc.geometry != ROSSBI_GEOM_CYL) return ROSSBI_ERR_ARG;
-  if (!state[RHO] || (g->nf == 9 && !state[DRHO])) return ROSSBI_ERR_ARG;
+  if (!state[RHO]) return ROSSBI_ERR_ARG;
+  for (int b = 5; b < g->nf; b += 4)
+    if (!state[b + 3]) return ROSSBI_ERR_ARG;
   rossbi_status st = ensure_ind_tables(g);
   if (st == ROSSBI_OK) st = indirect_moments(g, (void* const*)state);
   if (st != ROSSBI_OK) return st;
@@ -1510,8 +1617,8 @@ extern "C" rossbi_status rossbi_step_noalloc(rossbi_grid* g, void* const* state,
   if (!g || !g->eq_set || !state) return ROSSBI_ERR_ARG;
   for (int f = 0; f < g->nf; ++f)
     if (!state[f]) return ROSSBI_ERR_ARG;
-  if (g->nf == 9 && !dust) return ROSSBI_ERR_ARG;
-  if (g->nf == 9 && dust->drag_law == 2) return ROSSBI_ERR_ARG;
+  if (g->nf > 5 && !dust) return ROSSBI_ERR_ARG;
+  if (g->nf > 5 && dust->drag_law == 2) return ROSSBI_ERR_ARG;
   if (dt < 0.0 || !std::isfinite(dt)) return ROSSBI_ERR_ARG;
   if (dt == 0.0 && !g->dt_on_device) return ROSSBI_ERR_ARG;
   // the array's address is per device: only the grid's own device may be current
@@ -1528,7 +1635,7 @@ extern "C" rossbi_status rossbi_step_noalloc(rossbi_grid* g, void* const* state,
   void* base = nullptr;
   st = noalloc_scratch_ptr(&base);
   if (st != ROSSBI_OK) return st;
-  void* sc[9];
+  void* sc[NF_MAX];
   for (int f = 0; f < g->nf; ++f) sc[f] = (char*)base + (size_t)f * field_bytes;
   double* partials = (double*)((char*)base + (size_t)g->nf * field_bytes);
   // the same two stages as rossbi_step (with the indirect gravity's moments

@@ -21,9 +21,9 @@ namespace rossbi {
 
 struct StageArgs {
   DevGrid g;
-  const double* in[9];     // stage input (stencil) state
-  const double* base[9];   // E^n, base of the update
-  double* out[9];          // updated state
+  const double* in[NF_MAX];    // stage input (stencil) state
+  const double* base[NF_MAX];  // E^n, base of the update
+  double* out[NF_MAX];         // updated state
   double* gout;            // mode 1: G(E) - R0 written here, [nf][ncell]
   double dt_host;
   const unsigned long long* dt_dev;  // if set, dt is read from this device slot
@@ -78,11 +78,12 @@ __device__ __forceinline__ void parabola_weights(const T* rcoef, int gi, int nr,
 }
 
 // Primitive dust reconstruction (u, v, w, rho_d) of the cell at s (stride S
-// along the sweep) from conservative shared-memory fields (5..8 of the block).
+// along the sweep) from the conservative shared-memory fields b .. b + 3 of
+// one dust species (momenta, then density).
 template <class T, int BOX, int S>
-__device__ __forceinline__ void dust_recon(const T* sE, int sidx, const T* w, T* wm, T* wp) {
+__device__ __forceinline__ void dust_recon(const T* sE, int sidx, int b, const T* w, T* wm, T* wp) {
   T pm[4], p0[4], pp[4];
-  const T* r = sE + 8 * BOX + sidx;
+  const T* r = sE + (b + 3) * BOX + sidx;
   pm[3] = r[-S];
   p0[3] = r[0];
   pp[3] = r[S];
@@ -91,7 +92,7 @@ __device__ __forceinline__ void dust_recon(const T* sE, int sidx, const T* w, T*
   const T ip = pp[3] > T(0) ? T(1) / pp[3] : T(0);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const T* m = sE + (5 + c) * BOX + sidx;
+    const T* m = sE + (b + c) * BOX + sidx;
     pm[c] = m[-S] * im;
     p0[c] = m[0] * i0;
     pp[c] = m[S] * ip;
@@ -257,10 +258,12 @@ __device__ __forceinline__ void sweep_full(const StageArgs& a, const double* sE,
         }
       }
     }
-    // ---------------- dust: fields 5..8, primitive reconstruction, kinetic flux
-    if (NF == 9) {
+    // ---------------- dust: each species' fields b .. b + 3, primitive
+    // reconstruction, kinetic flux
+#pragma unroll 1
+    for (int b = 5; b < NF; b += 4) {
       double qm[4], qp[4];
-      dust_recon<double, BOX, STRIDE>(sE, sidx, w, qm, qp);
+      dust_recon<double, BOX, STRIDE>(sE, sidx, b, w, qm, qp);
       double F[4];
       {
         double WL[4];
@@ -279,7 +282,7 @@ __device__ __forceinline__ void sweep_full(const StageArgs& a, const double* sE,
       for (int f = 0; f < 4; ++f) {
         const double Fu = __shfl_down_sync(FULL, F[f], 1, L);
         if (do_acc) {
-          double* dst = sG + (5 + f) * NCORE + (z * TT + y) * TR + x;
+          double* dst = sG + (b + f) * NCORE + (z * TT + y) * TR + x;
           if (D == 0) *dst = F[f] - Fu;
           else *dst += F[f] - Fu;
         }
@@ -413,7 +416,7 @@ __global__ void __launch_bounds__(NT, 1) stage_full_kernel(const StageArgs a) {
     double E[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) E[f] = a.base[f][lin] + tau * G[f] * iv;
-    if (NF == 9) apply_drag<XT>(g, gi, E, tau, a.drag);
+    if constexpr (NF > 5) apply_drag<XT, (NF - 5) / 4>(g, gi, E, tau, a.drag);
 #pragma unroll
     for (int f = 0; f < NF; ++f) a.out[f][lin] = E[f];
     if (a.stage2) {

@@ -328,9 +328,9 @@ template <class T>
 struct PertArgs {
   DevGrid g;          // geometry, sizes, boundary conditions, double tables
   PertTables<T> t;
-  const T* in[9];
-  const T* base[9];
-  T* out[9];
+  const T* in[NF_MAX];
+  const T* base[NF_MAX];
+  T* out[NF_MAX];
   double dt_host;
   const unsigned long long* dt_dev;
   double tau_frac;
@@ -339,6 +339,11 @@ struct PertArgs {
   double* partials;  // stage 2: [nf + 1][gridDim.x] block sums of V*E', then block dt minima
   unsigned* status;
   int tiles_r, tiles_t;
+  // the grid's and the drag's parameters in the state precision, converted
+  // once on the host (GB300's FP64 pipe is narrow: per-use conversions of the
+  // double originals cost latency in the float kernel)
+  T gam, om, cfl, dx1, dx2, stokes, rhos_rp, kappa;
+  T st_factor[ND_MAX];  // Stokes-number factor of each dust species
 };
 
 // Primitive perturbations (du, dv, dw, dP, drho in the field slots MU, MV,
@@ -419,7 +424,7 @@ __device__ __forceinline__ void sweep_pert(const PertArgs<T>& a, const T* sE, T*
   constexpr int NW = NT / 32;
   constexpr unsigned FULL = 0xffffffffu;
   const DevGrid& g = a.g;
-  const T gam = (T)g.gamma;
+  const T gam = a.gam;
   const bool has_eq = g.has_eq != 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
@@ -442,7 +447,7 @@ __device__ __forceinline__ void sweep_pert(const PertArgs<T>& a, const T* sE, T*
     const bool do_acc = line_ok && c >= 0 && c < TD && gd < nd;
     const int sidx = do_recon ? ((z + 2) * BY + (y + 2)) * BX + (x + 2) : (2 * BY + 2) * BX + 2;
     T w[9];
-    parabola_weights<T, D>(a.t.rcoef, gi, g.nr, (T)g.dx[D], w);
+    parabola_weights<T, D>(a.t.rcoef, gi, g.nr, D == 1 ? a.dx1 : a.dx2, w);
     const int ci = clampi(gi, 0, g.nr - 1), ck = clampi(gk, 0, g.nz - 1);
     T area = T(0);
     if (do_face) area = D == 0 ? a.t.area_r[clampi(gi, 0, g.nr)] : (D == 1 ? a.t.area_t[ci] : a.t.area_z[ci]);
@@ -516,9 +521,10 @@ __device__ __forceinline__ void sweep_pert(const PertArgs<T>& a, const T* sE, T*
         }
       }
     }
-    if (NF == 9) {  // dust: primitive reconstruction, kinetic flux
+#pragma unroll 1
+    for (int b = 5; b < NF; b += 4) {  // each dust species: primitive reconstruction, kinetic flux
       T qm[4], qp[4];
-      dust_recon<T, BOX, STRIDE>(sE, sidx, w, qm, qp);
+      dust_recon<T, BOX, STRIDE>(sE, sidx, b, w, qm, qp);
       T F[4];
       {
         T WL[4];
@@ -537,7 +543,7 @@ __device__ __forceinline__ void sweep_pert(const PertArgs<T>& a, const T* sE, T*
       for (int f = 0; f < 4; ++f) {
         const T Fu = __shfl_down_sync(FULL, F[f], 1, L);
         if (do_acc) {
-          T* dst = sG + (5 + f) * NCORE + (z * TT + y) * TR + x;
+          T* dst = sG + (b + f) * NCORE + (z * TT + y) * TR + x;
           if (D == 0) *dst = F[f] - Fu;
           else *dst += F[f] - Fu;
         }
@@ -590,8 +596,9 @@ __device__ __forceinline__ void cell_prim(T g, const PCell<T>& c, const T* q, T&
 // q: the staged cell, primitive gas perturbations (du, dv, dw, dP, drho) in
 // slots 0..4 and the conservative dust fields in slots 5..8.
 template <class T, int NF, bool XT>
-__device__ __forceinline__ void pert_sources(const DevGrid& g, const PCell<T>& c, int j, const T* q, T* S) {
-  const T Om = (T)g.omega;
+__device__ __forceinline__ void pert_sources(const PertArgs<T>& a, const PCell<T>& c, int j, const T* q, T* S) {
+  const DevGrid& g = a.g;
+  const T Om = a.om;
   const T rho = c.rho0 + q[RHO], du = q[MU], dv = q[MV], dw = q[MW], dp = q[EN];
   const T v = c.v0 + dv;
   S[MU] = q[RHO] * c.Cr + rho * dv * c.cor + rho * dv * dv * c.ir + dp * c.ir;
@@ -599,19 +606,20 @@ __device__ __forceinline__ void pert_sources(const DevGrid& g, const PCell<T>& c
   S[MW] = q[RHO] * c.fz;
   S[EN] = rho * du * c.gr + rho * dw * c.fz;
   S[RHO] = T(0);
-  if (NF == 9) {
-    const T rd = q[DRHO];
+#pragma unroll
+  for (int b = 5; b < NF; b += 4) {  // each dust species
+    const T rd = q[b + 3];
     if (rd > T(0)) {
       const T ird = T(1) / rd;
-      const T dvd = (q[DMV] - rd * c.v0) * ird;  // v_d - v0
+      const T dvd = (q[b + 1] - rd * c.v0) * ird;  // v_d - v0
       const T vd = c.v0 + dvd;
-      S[DMU] = rd * (c.Cr + dvd * c.cor + dvd * dvd * c.ir);
-      S[DMV] = -q[DMU] * (vd * c.ir + T(2) * Om);
-      S[DMW] = rd * c.fz;
+      S[b] = rd * (c.Cr + dvd * c.cor + dvd * dvd * c.ir);
+      S[b + 1] = -q[b] * (vd * c.ir + T(2) * Om);
+      S[b + 2] = rd * c.fz;
     } else {
-      S[DMU] = S[DMV] = S[DMW] = T(0);
+      S[b] = S[b + 1] = S[b + 2] = T(0);
     }
-    S[DRHO] = T(0);
+    S[b + 3] = T(0);
   }
   if (XT && g.x_ind != 0.0) {
     T gr, gt;  // grad Phi_ind, (r, theta), tabulated per axis-1 index in the state precision
@@ -625,57 +633,104 @@ __device__ __forceinline__ void pert_sources(const DevGrid& g, const PCell<T>& c
     S[MU] -= rho * gr;
     S[MV] -= rho * gt;
     S[EN] -= rho * (du * gr + v * gt);
-    if (NF == 9 && q[DRHO] > T(0)) {
-      S[DMU] -= q[DRHO] * gr;
-      S[DMV] -= q[DRHO] * gt;
+#pragma unroll
+    for (int b = 5; b < NF; b += 4) {
+      if (q[b + 3] > T(0)) {
+        S[b] -= q[b + 3] * gr;
+        S[b + 1] -= q[b + 3] * gt;
+      }
     }
   }
 }
 
-// Semi-implicit drag on a perturbation-form cell state (same closed form as the
-// full-state kernel; the gas velocity is u0 + du).
+// Stopping time of dust species s in a perturbation-form cell (as
+// stopping_time of the full-state kernel; gas density rg, pressure p0 + dp).
 template <class T, bool XT>
-__device__ __forceinline__ void pert_drag(const DevGrid& g, const PertTables<T>& t, const PCell<T>& c, int i, T* q,
-                                          T tau, const DragArgs& d) {
-  const T gam = (T)g.gamma;
+__device__ __forceinline__ T pert_stopping_time(const PertArgs<T>& a, const PCell<T>& c, int i, T rg, T dp, int s) {
+  if (a.drag.law == 0) {
+    const T st = a.stokes * a.st_factor[s];
+    return a.g.geom == GEOM_CYL ? st / a.t.omk[i] : st;
+  }
+  const T cs = Math<T>::sqrt_(a.gam * (c.p0 + dp) / rg);
+  T ts = a.rhos_rp * a.st_factor[s] / (rg * cs);
+  if (XT && a.drag.law == 2) {  // Stokes regime of Sect. 2.9 above r_p = 9 lambda / 4
+    const T x = a.kappa * rg;
+    if (x > T(2.25)) ts = ts * (T(4.0 / 9.0) * x);
+  }
+  return ts;
+}
+
+// Semi-implicit drag on a perturbation-form cell state (the closed forms of
+// apply_drag; the gas velocity is u0 + du).  Several species: the gas
+// velocity moves by D = sum rho_k w_k (v_k - v_g) / (rho_g + sum rho_k w_k)
+// and species k by w_k (D - (v_k - v_g)), w_k = a_k / (1 + a_k), every
+// quantity a difference of velocities, never the large u0 itself.
+template <class T, int NF, bool XT>
+__device__ __forceinline__ void pert_drag(const PertArgs<T>& a, const PCell<T>& c, int i, T* q, T tau) {
+  const T gam = a.gam;
   T rg, du, dv, dw, dp;
   cell_prim(gam, c, q, rg, du, dv, dw, dp);
-  const T rd = q[DRHO];
-  if (!(rd > T(0)) || !(rg > T(0))) return;
-  T ts;
-  if (d.law == 0) {
-    ts = g.geom == GEOM_CYL ? (T)d.stokes / t.omk[i] : (T)d.stokes;
-  } else {
-    const T cs = Math<T>::sqrt_(gam * (c.p0 + dp) / rg);
-    ts = (T)d.rhos_rp / (rg * cs);
-    if (XT && d.law == 2) {  // Stokes regime of Sect. 2.9 above r_p = 9 lambda / 4
-      const T x = (T)d.kappa * rg;
-      if (x > T(2.25)) ts = ts * (T(4.0 / 9.0) * x);
-    }
-  }
-  const T kk = tau * (T(1) + rd / rg) / ts;
-  const T mu = rg * rd / (rg + rd);
-  const T relax = kk / (T(1) + kk);
-  const T ird = T(1) / rd;
   const T u0[3] = {T(0), c.v0, T(0)};
   const T dug[3] = {du, dv, dw};
+  if constexpr (NF == 9) {
+    const T rd = q[DRHO];
+    if (!(rd > T(0)) || !(rg > T(0))) return;
+    const T ts = pert_stopping_time<T, XT>(a, c, i, rg, dp, 0);
+    const T kk = tau * (T(1) + rd / rg) / ts;
+    const T mu = rg * rd / (rg + rd);
+    const T relax = kk / (T(1) + kk);
+    const T ird = T(1) / rd;
+    T dE = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const T dvd = (q[DMU + k] - rd * u0[k]) * ird;  // v_d - u0
+      const T X = mu * (dvd - dug[k]) * relax;
+      const T vg_ex = u0[k] + dug[k];
+      q[MU + k] += X;
+      q[DMU + k] -= X;
+      dE += T(0.5) * X * (T(2) * vg_ex + X / rg);
+    }
+    q[EN] += dE;
+  } else {
+  constexpr int ND = (NF - 5) / 4;
+  if (!(rg > T(0))) return;
+  T wk[ND], den = rg, num[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int s = 0; s < ND; ++s) {
+    const int b = 5 + 4 * s;
+    wk[s] = T(0);
+    const T rd = q[b + 3];
+    if (!(rd > T(0))) continue;
+    const T ak = tau / pert_stopping_time<T, XT>(a, c, i, rg, dp, s);
+    wk[s] = ak / (T(1) + ak);
+    den += rd * wk[s];
+    const T ird = T(1) / rd;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) num[k] += rd * wk[s] * ((q[b + k] - rd * u0[k]) * ird - dug[k]);
+  }
   T dE = T(0);
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const T dvd = (q[DMU + k] - rd * u0[k]) * ird;  // v_d - u0
-    const T X = mu * (dvd - dug[k]) * relax;
-    const T vg_ex = u0[k] + dug[k];
-    q[MU + k] += X;
-    q[DMU + k] -= X;
-    dE += T(0.5) * X * (T(2) * vg_ex + X / rg);
+    const T D = num[k] / den;  // v_g' - v_g
+#pragma unroll
+    for (int s = 0; s < ND; ++s) {
+      const int b = 5 + 4 * s;
+      const T rd = q[b + 3];
+      if (!(rd > T(0))) continue;
+      const T rel = (q[b + k] - rd * u0[k]) / rd - dug[k];  // v_k - v_g
+      q[b + k] += rd * wk[s] * (D - rel);
+    }
+    q[MU + k] += rg * D;
+    dE += T(0.5) * rg * D * (T(2) * (u0[k] + dug[k]) + D);
   }
   q[EN] += dE;
+  }
 }
 
 template <class T, int NF>
-__device__ __forceinline__ T pert_cell_dt(const DevGrid& g, const PertTables<T>& t, const PCell<T>& c, int i,
-                                          const T* q, bool& bad) {
-  const T gam = (T)g.gamma;
+__device__ __forceinline__ T pert_cell_dt(const PertArgs<T>& a, const PCell<T>& c, int i, const T* q, bool& bad) {
+  const PertTables<T>& t = a.t;
+  const T gam = a.gam;
   T rho, du, dv, dw, dp;
   cell_prim(gam, c, q, rho, du, dv, dw, dp);
   const T p = c.p0 + dp;
@@ -683,14 +738,15 @@ __device__ __forceinline__ T pert_cell_dt(const DevGrid& g, const PertTables<T>&
   const T v = c.v0 + dv;
   const T vel = Math<T>::sqrt_(du * du + v * v + dw * dw);
   const T cs = Math<T>::sqrt_(gam * p / rho);
-  const T V = t.vol[i], A = t.maxA[i], cfl = (T)g.cfl;
+  const T V = t.vol[i], A = t.maxA[i], cfl = a.cfl;
   T dt = cfl * V / ((vel + cs) * A);
-  if (NF == 9) {
-    if (q[DRHO] > T(0)) {
-      const T vd = Math<T>::sqrt_(q[DMU] * q[DMU] + q[DMV] * q[DMV] + q[DMW] * q[DMW]) / q[DRHO];
+#pragma unroll
+  for (int b = 5; b < NF; b += 4) {
+    if (q[b + 3] > T(0)) {
+      const T vd = Math<T>::sqrt_(q[b] * q[b] + q[b + 1] * q[b + 1] + q[b + 2] * q[b + 2]) / q[b + 3];
       if (vd > T(0)) dt = fmin(dt, cfl * V / (vd * A));
     }
-    bad |= !(q[DRHO] >= T(0));
+    bad |= !(q[b + 3] >= T(0));
   }
   return dt;
 }
@@ -761,7 +817,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
           ce.v0 = e0[u][1];
           ce.p0 = e0[u][2];
           T rho, du, dv, dw, dp;
-          cell_prim((T)g.gamma, ce, v[u], rho, du, dv, dw, dp);
+          cell_prim(a.gam, ce, v[u], rho, du, dv, dw, dp);
           sE[MU * BOX + idx] = du;
           sE[MV * BOX + idx] = dv;
           sE[MW * BOX + idx] = dw;
@@ -803,11 +859,11 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
       T qc[5];
 #pragma unroll
       for (int f = 0; f < 5; ++f) qc[f] = q[f];
-      face_prim<T>((T)g.gamma, ce.rho0, ce.v0, qc, q);
+      face_prim<T>(a.gam, ce.rho0, ce.v0, qc, q);
     }
     if (g.geom == GEOM_CYL) {
       T S[NF];
-      pert_sources<T, NF, XT>(g, ce, gj, q, S);
+      pert_sources<T, NF, XT>(a, ce, gj, q, S);
       const T V = a.t.vol[gi];
 #pragma unroll
       for (int f = 0; f < NF; ++f) G[f] += V * S[f];
@@ -826,20 +882,21 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
     T E[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) E[f] = a.base[f][lin] + tau * G[f] * iv;
-    if (NF == 9) pert_drag<T, XT>(g, a.t, ce, gi, E, tau, a.drag);
+    if constexpr (NF > 5) pert_drag<T, NF, XT>(a, ce, gi, E, tau);
 #pragma unroll
     for (int f = 0; f < NF; ++f) a.out[f][lin] = E[f];
     bool bad_in = false;
     if (a.stage2) {
       bool bad = false;
-      dtmin = fmin(dtmin, pert_cell_dt<T, NF>(g, a.t, ce, gi, E, bad));
+      dtmin = fmin(dtmin, pert_cell_dt<T, NF>(a, ce, gi, E, bad));
       if (bad) status |= STATUS_NONPHYSICAL;
       const T V = a.t.vol[gi];
 #pragma unroll
       for (int f = 0; f < NF; ++f) sums[f] += V * E[f];
     } else {
       bad_in = !(ce.rho0 + q[RHO] > T(0)) || !(ce.p0 + q[EN] > T(0));
-      if (NF == 9) bad_in |= !(q[DRHO] >= T(0));
+#pragma unroll
+      for (int b = 5; b < NF; b += 4) bad_in |= !(q[b + 3] >= T(0));
       if (bad_in) status |= STATUS_NONPHYSICAL;
     }
   }
@@ -887,7 +944,7 @@ __global__ void pert_cfl_kernel(const PertArgs<T> a, unsigned long long* slot) {
     for (int f = 0; f < NF; ++f) q[f] = a.in[f][lin];
     const int i = (int)(lin % g.nr), k = (int)(lin / ((size_t)g.nr * g.nth));
     bool bad = false;
-    m = fmin(m, (double)pert_cell_dt<T, NF>(g, a.t, cell_eq(a.t, g, i, k), i, q, bad));
+    m = fmin(m, (double)pert_cell_dt<T, NF>(a, cell_eq(a.t, g, i, k), i, q, bad));
     if (bad) status |= STATUS_NONPHYSICAL;
   }
   m = block_min<256>(m, red);

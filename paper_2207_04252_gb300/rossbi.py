@@ -26,7 +26,8 @@ ROSSBI_RECON_CONSERVATIVE, ROSSBI_RECON_PRIMITIVE = 0, 1
 
 # every function declared in include/rossbi.h
 EXPORTS = (
-    "rossbi_init_grid", "rossbi_set_equilibrium", "rossbi_set_indirect", "rossbi_indirect_moments", "rossbi_set_damping", "rossbi_get_equilibrium", "rossbi_cfl_dt", "rossbi_step",
+    "rossbi_init_grid", "rossbi_set_equilibrium", "rossbi_set_indirect", "rossbi_indirect_moments", "rossbi_set_damping", "rossbi_set_dust_species", "rossbi_pack_theta_rows",
+    "rossbi_unpack_theta_rows", "rossbi_get_equilibrium", "rossbi_cfl_dt", "rossbi_step",
     "rossbi_step_host", "rossbi_step_noalloc", "rossbi_adjoint_step", "rossbi_adjoint_dstokes",
     "rossbi_conservation_sums", "rossbi_fallback_count", "rossbi_take_status", "rossbi_profile_enable",
     "rossbi_profile_read", "rossbi_nfields", "rossbi_precision", "rossbi_destroy", "rossbi_status_string",
@@ -80,6 +81,9 @@ def load(path: str = LIB_PATH):
     L.rossbi_set_indirect.argtypes = [_VP, ctypes.c_double]
     L.rossbi_indirect_moments.argtypes = [_VP, _PP, _DP]
     L.rossbi_set_damping.argtypes = [_VP, ctypes.POINTER(rossbi_damping_params)]
+    L.rossbi_set_dust_species.argtypes = [_VP, _DP, ctypes.c_int]
+    L.rossbi_pack_theta_rows.argtypes = [_VP, _PP, ctypes.c_int, ctypes.c_int, _VP]
+    L.rossbi_unpack_theta_rows.argtypes = [_VP, _PP, ctypes.c_int, ctypes.c_int, _VP]
     L.rossbi_get_equilibrium.argtypes = [_VP, _DP]
     L.rossbi_cfl_dt.argtypes = [_VP, _PP, _DP]
     L.rossbi_step.argtypes = [_VP, _PP, _PP, ctypes.c_double, ctypes.POINTER(rossbi_dust_params), _DP]
@@ -217,6 +221,24 @@ def rossbi_set_damping(grid, zones):
     """Wave-killing zones (r_edge_in, r_edge_out, period_factor), or None for off."""
     p = None if zones is None else ctypes.byref(rossbi_damping_params(*map(float, zones)))
     _check(load().rossbi_set_damping(grid, p), "rossbi_set_damping")
+
+
+def rossbi_set_dust_species(grid, stokes_factors):
+    """Stokes-number factors of the dust species (factor[0] must be 1)."""
+    f = np.ascontiguousarray(stokes_factors, dtype=np.float64)
+    _check(load().rossbi_set_dust_species(grid, f.ctypes.data_as(_DP), len(f)), "rossbi_set_dust_species")
+
+
+def rossbi_pack_theta_rows(grid, state, j0, rows, buf):
+    """Copy theta rows j0 .. j0 + rows - 1 of every field into the device buffer buf."""
+    _check(load().rossbi_pack_theta_rows(grid, _fields(state, rossbi_nfields(grid)), int(j0), int(rows),
+                                         ctypes.c_void_p(buf.data_ptr())), "rossbi_pack_theta_rows")
+
+
+def rossbi_unpack_theta_rows(grid, state, j0, rows, buf):
+    """Copy the device buffer buf into theta rows j0 .. j0 + rows - 1 of every field."""
+    _check(load().rossbi_unpack_theta_rows(grid, _fields(state, rossbi_nfields(grid)), int(j0), int(rows),
+                                           ctypes.c_void_p(buf.data_ptr())), "rossbi_unpack_theta_rows")
 
 
 def rossbi_indirect_moments(grid, state) -> np.ndarray:

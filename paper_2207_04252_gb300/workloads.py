@@ -13,7 +13,8 @@ Recipes (all on the library's equilibrium E0):
            - (rv dtheta)^2/(2 s_t^2)), s_r = width * H(rv), s_t = chi s_r,
            psi0 set by the centre vorticity -amp * (3/2) Omega_K(rv);
            u' = (1/r) dpsi/dtheta, v' = -dpsi/dr, rho and P at equilibrium.
-           Dust: rho_d = ratio rho0 (1 + a_d xi_d), moving with the gas.
+           Dust: rho_d = ratio rho0 (1 + a_d xi_d), moving with the gas; with
+           several species each takes ratio / n of it, with its own noise.
 """
 import math
 
@@ -43,6 +44,8 @@ class Grid:
         self.perturbation = precision in (R.ROSSBI_FP32_PERT, R.ROSSBI_FP64_PERT)
         self.dust = (w.stokes, w.drag_law, w.drag_kappa) if w.n_dust else None
         self.shape = (self.nf, w.nz, w.nth, w.nr)
+        if w.dust_stokes_factors:
+            R.rossbi_set_dust_species(self.h, w.dust_stokes_factors)
 
     def close(self):
         if self.h:
@@ -131,12 +134,21 @@ class Grid:
         T[syn.F_MU] = rho0 * u1
         T[syn.F_MV] = rho0 * v1
         T[syn.F_EN] = rho0 * (up * u1 + v0 * v1 + vp * v1)
-        if self.nf > 5:
-            xi = syn.uniform_pm1(w.seed, syn.F_DRHO, w.ncell).reshape(w.nz, w.nth, w.nr)
-            rd = w.dust_ratio * rho0 * (1.0 + w.dust_noise * xi)
-            T[syn.F_DMU] = rd * u1
-            T[syn.F_DMV] = rd * v1
+        for b, rd in self._dust_densities(rho0):
+            T[b] = rd * u1
+            T[b + 1] = rd * v1
         return T
+
+    def _dust_densities(self, rho0):
+        """(first field, initial density) of each dust species: an equal share
+        of the dust-to-gas ratio, with the species' own seeded noise."""
+        w = self.w
+        nd = (self.nf - 5) // 4
+        out = []
+        for s in range(nd):
+            xi = syn.uniform_pm1(w.seed, syn.F_DRHO + 4 * s, w.ncell).reshape(w.nz, w.nth, w.nr)
+            out.append((5 + 4 * s, w.dust_ratio / nd * rho0 * (1.0 + w.dust_noise * xi)))
+        return out
 
     def dust_velocity(self) -> np.ndarray:
         """Initial dust velocity (u, v, w), (3, nz, nth, nr): the gas velocity of the recipe."""
@@ -180,12 +192,10 @@ class Grid:
         Ep[syn.F_MU] = rho0 * up
         Ep[syn.F_MV] = rho0 * vp
         Ep[syn.F_EN] = 0.5 * rho0 * (up * up + 2.0 * v0 * vp + vp * vp)
-        if self.nf > 5:
-            xi = syn.uniform_pm1(w.seed, syn.F_DRHO, w.ncell).reshape(w.nz, w.nth, w.nr)
-            rd = w.dust_ratio * rho0 * (1.0 + w.dust_noise * xi)
-            Ep[syn.F_DRHO] = rd
-            Ep[syn.F_DMU] = rd * up
-            Ep[syn.F_DMV] = rd * (v0 + vp)
+        for b, rd in self._dust_densities(rho0):
+            Ep[b + 3] = rd
+            Ep[b] = rd * up
+            Ep[b + 1] = rd * (v0 + vp)
         return Ep
 
     def initial_state(self, device="cuda") -> torch.Tensor:

@@ -66,6 +66,7 @@ class Workload:
     t_end: float = 0.0           # >0: run to this time, clipping the last step
     checkpoint_every: int = 0
     recon: int = RECON_CONSERVATIVE
+    dust_stokes_factors: tuple = ()  # several species: St of species s = stokes x factor[s] (factor[0] = 1)
 
     @property
     def ncell(self) -> int:

@@ -70,7 +70,13 @@ def _run_gpu(grid, state, steps=None, t_end=None):
     return state, t, dts
 
 
-EL64 = 1e-9  # element-wise bar of the FP64 form, relative to the largest departure
+# Element-wise bars of the FP64 form, relative to the largest departure of
+# the quantity: 20x the oracle's own element-wise response, measured like the
+# L1 horizons above (a 1e-15 relative input perturbation), rounded up, and at
+# least 1e-9.  Measured: disc 24x32x32 / 100 steps 9.5e-8, 15x7x33 / 20 steps
+# 4.7e-9; vortex 20x36x32 / 15 steps 3.5e-10, 29x13x32 / 20 steps 1.3e-8;
+# primitive option: vortex 1.0e-10, disc 4.7e-9 (100 steps).
+EL64 = 1e-9
 
 
 def _compare(grid, o, state_gpu, E_ref, tol=TOL64, el_tol=EL64):
@@ -124,7 +130,7 @@ def test_sod_box(lib):
     assert np.abs(g.full_state(s2)[4, 0, 0, :] - exact).mean() < 0.01
 
 
-def _parity_run(lib, w, steps, tol=TOL64, precision=None):
+def _parity_run(lib, w, steps, tol=TOL64, precision=None, el_tol=EL64):
     import torch
     R, W = lib
     o = oracle.Oracle(w)
@@ -140,24 +146,25 @@ def _parity_run(lib, w, steps, tol=TOL64, precision=None):
     for dt in dts:
         g.step(s, dt=dt)
     assert g.take_status() == 0 and o.take_status() == 0
-    return _compare(g, o, s, E, tol)
+    return _compare(g, o, s, E, tol, el_tol)
 
 
-@pytest.mark.parametrize("n,steps", [((24, 32, 32), 100), ((15, 7, 33), 20)])
-def test_disc_noise(lib, n, steps):
-    _parity_run(lib, syn.scaled(syn.DISC_NOISE, *n, steps=steps), steps)
+@pytest.mark.parametrize("n,steps,el_tol", [((24, 32, 32), 100, 2e-6), ((15, 7, 33), 20, 1e-7)])
+def test_disc_noise(lib, n, steps, el_tol):
+    _parity_run(lib, syn.scaled(syn.DISC_NOISE, *n, steps=steps), steps, el_tol=el_tol)
 
 
-@pytest.mark.parametrize("n,steps", [((20, 36, 32), 15), ((29, 13, 32), 20)])
-def test_vortex_bifluid(lib, n, steps):
-    _parity_run(lib, syn.scaled(syn.VORTEX, *n, steps=steps), steps)
+@pytest.mark.parametrize("n,steps,el_tol", [((20, 36, 32), 15, 1e-8), ((29, 13, 32), 20, 3e-7)])
+def test_vortex_bifluid(lib, n, steps, el_tol):
+    _parity_run(lib, syn.scaled(syn.VORTEX, *n, steps=steps), steps, el_tol=el_tol)
 
 
-@pytest.mark.parametrize("wl,n,steps", [(syn.VORTEX, (20, 36, 32), 100), (syn.DISC_NOISE, (24, 32, 32), 100)])
-def test_primitive_option(lib, wl, n, steps):
+@pytest.mark.parametrize("wl,n,steps,el_tol", [(syn.VORTEX, (20, 36, 32), 100, 2e-9),
+                                               (syn.DISC_NOISE, (24, 32, 32), 100, 1e-7)])
+def test_primitive_option(lib, wl, n, steps, el_tol):
     """The primitive-departure option (not the paper's scheme) over the long
     horizon its conditioning allows."""
-    _parity_run(lib, syn.scaled(wl, *n, steps=steps, recon=syn.RECON_PRIMITIVE), steps)
+    _parity_run(lib, syn.scaled(wl, *n, steps=steps, recon=syn.RECON_PRIMITIVE), steps, el_tol=el_tol)
 
 
 def test_equilibrium_bit_exact(lib):
