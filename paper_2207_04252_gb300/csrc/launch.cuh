@@ -15,11 +15,12 @@ namespace rossbi {
 // Tiles of the stage kernels: 14 x 6 x 6 cells, lines of 16 / 8 / 8 lanes.
 constexpr int F64_TR = 14, F64_TT = 6, F64_TZ = 6, F64_NT = 192;
 constexpr int P32_TR = 14, P32_TT = 6, P32_TZ = 6, P32_NT = 256, P32_MINB = 2;
-// With more than two dust species the FP64-state kernels' staged tile and
-// halo of 14 x 6 x 6 cells no longer fit in shared memory (17 fields:
-// 248 KB): they take tiles two z cells thick (lines of 4 lanes in z).
+// With more than one dust species the FP64-state kernels' staged 14 x 6 x 6
+// tile with its halo (18 x 10 x 10 cells) no longer fits in shared memory
+// (13 fields: 234 KB of the 227 KB a block may have): they take tiles two z
+// cells thick (lines of 4 lanes in z; 13 fields: 127 KB, 21: 205 KB).
 constexpr int THIN_TZ = 2;
-constexpr int tile_z(bool fp64_state, int nf) { return fp64_state && nf > 13 ? THIN_TZ : 6; }
+constexpr int tile_z(bool fp64_state, int nf) { return fp64_state && nf > 9 ? THIN_TZ : 6; }
 
 // Calls f(std::integral_constant<int, NF>) for the field count nf (5 + 4 x
 // the number of dust species, 0 .. 4).

@@ -839,9 +839,9 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
 
   const T tau = (T)(a.tau_frac * (a.dt_dev ? __longlong_as_double((long long)*a.dt_dev) : a.dt_host));
   T dtmin = T(INFINITY);
-  T sums[NF];  // a thread's few cells in T; blocks and the grid are summed in FP64
+  double sums[NF];  // the conservation partials of V E', in FP64 from the first product
 #pragma unroll
-  for (int f = 0; f < NF; ++f) sums[f] = T(0);
+  for (int f = 0; f < NF; ++f) sums[f] = 0.0;
   for (int cidx = threadIdx.x; cidx < NCORE; cidx += NT) {
     const int x = cidx % TR, y = (cidx / TR) % TT, z = cidx / (TR * TT);
     const int gi = i0 + x, gj = j0 + y, gk = k0 + z;
@@ -890,9 +890,9 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
       bool bad = false;
       dtmin = fmin(dtmin, pert_cell_dt<T, NF>(a, ce, gi, E, bad));
       if (bad) status |= STATUS_NONPHYSICAL;
-      const T V = a.t.vol[gi];
+      const double V = g.vol[gi];
 #pragma unroll
-      for (int f = 0; f < NF; ++f) sums[f] += V * E[f];
+      for (int f = 0; f < NF; ++f) sums[f] += V * (double)E[f];
     } else {
       bad_in = !(ce.rho0 + q[RHO] > T(0)) || !(ce.p0 + q[EN] > T(0));
 #pragma unroll
@@ -901,9 +901,10 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
     }
   }
   if (a.stage2) {
-    // warps reduce in the state precision (a warp covers ~80 cells), the
-    // block and the grid in FP64; the sweeps are over, so the start of the
-    // staging area is free (and the epilogue reads only core cells)
+    // threads, warps, the block and the grid sum in FP64 (the CFL minimum,
+    // exact in any precision, stays in the state's); the sweeps are over, so
+    // the start of the staging area is free (the epilogue reads only core
+    // cells, which begin two z planes into it)
     constexpr int NW = NT / 32;
     double* red = reinterpret_cast<double*>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -916,7 +917,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
     if (lane == 0) {
       red[warp * (NF + 1)] = (double)dtmin;
 #pragma unroll
-      for (int f = 0; f < NF; ++f) red[warp * (NF + 1) + 1 + f] = (double)sums[f];
+      for (int f = 0; f < NF; ++f) red[warp * (NF + 1) + 1 + f] = sums[f];
     }
     __syncthreads();
     if (threadIdx.x <= NF) {

@@ -52,3 +52,14 @@ def test_committed_profiles_parse(tag):
         assert float(vals["cells"]) > 0 and float(vals["dram_bytes_per_launch"]) > 0
         assert float(vals["warp_instructions_per_cell"]) > 0
         assert len(vals["source_hash"]) == 16
+
+
+def test_cpu_baseline_uses_every_process():
+    """The CPU baseline runs one oracle process per core it is given and
+    reports the job's throughput over the common wall-clock span."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import synthetic as syn
+    d = bench.cpu_baseline(syn.THROUGHPUT, steps=1, shape=(8, 12, 8), procs=2)
+    assert d["cores"] == 2 and d["kind"] == "oracle" and d["value"] > 0
+    assert d["value"] > d["per_process_value"]  # two processes at once beat one

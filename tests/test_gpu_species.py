@@ -88,8 +88,11 @@ def test_species_parity(lib, reference, form):
     g = W.Grid(w, precision=prec)
     assert g.nf == 5 + 4 * w.n_dust
     s = g.initial_state()
-    np.testing.assert_allclose(g.full_state(s), E0, rtol=1e-6 if form == "fp32_pert" else 1e-14,
-                               atol=1e-6 * np.abs(E0).max() if form == "fp32_pert" else 1e-300)
+    # the two sides build the initial state each from its own equilibrium and
+    # recipe: equal to rounding (float storage in the FP32 form)
+    scale = np.abs(E0).max(axis=(1, 2, 3), keepdims=True)
+    err0 = np.abs(g.full_state(s) - E0) / scale
+    assert err0.max() <= (1e-6 if form == "fp32_pert" else 1e-13), err0.max()
     for dt in dts:
         g.step(s, dt=dt)
     assert g.take_status() == 0
@@ -166,12 +169,21 @@ def test_species_indirect_moments(lib):
     w = _workload(3, (1.0, 0.3, 3.0), (24, 20, 32))
     o = oracle.Oracle(w)
     o.set_indirect(1.0)
+    import torch
+    from tests.test_oracle_indirect import bump
     g = W.Grid(w)
-    s = g.initial_state()
-    s[9:13] *= 1.5  # a lopsided second species would do; a heavier one suffices to move A, B
+    E = bump(g.full_state(g.initial_state()), g.centres(0), g.centres(1), g.centres(2))  # gas and species 0
+    th = g.centres(1)[None, :, None]
+    for b, c in ((9, 4.0), (13, 5.5)):  # the other species off centre elsewhere
+        E[b:b + 4] *= (1.0 + 0.3 * np.exp(-(np.angle(np.exp(1j * (th - c))) / 0.5) ** 2))[None]
+    s = torch.from_numpy(E).cuda()
     ab = g.indirect_moments(s)
-    ref = o.indirect(g.full_state(s))
-    assert np.abs(ab - ref).max() <= 1e-12 * np.hypot(*ref)
+    ref = o.indirect(E)
+    assert np.abs(ab - ref).max() <= 1e-12 * np.hypot(*ref), (ab, ref)
+    # every species counts: without the third species' excess the moments move
+    E2 = E.copy()
+    E2[13:17] = bump(g.full_state(g.initial_state()), g.centres(0), g.centres(1), g.centres(2))[13:17]
+    assert np.abs(o.indirect(E2) - ref).max() > 1e-3 * np.hypot(*ref)
     g.close()
 
 
