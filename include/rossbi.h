@@ -140,6 +140,16 @@ typedef struct {
   double r_edge_in, r_edge_out, period_factor;
 } rossbi_damping_params;
 
+/* Vertical sheared damped boundary (Sect. 2.4 names it, after the works it
+ * cites, without a formula): the equilibrium ghost cells beyond +-z_max
+ * (bc ROSSBI_BC_EQUILIBRIUM in z, the sheared Keplerian flow) and, in
+ * |z| > z_edge, the relaxation of the radial wave-killing zones turned
+ * vertical, with tau = period_factor x the Keplerian orbital period
+ * 2 pi / Omega_K(r) at the cell's radius. */
+typedef struct {
+  double z_edge, period_factor;
+} rossbi_vertical_damping_params;
+
 /* Creates a grid: mesh, metrics and device tables (Sects. 2.2-2.4).
  * cuda_stream: a cudaStream_t (NULL = legacy default stream); not owned.
  * On success *out is a new grid to be freed with rossbi_destroy.
@@ -187,8 +197,9 @@ rossbi_status rossbi_set_indirect(rossbi_grid* g, double x_ref);
  * part of G, so it acts inside both RK stages and in rossbi_adjoint_step.
  * Dust is not damped.  p == NULL switches the zones off (the default);
  * otherwise r_in < r_edge_in <= r_edge_out < r_out and period_factor > 0.
- * Cylindrical grids with a disc equilibrium only.  Allocates an nr-entry
- * table on first use; synchronises the stream.
+ * Cylindrical grids with a disc equilibrium only.  Allocates an nz x nr
+ * rate table (shared with the vertical damped boundary); synchronises the
+ * stream.
  * Errors: ROSSBI_ERR_ARG, ROSSBI_ERR_OOM, ROSSBI_ERR_CUDA. */
 rossbi_status rossbi_set_damping(rossbi_grid* g, const rossbi_damping_params* p);
 
@@ -224,6 +235,18 @@ rossbi_status rossbi_unpack_theta_rows(rossbi_grid* g, void* const* state, int j
  * Default: every factor 1.  Takes effect from the next step.
  * Errors: ROSSBI_ERR_ARG (NULL, n != n_dust, n_dust = 0, a bad factor). */
 rossbi_status rossbi_set_dust_species(rossbi_grid* g, const double* stokes_factor, int n);
+
+/* The vertical sheared damped boundary (rossbi_vertical_damping_params).
+ * Inside |z| > z_edge the five conservative gas departures relax towards the
+ * equilibrium, dE'/dt = -E' R(z) / tau(r), R the parabola that is 1 at
+ * |z| = z_max and 0, with zero slope, at z_edge (rates tabulated at cell
+ * centres); the rate adds to the radial zones' and, like it, is a term of G
+ * (both RK stages and rossbi_adjoint_step).  Dust is not damped.  p == NULL
+ * switches it off (the default); otherwise 0 <= z_edge < z_max and
+ * period_factor > 0.  Cylindrical grids with a disc equilibrium, symmetric
+ * about z = 0, only.  Synchronises the stream.
+ * Errors: ROSSBI_ERR_ARG, ROSSBI_ERR_OOM, ROSSBI_ERR_CUDA. */
+rossbi_status rossbi_set_vertical_damping(rossbi_grid* g, const rossbi_vertical_damping_params* p);
 
 /* The disc moments (A_disc, B_disc) of Sect. 2.10 of a state, without the
  * constant X_ref: the sums over cells of V (rho - rho_0 + rho_d) r cos(theta)

@@ -86,6 +86,9 @@ def lib():
         L.orc_sources.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]
         L.orc_set_species_stokes.argtypes = [ctypes.c_void_p, _D, ctypes.c_int]
         L.orc_set_recon.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.orc_set_vertical_damping.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]
+        L.orc_damping_rate.restype = ctypes.c_double
+        L.orc_damping_rate.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
         L.orc_recon_faces.argtypes = [ctypes.c_void_p, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       _D, _D]
         _lib = L
@@ -186,6 +189,16 @@ class Oracle:
         period_factor <= 0 switches them off."""
         if lib().orc_set_damping(self.h, float(r_ein), float(r_eout), float(period_factor)):
             raise ValueError("damping zones must lie inside the radial extent of a cylindrical grid")
+
+    def set_vertical_damping(self, z_edge, period_factor=1.0):
+        """Vertical sheared damped boundary (reading R21): relaxation in
+        |z| > z_edge; a period_factor <= 0 switches it off."""
+        if lib().orc_set_vertical_damping(self.h, float(z_edge), float(period_factor)):
+            raise ValueError("the vertical zone must lie inside a cylindrical grid symmetric about z = 0")
+
+    def damping_rate(self, i, k):
+        """Relaxation rate of the damping zones at cell (i, k) (R17 + R21)."""
+        return lib().orc_damping_rate(self.h, int(i), int(k))
 
     def sources(self, i, j, k, U):
         """App. B source vector per unit volume of the state U at cell (i, j, k)."""

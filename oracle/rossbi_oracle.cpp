@@ -84,6 +84,15 @@
 //      profile and the constants, which come from the cited work: the pins
 //      check the structure (local, linear, gas-only, the parabola through
 //      its end conditions, the period) and the equilibrium.
+//  R21 vertical sheared damped boundary (Sect. 2.4 names it, after the works
+//      it cites, with no formula): the ghost cells beyond z = +-z_max carry
+//      the sheared equilibrium flow (E' = 0, the equilibrium boundary of
+//      Sect. 2.4), and in |z| > z_e the five conservative gas departures
+//      relax towards it as in R17, dE'/dt = -E' R(z) / tau(r), with R the
+//      parabola that is 1 at |z| = z_max and 0 (zero slope) at |z| = z_e, and
+//      tau = f x the Keplerian orbital period at the cell's radius.  Its rate
+//      adds to R17's radial one.  Parity unpinned for the profile and the
+//      constants, as for R17.
 //  R19 Stokes regime (Sect. 2.9, drag law 2): the Epstein stopping time of
 //      law 1 applies while r_p <= 9 lambda / 4; above, t_s = (4/9)(r_p/lambda)
 //      t_E (continuous at the switch).  The mean free path is lambda =
@@ -166,6 +175,8 @@ struct Oracle {
   double x_ind = 0.0;      // X_ref of the indirect-gravity term (Sect. 2.10), 0 = off
   bool damp = false;       // wave-killing zones of reading R17
   double damp_ein = 0.0, damp_eout = 0.0, damp_tau_in = 0.0, damp_tau_out = 0.0;
+  bool damp_z = false;     // vertical sheared damped boundary of reading R21
+  double damp_ze = 0.0, damp_zf = 0.0;
   double kappa = 0.0;      // r_p / lambda_0 of the Stokes regime (reading R19)
   int nd = 0;              // dust species
   int recon = RECON_CONSERVATIVE;  // gas reconstruction (reading R2)
@@ -811,19 +822,30 @@ static void indirect_moments(const Oracle& o, const Acc& E, T gind[2]) {
 }
 
 // Reading R17: relaxation rate R(r) / tau of the wave-killing zones at the
-// centre of radial cell i (0 in the interior).
-static double damping_rate(const Oracle& o, int i) {
-  if (!o.damp) return 0.0;
-  const double r = XC(o, 0, i), rin = o.d.x0[0], rout = o.d.x1[0];
-  if (r < o.damp_ein) {
-    const double x = (o.damp_ein - r) / (o.damp_ein - rin);
-    return x * x / o.damp_tau_in;
+// centre of radial cell i (0 in the interior), plus reading R21's vertical
+// rate at the centre of cell (i, k).
+static double damping_rate(const Oracle& o, int i, int k) {
+  double rate = 0.0;
+  const double r = XC(o, 0, i);
+  if (o.damp) {
+    const double rin = o.d.x0[0], rout = o.d.x1[0];
+    if (r < o.damp_ein) {
+      const double x = (o.damp_ein - r) / (o.damp_ein - rin);
+      rate = x * x / o.damp_tau_in;
+    } else if (r > o.damp_eout) {
+      const double x = (r - o.damp_eout) / (rout - o.damp_eout);
+      rate = x * x / o.damp_tau_out;
+    }
   }
-  if (r > o.damp_eout) {
-    const double x = (r - o.damp_eout) / (rout - o.damp_eout);
-    return x * x / o.damp_tau_out;
+  if (o.damp_z) {
+    const double az = std::fabs(XC(o, 2, k)), zmax = o.d.x1[2];
+    if (az > o.damp_ze) {
+      const double x = (az - o.damp_ze) / (zmax - o.damp_ze);
+      const double tau = o.damp_zf * 2.0 * M_PI / std::sqrt(o.d.gm / (r * r * r));
+      rate += x * x / tau;
+    }
   }
-  return 0.0;
+  return rate;
 }
 
 // ---------------------------------------------------------------- G(E) per cell
@@ -866,7 +888,7 @@ static void G_cell(Oracle& o, const Acc& E, int i, int j, int k, T G[NFMAX], con
     if (U[5 + 4 * sp + 3] < 0.0) o.status |= ST_NONPHYSICAL;
   sources(o, i, j, k, U, gind, S);
   for (int f = 0; f < o.nf; ++f) G[f] += m.V * S[f];
-  const double kd = damping_rate(o, i);  // reading R17
+  const double kd = damping_rate(o, i, k);  // readings R17, R21
   if (kd != 0.0)
     for (int f = 0; f < 5; ++f) G[f] -= m.V * kd * (U[f] - (o.has_eq ? E0C(o, i, k)[f] : 0.0));
 }
@@ -1242,6 +1264,23 @@ int orc_set_damping(void* h, double r_ein, double r_eout, double f) {
   o.damp_tau_out = f * 2.0 * M_PI / std::sqrt(o.d.gm / (rout * rout * rout));
   return 0;
 }
+
+// Vertical sheared damped boundary of reading R21: |z| > z_edge relaxes the
+// gas departures with tau = f x the local orbital period; f <= 0 switches it
+// off.  Cylindrical grids symmetric about z = 0 only.
+int orc_set_vertical_damping(void* h, double z_edge, double f) {
+  Oracle& o = *(Oracle*)h;
+  o.damp_z = false;
+  if (!(f > 0.0)) return 0;
+  if (o.d.geometry != GEOM_CYL || !(o.d.x0[2] == -o.d.x1[2]) || !(z_edge >= 0.0) || !(z_edge < o.d.x1[2])) return 1;
+  o.damp_z = true;
+  o.damp_ze = z_edge;
+  o.damp_zf = f;
+  return 0;
+}
+
+// Relaxation rate of the damping zones (readings R17, R21) at cell (i, k).
+double orc_damping_rate(void* h, int i, int k) { return damping_rate(*(Oracle*)h, i, k); }
 
 // App. B source vector per unit volume of the state U (nf values) at the
 // centre of cell (i, j, k), without the indirect term.

@@ -588,7 +588,7 @@ __global__ void __launch_bounds__(ADJ_PT_NT) adj_point_kernel(const AdjPointArgs
       }
       sources_vjp(g, gi, gk, E, s, src);
       if (g.damp_k) {  // wave-killing zones: d(-V k E'_f)/dE_f = -V k
-        const double kd = g.damp_k[gi];
+        const double kd = g.damp_k[(size_t)gk * g.nr + gi];
 #pragma unroll
         for (int f = 0; f < 5; ++f) src[f] -= kd * s[f];
       }

@@ -55,8 +55,9 @@ struct DevGrid {
   const double* ind_cs;
   const double* ind_g;
   const float* ind_gf;
-  // wave-killing zones (Sect. 2.4; de Val-Borro et al. 2006 relaxation):
-  // rate R(r) / tau of radial cell i [nr] in double and in float, or null
+  // damping zones (Sect. 2.4; the de Val-Borro et al. 2006 relaxation): the
+  // rate of the radial wave-killing zones plus that of the vertical damped
+  // boundary at each cell centre [nz][nr], in double and in float, or null
   const double* damp_k;
   const float* damp_kf;
   // dust species s has the Stokes number St x st_factor[s] (st_factor[0] = 1)

@@ -67,7 +67,11 @@ struct rossbi_grid {
   double* d_ind = nullptr;
   double* d_adj_ind = nullptr;         // adjoint of the indirect term: [2 stages][2][adj_blocks] partials,
                                        // [2 stages][2] reduced, [2][nth] stage-1 gradient table
-  double* d_damp = nullptr;            // wave-killing rates R(r) / tau per radial cell [nr]
+  double* d_damp = nullptr;            // relaxation rates of the damping zones per cell centre [nz][nr]
+                                       // in double, then [nz][nr] in float
+  bool damp_r = false, damp_z = false; // radial wave-killing zones; vertical sheared damped boundary
+  rossbi_damping_params damp_rp{};
+  rossbi_vertical_damping_params damp_zp{};
   int adj_blocks = 0;
   // stage-kernel timing (rossbi_profile_*)
   bool profiling = false;
@@ -1441,42 +1445,92 @@ rossbi_status rossbi_set_indirect(rossbi_grid* g, double x_ref) {
   return ROSSBI_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// The rate table of the damping zones, per cell centre (nz, nr): the radial
+// wave-killing zones (a parabola in r, 1 / tau at the boundary, 0 with zero
+// slope at the zone edge, tau = f x the orbital period at that boundary)
+// plus the vertical damped boundary (the same parabola in |z|, tau = f x the
+// orbital period at the cell's radius).  Both off: no table.
+rossbi_status build_damping(rossbi_grid* g) {
+  const rossbi_grid_desc& d = g->desc;
+  g->dg.damp_k = nullptr;
+  g->dg.damp_kf = nullptr;
+  if (!g->damp_r && !g->damp_z) return ROSSBI_OK;
+  const double pi = 3.14159265358979323846;
+  const double rin = d.x0[0], rout = d.x1[0], zmax = d.x1[2], dz = (d.x1[2] - d.x0[2]) / d.nz;
+  const size_t n = (size_t)d.nz * d.nr;
+  std::vector<double> k(n + (n + 1) / 2, 0.0);  // rates, then the same as floats
+  const rossbi_damping_params& p = g->damp_rp;
+  const double tau_in = p.period_factor * 2.0 * pi / std::sqrt(d.gm / (rin * rin * rin));
+  const double tau_out = p.period_factor * 2.0 * pi / std::sqrt(d.gm / (rout * rout * rout));
+  for (int kk = 0; kk < d.nz; ++kk) {
+    const double az = std::fabs(d.x0[2] + (kk + 0.5) * dz);
+    for (int i = 0; i < d.nr; ++i) {
+      const double r = axis0_centre(d, i);
+      double rate = 0.0;
+      if (g->damp_r) {
+        if (r < p.r_edge_in) {
+          const double x = (p.r_edge_in - r) / (p.r_edge_in - rin);
+          rate = x * x / tau_in;
+        } else if (r > p.r_edge_out) {
+          const double x = (r - p.r_edge_out) / (rout - p.r_edge_out);
+          rate = x * x / tau_out;
+        }
+      }
+      if (g->damp_z && az > g->damp_zp.z_edge) {
+        const double x = (az - g->damp_zp.z_edge) / (zmax - g->damp_zp.z_edge);
+        rate += x * x / (g->damp_zp.period_factor * 2.0 * pi / std::sqrt(d.gm / (r * r * r)));
+      }
+      k[(size_t)kk * d.nr + i] = rate;
+    }
+  }
+  std::vector<float> kf(n);
+  for (size_t q = 0; q < n; ++q) kf[q] = (float)k[q];
+  std::memcpy(k.data() + n, kf.data(), n * sizeof(float));
+  rossbi_status st = upload(&g->d_damp, k, g->stream);
+  if (st == ROSSBI_OK && cudaStreamSynchronize(g->stream) != cudaSuccess) st = ROSSBI_ERR_CUDA;
+  if (st != ROSSBI_OK) return st;
+  g->dg.damp_k = g->d_damp;
+  g->dg.damp_kf = reinterpret_cast<const float*>(g->d_damp + n);
+  return ROSSBI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 rossbi_status rossbi_set_damping(rossbi_grid* g, const rossbi_damping_params* p) {
   if (!g) return ROSSBI_ERR_ARG;
   if (!p) {
-    g->dg.damp_k = nullptr;
-    return ROSSBI_OK;
+    g->damp_r = false;
+    return build_damping(g);
   }
   const rossbi_grid_desc& d = g->desc;
   const double rin = d.x0[0], rout = d.x1[0];
   if (d.geometry != ROSSBI_GEOM_CYL || !g->eq_set || !g->has_disc) return ROSSBI_ERR_ARG;
   if (!(p->r_edge_in > rin) || !(p->r_edge_out < rout) || !(p->r_edge_in <= p->r_edge_out)) return ROSSBI_ERR_ARG;
   if (!(p->period_factor > 0.0) || !std::isfinite(p->period_factor)) return ROSSBI_ERR_ARG;
-  const double pi = 3.14159265358979323846;
-  const double tau_in = p->period_factor * 2.0 * pi / std::sqrt(d.gm / (rin * rin * rin));
-  const double tau_out = p->period_factor * 2.0 * pi / std::sqrt(d.gm / (rout * rout * rout));
-  std::vector<double> k(d.nr + (d.nr + 1) / 2, 0.0);  // rates, then the same as floats
-  for (int i = 0; i < d.nr; ++i) {  // parabola: 1 at the boundary, 0 with zero slope at the zone edge
-    const double r = axis0_centre(d, i);
-    if (r < p->r_edge_in) {
-      const double x = (p->r_edge_in - r) / (p->r_edge_in - rin);
-      k[i] = x * x / tau_in;
-    } else if (r > p->r_edge_out) {
-      const double x = (r - p->r_edge_out) / (rout - p->r_edge_out);
-      k[i] = x * x / tau_out;
-    }
+  g->damp_r = true;
+  g->damp_rp = *p;
+  return build_damping(g);
+}
+
+rossbi_status rossbi_set_vertical_damping(rossbi_grid* g, const rossbi_vertical_damping_params* p) {
+  if (!g) return ROSSBI_ERR_ARG;
+  if (!p) {
+    g->damp_z = false;
+    return build_damping(g);
   }
-  std::vector<float> kf(d.nr);
-  for (int i = 0; i < d.nr; ++i) kf[i] = (float)k[i];
-  std::memcpy(k.data() + d.nr, kf.data(), d.nr * sizeof(float));
-  g->dg.damp_k = nullptr;
-  g->dg.damp_kf = nullptr;
-  rossbi_status st = upload(&g->d_damp, k, g->stream);
-  if (st == ROSSBI_OK && cudaStreamSynchronize(g->stream) != cudaSuccess) st = ROSSBI_ERR_CUDA;
-  if (st != ROSSBI_OK) return st;
-  g->dg.damp_k = g->d_damp;
-  g->dg.damp_kf = reinterpret_cast<const float*>(g->d_damp + d.nr);
-  return ROSSBI_OK;
+  const rossbi_grid_desc& d = g->desc;
+  if (d.geometry != ROSSBI_GEOM_CYL || !g->eq_set || !g->has_disc || !(d.x0[2] == -d.x1[2])) return ROSSBI_ERR_ARG;
+  if (!(p->z_edge >= 0.0) || !(p->z_edge < d.x1[2])) return ROSSBI_ERR_ARG;
+  if (!(p->period_factor > 0.0) || !std::isfinite(p->period_factor)) return ROSSBI_ERR_ARG;
+  g->damp_z = true;
+  g->damp_zp = *p;
+  return build_damping(g);
 }
 
 rossbi_status theta_rows(rossbi_grid* g, void* const* state, int j0, int rows, void* buf, int unpack) {

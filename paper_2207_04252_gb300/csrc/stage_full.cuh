@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(NT, 1) stage_full_kernel(const StageArgs a) {
       for (int f = 0; f < 5; ++f) G[f] -= g.r0[((size_t)f * g.nz + gk) * g.nr + gi];
     }
     if (XT && g.damp_k) {  // wave-killing zones: the gas departures relax towards E0
-      const double kd = g.damp_k[gi];
+      const double kd = g.damp_k[(size_t)gk * g.nr + gi];
       if (kd != 0.0) {
         const double V = g.vol[gi];
 #pragma unroll

@@ -870,8 +870,8 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
     }
     if (XT && g.damp_k) {  // wave-killing zones: the gas departures E' relax towards 0
       T kd;
-      if constexpr (sizeof(T) == 4) kd = g.damp_kf[gi];
-      else kd = g.damp_k[gi];
+      if constexpr (sizeof(T) == 4) kd = g.damp_kf[(size_t)gk * g.nr + gi];
+      else kd = g.damp_k[(size_t)gk * g.nr + gi];
       if (kd != T(0)) {
         const T V = a.t.vol[gi];
 #pragma unroll

@@ -26,7 +26,7 @@ ROSSBI_RECON_CONSERVATIVE, ROSSBI_RECON_PRIMITIVE = 0, 1
 
 # every function declared in include/rossbi.h
 EXPORTS = (
-    "rossbi_init_grid", "rossbi_set_equilibrium", "rossbi_set_indirect", "rossbi_indirect_moments", "rossbi_set_damping", "rossbi_set_dust_species", "rossbi_pack_theta_rows",
+    "rossbi_init_grid", "rossbi_set_equilibrium", "rossbi_set_indirect", "rossbi_indirect_moments", "rossbi_set_damping", "rossbi_set_vertical_damping", "rossbi_set_dust_species", "rossbi_pack_theta_rows",
     "rossbi_unpack_theta_rows", "rossbi_get_equilibrium", "rossbi_cfl_dt", "rossbi_step",
     "rossbi_step_host", "rossbi_step_noalloc", "rossbi_adjoint_step", "rossbi_adjoint_dstokes",
     "rossbi_conservation_sums", "rossbi_fallback_count", "rossbi_take_status", "rossbi_profile_enable",
@@ -56,6 +56,10 @@ class rossbi_damping_params(ctypes.Structure):
     _fields_ = [("r_edge_in", ctypes.c_double), ("r_edge_out", ctypes.c_double), ("period_factor", ctypes.c_double)]
 
 
+class rossbi_vertical_damping_params(ctypes.Structure):
+    _fields_ = [("z_edge", ctypes.c_double), ("period_factor", ctypes.c_double)]
+
+
 class RossbiError(RuntimeError):
     def __init__(self, code, where):
         self.code = code
@@ -82,6 +86,7 @@ def load(path: str = LIB_PATH):
     L.rossbi_indirect_moments.argtypes = [_VP, _PP, _DP]
     L.rossbi_set_damping.argtypes = [_VP, ctypes.POINTER(rossbi_damping_params)]
     L.rossbi_set_dust_species.argtypes = [_VP, _DP, ctypes.c_int]
+    L.rossbi_set_vertical_damping.argtypes = [_VP, ctypes.POINTER(rossbi_vertical_damping_params)]
     L.rossbi_pack_theta_rows.argtypes = [_VP, _PP, ctypes.c_int, ctypes.c_int, _VP]
     L.rossbi_unpack_theta_rows.argtypes = [_VP, _PP, ctypes.c_int, ctypes.c_int, _VP]
     L.rossbi_get_equilibrium.argtypes = [_VP, _DP]
@@ -221,6 +226,12 @@ def rossbi_set_damping(grid, zones):
     """Wave-killing zones (r_edge_in, r_edge_out, period_factor), or None for off."""
     p = None if zones is None else ctypes.byref(rossbi_damping_params(*map(float, zones)))
     _check(load().rossbi_set_damping(grid, p), "rossbi_set_damping")
+
+
+def rossbi_set_vertical_damping(grid, zone):
+    """Vertical sheared damped boundary (z_edge, period_factor), or None for off."""
+    p = None if zone is None else ctypes.byref(rossbi_vertical_damping_params(*map(float, zone)))
+    _check(load().rossbi_set_vertical_damping(grid, p), "rossbi_set_vertical_damping")
 
 
 def rossbi_set_dust_species(grid, stokes_factors):

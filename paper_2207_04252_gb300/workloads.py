@@ -78,6 +78,10 @@ class Grid:
         """Wave-killing zones (r_edge_in, r_edge_out, period_factor), or None."""
         R.rossbi_set_damping(self.h, zones)
 
+    def set_vertical_damping(self, zone):
+        """Vertical sheared damped boundary (z_edge, period_factor), or None."""
+        R.rossbi_set_vertical_damping(self.h, zone)
+
     def indirect_moments(self, state):
         """(A_disc, B_disc) of Sect. 2.10 of a state, FP64."""
         return R.rossbi_indirect_moments(self.h, state)

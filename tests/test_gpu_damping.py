@@ -135,3 +135,93 @@ def test_argument_errors(lib):
         box.set_damping((0.2, 0.8, 1.0))
     box.set_damping(None)
     box.close()
+
+
+# ---------------------------------------------------------------- vertical sheared damped boundary (reading R21)
+ZONE_Z = (0.06, 0.01)
+
+
+def _reference_z(w, steps, with_radial):
+    o = oracle.Oracle(w)
+    E0 = oracle.initial_state(o)
+    if with_radial:
+        o.set_damping(*ZONES)
+    o.set_vertical_damping(*ZONE_Z)
+    E, _, dts = o.run(E0.copy(), steps=steps)
+    assert o.take_status() == 0
+    o.set_vertical_damping(ZONE_Z[0], 0.0)
+    E_off, _, _ = o.run(E0.copy(), dts=dts)
+    return o, E, E_off, dts
+
+
+@pytest.fixture(scope="module", params=["disc", "vortex_with_radial"])
+def reference_z(request):
+    if request.param == "disc":
+        w = syn.scaled(syn.DISC_NOISE, 24, 20, 32)
+        return (w, False) + _reference_z(w, 40, False)
+    w = syn.scaled(syn.VORTEX, 24, 20, 32)
+    return (w, True) + _reference_z(w, 15, True)
+
+
+@pytest.mark.parametrize("form", ["fp64", "fp64_pert", "fp32_pert"])
+def test_vertical_damping_parity(lib, reference_z, form):
+    R, W = lib
+    w, with_radial, o, E_ref, E_off, dts = reference_z
+    prec = {"fp64": R.ROSSBI_FP64, "fp64_pert": R.ROSSBI_FP64_PERT, "fp32_pert": R.ROSSBI_FP32_PERT}[form]
+    tol = 1e-5 if form == "fp32_pert" else 1e-12
+    g = W.Grid(w, precision=prec)
+    if with_radial:
+        g.set_damping(ZONES)
+    g.set_vertical_damping(ZONE_Z)
+    s = g.initial_state("cuda")
+    for dt in dts:
+        g.step(s, dt=dt)
+    assert g.take_status() == 0
+    V = o.volumes()
+    errs = rel_l1(g.full_state(s), E_ref, V)
+    assert all(e <= tol for e in errs.values()), errs
+    Eq = o.equilibrium_state()
+    dev = np.abs(E_off - E_ref)[4].sum() / np.abs(E_ref - Eq)[4].sum()
+    assert dev > 20 * tol, dev
+    g.close()
+
+
+def test_vertical_damping_adjoint_and_equilibrium(lib):
+    import torch
+    R, W = lib
+    w = syn.scaled(syn.VORTEX, 20, 18, 32)
+    o = oracle.Oracle(w)
+    o.set_damping(*ZONES)
+    o.set_vertical_damping(*ZONE_Z)
+    rng = np.random.default_rng(5)
+    E0 = jitter(oracle.initial_state(o), w.gamma, rng, 1e-3)
+    dt = o.cfl_dt(E0)
+    scale = np.abs(E0).mean(axis=(1, 2, 3), keepdims=True) + 1e-30
+    lam = rng.standard_normal(E0.shape) / scale
+    delta = rng.standard_normal(E0.shape) * scale
+    _, t = o.step_tlm(E0, delta, dt)
+    assert o.take_status() == 0
+    g = W.Grid(w)
+    g.set_damping(ZONES)
+    g.set_vertical_damping(ZONE_Z)
+    lam_d = torch.from_numpy(lam).cuda().contiguous()
+    g.adjoint_step(torch.from_numpy(E0).cuda().contiguous(), dt, lam_d)
+    assert g.take_status() == 0
+    lhs, rhs = float((lam * t).sum()), float((lam_d.cpu().numpy() * delta).sum())
+    assert abs(lhs - rhs) <= 1e-12 * float(np.abs(lam * t).sum()), (lhs, rhs)
+    # an undisturbed disc stays bit for bit
+    g2 = W.Grid(replace(syn.scaled(syn.DISC_NOISE, 24, 20, 32), noise_amp=0.0))
+    g2.set_vertical_damping(ZONE_Z)
+    s = g2.initial_state("cuda")
+    s0 = s.clone()
+    dt2 = g2.cfl_dt(s)
+    for _ in range(5):
+        g2.step(s, dt=dt2)
+    assert bool(torch.equal(s, s0))
+    for bad in ((-0.01, 1.0), (0.2, 1.0), (0.06, 0.0), (0.06, float("inf"))):
+        with pytest.raises(R.RossbiError) as e:
+            g2.set_vertical_damping(bad)
+        assert e.value.code == R.ROSSBI_ERR_ARG
+    g2.set_vertical_damping(None)
+    g.close()
+    g2.close()
