@@ -15,6 +15,9 @@ Recipes (all on the library's equilibrium E0):
            u' = (1/r) dpsi/dtheta, v' = -dpsi/dr, rho and P at equilibrium.
            Dust: rho_d = ratio rho0 (1 + a_d xi_d), moving with the gas; with
            several species each takes ratio / n of it, with its own noise.
+  rwi    : rho = rho0 (1 + delta G), G a radial Gaussian at r0, at the
+           equilibrium temperature (P scaled alike, velocities kept), and the
+           seed v_r = eps v_theta0 sin(m theta) G (v_theta0 inertial).
 """
 import math
 
@@ -189,6 +192,19 @@ class Grid:
             Ep[syn.F_RHO] = drho
             Ep[syn.F_MV] = drho * v0
             Ep[syn.F_EN] = 0.5 * drho * v0 * v0
+            return Ep
+        if w.ic == "rwi":  # density bump at the equilibrium temperature, seeded v_r of mode m
+            r = self.centres(0)[None, None, :]
+            th = self.centres(1)[None, :, None]
+            G = np.exp(-((r - w.rwi_r0) / (math.sqrt(2.0) * w.rwi_width)) ** 2)
+            P0 = (g - 1.0) * (E0[syn.F_EN][:, None, :] - 0.5 * rho0 * v0 * v0)
+            vth0 = v0 + w.omega_frame * r  # the inertial equilibrium azimuthal velocity
+            vr = w.rwi_eps * vth0 * np.sin(w.rwi_mode * th) * G
+            drho = rho0 * w.rwi_delta * G
+            Ep[syn.F_RHO] = drho
+            Ep[syn.F_MU] = (rho0 + drho) * vr
+            Ep[syn.F_MV] = drho * v0
+            Ep[syn.F_EN] = 0.5 * drho * v0 * v0 + 0.5 * (rho0 + drho) * vr * vr + P0 * w.rwi_delta * G / (g - 1.0)
             return Ep
         if w.ic != "vortex":
             raise ValueError(w.ic)

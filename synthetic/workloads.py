@@ -44,7 +44,7 @@ class Workload:
     x1: tuple
     bc_lo: tuple
     bc_hi: tuple
-    ic: str                      # "sod", "noise", "vortex", "explosion"
+    ic: str                      # "sod", "noise", "vortex", "explosion", "rwi"
     steps: int
     gamma: float = 1.4
     gm: float = 1.0
@@ -67,6 +67,11 @@ class Workload:
     checkpoint_every: int = 0
     recon: int = RECON_CONSERVATIVE
     dust_stokes_factors: tuple = ()  # several species: St of species s = stokes x factor[s] (factor[0] = 1)
+    rwi_mode: int = 0            # "rwi": azimuthal mode m of the seed
+    rwi_delta: float = 0.0       # relative amplitude of the density bump
+    rwi_width: float = 0.0       # Delta_r of the bump
+    rwi_eps: float = 0.0         # seed amplitude, v_r = eps v_theta0 sin(m theta) G(r)
+    rwi_r0: float = 1.0          # radius of the bump
 
     @property
     def ncell(self) -> int:
@@ -120,6 +125,16 @@ THROUGHPUT = _disc("bifluid_two_vortices_512x1024x128", 512, 1024, 128, 50, ic="
                    seed=4252, vortices=((0.8, 0.0), (1.3, math.pi)), dust_ratio=0.01, dust_noise=1e-3,
                    stokes=0.05)
 
+# Rossby wave instability (Sect. 4.3): a radial Gaussian density bump on the
+# equilibrium, rho = rho0 (1 + delta G), G = exp(-((r - r0)/(sqrt(2) Delta_r))^2),
+# at the equilibrium temperature (P scaled alike, velocities kept), and the
+# seed v_r = eps v_theta0 sin(m theta) G with eps = 1e-4 and mode m.  The paper
+# takes the setup of Meheut et al. (2012) without printing delta and Delta_r:
+# delta = 0.25 and Delta_r = 0.05 r0 (= H(r0)) here.  Gas only, in the
+# equal-Mach frame; growth rates of the modes are measured, not pinned.
+RWI = _disc("rwi_m4_128x256x32", 128, 256, 32, 2000, ic="rwi", rwi_mode=4, rwi_delta=0.25, rwi_width=0.05,
+            rwi_eps=1e-4, omega_frame=equal_mach_frame(0.5, 2.0))
+
 # Cylindrical explosion (Sect. 4.1; Toro ch. 17): a 2-D Riemann problem on the
 # polar mesh, (rho, P) = (1, 1) for r <= 0.4 and (0.125, 0.1) outside, at rest;
 # no gravity, no rotation, no equilibrium, gamma = 1.4; N_r x N_theta =
@@ -134,7 +149,7 @@ EXPLOSION = Workload(
     bc_lo=(BC_OUTFLOW, BC_PERIODIC, BC_PERIODIC), bc_hi=(BC_OUTFLOW, BC_PERIODIC, BC_PERIODIC),
     ic="explosion", steps=0, gm=0.0, omega_frame=0.0, t_end=0.25)
 
-ALL = (SOD, DISC_NOISE, VORTEX, ADJOINT, THROUGHPUT, EXPLOSION)
+ALL = (SOD, DISC_NOISE, VORTEX, ADJOINT, THROUGHPUT, EXPLOSION, RWI)
 
 
 def by_name(name: str) -> Workload:
