@@ -15,9 +15,10 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librossbi.so")
 SOURCES = [os.path.join(CSRC, f) for f in
-           ("rossbi.cu", "k_stage_full.cu", "k_stage_pert_f32.cu", "k_stage_pert_f32_gen.cu",
-            "k_stage_pert_f64.cu", "k_adjoint.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")] + \
+           ("k_stage_full.cu", "k_stage_full_prim.cu", "k_stage_pert_f32.cu", "k_stage_pert_f32_prim.cu",
+            "k_stage_pert_f32_gen.cu", "k_stage_pert_f32_gen_prim.cu", "k_stage_pert_f64.cu",
+            "k_stage_pert_f64_prim.cu", "k_adjoint.cu", "rossbi.cu")]
+DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".cu"))] + \
     [os.path.join(ROOT, "include", "rossbi.h"), os.path.abspath(__file__)]
 
 COMPILE_FLAGS = [

@@ -1,6 +1,15 @@
 // Launcher of the FP32 perturbation-form stage kernel (stage_pert.cuh) for
-// gamma = 7/5 (the integer-power forms of the solver).
+// one power form of the solver (ROSSBI_POW: the gamma = 7/5 integer powers
+// unless the including translation unit chose the general ones) and one gas
+// reconstruction mode (ROSSBI_RC, conservative unless chosen otherwise).
 #include "launch.cuh"
+
+#ifndef ROSSBI_RC
+#define ROSSBI_RC RECON_CONS
+#endif
+#ifndef ROSSBI_POW
+#define ROSSBI_POW PowG75
+#endif
 
 namespace rossbi {
 namespace {
@@ -19,20 +28,14 @@ cudaError_t launch(const PertArgs<float>& a, int nblocks, cudaStream_t s) {
 
 }  // namespace
 
-template <class P>
-cudaError_t run_stage_pert_f32_p(const PertArgs<float>& a, int nblocks, cudaStream_t s, bool xt) {
+template <class P, int RC>
+cudaError_t run_stage_pert_f32_rc(const PertArgs<float>& a, int nblocks, cudaStream_t s, bool xt) {
   return by_nf(a.g.nf, [&](auto nf) {
     constexpr int NF = decltype(nf)::value;
-    if (a.g.recon == RECON_PRIM)
-      return xt ? launch<NF, P, true, RECON_PRIM>(a, nblocks, s) : launch<NF, P, false, RECON_PRIM>(a, nblocks, s);
-    return xt ? launch<NF, P, true, RECON_CONS>(a, nblocks, s) : launch<NF, P, false, RECON_CONS>(a, nblocks, s);
+    return xt ? launch<NF, P, true, RC>(a, nblocks, s) : launch<NF, P, false, RC>(a, nblocks, s);
   });
 }
 
-#ifndef ROSSBI_F32_GENERIC_GAMMA
-template cudaError_t run_stage_pert_f32_p<PowG75>(const PertArgs<float>&, int, cudaStream_t, bool);
-#else
-template cudaError_t run_stage_pert_f32_p<PowGeneric<float>>(const PertArgs<float>&, int, cudaStream_t, bool);
-#endif
+template cudaError_t run_stage_pert_f32_rc<ROSSBI_POW, ROSSBI_RC>(const PertArgs<float>&, int, cudaStream_t, bool);
 
 }  // namespace rossbi

@@ -1,5 +1,11 @@
-// Launcher of the FP64 perturbation-form stage kernel (stage_pert.cuh).
+// Launcher of the FP64 perturbation-form stage kernel (stage_pert.cuh) for
+// one gas reconstruction mode (ROSSBI_RC, conservative unless the including
+// translation unit chose another).
 #include "launch.cuh"
+
+#ifndef ROSSBI_RC
+#define ROSSBI_RC RECON_CONS
+#endif
 
 namespace rossbi {
 namespace {
@@ -16,20 +22,17 @@ cudaError_t launch(const PertArgs<double>& a, int nblocks, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int NF, int RC>
-cudaError_t launch_x(const PertArgs<double>& a, int nblocks, cudaStream_t s, bool xt) {
-  constexpr int TZ = tile_z(true, NF);
-  return xt ? launch<NF, TZ, true, RC>(a, nblocks, s) : launch<NF, TZ, false, RC>(a, nblocks, s);
-}
-
 }  // namespace
 
-cudaError_t run_stage_pert_f64(const PertArgs<double>& a, int nblocks, cudaStream_t s, bool xt) {
+template <int RC>
+cudaError_t run_stage_pert_f64_rc(const PertArgs<double>& a, int nblocks, cudaStream_t s, bool xt) {
   return by_nf(a.g.nf, [&](auto nf) {
     constexpr int NF = decltype(nf)::value;
-    return a.g.recon == RECON_PRIM ? launch_x<NF, RECON_PRIM>(a, nblocks, s, xt)
-                                   : launch_x<NF, RECON_CONS>(a, nblocks, s, xt);
+    constexpr int TZ = tile_z(true, NF);
+    return xt ? launch<NF, TZ, true, RC>(a, nblocks, s) : launch<NF, TZ, false, RC>(a, nblocks, s);
   });
 }
+
+template cudaError_t run_stage_pert_f64_rc<ROSSBI_RC>(const PertArgs<double>&, int, cudaStream_t, bool);
 
 }  // namespace rossbi

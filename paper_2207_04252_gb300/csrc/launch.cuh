@@ -22,6 +22,15 @@ constexpr int P32_TR = 14, P32_TT = 6, P32_TZ = 6, P32_NT = 256, P32_MINB = 2;
 constexpr int THIN_TZ = 2;
 constexpr int tile_z(bool fp64_state, int nf) { return fp64_state && nf > 9 ? THIN_TZ : 6; }
 
+// The FP64 kernel's flat tile, 14 x 30 x 1 cells without a z halo or z
+// sweep, for grids one z cell thick whose z boundaries are periodic or
+// outflow (the cell's two z faces then carry the same flux), with at most
+// one dust species: the cylindrical explosion of Sect. 4.1 runs on it.
+constexpr int FLAT_TT = 30;
+inline bool flat_grid(int nz, int bc_lo_z, int bc_hi_z, int nf) {
+  return nz == 1 && bc_lo_z != BC_EQUILIBRIUM && bc_hi_z != BC_EQUILIBRIUM && nf <= 9;
+}
+
 // Calls f(std::integral_constant<int, NF>) for the field count nf (5 + 4 x
 // the number of dust species, 0 .. 4).
 template <class F>
@@ -53,19 +62,34 @@ cudaError_t set_smem_once(K kern, size_t smem, unsigned long long& done) {
   return e;
 }
 
+// Each launcher is instantiated per gas reconstruction mode RC in a
+// translation unit of its own (they compile in parallel).
 // One launch of the FP64 stage kernel over nblocks tiles; xt selects the
-// instantiation with the optional terms (indirect gravity, wave-killing
-// zones, Stokes drag regime).
-cudaError_t run_stage_full(const StageArgs& a, int nblocks, cudaStream_t s, bool xt);
+// instantiation with the optional terms (indirect gravity, damping zones,
+// Stokes drag regime).
+template <int RC>
+cudaError_t run_stage_full_rc(const StageArgs& a, int nblocks, cudaStream_t s, bool xt);
+inline cudaError_t run_stage_full(const StageArgs& a, int nblocks, cudaStream_t s, bool xt) {
+  return a.g.recon == RECON_PRIM ? run_stage_full_rc<RECON_PRIM>(a, nblocks, s, xt)
+                                 : run_stage_full_rc<RECON_CONS>(a, nblocks, s, xt);
+}
 // One launch of the perturbation-form stage kernel (float or double); g75
 // selects the gamma = 7/5 power forms of the float solver.
-template <class P>
-cudaError_t run_stage_pert_f32_p(const PertArgs<float>& a, int nblocks, cudaStream_t s, bool xt);
+template <class P, int RC>
+cudaError_t run_stage_pert_f32_rc(const PertArgs<float>& a, int nblocks, cudaStream_t s, bool xt);
 inline cudaError_t run_stage_pert_f32(const PertArgs<float>& a, int nblocks, cudaStream_t s, bool xt, bool g75) {
-  return g75 ? run_stage_pert_f32_p<PowG75>(a, nblocks, s, xt)
-             : run_stage_pert_f32_p<PowGeneric<float>>(a, nblocks, s, xt);
+  if (a.g.recon == RECON_PRIM)
+    return g75 ? run_stage_pert_f32_rc<PowG75, RECON_PRIM>(a, nblocks, s, xt)
+               : run_stage_pert_f32_rc<PowGeneric<float>, RECON_PRIM>(a, nblocks, s, xt);
+  return g75 ? run_stage_pert_f32_rc<PowG75, RECON_CONS>(a, nblocks, s, xt)
+             : run_stage_pert_f32_rc<PowGeneric<float>, RECON_CONS>(a, nblocks, s, xt);
 }
-cudaError_t run_stage_pert_f64(const PertArgs<double>& a, int nblocks, cudaStream_t s, bool xt);
+template <int RC>
+cudaError_t run_stage_pert_f64_rc(const PertArgs<double>& a, int nblocks, cudaStream_t s, bool xt);
+inline cudaError_t run_stage_pert_f64(const PertArgs<double>& a, int nblocks, cudaStream_t s, bool xt) {
+  return a.g.recon == RECON_PRIM ? run_stage_pert_f64_rc<RECON_PRIM>(a, nblocks, s, xt)
+                                 : run_stage_pert_f64_rc<RECON_CONS>(a, nblocks, s, xt);
+}
 // One launch of the adjoint flux kernel along axis 0, 1 or 2.
 cudaError_t run_adj_flux(const AdjFluxArgs& a, int axis, cudaStream_t s);
 

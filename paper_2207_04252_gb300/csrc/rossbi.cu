@@ -52,6 +52,7 @@ struct rossbi_grid {
   void* d_scratch = nullptr;           // E* when the caller passes none
   void* d_hoststate = nullptr;         // device copy for rossbi_step_host
   int tiles_r = 0, tiles_t = 0, tiles_z = 0;
+  int tile_tt = 6;                     // theta extent of a stage-kernel tile
   // perturbation forms: equilibrium and metric tables in the state precision
   void* d_ptab = nullptr;              // one allocation holding every table below
   PertTables<float> pt_f{};
@@ -445,7 +446,7 @@ StageArgs base_args(rossbi_grid* g) {
 // (same dtheta, so the same arithmetic as every column of the full grid).
 rossbi_status empty_run(rossbi_grid* g) {
   const rossbi_grid_desc& d = g->desc;
-  const int nth_s = std::min(d.nth, F64_TT);
+  const int nth_s = std::min(d.nth, g->tile_tt);
   const size_t nslab = (size_t)d.nr * nth_s * d.nz;
   std::vector<double> E0(nslab * g->nf, 0.0);
   for (int f = 0; f < 5; ++f)
@@ -1121,8 +1122,10 @@ rossbi_status rossbi_init_grid(const rossbi_grid_desc* desc, void* cuda_stream, 
   g->nf = 5 + 4 * desc->n_dust;
   g->ncell = (size_t)desc->nr * desc->nth * desc->nz;
   const bool pert = desc->precision != ROSSBI_FP64;  // tile of the form's stage kernel
-  const int tr = pert ? P32_TR : F64_TR, tt = pert ? P32_TT : F64_TT;
-  const int tz = tile_z(desc->precision != ROSSBI_FP32_PERT, g->nf);
+  const bool flat = !pert && flat_grid(desc->nz, desc->bc_lo[2], desc->bc_hi[2], g->nf);
+  const int tr = pert ? P32_TR : F64_TR, tt = pert ? P32_TT : (flat ? FLAT_TT : F64_TT);
+  const int tz = flat ? 1 : tile_z(desc->precision != ROSSBI_FP32_PERT, g->nf);
+  g->tile_tt = tt;
   g->tiles_r = (desc->nr + tr - 1) / tr;
   g->tiles_t = (desc->nth + tt - 1) / tt;
   g->tiles_z = (desc->nz + tz - 1) / tz;

@@ -125,7 +125,8 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? l
 template <int NF, int TR, int TT, int TZ, int NT, int D, int RC>
 __device__ __forceinline__ void sweep_full(const StageArgs& a, const double* sE, double* sG, int i0, int j0, int k0,
                                            unsigned& status) {
-  constexpr int BX = TR + 4, BY = TT + 4, BZ = TZ + 4, BOX = BX * BY * BZ, NCORE = TR * TT * TZ;
+  constexpr int ZH = TZ == 1 ? 0 : 2;  // z halo (none in the flat one-z-cell tile)
+  constexpr int BX = TR + 4, BY = TT + 4, BZ = TZ + 2 * ZH, BOX = BX * BY * BZ, NCORE = TR * TT * TZ;
   constexpr int TD = D == 0 ? TR : (D == 1 ? TT : TZ);
   constexpr int L = pow2ceil(TD + 2);
   static_assert(L <= 32, "line does not fit a warp");
@@ -156,7 +157,7 @@ __device__ __forceinline__ void sweep_full(const StageArgs& a, const double* sE,
     const bool do_recon = line_ok && c <= TD && gd <= nd;
     const bool do_face = do_recon && c >= 0;
     const bool do_acc = line_ok && c >= 0 && c < TD && gd < nd;
-    const int sidx = do_recon ? ((z + 2) * BY + (y + 2)) * BX + (x + 2) : (2 * BY + 2) * BX + 2;
+    const int sidx = do_recon ? ((z + ZH) * BY + (y + 2)) * BX + (x + 2) : (ZH * BY + 2) * BX + 2;
 
     // parabola weights of this cell along D
     double w[9];
@@ -320,9 +321,14 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 
 // XT: the optional terms (indirect gravity, wave-killing zones) are compiled
 // in; the plain instantiation carries none of their code.
+// TZ = 1 is the flat tile of a grid one z cell thick whose z boundaries are
+// periodic or outflow: both z ghosts of the cell are the cell itself, its two
+// z faces carry the same flux, and the z sweep, whose divergence is exactly
+// zero, is skipped (as is the z halo).
 template <int NF, int TR, int TT, int TZ, int NT, bool XT, int RC>
 __global__ void __launch_bounds__(NT, 1) stage_full_kernel(const StageArgs a) {
-  constexpr int BX = TR + 4, BY = TT + 4, BZ = TZ + 4, BOX = BX * BY * BZ, NCORE = TR * TT * TZ;
+  constexpr int ZH = TZ == 1 ? 0 : 2;
+  constexpr int BX = TR + 4, BY = TT + 4, BZ = TZ + 2 * ZH, BOX = BX * BY * BZ, NCORE = TR * TT * TZ;
   extern __shared__ double smem[];
   double* sE = smem;
   double* sG = smem + NF * BOX;
@@ -337,7 +343,7 @@ __global__ void __launch_bounds__(NT, 1) stage_full_kernel(const StageArgs a) {
   // E' = E - E0 (or, with RC = RECON_PRIM, the primitive departures
   // u', v', w', P', rho') in slots 0..4, the dust as it is
   for (int idx = threadIdx.x; idx < BOX; idx += NT) {
-    const int x = idx % BX - 2, y = (idx / BX) % BY - 2, z = idx / (BX * BY) - 2;
+    const int x = idx % BX - 2, y = (idx / BX) % BY - 2, z = idx / (BX * BY) - ZH;
     const int outside = (x < 0 || x >= TR) + (y < 0 || y >= TT) + (z < 0 || z >= TZ);
     if (outside > 1) continue;
     int c[3] = {i0 + x, j0 + y, k0 + z};
@@ -367,8 +373,10 @@ __global__ void __launch_bounds__(NT, 1) stage_full_kernel(const StageArgs a) {
   __syncthreads();
   sweep_full<NF, TR, TT, TZ, NT, 1, RC>(a, sE, sG, i0, j0, k0, status);
   __syncthreads();
-  sweep_full<NF, TR, TT, TZ, NT, 2, RC>(a, sE, sG, i0, j0, k0, status);
-  __syncthreads();
+  if constexpr (TZ > 1) {
+    sweep_full<NF, TR, TT, TZ, NT, 2, RC>(a, sE, sG, i0, j0, k0, status);
+    __syncthreads();
+  }
 
   const double tau = a.tau_frac * (a.dt_dev ? __longlong_as_double((long long)*a.dt_dev) : a.dt_host);
   const size_t ncell = (size_t)g.nr * g.nth * g.nz;
