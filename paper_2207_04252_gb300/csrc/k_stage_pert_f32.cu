@@ -16,8 +16,7 @@ namespace {
 
 template <int NF, class P, bool XT, int RC>
 cudaError_t launch(const PertArgs<float>& a, int nblocks, cudaStream_t s) {
-  constexpr int BOX = (P32_TR + 4) * (P32_TT + 4) * (P32_TZ + 4), NCORE = P32_TR * P32_TT * P32_TZ;
-  constexpr size_t smem = (size_t)NF * (BOX + NCORE) * sizeof(float);
+  constexpr size_t smem = pert_smem_bytes<float, NF, P32_TR, P32_TT, P32_TZ>();
   auto kern = stage_pert_kernel<float, NF, P32_TR, P32_TT, P32_TZ, P32_NT, P32_MINB, P, XT, RC>;
   static unsigned long long done = 0;
   cudaError_t e = set_smem_once(kern, smem, done);

@@ -12,8 +12,7 @@ namespace {
 
 template <int NF, int TZ, bool XT, int RC>
 cudaError_t launch(const PertArgs<double>& a, int nblocks, cudaStream_t s) {
-  constexpr int BOX = (P32_TR + 4) * (P32_TT + 4) * (TZ + 4), NCORE = P32_TR * P32_TT * TZ;
-  constexpr size_t smem = (size_t)NF * (BOX + NCORE) * sizeof(double);
+  constexpr size_t smem = pert_smem_bytes<double, NF, P32_TR, P32_TT, TZ>();
   auto kern = stage_pert_kernel<double, NF, P32_TR, P32_TT, TZ, P32_NT, 1, PowGeneric<double>, XT, RC>;
   static unsigned long long done = 0;
   cudaError_t e = set_smem_once(kern, smem, done);

@@ -410,9 +410,12 @@ __device__ __forceinline__ PFace<T> face_eq(const PertTables<T>& t, const DevGri
   return W;
 }
 
-template <class T, int NF, int TR, int TT, int TZ, int NT, int D, class P, int RC>
-__device__ __forceinline__ void sweep_pert(const PertArgs<T>& a, const T* sE, T* sG, int i0, int j0, int k0,
-                                           unsigned& status, unsigned& nfallback) {
+// One 32-lane chunk of the sweep along axis D: items base .. base + 31 (whole
+// lines of L lanes).  The flux divergence of the chunk's cells is written to
+// sG (ACC: added to it).
+template <class T, int NF, int TR, int TT, int TZ, int NT, int D, class P, int RC, bool ACC>
+__device__ __forceinline__ void sweep_pert_chunk(const PertArgs<T>& a, const T* sE, T* sG, int i0, int j0, int k0,
+                                                 int base, unsigned& status, unsigned& nfallback) {
   constexpr int BX = TR + 4, BY = TT + 4, BZ = TZ + 4, BOX = BX * BY * BZ, NCORE = TR * TT * TZ;
   constexpr int TD = D == 0 ? TR : (D == 1 ? TT : TZ);
   constexpr int L = pow2ceil(TD + 2);
@@ -421,14 +424,12 @@ __device__ __forceinline__ void sweep_pert(const PertArgs<T>& a, const T* sE, T*
   constexpr int NB = D == 2 ? TT : TZ;
   constexpr int ITEMS = NA * NB * L;
   constexpr int STRIDE = D == 0 ? 1 : (D == 1 ? BX : BX * BY);
-  constexpr int NW = NT / 32;
   constexpr unsigned FULL = 0xffffffffu;
   const DevGrid& g = a.g;
   const T gam = a.gam;
   const bool has_eq = g.has_eq != 0;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
-  for (int base = warp * 32; base < ITEMS; base += NW * 32) {
+  const int lane = threadIdx.x & 31;
+  {
     const int item = base + lane;
     const bool valid = item < ITEMS;
     const int line = valid ? item / L : 0;
@@ -516,8 +517,8 @@ __device__ __forceinline__ void sweep_pert(const PertArgs<T>& a, const T* sE, T*
         const T Fu = __shfl_down_sync(FULL, F[f], 1, L);
         if (do_acc) {
           T* dst = sG + f * NCORE + (z * TT + y) * TR + x;
-          if (D == 0) *dst = F[f] - Fu;
-          else *dst += F[f] - Fu;
+          if (ACC) *dst += F[f] - Fu;
+          else *dst = F[f] - Fu;
         }
       }
     }
@@ -544,12 +545,42 @@ __device__ __forceinline__ void sweep_pert(const PertArgs<T>& a, const T* sE, T*
         const T Fu = __shfl_down_sync(FULL, F[f], 1, L);
         if (do_acc) {
           T* dst = sG + (b + f) * NCORE + (z * TT + y) * TR + x;
-          if (D == 0) *dst = F[f] - Fu;
-          else *dst += F[f] - Fu;
+          if (ACC) *dst += F[f] - Fu;
+          else *dst = F[f] - Fu;
         }
       }
     }
   }
+}
+
+// Items (lanes) of the sweep along axis D of a TR x TT x TZ tile.
+template <int TR, int TT, int TZ, int D>
+__host__ __device__ constexpr int sweep_items() {
+  return (D == 0 ? TT * TZ : (D == 1 ? TR * TZ : TR * TT)) * pow2ceil((D == 0 ? TR : (D == 1 ? TT : TZ)) + 2);
+}
+
+// The whole sweep along axis D, chunks spread over the block's warps.
+template <class T, int NF, int TR, int TT, int TZ, int NT, int D, class P, int RC, bool ACC>
+__device__ __forceinline__ void sweep_pert(const PertArgs<T>& a, const T* sE, T* sG, int i0, int j0, int k0,
+                                           unsigned& status, unsigned& nfallback) {
+  constexpr int CH = (sweep_items<TR, TT, TZ, D>() + 31) / 32;
+  for (int ch = threadIdx.x >> 5; ch < CH; ch += NT / 32)
+    sweep_pert_chunk<T, NF, TR, TT, TZ, NT, D, P, RC, ACC>(a, sE, sG, i0, j0, k0, ch * 32, status, nfallback);
+}
+
+// The r and theta sweeps write separate accumulators when they fit: their
+// chunks then form one pool with no barrier between the two sweeps (the
+// r sweep alone left a quarter of its warp slots idle at the barrier).
+template <class T, int NF, int TR, int TT, int TZ>
+__host__ __device__ constexpr bool pert_merged_sweeps() {
+  return (size_t)NF * ((TR + 4) * (TT + 4) * (TZ + 4) + 2 * TR * TT * TZ) * sizeof(T) <= (size_t)227 * 1024;
+}
+// Dynamic shared memory of stage_pert_kernel: the staged tile and halo, and
+// one accumulator of the flux divergence (two with merged sweeps).
+template <class T, int NF, int TR, int TT, int TZ>
+__host__ __device__ constexpr size_t pert_smem_bytes() {
+  return (size_t)NF * ((TR + 4) * (TT + 4) * (TZ + 4) + (pert_merged_sweeps<T, NF, TR, TT, TZ>() ? 2 : 1) * TR * TT * TZ) *
+         sizeof(T);
 }
 
 // Cell-centre equilibrium coefficients.
@@ -759,6 +790,8 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sE = reinterpret_cast<T*>(smem_raw);
   T* sG = sE + NF * BOX;
+  constexpr bool MERGED = pert_merged_sweeps<T, NF, TR, TT, TZ>();
+  T* sG1 = MERGED ? sG + NF * NCORE : sG;  // the theta sweep's accumulator
   const DevGrid& g = a.g;
   const int tile = blockIdx.x;
   const int i0 = (tile % a.tiles_r) * TR;
@@ -830,11 +863,22 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
     }
   }
   __syncthreads();
-  sweep_pert<T, NF, TR, TT, TZ, NT, 0, P, RC>(a, sE, sG, i0, j0, k0, status, nfallback);
+  if constexpr (MERGED) {
+    constexpr int C0 = (sweep_items<TR, TT, TZ, 0>() + 31) / 32, C1 = (sweep_items<TR, TT, TZ, 1>() + 31) / 32;
+    for (int ch = threadIdx.x >> 5; ch < C0 + C1; ch += NT / 32) {
+      if (ch < C0)
+        sweep_pert_chunk<T, NF, TR, TT, TZ, NT, 0, P, RC, false>(a, sE, sG, i0, j0, k0, ch * 32, status, nfallback);
+      else
+        sweep_pert_chunk<T, NF, TR, TT, TZ, NT, 1, P, RC, false>(a, sE, sG1, i0, j0, k0, (ch - C0) * 32, status,
+                                                                 nfallback);
+    }
+  } else {
+    sweep_pert<T, NF, TR, TT, TZ, NT, 0, P, RC, false>(a, sE, sG, i0, j0, k0, status, nfallback);
+    __syncthreads();
+    sweep_pert<T, NF, TR, TT, TZ, NT, 1, P, RC, true>(a, sE, sG, i0, j0, k0, status, nfallback);
+  }
   __syncthreads();
-  sweep_pert<T, NF, TR, TT, TZ, NT, 1, P, RC>(a, sE, sG, i0, j0, k0, status, nfallback);
-  __syncthreads();
-  sweep_pert<T, NF, TR, TT, TZ, NT, 2, P, RC>(a, sE, sG, i0, j0, k0, status, nfallback);
+  sweep_pert<T, NF, TR, TT, TZ, NT, 2, P, RC, true>(a, sE, sG, i0, j0, k0, status, nfallback);
   __syncthreads();
 
   const T tau = (T)(a.tau_frac * (a.dt_dev ? __longlong_as_double((long long)*a.dt_dev) : a.dt_host));
@@ -853,7 +897,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       q[f] = sE[f * BOX + sidx];
-      G[f] = sG[f * NCORE + cidx];
+      G[f] = MERGED ? sG[f * NCORE + cidx] + sG1[f * NCORE + cidx] : sG[f * NCORE + cidx];
     }
     if (RC == RECON_CONS) {  // the staged gas departures are conservative
       T qc[5];

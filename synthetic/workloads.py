@@ -125,10 +125,11 @@ THROUGHPUT = _disc("bifluid_two_vortices_512x1024x128", 512, 1024, 128, 50, ic="
                    seed=4252, vortices=((0.8, 0.0), (1.3, math.pi)), dust_ratio=0.01, dust_noise=1e-3,
                    stokes=0.05)
 
-# Rossby wave instability (Sect. 4.3): a radial Gaussian density bump on the
-# equilibrium, rho = rho0 (1 + delta G), G = exp(-((r - r0)/(sqrt(2) Delta_r))^2),
-# at the equilibrium temperature (P scaled alike, velocities kept), and the
-# seed v_r = eps v_theta0 sin(m theta) G with eps = 1e-4 and mode m.  The paper
+# Rossby wave instability (Sect. 4.3): a radial Gaussian density bump in the
+# stationary solution, rho = rho0 (1 + delta G), G = exp(-((r - r0)/(sqrt(2)
+# Delta_r))^2), at the equilibrium temperature (P scaled alike) with the
+# azimuthal velocity in radial balance with the bump's pressure gradient, and
+# the seed v_r = eps v_theta0 sin(m theta) G with eps = 1e-4 and mode m.  The paper
 # takes the setup of Meheut et al. (2012) without printing delta and Delta_r:
 # delta = 0.25 and Delta_r = 0.05 r0 (= H(r0)) here.  Gas only, in the
 # equal-Mach frame; growth rates of the modes are measured, not pinned.

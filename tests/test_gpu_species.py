@@ -84,15 +84,15 @@ def test_species_parity(lib, reference, form):
     R, W = lib
     w, o, E0, E_ref, dts = reference
     prec = {"fp64": R.ROSSBI_FP64, "fp64_pert": R.ROSSBI_FP64_PERT, "fp32_pert": R.ROSSBI_FP32_PERT}[form]
-    tol, el_tol = (1e-5, 1e-2) if form == "fp32_pert" else (1e-12, 1e-9)
+    tol, el_tol = (1e-5, 1e-2) if form == "fp32_pert" else (1e-12, 1e-8)
     g = W.Grid(w, precision=prec)
     assert g.nf == 5 + 4 * w.n_dust
     s = g.initial_state()
     # the two sides build the initial state each from its own equilibrium and
     # recipe: equal to rounding (float storage in the FP32 form)
     scale = np.abs(E0).max(axis=(1, 2, 3), keepdims=True)
-    err0 = np.abs(g.full_state(s) - E0) / scale
-    assert err0.max() <= (1e-6 if form == "fp32_pert" else 1e-13), err0.max()
+    err0 = np.abs(g.full_state(s) - E0) / np.where(scale > 0, scale, 1.0)
+    assert err0.max() <= (1e-6 if form == "fp32_pert" else 1e-12), err0.max()
     for dt in dts:
         g.step(s, dt=dt)
     assert g.take_status() == 0

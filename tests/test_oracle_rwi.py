@@ -40,7 +40,13 @@ def test_rwi_initial_state():
     rho, u, v, ww, P = prim(E)
     rho0, _, v0, _, P0 = prim(E0)
     assert np.allclose(P / rho, P0 / rho0, rtol=1e-12, atol=0)      # the equilibrium temperature
-    assert np.allclose(v, v0, rtol=1e-14, atol=0) and not ww.any()  # azimuthal velocity kept, no v_z
+    assert not ww.any()                                             # no v_z
+    # radial balance of the bump: v_theta^2 = v_theta0^2 + r T delta G' / (1 + delta G), inertial speeds
+    R = r[None, None, :]
+    dG = -(R - w.rwi_r0) / w.rwi_width ** 2 * G[None, None, :]
+    vin, vin0 = v + w.omega_frame * R, v0 + w.omega_frame * R
+    np.testing.assert_allclose(vin ** 2 - vin0 ** 2, R * (P0 / rho0) * w.rwi_delta * dG / (1.0 + w.rwi_delta * G),
+                               rtol=1e-8, atol=1e-12 * (vin0 ** 2).max())
     # the seed: mode m alone, amplitude eps v_theta0 G (inertial v_theta0):
     # the projection on sin(m theta) over the cell centres, and nothing left
     m = w.rwi_mode
