@@ -114,9 +114,16 @@ typedef struct {
 } rossbi_grid_desc;
 
 /* Disc equilibrium parameters (App. A): Sigma = sigma0 r^beta_sigma,
- * T = T0 r^beta_T (k_B/(mu m_u) = 1). */
+ * T = T0 r^beta_T (k_B/(mu m_u) = 1).  Optionally the radial density bump of
+ * the Rossby-wave-instability disc (Sect. 4.3) as part of the equilibrium:
+ * rho and P scaled by 1 + bump_delta G(r), G = exp(-(r - bump_r0)^2 /
+ * (2 bump_width^2)), at the same temperature, with v_theta in radial balance
+ * with the bumped pressure (a stationary solution of its own).
+ * bump_delta = 0 (zero-initialised) means no bump; otherwise
+ * bump_delta > -1 and bump_width > 0. */
 typedef struct {
   double sigma0, beta_sigma, T0, beta_T;
+  double bump_delta, bump_r0, bump_width;
 } rossbi_disc_params;
 
 /* Drag (Sect. 2.9).  drag_law 0: t_s = stokes / Omega_K(r) (Box: t_s = stokes);

@@ -144,7 +144,7 @@ class Oracle:
         if w.dust_stokes_factors:
             self.set_species_stokes(w.dust_stokes_factors)
         if w.disc is not None:
-            disc = np.array(w.disc, dtype=np.float64)
+            disc = np.array(w.disc_params(), dtype=np.float64)
             self.status |= lib().orc_set_equilibrium(self.h, _p(disc))
 
     def __del__(self):
@@ -389,27 +389,15 @@ def initial_state(o: Oracle) -> np.ndarray:
             E[b] = rd * up
             E[b + 1] = rd * (v0 + vp)
             E[b + 2] = 0.0
-    elif w.ic == "rwi":  # Sect. 4.3: stationary density bump, seeded v_r of mode m
+    elif w.ic == "rwi":  # Sect. 4.3: the bumped equilibrium (reading R22), seeded v_r of mode m
         r, _ = o.coords(0)
         th, _ = o.coords(1)
         z, _ = o.coords(2)
-        R = r[None, None, :]
-        G = np.exp(-((R - w.rwi_r0) / (math.sqrt(2.0) * w.rwi_width)) ** 2)
-        dG = -(R - w.rwi_r0) / w.rwi_width ** 2 * G             # dG/dr
-        s = 1.0 + w.rwi_delta * G
-        rho = rho0 * s
-        P0 = (g - 1.0) * (E0[syn.F_EN] - 0.5 * E0[syn.F_MV] ** 2 / rho0)
-        T = P0 / rho0
+        G = np.exp(-((r - w.rwi_r0) / (math.sqrt(2.0) * w.rwi_width)) ** 2)[None, None, :]
         vth0 = np.array([[o.eq_prim(ri, zk)[1] for ri in r] for zk in z])[:, None, :]  # inertial v_theta0
-        # radial balance with the bump's own pressure gradient (P = T rho, T kept)
-        vth = np.sqrt(vth0 * vth0 + R * T * w.rwi_delta * dG / s)
-        v = vth - w.omega_frame * R                               # frame-relative
         vr = w.rwi_eps * vth0 * np.sin(w.rwi_mode * th)[None, :, None] * G
-        E[syn.F_RHO] = rho
-        E[syn.F_MU] = rho * vr
-        E[syn.F_MV] = rho * v
-        E[syn.F_MW] = 0.0
-        E[syn.F_EN] = 0.5 * rho * (vr * vr + v * v) + P0 * s / (g - 1.0)
+        E[syn.F_MU] = rho0 * vr
+        E[syn.F_EN] += 0.5 * rho0 * vr * vr
     else:
         raise ValueError(w.ic)
     return E

@@ -105,6 +105,14 @@
 //      coupled to the gas only, by its own drag (Stokes number St x f_s); the
 //      semi-implicit drag solves the coupled backward-Euler system in closed
 //      form (one species keeps the closed form of R7).
+//  R22 Rossby-wave-instability disc (Sect. 4.3 adds a radial Gaussian density
+//      bump to the stationary solution without saying how it is balanced):
+//      the bump is part of the equilibrium E0.  rho and P are scaled by
+//      s = 1 + delta G(r), G = exp(-(r - r0)^2 / (2 Delta_r^2)), at the
+//      equilibrium temperature, and v_theta0 follows from radial balance with
+//      the bumped pressure, so the bumped disc is itself a stationary
+//      solution (of the equations, and of the balanced scheme of Sect. 2.8
+//      exactly) and the run evolves only the seeded v_r of mode m.
 //
 // Parity unpinned (readings checked only for their properties and for
 // self-consistency, since the paper gives no formula or value to test them
@@ -168,6 +176,7 @@ struct Oracle {
   std::vector<double> xc[3], xf[3];  // centre / lower face of cell c at [c + NG]
   bool has_eq = false;
   double sigma0 = 0, beta_sigma = 0, T0 = 0, beta_T = 0;
+  double bump_delta = 0, bump_r0 = 1, bump_width = 0;  // radial density bump of reading R22
   // equilibrium conservative gas state (5 values) at centres, r faces and z faces,
   // over the index ranges extended by NG ghosts
   std::vector<double> e0c, e0r, e0z;
@@ -240,8 +249,19 @@ static void eq_prim(const Oracle& o, double r, double z, double& rho, double& vt
   rho = o.sigma0 * pow(r, o.beta_sigma) / (sqrt(M_PI) * H) * exp(gm / cs2 * g);
   p = cs2 * rho;
   // d ln P0 / dr, differentiated by hand from the expressions above
-  const double dlnp = (o.beta_T + o.beta_sigma - 0.5 * (o.beta_T + 3.0)) / r +
+  double dlnp = (o.beta_T + o.beta_sigma - 0.5 * (o.beta_T + 3.0)) / r +
                       gm / cs2 * (-o.beta_T * g / r - r / (R * R * R) + 1.0 / (r * r));
+  // Sect. 4.3 (reading R22): a radial Gaussian density bump at r0 of width
+  // Delta_r, rho and P both scaled by s = 1 + delta G(r) (the temperature
+  // kept, so vertical balance holds unchanged); d ln P / dr gains s'/s
+  if (o.bump_delta != 0.0) {
+    const double x = (r - o.bump_r0) / o.bump_width;
+    const double G = exp(-0.5 * x * x);
+    const double s = 1.0 + o.bump_delta * G;
+    rho *= s;
+    p *= s;
+    dlnp += o.bump_delta * G * (-x / o.bump_width) / s;
+  }
   // v_theta0^2 = -r f_star,r + (r/rho) dP/dr
   vth = sqrt(gm * r * r / (R * R * R) + r * cs2 * dlnp);
 }
@@ -1095,7 +1115,8 @@ void orc_destroy(void* h) { delete (Oracle*)h; }
 int orc_nfields(void* h) { return ((Oracle*)h)->nf; }
 
 // Sets the disc equilibrium (App. A) and runs the empty run of Sect. 2.8.
-// disc = {sigma0, beta_sigma, T0, beta_T}, or NULL for no equilibrium.
+// disc = {sigma0, beta_sigma, T0, beta_T, bump_delta, bump_r0, bump_width}
+// (bump_delta = 0: no bump), or NULL for no equilibrium.
 int orc_set_equilibrium(void* h, const double* disc) {
   Oracle& o = *(Oracle*)h;
   o.has_eq = disc != nullptr;
@@ -1104,6 +1125,9 @@ int orc_set_equilibrium(void* h, const double* disc) {
     o.beta_sigma = disc[1];
     o.T0 = disc[2];
     o.beta_T = disc[3];
+    o.bump_delta = disc[4];
+    o.bump_r0 = disc[5];
+    o.bump_width = disc[6];
   }
   build_tables(o);
   o.r0.clear();

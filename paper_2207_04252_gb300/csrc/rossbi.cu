@@ -123,8 +123,16 @@ void equilibrium_prim(const rossbi_grid_desc& d, const rossbi_disc_params& p, do
   const double gpot = 1.0 / R - 1.0 / r;
   rho = p.sigma0 * std::pow(r, p.beta_sigma) / (std::sqrt(M_PI) * H) * std::exp(d.gm / cs2 * gpot);
   pres = cs2 * rho;
-  const double dlnp = (p.beta_T + p.beta_sigma - 0.5 * (p.beta_T + 3.0)) / r +
-                      d.gm / cs2 * (-p.beta_T * gpot / r - r / (R * R * R) + 1.0 / (r * r));
+  double dlnp = (p.beta_T + p.beta_sigma - 0.5 * (p.beta_T + 3.0)) / r +
+                d.gm / cs2 * (-p.beta_T * gpot / r - r / (R * R * R) + 1.0 / (r * r));
+  if (p.bump_delta != 0.0) {  // Sect. 4.3: rho, P x (1 + delta G) at the same T; d ln P / dr gains its log-derivative
+    const double x = (r - p.bump_r0) / p.bump_width;
+    const double G = std::exp(-0.5 * x * x);
+    const double s = 1.0 + p.bump_delta * G;
+    rho *= s;
+    pres *= s;
+    dlnp -= p.bump_delta * G * x / (p.bump_width * s);
+  }
   vth = std::sqrt(d.gm * r * r / (R * R * R) + r * cs2 * dlnp);
   if (dlnp_out) *dlnp_out = dlnp;
 }
@@ -438,7 +446,7 @@ StageArgs base_args(rossbi_grid* g) {
   a.g = g->dg;
   a.status = g->d_status;
   a.tiles_r = g->tiles_r;
-  a.tiles_t = g->tiles_t;
+  a.tiles_z = g->tiles_z;
   return a;
 }
 
@@ -470,8 +478,7 @@ rossbi_status empty_run(rossbi_grid* g) {
     for (int f = 0; f < g->nf; ++f) a.in[f] = dE + f * nslab;
     a.gout = dG;
     a.mode = 1;
-    a.tiles_t = 1;
-    const int nblocks = g->tiles_r * 1 * g->tiles_z;
+    const int nblocks = g->tiles_r * 1 * g->tiles_z;  // one tile along theta
     st = launch_stage(g, a, nblocks);
     if (st != ROSSBI_OK) break;
     std::vector<double> G(E0.size());
@@ -613,7 +620,7 @@ PertArgs<T> pert_args(rossbi_grid* g) {
   else a.t = g->pt_d;
   a.status = g->d_status;
   a.tiles_r = g->tiles_r;
-  a.tiles_t = g->tiles_t;
+  a.tiles_z = g->tiles_z;
   a.gam = (T)g->dg.gamma;
   a.om = (T)g->dg.omega;
   a.cfl = (T)g->dg.cfl;
@@ -1233,6 +1240,10 @@ rossbi_status rossbi_set_equilibrium(rossbi_grid* g, const rossbi_disc_params* d
   // coefficients are tabulated from a disc equilibrium
   if (d.geometry == ROSSBI_GEOM_CYL && !disc && d.precision != ROSSBI_FP64) return ROSSBI_ERR_UNSUPPORTED;
   if (d.geometry == ROSSBI_GEOM_CYL && disc && !(d.gm > 0.0)) return ROSSBI_ERR_ARG;  // Keplerian disc
+  if (disc && disc->bump_delta != 0.0 &&
+      (!(disc->bump_delta > -1.0) || !(disc->bump_width > 0.0) || !std::isfinite(disc->bump_delta) ||
+       !std::isfinite(disc->bump_width) || !std::isfinite(disc->bump_r0)))
+    return ROSSBI_ERR_ARG;
   g->eq_set = false;
   g->dg.has_eq = 0;
   g->dg.e0c = g->dg.e0r = g->dg.e0z = g->dg.r0 = nullptr;

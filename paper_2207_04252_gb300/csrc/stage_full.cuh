@@ -33,7 +33,7 @@ struct StageArgs {
   double* partials;                  // stage 2: [nf + 1][gridDim.x] block sums of V*E, then block dt minima
   unsigned* status;
   int mode;                          // 0 update, 1 residual only (empty run)
-  int tiles_r, tiles_t;
+  int tiles_r, tiles_z;  // tile counts along r and z (block -> tile: r fastest, then z, then theta)
 };
 
 template <class T>
@@ -334,9 +334,12 @@ __global__ void __launch_bounds__(NT, 1) stage_full_kernel(const StageArgs a) {
   double* sG = smem + NF * BOX;
   const DevGrid& g = a.g;
   const int tile = blockIdx.x;
+  // r fastest, then z, then theta: the tiles whose halos a tile re-reads
+  // (its r, z and theta neighbours) run at most tiles_r x tiles_z blocks
+  // apart, so the re-reads hit in L2
   const int i0 = (tile % a.tiles_r) * TR;
-  const int j0 = ((tile / a.tiles_r) % a.tiles_t) * TT;
-  const int k0 = (tile / (a.tiles_r * a.tiles_t)) * TZ;
+  const int k0 = ((tile / a.tiles_r) % a.tiles_z) * TZ;
+  const int j0 = (tile / (a.tiles_r * a.tiles_z)) * TT;
   unsigned status = 0;
 
   // tile + halo as deviations (corners are never read): the gas departures

@@ -79,6 +79,7 @@ __device__ __forceinline__ T sqrt1pm1(T t) {
 // Generic gamma: log1p / expm1.
 template <class T>
 struct PowGeneric {
+  static constexpr bool series = false;
   static __device__ __forceinline__ T rar(T x, T g) { return pow1pm1(x, (g - T(1)) / (T(2) * g)); }
   static __device__ __forceinline__ T dens(T x, T g, T) { return pow1pm1(x, T(1) / g); }
   static __device__ __forceinline__ T fan_rho(T y, T g) { return pow1pm1(y, T(2) / (g - T(1))); }
@@ -89,6 +90,27 @@ struct PowGeneric {
 // the hardware log2 / exp2 estimate of z; (1 + x)^(5/7) - 1 = (z - 1)(1 + z +
 // z^2 + z^3 + z^4); the fan exponents 5 and 7 are exact polynomials.
 struct PowG75 {
+  // Near p = p_K (|x| <= xs, x = p/p_K - 1) the pressure function of a side
+  // is f = (c/gamma) x S(x) and f' = T(x)/(rho c), with S, T the Taylor
+  // series of the rarefaction branch (x <= 0: S = ((1+x)^(1/7) - 1)/(x/7),
+  // T = (1+x)^(-6/7)) or the shock branch (x > 0: S = (1 + 6x/7)^(-1/2),
+  // T = (1 + 6x/7)^(-3/2) (1 + 3x/7)) to x^4; the branches agree to x^2 (f is
+  // C^2 at p_K).  Truncation at |x| = 1/32: 4e-9 relative in f, 2.2e-8 in f'.
+  static constexpr bool series = true;
+  static constexpr float xs = 0.03125f;
+  static constexpr float inv_gamma = 0.714285714f;
+  static constexpr float beta = 0.142857143f;  // (gamma - 1) / (2 gamma)
+  static __device__ __forceinline__ void pressure_series(float x, float& S, float& Td) {
+    const bool rar = x <= 0.0f;
+    const float s2 = rar ? 0.265306122f : 0.275510204f;    // 13/49 | 27/98
+    const float s3 = rar ? -0.189504373f : -0.196793003f;  // -65/343 | -135/686
+    const float s4 = rar ? 0.146189088f : 0.147594752f;    // 351/2401 | 2835/19208
+    const float t2 = rar ? 0.795918367f : 0.826530612f;    // 39/49 | 81/98
+    const float t3 = rar ? -0.758017493f : -0.787172012f;  // -260/343 | -270/343
+    const float t4 = rar ? 0.730945440f : 0.737973761f;    // 1755/2401 | 14175/19208
+    S = 1.0f + x * (-0.428571429f + x * (s2 + x * (s3 + x * s4)));
+    Td = 1.0f + x * (-0.857142857f + x * (t2 + x * (t3 + x * t4)));
+  }
   static __device__ __forceinline__ float rar(float x, float) {
     const float z = exp2f(__log2f(1.0f + x) * 0.142857142857f);
     const float s = 1.0f + z * (1.0f + z * (1.0f + z * (1.0f + z * (1.0f + z * (1.0f + z)))));
@@ -145,10 +167,27 @@ __device__ __forceinline__ bool pert_side(T g, const PFace<T>& W0, const T* q, b
   return true;
 }
 
+// Reciprocals of a side that the series form of its pressure function uses.
+template <class T>
+struct PSideInv {
+  T ip, cg, irc;  // 1/p, c/gamma, 1/(rho c)
+};
+
 // Pressure function of side K at trial p = p0 + d, in perturbation form.
 template <class T, class P>
-__device__ __forceinline__ void pert_pressure_fn(T g, const PSide<T>& K, T p, T d, T& f, T& fd) {
+__device__ __forceinline__ void pert_pressure_fn(T g, const PSide<T>& K, const PSideInv<T>& I, T p, T d, T& f,
+                                                 T& fd) {
   const T dpk = d - K.dp;  // p - p_K
+  if constexpr (P::series) {
+    const T x = dpk * I.ip;
+    if (Math<T>::abs_(x) <= P::xs) {
+      T S, Td;
+      P::pressure_series(x, S, Td);
+      f = I.cg * x * S;
+      fd = I.irc * Td;
+      return;
+    }
+  }
   if (dpk <= T(0)) {
     const T x = dpk / K.p;
     const T r = P::rar(x, g);  // (p/p_K)^((g-1)/2g) - 1
@@ -191,12 +230,21 @@ __device__ __forceinline__ int pert_riemann(T g, const PFace<T>& W0, const PSide
   T d = T(0.5) * (L.dp + R.dp) - T(0.125) * du * (L.rho + R.rho) * (L.c + R.c);  // PVRS in dp
   if (W0.p + d < floor_p) d = floor_p - W0.p;
   const T scale = Math<T>::abs_(L.dp) + Math<T>::abs_(R.dp) + (L.rho * L.c + R.rho * R.c) * Math<T>::abs_(du);
+  PSideInv<T> IL{}, IR{};
+  if constexpr (P::series) {
+    IL.ip = T(1) / L.p;
+    IR.ip = T(1) / R.p;
+    IL.cg = L.c * P::inv_gamma;
+    IR.cg = R.c * P::inv_gamma;
+    IL.irc = T(1) / (L.rho * L.c);
+    IR.irc = T(1) / (R.rho * R.c);
+  }
   T fl, fdl, fr, fdr, step = T(0);
   bool conv = false;
   for (int it = 0; it < Math<T>::max_iter; ++it) {
     const T p = W0.p + d;
-    pert_pressure_fn<T, P>(g, L, p, d, fl, fdl);
-    pert_pressure_fn<T, P>(g, R, p, d, fr, fdr);
+    pert_pressure_fn<T, P>(g, L, IL, p, d, fl, fdl);
+    pert_pressure_fn<T, P>(g, R, IR, p, d, fr, fdr);
     T dn = d - (fl + fr + du) / (fdl + fdr);
     if (W0.p + dn < floor_p) dn = floor_p - W0.p;
     step = dn - d;
@@ -210,6 +258,22 @@ __device__ __forceinline__ int pert_riemann(T g, const PFace<T>& W0, const PSide
   if (!conv) return 1;
   const T ps = W0.p + d;
   if (ps < T(0.1) * fmin(L.p, R.p)) return 1;  // strong rarefaction: near vacuum
+  // p*/p_K - 1 and the rarefaction power (p*/p_K)^((g-1)/2g) - 1 of a side,
+  // from the series near p_K
+  auto rel = [&](T dpk, T pk, const PSideInv<T>& I) -> T {
+    if constexpr (P::series) return dpk * I.ip;
+    else return dpk / pk;
+  };
+  auto rar = [&](T x) -> T {
+    if constexpr (P::series) {
+      if (Math<T>::abs_(x) <= P::xs) {
+        T S, Td;
+        P::pressure_series(x, S, Td);
+        return P::beta * x * S;
+      }
+    }
+    return P::rar(x, g);
+  };
   // f_K at the converged p* from the last evaluation, one (converged) Newton
   // step away; the second-order remainder is below rounding
   fl += fdl * step;
@@ -219,10 +283,10 @@ __device__ __forceinline__ int pert_riemann(T g, const PFace<T>& W0, const PSide
   const T g6 = (g - T(1)) / (g + T(1));
   if (us >= T(0)) {
     side = -1;
-    const T x = (d - L.dp) / L.p;  // p*/p_L - 1
+    const T x = rel(d - L.dp, L.p, IL);  // p*/p_L - 1
     if (d <= L.dp) {
       if (L.un - L.c >= T(0)) { drho = L.drho; dun = L.dun; dp = L.dp; return 0; }
-      const T r = P::rar(x, g);
+      const T r = rar(x);
       const T cs = L.c * (T(1) + r);
       if (us - cs < T(0)) { drho = L.drho + L.rho * P::dens(x, g, r); dun = dus; dp = d; return 0; }
       fan_pert<T, P>(g, W0, L, true, drho, dun, dp);
@@ -237,7 +301,7 @@ __device__ __forceinline__ int pert_riemann(T g, const PFace<T>& W0, const PSide
     return 0;
   }
   side = 1;
-  const T x = (d - R.dp) / R.p;  // p*/p_R - 1
+  const T x = rel(d - R.dp, R.p, IR);  // p*/p_R - 1
   if (d > R.dp) {
     if (R.un + R.c * Math<T>::sqrt_(T(1) + (g + T(1)) / (T(2) * g) * x) <= T(0)) {
       drho = R.drho; dun = R.dun; dp = R.dp; return 0;
@@ -248,7 +312,7 @@ __device__ __forceinline__ int pert_riemann(T g, const PFace<T>& W0, const PSide
     return 0;
   }
   if (R.un + R.c <= T(0)) { drho = R.drho; dun = R.dun; dp = R.dp; return 0; }
-  const T r = P::rar(x, g);
+  const T r = rar(x);
   const T cs = R.c * (T(1) + r);
   if (us + cs > T(0)) { drho = R.drho + R.rho * P::dens(x, g, r); dun = dus; dp = d; return 0; }
   fan_pert<T, P>(g, W0, R, false, drho, dun, dp);
@@ -272,39 +336,63 @@ __device__ __forceinline__ void pert_flux(T g, const PFace<T>& W0, T drho, T dun
   F[4] = dh * un + W0.h * dun;
 }
 
-// FP64 full-state solver on W0 + dW for the faces the perturbation solver
-// hands back; kept out of line so the common path stays small.
+// Face state perturbation of a Riemann solve, the side whose transverse
+// velocity it carries (-1 left, +1 right, 0 vacuum) and status bits.
 template <class T>
-__device__ __noinline__ int pert_fallback_fp64(T g, const PFace<T>& W0, const PSide<T>& L, const PSide<T>& R,
-                                               T& drho, T& dun, T& dp, unsigned& status) {
+struct PStar {
+  T drho, dun, dp;
+  int side;
+  unsigned status;
+};
+
+// FP64 full-state solver on W0 + dW for the faces the perturbation solver
+// hands back; kept out of line so the common path stays small.  Arguments
+// and result by value: a pointer or reference into the caller's frame would
+// keep the caller's face states in local memory.
+template <class T>
+__device__ __noinline__ PStar<T> pert_fallback_fp64(T g, const PFace<T> W0, const PSide<T> L, const PSide<T> R) {
   const double rl = (double)W0.rho + (double)L.drho, rr = (double)W0.rho + (double)R.drho;
   const double ul = (double)W0.un + (double)L.dun, ur = (double)W0.un + (double)R.dun;
   const double pl = (double)W0.p + (double)L.dp, pr = (double)W0.p + (double)R.dp;
   double rho, u, p;
-  const int side = riemann_face((double)g, rl, ul, pl, rr, ur, pr, rho, u, p, status);
-  drho = (T)(rho - (double)W0.rho);
-  dun = (T)(u - (double)W0.un);
-  dp = (T)(p - (double)W0.p);
-  return side;
+  PStar<T> o;
+  o.status = 0;
+  o.side = riemann_face((double)g, rl, ul, pl, rr, ur, pr, rho, u, p, o.status);
+  o.drho = (T)(rho - (double)W0.rho);
+  o.dun = (T)(u - (double)W0.un);
+  o.dp = (T)(p - (double)W0.p);
+  return o;
 }
 
+// Face-order gas flux perturbation (as pert_flux), status bits and whether
+// the FP64 fallback solved the face.
+template <class T>
+struct PFlux {
+  T F[5];
+  unsigned status, fallback;
+};
+
 // Gas flux perturbation through a face from the primitive perturbations of
-// its two reconstructed states (already checked physical); face-order output
-// as pert_flux.  One out-of-line copy serves the three sweep directions.
+// its two reconstructed states (already checked physical).  One out-of-line
+// copy serves the three sweep directions; arguments and result by value.
 template <class T, class P>
-__device__ __noinline__ void pert_face_flux(T g, const PFace<T> W0, const PSide<T> L, const PSide<T> R, T* F,
-                                            unsigned* status, unsigned* nfallback) {
-  T drho, dun, dp;
-  int side = 0;
-  if (pert_riemann<T, P>(g, W0, L, R, drho, dun, dp, side) != 0) {
-    ++*nfallback;
-    side = pert_fallback_fp64(g, W0, L, R, drho, dun, dp, *status);
+__device__ __noinline__ PFlux<T> pert_face_flux(T g, const PFace<T> W0, const PSide<T> L, const PSide<T> R) {
+  PFlux<T> o;
+  o.status = 0;
+  o.fallback = 0;
+  PStar<T> st;
+  st.side = 0;
+  if (pert_riemann<T, P>(g, W0, L, R, st.drho, st.dun, st.dp, st.side) != 0) {
+    o.fallback = 1;
+    st = pert_fallback_fp64(g, W0, L, R);
+    o.status = st.status;
   }
   T dut1 = T(0), dut2 = T(0);
-  if (side < 0) { dut1 = L.dut1; dut2 = L.dut2; }
-  else if (side > 0) { dut1 = R.dut1; dut2 = R.dut2; }
+  if (st.side < 0) { dut1 = L.dut1; dut2 = L.dut2; }
+  else if (st.side > 0) { dut1 = R.dut1; dut2 = R.dut2; }
   else { dut1 = -W0.ut1; dut2 = -W0.ut2; }  // vacuum: no transverse motion
-  pert_flux<T>(g, W0, drho, dun, dut1, dut2, dp, F);
+  pert_flux<T>(g, W0, st.drho, st.dun, dut1, dut2, st.dp, o.F);
+  return o;
 }
 
 template <class T>
@@ -338,7 +426,7 @@ struct PertArgs {
   int stage2;
   double* partials;  // stage 2: [nf + 1][gridDim.x] block sums of V*E', then block dt minima
   unsigned* status;
-  int tiles_r, tiles_t;
+  int tiles_r, tiles_z;  // tile counts along r and z (block -> tile: r fastest, then z, then theta)
   // the grid's and the drag's parameters in the state precision, converted
   // once on the host (GB300's FP64 pipe is narrow: per-use conversions of the
   // double originals cost latency in the float kernel)
@@ -495,13 +583,14 @@ __device__ __forceinline__ void sweep_pert_chunk(const PertArgs<T>& a, const T* 
         const bool okl = __shfl_up_sync(FULL, ok ? 1 : 0, 1, L) != 0;
         if (do_face) {
           if (ok && okl) {
-            T Ff[5];
-            pert_face_flux<T, P>(gam, Wm, sl, sm, Ff, &status, &nfallback);
-            F[RHO] = Ff[0] * area;
-            F[Axes<D>::n] = Ff[1] * area;
-            F[Axes<D>::t1] = Ff[2] * area;
-            F[Axes<D>::t2] = Ff[3] * area;
-            F[EN] = Ff[4] * area;
+            const PFlux<T> ff = pert_face_flux<T, P>(gam, Wm, sl, sm);
+            status |= ff.status;
+            nfallback += ff.fallback;
+            F[RHO] = ff.F[0] * area;
+            F[Axes<D>::n] = ff.F[1] * area;
+            F[Axes<D>::t1] = ff.F[2] * area;
+            F[Axes<D>::t2] = ff.F[3] * area;
+            F[EN] = ff.F[4] * area;
           } else {
             status |= STATUS_NONPHYSICAL;
 #pragma unroll
@@ -568,19 +657,14 @@ __device__ __forceinline__ void sweep_pert(const PertArgs<T>& a, const T* sE, T*
     sweep_pert_chunk<T, NF, TR, TT, TZ, NT, D, P, RC, ACC>(a, sE, sG, i0, j0, k0, ch * 32, status, nfallback);
 }
 
-// The r and theta sweeps write separate accumulators when they fit: their
-// chunks then form one pool with no barrier between the two sweeps (the
-// r sweep alone left a quarter of its warp slots idle at the barrier).
-template <class T, int NF, int TR, int TT, int TZ>
-__host__ __device__ constexpr bool pert_merged_sweeps() {
-  return (size_t)NF * ((TR + 4) * (TT + 4) * (TZ + 4) + 2 * TR * TT * TZ) * sizeof(T) <= (size_t)227 * 1024;
-}
 // Dynamic shared memory of stage_pert_kernel: the staged tile and halo, and
-// one accumulator of the flux divergence (two with merged sweeps).
+// the accumulator of the flux divergence.  (A second accumulator, which let
+// the r and theta sweeps share one pool of chunks without a barrier between
+// them, measured 15 % slower on the FP32 bench grid: 101 KB per block leaves
+// two blocks per SM too little L1 for the face solver's stack.)
 template <class T, int NF, int TR, int TT, int TZ>
 __host__ __device__ constexpr size_t pert_smem_bytes() {
-  return (size_t)NF * ((TR + 4) * (TT + 4) * (TZ + 4) + (pert_merged_sweeps<T, NF, TR, TT, TZ>() ? 2 : 1) * TR * TT * TZ) *
-         sizeof(T);
+  return (size_t)NF * ((TR + 4) * (TT + 4) * (TZ + 4) + TR * TT * TZ) * sizeof(T);
 }
 
 // Cell-centre equilibrium coefficients.
@@ -790,13 +874,14 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sE = reinterpret_cast<T*>(smem_raw);
   T* sG = sE + NF * BOX;
-  constexpr bool MERGED = pert_merged_sweeps<T, NF, TR, TT, TZ>();
-  T* sG1 = MERGED ? sG + NF * NCORE : sG;  // the theta sweep's accumulator
   const DevGrid& g = a.g;
   const int tile = blockIdx.x;
+  // r fastest, then z, then theta: the tiles whose halos a tile re-reads
+  // (its r, z and theta neighbours) run at most tiles_r x tiles_z blocks
+  // apart, so the re-reads hit in L2
   const int i0 = (tile % a.tiles_r) * TR;
-  const int j0 = ((tile / a.tiles_r) % a.tiles_t) * TT;
-  const int k0 = (tile / (a.tiles_r * a.tiles_t)) * TZ;
+  const int k0 = ((tile / a.tiles_r) % a.tiles_z) * TZ;
+  const int j0 = (tile / (a.tiles_r * a.tiles_z)) * TT;
   unsigned status = 0, nfallback = 0;
 
   // staging in batches of CH cells per thread: every load of a batch is
@@ -863,20 +948,9 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
     }
   }
   __syncthreads();
-  if constexpr (MERGED) {
-    constexpr int C0 = (sweep_items<TR, TT, TZ, 0>() + 31) / 32, C1 = (sweep_items<TR, TT, TZ, 1>() + 31) / 32;
-    for (int ch = threadIdx.x >> 5; ch < C0 + C1; ch += NT / 32) {
-      if (ch < C0)
-        sweep_pert_chunk<T, NF, TR, TT, TZ, NT, 0, P, RC, false>(a, sE, sG, i0, j0, k0, ch * 32, status, nfallback);
-      else
-        sweep_pert_chunk<T, NF, TR, TT, TZ, NT, 1, P, RC, false>(a, sE, sG1, i0, j0, k0, (ch - C0) * 32, status,
-                                                                 nfallback);
-    }
-  } else {
-    sweep_pert<T, NF, TR, TT, TZ, NT, 0, P, RC, false>(a, sE, sG, i0, j0, k0, status, nfallback);
-    __syncthreads();
-    sweep_pert<T, NF, TR, TT, TZ, NT, 1, P, RC, true>(a, sE, sG, i0, j0, k0, status, nfallback);
-  }
+  sweep_pert<T, NF, TR, TT, TZ, NT, 0, P, RC, false>(a, sE, sG, i0, j0, k0, status, nfallback);
+  __syncthreads();
+  sweep_pert<T, NF, TR, TT, TZ, NT, 1, P, RC, true>(a, sE, sG, i0, j0, k0, status, nfallback);
   __syncthreads();
   sweep_pert<T, NF, TR, TT, TZ, NT, 2, P, RC, true>(a, sE, sG, i0, j0, k0, status, nfallback);
   __syncthreads();
@@ -897,7 +971,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       q[f] = sE[f * BOX + sidx];
-      G[f] = MERGED ? sG[f * NCORE + cidx] + sG1[f * NCORE + cidx] : sG[f * NCORE + cidx];
+      G[f] = sG[f * NCORE + cidx];
     }
     if (RC == RECON_CONS) {  // the staged gas departures are conservative
       T qc[5];
@@ -925,7 +999,11 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
     const T iv = a.t.ivol[gi];
     T E[NF];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) E[f] = a.base[f][lin] + tau * G[f] * iv;
+    for (int f = 0; f < NF; ++f) {
+      // stage 1 updates its own input, whose raw values are staged
+      const T b = !a.stage2 && (RC == RECON_CONS || f >= 5) ? sE[f * BOX + sidx] : a.base[f][lin];
+      E[f] = b + tau * G[f] * iv;
+    }
     if constexpr (NF > 5) pert_drag<T, NF, XT>(a, ce, gi, E, tau);
 #pragma unroll
     for (int f = 0; f < NF; ++f) a.out[f][lin] = E[f];
@@ -945,30 +1023,36 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
     }
   }
   if (a.stage2) {
-    // threads, warps, the block and the grid sum in FP64 (the CFL minimum,
-    // exact in any precision, stays in the state's); the sweeps are over, so
-    // the start of the staging area is free (the epilogue reads only core
-    // cells, which begin two z planes into it)
-    constexpr int NW = NT / 32;
-    double* red = reinterpret_cast<double*>(smem_raw);
+    // the block's sums in FP64: each thread's partials to shared memory (the
+    // staging area, free once every thread is past the epilogue), then NF x 8
+    // threads add 32 of them each and 8-lane shuffles finish; the CFL minimum,
+    // exact in any precision, stays in the state's
+    constexpr int NW = NT / 32, SEG = NT / 8;
+    static_assert(NT % 8 == 0 && NF * 8 <= NT, "reduction layout");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      dtmin = fmin(dtmin, __shfl_xor_sync(0xffffffffu, dtmin, o));
-#pragma unroll
-      for (int f = 0; f < NF; ++f) sums[f] += __shfl_down_sync(0xffffffffu, sums[f], o);
-    }
-    if (lane == 0) {
-      red[warp * (NF + 1)] = (double)dtmin;
-#pragma unroll
-      for (int f = 0; f < NF; ++f) red[warp * (NF + 1) + 1 + f] = sums[f];
-    }
+    for (int o = 16; o > 0; o >>= 1) dtmin = fmin(dtmin, __shfl_xor_sync(0xffffffffu, dtmin, o));
     __syncthreads();
-    if (threadIdx.x <= NF) {
-      const int q = threadIdx.x;
-      double acc = q == 0 ? red[0] : red[q];
-      for (int w = 1; w < NW; ++w) acc = q == 0 ? fmin(acc, red[w * (NF + 1)]) : acc + red[w * (NF + 1) + q];
-      a.partials[(size_t)(q == 0 ? NF : q - 1) * gridDim.x + blockIdx.x] = acc;
+    double* red = reinterpret_cast<double*>(smem_raw);  // [NF][NT] partials, then [NW] minima
+#pragma unroll
+    for (int f = 0; f < NF; ++f) red[f * NT + threadIdx.x] = sums[f];
+    if (lane == 0) red[NF * NT + warp] = (double)dtmin;
+    __syncthreads();
+    if (threadIdx.x < NF * 8) {
+      const int f = threadIdx.x >> 3, seg = threadIdx.x & 7;
+      const double* src = red + f * NT + seg * SEG;
+      double acc = 0.0;
+#pragma unroll 8
+      for (int u = 0; u < SEG; ++u) acc += src[u];
+      const unsigned grp = 0xffu << (lane & 24);  // this 8-lane group (all of it active)
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) acc += __shfl_down_sync(grp, acc, o, 8);
+      if (seg == 0) a.partials[(size_t)f * gridDim.x + blockIdx.x] = acc;
+    }
+    if (threadIdx.x == NT - 1) {
+      double m = red[NF * NT];
+      for (int w = 1; w < NW; ++w) m = fmin(m, red[NF * NT + w]);
+      a.partials[(size_t)NF * gridDim.x + blockIdx.x] = m;
     }
   }
   if (status) atomicOr(a.status, status);

@@ -45,7 +45,8 @@ class rossbi_grid_desc(ctypes.Structure):
 
 class rossbi_disc_params(ctypes.Structure):
     _fields_ = [("sigma0", ctypes.c_double), ("beta_sigma", ctypes.c_double), ("T0", ctypes.c_double),
-                ("beta_T", ctypes.c_double)]
+                ("beta_T", ctypes.c_double), ("bump_delta", ctypes.c_double), ("bump_r0", ctypes.c_double),
+                ("bump_width", ctypes.c_double)]
 
 
 class rossbi_dust_params(ctypes.Structure):
@@ -156,6 +157,7 @@ def rossbi_init_grid(desc: rossbi_grid_desc, stream=None):
 
 
 def rossbi_set_equilibrium(grid, disc):
+    # four power-law parameters, optionally followed by the bump's three
     p = None if disc is None else ctypes.byref(rossbi_disc_params(*disc))
     _check(load().rossbi_set_equilibrium(grid, p), "rossbi_set_equilibrium")
 

@@ -15,11 +15,10 @@ Recipes (all on the library's equilibrium E0):
            u' = (1/r) dpsi/dtheta, v' = -dpsi/dr, rho and P at equilibrium.
            Dust: rho_d = ratio rho0 (1 + a_d xi_d), moving with the gas; with
            several species each takes ratio / n of it, with its own noise.
-  rwi    : rho = rho0 (1 + delta G), G a radial Gaussian at r0, at the
-           equilibrium temperature (P scaled alike), the azimuthal velocity
-           in radial balance with the bump's pressure gradient,
-           v_theta^2 = v_theta0^2 + r T delta G' / (1 + delta G), and the
-           seed v_r = eps v_theta0 sin(m theta) G (v_theta0 inertial).
+  rwi    : the equilibrium carries the radial density bump (rho, P x (1 +
+           delta G), G a Gaussian at r0, v_theta0 in radial balance with it:
+           rossbi_disc_params' bump); the departure is the seed
+           v_r = eps v_theta0 sin(m theta) G (v_theta0 inertial).
 """
 import math
 
@@ -39,7 +38,7 @@ class Grid:
                            w.omega_frame, w.cfl, w.n_dust, precision, w.recon)
         self.h = R.rossbi_init_grid(desc, stream)
         try:
-            R.rossbi_set_equilibrium(self.h, w.disc)
+            R.rossbi_set_equilibrium(self.h, w.disc_params())
         except Exception:
             R.rossbi_destroy(self.h)
             self.h = None
@@ -195,24 +194,14 @@ class Grid:
             Ep[syn.F_MV] = drho * v0
             Ep[syn.F_EN] = 0.5 * drho * v0 * v0
             return Ep
-        if w.ic == "rwi":  # stationary density bump at the equilibrium temperature, seeded v_r of mode m
+        if w.ic == "rwi":  # the density bump belongs to the equilibrium; only the seeded v_r of mode m departs
             r = self.centres(0)[None, None, :]
             th = self.centres(1)[None, :, None]
             G = np.exp(-((r - w.rwi_r0) / (math.sqrt(2.0) * w.rwi_width)) ** 2)
-            dG = -(r - w.rwi_r0) / w.rwi_width ** 2 * G
-            sc = 1.0 + w.rwi_delta * G
-            P0 = (g - 1.0) * (E0[syn.F_EN][:, None, :] - 0.5 * rho0 * v0 * v0)
             vth0 = v0 + w.omega_frame * r  # the inertial equilibrium azimuthal velocity
-            # radial balance with the bump's own pressure gradient (P = T rho, T kept)
-            dv = np.sqrt(vth0 * vth0 + r * (P0 / rho0) * w.rwi_delta * dG / sc) - vth0
             vr = w.rwi_eps * vth0 * np.sin(w.rwi_mode * th) * G
-            rho = rho0 * sc
-            drho = rho - rho0
-            Ep[syn.F_RHO] = drho
-            Ep[syn.F_MU] = rho * vr
-            Ep[syn.F_MV] = drho * v0 + rho * dv
-            Ep[syn.F_EN] = (0.5 * drho * v0 * v0 + rho * v0 * dv + 0.5 * rho * dv * dv + 0.5 * rho * vr * vr
-                            + P0 * w.rwi_delta * G / (g - 1.0))
+            Ep[syn.F_MU] = rho0 * vr
+            Ep[syn.F_EN] = 0.5 * rho0 * vr * vr
             return Ep
         if w.ic != "vortex":
             raise ValueError(w.ic)

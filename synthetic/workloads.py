@@ -51,7 +51,7 @@ class Workload:
     omega_frame: float = 1.0
     cfl: float = 0.5
     n_dust: int = 0
-    disc: tuple = None           # (sigma0, beta_sigma, T0, beta_T) or None
+    disc: tuple = None           # (sigma0, beta_sigma, T0, beta_T) or None; see disc_params
     seed: int = 0
     noise_amp: float = 0.0       # relative gas-density noise amplitude
     vortices: tuple = ()         # ((r_v, theta_v), ...)
@@ -68,10 +68,19 @@ class Workload:
     recon: int = RECON_CONSERVATIVE
     dust_stokes_factors: tuple = ()  # several species: St of species s = stokes x factor[s] (factor[0] = 1)
     rwi_mode: int = 0            # "rwi": azimuthal mode m of the seed
-    rwi_delta: float = 0.0       # relative amplitude of the density bump
+    rwi_delta: float = 0.0       # relative amplitude of the equilibrium's density bump
     rwi_width: float = 0.0       # Delta_r of the bump
     rwi_eps: float = 0.0         # seed amplitude, v_r = eps v_theta0 sin(m theta) G(r)
     rwi_r0: float = 1.0          # radius of the bump
+
+    def disc_params(self):
+        """The equilibrium's seven parameters (sigma0, beta_sigma, T0, beta_T,
+        bump_delta, bump_r0, bump_width) as both libraries take them: the
+        radial density bump only on the "rwi" workloads, else delta = 0."""
+        if self.disc is None:
+            return None
+        bump = (self.rwi_delta, self.rwi_r0, self.rwi_width) if self.ic == "rwi" else (0.0, 1.0, 0.0)
+        return tuple(self.disc) + bump
 
     @property
     def ncell(self) -> int:
@@ -129,12 +138,18 @@ THROUGHPUT = _disc("bifluid_two_vortices_512x1024x128", 512, 1024, 128, 50, ic="
 # stationary solution, rho = rho0 (1 + delta G), G = exp(-((r - r0)/(sqrt(2)
 # Delta_r))^2), at the equilibrium temperature (P scaled alike) with the
 # azimuthal velocity in radial balance with the bump's pressure gradient, and
-# the seed v_r = eps v_theta0 sin(m theta) G with eps = 1e-4 and mode m.  The paper
-# takes the setup of Meheut et al. (2012) without printing delta and Delta_r:
-# delta = 0.25 and Delta_r = 0.05 r0 (= H(r0)) here.  Gas only, in the
-# equal-Mach frame; growth rates of the modes are measured, not pinned.
-RWI = _disc("rwi_m4_128x256x32", 128, 256, 32, 2000, ic="rwi", rwi_mode=4, rwi_delta=0.25, rwi_width=0.05,
-            rwi_eps=1e-4, omega_frame=equal_mach_frame(0.5, 2.0))
+# the seed v_r = eps v_theta0 sin(m theta) G with eps = 1e-4 and mode m.  The
+# paper takes the setup of a cited work without printing delta and Delta_r:
+# delta = 0.25 and Delta_r = 0.05 r0 (= H(r0)) here.  The bump is resolved by
+# a narrower annulus, r in [0.6, 1.6] (128 log-spaced cells: 6.5 per Delta_r),
+# and a thinner disc, z in +-2 H(r0); gas only, in that annulus's equal-Mach
+# frame.  The modes' growth is measured, not pinned.
+RWI = Workload(
+    name="rwi_m4_128x256x16", geometry=GEOM_CYL, nr=128, nth=256, nz=16,
+    x0=(0.6, 0.0, -2.0 * H_ASPECT), x1=(1.6, 2.0 * math.pi, 2.0 * H_ASPECT),
+    bc_lo=(BC_EQUILIBRIUM, BC_PERIODIC, BC_EQUILIBRIUM), bc_hi=(BC_EQUILIBRIUM, BC_PERIODIC, BC_EQUILIBRIUM),
+    disc=DISC_PARAMS, ic="rwi", steps=4000, rwi_mode=4, rwi_delta=0.25, rwi_width=0.05, rwi_eps=1e-4,
+    omega_frame=equal_mach_frame(0.6, 1.6))
 
 # Cylindrical explosion (Sect. 4.1; Toro ch. 17): a 2-D Riemann problem on the
 # polar mesh, (rho, P) = (1, 1) for r <= 0.4 and (0.125, 0.1) outside, at rest;

@@ -199,3 +199,87 @@ def test_pert_box_conservation(lib):
         scale = np.abs(s0) + 1e-3
         for f in (4, 8):
             assert abs(s1[f] - s0[f]) <= tol * scale[f]
+
+
+def _group_errors(w, E0, a, b, b_is_pert):
+    """Relative L1 per conserved group of state b against the FP64 state a
+    (dust groups summed over species), read one field at a time."""
+    rr = w.x0[0] * (w.x1[0] / w.x0[0]) ** (np.arange(w.nr + 1) / w.nr)
+    V = 0.5 * (rr[1:] ** 2 - rr[:-1] ** 2)
+    nd = (a.shape[0] - 5) // 4
+    groups = {"mass": [4], "momentum": [0, 1, 2], "energy": [3]}
+    if nd:
+        groups["dust_mass"] = [8 + 4 * s for s in range(nd)]
+        groups["dust_momentum"] = [5 + 4 * s + c for s in range(nd) for c in range(3)]
+    out = {}
+    for name, fields in groups.items():
+        num = den = 0.0
+        for q in fields:
+            x64 = a[q].double().cpu().numpy()
+            x = b[q].double().cpu().numpy()
+            if b_is_pert and q < 5:
+                x = x + E0[q][:, None, :]
+            num += float((V * np.abs(x - x64)).sum())
+            den += float((V * np.abs(x64)).sum())
+        out[name] = num / den
+    return out
+
+
+def test_fp32_full_size_vortex_200_steps(lib):
+    """The bi-fluid vortex at its full 256x512x64 size over its 200 steps,
+    FP32 form against FP64 form on the FP64 form's dt sequence.
+
+    After 100 steps the FP32 form is within 1e-5 relative L1 per conserved
+    quantity.  Past that the vortex amplifies any perturbation of the state:
+    the FP64 form started from the same state perturbed by 6e-8 relative
+    (seeded Gaussian, FP32's rounding of a stored value) departs from the
+    unperturbed FP64 run by ~2e-5 after 200 steps.  So at 200 steps the
+    check is that the FP32 form stays inside that spread: its error is no
+    larger than the FP64 form's own response to an FP32-sized rounding of
+    its input.  FP64-fallback faces stay below 1e-5 of all faces."""
+    import torch
+    R, W = lib
+    w = syn.VORTEX
+    g64 = W.Grid(w, precision=R.ROSSBI_FP64)
+    gp = W.Grid(w, precision=R.ROSSBI_FP64)
+    g32 = W.Grid(w, precision=R.ROSSBI_FP32_PERT)
+    a, c, b = g64.initial_state(), gp.initial_state(), g32.initial_state()
+    gen = torch.Generator(device=c.device).manual_seed(2207)
+    c.mul_(1.0 + 6e-8 * torch.randn(c.shape, device=c.device, dtype=c.dtype, generator=gen))
+    E0 = g64.equilibrium()
+    dt = g64.cfl_dt(a)
+    rep = {}
+    for n in range(1, 201):
+        ndt = g64.step(a, dt=dt, want_next_dt=True)
+        gp.step(c, dt=dt)
+        g32.step(b, dt=dt)
+        dt = ndt
+        if n in (100, 200):
+            rep[n] = (_group_errors(w, E0, a, b, True), _group_errors(w, E0, a, c, False))
+    status = g64.take_status() | gp.take_status() | g32.take_status()
+    nfb = R.rossbi_fallback_count(g32.h)
+    for g in (g64, gp, g32):
+        g.close()
+    for n, (e32, spread) in rep.items():
+        print(n, "fp32", {k: f"{v:.2e}" for k, v in e32.items()}, "fp64 spread", {k: f"{v:.2e}" for k, v in spread.items()})
+    print("fallback faces", nfb, "of", 200 * 2 * 3 * w.ncell)
+    assert status == 0
+    assert all(v <= TOL32 for v in rep[100][0].values()), rep[100]
+    e32, spread = rep[200]
+    assert all(e32[k] <= spread[k] for k in e32), rep[200]
+    assert nfb <= 1e-5 * 200 * 2 * 3 * w.ncell
+
+
+def test_fp32_full_size_throughput_50_steps(lib):
+    """The 67.1 M-cell two-vortex grid (the bench's timed workload) over its
+    50 steps: FP32 form against FP64 form on the FP64 form's dt sequence,
+    relative L1 per conserved quantity (dust groups included) <= 1e-5, with
+    the element-wise error and the FP64-fallback faces printed."""
+    import torch
+    import bench
+    R, W = lib
+    rep = bench.fp32_error_vs_fp64(R, W, syn, torch, syn.THROUGHPUT, 50)
+    print("fp32 vs fp64", rep)
+    assert rep["status"] == "ok"
+    assert all(e <= TOL32 for e in rep["rel_l1"].values()), rep["rel_l1"]
+    assert rep["fallback_faces"] <= 1e-5 * rep["faces"]
