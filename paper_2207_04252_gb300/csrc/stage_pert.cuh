@@ -46,6 +46,23 @@ struct PertTables {
   unsigned long long* fallbacks;  // count of FP64 fallback Riemann faces
 };
 
+// One state element global -> shared by an asynchronous copy (cp.async with
+// the L1-allocating .ca policy: the halo cells are read again by the
+// neighbouring tiles), and the wait for all of a thread's copies.
+template <class T>
+__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 template <class T> struct Math;
 template <> struct Math<float> {
   static __device__ __forceinline__ float log1p_(float x) { return log1pf(x); }
@@ -884,9 +901,29 @@ __global__ void __launch_bounds__(NT, MINB) stage_pert_kernel(const PertArgs<T> 
   const int j0 = (tile / (a.tiles_r * a.tiles_z)) * TT;
   unsigned status = 0, nfallback = 0;
 
+  if constexpr (RC == RECON_CONS) {
+    // the conservative departures are staged as they are stored: each cell's
+    // fields go global -> shared by asynchronous copies (cp.async, no
+    // registers), all of a thread's cells in flight at once; equilibrium
+    // ghosts are zero departures
+    for (int idx = threadIdx.x; idx < BOX; idx += NT) {
+      const int x = idx % BX - 2, y = (idx / BX) % BY - 2, z = idx / (BX * BY) - 2;
+      const int outside = (x < 0 || x >= TR) + (y < 0 || y >= TT) + (z < 0 || z >= TZ);
+      if (outside > 1) continue;  // edge and corner cells of the box: no sweep reads them
+      int c[3] = {i0 + x, j0 + y, k0 + z};
+      if (!resolve_cell(g, c)) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) sE[f * BOX + idx] = T(0);
+      } else {
+        const size_t lin = ((size_t)c[2] * g.nth + c[1]) * g.nr + c[0];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) cp_async_elem<T>(sE + f * BOX + idx, a.in[f] + lin);
+      }
+    }
+    cp_async_wait_all();
+  } else {
   // staging in batches of CH cells per thread: every load of a batch is
   // issued before any of them is used (memory-level parallelism)
-  {
     constexpr int NIT = (BOX + NT - 1) / NT;
     constexpr int CH = 2;
     for (int it0 = 0; it0 < NIT; it0 += CH) {
