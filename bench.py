@@ -7,8 +7,10 @@ with the state resident in HBM and the CFL step kept on the device.  The
 state (2.4 GB in the default FP32 perturbation form, 4.8 GB in FP64, for the
 512x1024x128 bi-fluid grid) is far larger than L2, so no flush is needed
 between steps.  The line also carries the FP64 form's throughput on the same
-grid and the FP32 form's relative L1 error against the FP64 form after 100
-steps of the 128x256x32 noisy disc.
+grid, the FP32 form's relative L1 error against the FP64 form over the timed
+workload's 50 steps (and over 100 steps of the 128x256x32 noisy disc), the
+roofline of the stage kernel against HBM, instruction issue and the FMA
+throughput measured in the same run, and the adjoint's cost.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32]
                   [--workload NAME] [--impl ours|reference]
@@ -569,6 +571,17 @@ def run_ours(args):
         # the 70 % HBM target is beyond an exact Riemann solve per face
         cells_per_s_cap = ISSUE_PEAK_WARP_INST_S / ipc
         roofline["hbm_frac_at_issue_roof"] = cells_per_s_cap * 2.5 * g.nf * elem / 1e9 / peak
+    # the ALU roof: the kernel's arithmetic (FLOP per cell-stage of the
+    # state's precision, counted by ncu in the committed capture) against the
+    # device's FMA throughput measured here
+    roofline_alu = None
+    if prof is not None and "flop_per_cell" in prof and rank == 0:
+        fma_peak = R.rossbi_measure_fma_peak(args.precision == "fp64", torch.cuda.current_stream())
+        achieved_f = float(prof["flop_per_cell"]) * w.ncell / avg_launch_s
+        roofline_alu = {"bound": "alu", "achieved": achieved_f / 1e12, "peak": fma_peak / 1e12, "unit": "TFLOP/s",
+                        "frac": achieved_f / fma_peak, "flop_per_cell": float(prof["flop_per_cell"]),
+                        "precision": args.precision, "peak_kind": "measured (FMA chains, this run)",
+                        "source": prof["_file"]}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -577,7 +590,7 @@ def run_ours(args):
                 "config": {"workload": w.name, "precision": args.precision, "cells": w.ncell, "fields": g.nf,
                            "state_bytes": state_bytes, "parallelism": f"replicas{world}",
                            "l2": "inputs larger than L2 (no flush needed)", "indirect_x_ref": args.indirect},
-                "roofline": roofline, "roofline_issue": roofline_issue, "e2e": e2e,
+                "roofline": roofline, "roofline_issue": roofline_issue, "roofline_alu": roofline_alu, "e2e": e2e,
                 "gpu_launches": (7 if args.indirect else 3) * args.steps, "clocks": clocks,
                 "status": R.status_string(status)}
         if args.precision == "fp32" and not args.no_extras:

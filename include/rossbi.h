@@ -388,6 +388,16 @@ rossbi_status rossbi_take_status(rossbi_grid* g);
 rossbi_status rossbi_profile_enable(rossbi_grid* g, int enable);
 rossbi_status rossbi_profile_read(rossbi_grid* g, double* stage_ms, int* stage_launches);
 
+/* Measurement: the device's fused multiply-add throughput in FLOP/s (2 per
+ * FMA), FP32 (fp64 = 0) or FP64 (fp64 != 0), timed with CUDA events on
+ * cuda_stream (a cudaStream_t; NULL = legacy default stream) over a kernel
+ * of eight independent FMA chains per thread on 8 blocks of 256 threads per
+ * SM, after one warm-up launch: the ALU roof against which the stage
+ * kernels' arithmetic is reported.  Takes ~0.1 s; synchronises the stream.
+ * Errors: ROSSBI_ERR_ARG (flops_per_s == NULL), ROSSBI_ERR_OOM,
+ * ROSSBI_ERR_CUDA. */
+rossbi_status rossbi_measure_fma_peak(int fp64, void* cuda_stream, double* flops_per_s);
+
 /* Number of conservative fields (5 + 4 n_dust) and the precision form. */
 int rossbi_nfields(const rossbi_grid* g);
 int rossbi_precision(const rossbi_grid* g);

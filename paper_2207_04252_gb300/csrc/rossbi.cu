@@ -1071,6 +1071,57 @@ rossbi_status step_device(rossbi_grid* g, void* const* state, void* const* scrat
 
 }  // namespace
 
+namespace {
+// Eight independent FMA chains per thread; the result is stored so that
+// nothing is eliminated.
+template <class T>
+__global__ void fma_peak_kernel(T* out, int iters) {
+  T a[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) a[c] = T(threadIdx.x + c) * T(1e-7);
+  const T m = T(0.9999999), k = T(1e-9);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      if constexpr (sizeof(T) == 4) a[c] = fmaf(a[c], m, k);
+      else a[c] = fma(a[c], m, k);
+    }
+  }
+  T s = T(0);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) s += a[c];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <class T>
+rossbi_status fma_peak(cudaStream_t st, int iters, double* flops) {
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = 8 * sms, threads = 256;
+  T* out = nullptr;
+  if (cudaMalloc(&out, (size_t)blocks * threads * sizeof(T)) != cudaSuccess) return ROSSBI_ERR_OOM;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  rossbi_status r = ROSSBI_OK;
+  float ms = 0.0f;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) r = ROSSBI_ERR_CUDA;
+  if (r == ROSSBI_OK) {
+    fma_peak_kernel<T><<<blocks, threads, 0, st>>>(out, iters);  // warm-up
+    cudaEventRecord(e0, st);
+    fma_peak_kernel<T><<<blocks, threads, 0, st>>>(out, iters);
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess ||
+        cudaGetLastError() != cudaSuccess)
+      r = ROSSBI_ERR_CUDA;
+  }
+  if (r == ROSSBI_OK) *flops = 2.0 * 8.0 * iters * (double)blocks * threads / (ms * 1e-3);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(out);
+  return r;
+}
+}  // namespace
+
 extern "C" {
 
 const char* rossbi_status_string(rossbi_status s) {
@@ -1425,6 +1476,12 @@ rossbi_status rossbi_fallback_count(rossbi_grid* g, unsigned long long* count) {
   CK(cudaStreamSynchronize(g->stream));
   CK(cudaMemcpy(count, g->d_fallbacks, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
   return ROSSBI_OK;
+}
+
+rossbi_status rossbi_measure_fma_peak(int fp64, void* cuda_stream, double* flops_per_s) {
+  if (!flops_per_s) return ROSSBI_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  return fp64 ? fma_peak<double>(st, 1 << 13, flops_per_s) : fma_peak<float>(st, 1 << 19, flops_per_s);
 }
 
 rossbi_status rossbi_profile_enable(rossbi_grid* g, int enable) {

@@ -30,6 +30,7 @@ EXPORTS = (
     "rossbi_unpack_theta_rows", "rossbi_get_equilibrium", "rossbi_cfl_dt", "rossbi_step",
     "rossbi_step_host", "rossbi_step_noalloc", "rossbi_adjoint_step", "rossbi_adjoint_dstokes",
     "rossbi_conservation_sums", "rossbi_fallback_count", "rossbi_take_status", "rossbi_profile_enable",
+    "rossbi_measure_fma_peak",
     "rossbi_profile_read", "rossbi_nfields", "rossbi_precision", "rossbi_destroy", "rossbi_status_string",
 )
 
@@ -100,6 +101,7 @@ def load(path: str = LIB_PATH):
     L.rossbi_conservation_sums.argtypes = [_VP, _PP, _DP]
     L.rossbi_take_status.argtypes = [_VP]
     L.rossbi_fallback_count.argtypes = [_VP, ctypes.POINTER(ctypes.c_ulonglong)]
+    L.rossbi_measure_fma_peak.argtypes = [ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_double)]
     L.rossbi_profile_enable.argtypes = [_VP, ctypes.c_int]
     L.rossbi_profile_read.argtypes = [_VP, _DP, ctypes.POINTER(ctypes.c_int)]
     L.rossbi_nfields.argtypes = [_VP]
@@ -285,6 +287,14 @@ def rossbi_conservation_sums(grid, state) -> np.ndarray:
     _check(load().rossbi_conservation_sums(grid, _fields(state, nf), out.ctypes.data_as(_DP)),
            "rossbi_conservation_sums")
     return out
+
+
+def rossbi_measure_fma_peak(fp64: bool, stream=None) -> float:
+    """Measured FMA throughput of the device in FLOP/s (FP32 or FP64)."""
+    v = ctypes.c_double()
+    _check(load().rossbi_measure_fma_peak(int(bool(fp64)), _stream_handle(stream), ctypes.byref(v)),
+           "rossbi_measure_fma_peak")
+    return v.value
 
 
 def rossbi_fallback_count(grid) -> int:
