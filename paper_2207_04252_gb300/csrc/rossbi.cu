@@ -288,7 +288,9 @@ __global__ void __launch_bounds__(IND_NT) indirect_moments_kernel(DevGrid g, con
       const float* wk = wf + (size_t)k * g.nr;
       for (int i = lane; i < g.nr; i += 32) {
         float x = rho[base + i];
-        for (int s = 0; s < dr.n; ++s) x += dr.p[s][base + i];
+#pragma unroll
+        for (int s = 0; s < ND_MAX; ++s)  // static indices: the pointer array stays in the parameter bank
+          if (s < dr.n) x += dr.p[s][base + i];
         m += x * wk[i];
       }
     } else {
@@ -297,7 +299,9 @@ __global__ void __launch_bounds__(IND_NT) indirect_moments_kernel(DevGrid g, con
       for (int i = lane; i < g.nr; i += 32) {
         double dm = rho[base + i];
         if (e0) dm -= e0[i];
-        for (int s = 0; s < dr.n; ++s) dm += dr.p[s][base + i];
+#pragma unroll
+        for (int s = 0; s < ND_MAX; ++s)
+          if (s < dr.n) dm += dr.p[s][base + i];
         m += dm * wk[i];
       }
     }
