@@ -271,7 +271,7 @@ struct DustRho {
 // row sums are weighted by cos / sin and accumulated in FP64.  Rows go to
 // warps in a fixed order, so the sums are reproducible.
 constexpr int IND_NT = 256, IND_BLOCKS = 152 * 4;
-template <class T>
+template <class T, int ND>
 __global__ void __launch_bounds__(IND_NT) indirect_moments_kernel(DevGrid g, const T* rho, const DustRho<T> dr,
                                                                   int full, const double* w, const float* wf,
                                                                   double* partials) {
@@ -289,8 +289,7 @@ __global__ void __launch_bounds__(IND_NT) indirect_moments_kernel(DevGrid g, con
       for (int i = lane; i < g.nr; i += 32) {
         float x = rho[base + i];
 #pragma unroll
-        for (int s = 0; s < ND_MAX; ++s)  // static indices: the pointer array stays in the parameter bank
-          if (s < dr.n) x += dr.p[s][base + i];
+        for (int s = 0; s < ND; ++s) x += dr.p[s][base + i];  // static indices: the pointers stay in the parameter bank
         m += x * wk[i];
       }
     } else {
@@ -300,8 +299,7 @@ __global__ void __launch_bounds__(IND_NT) indirect_moments_kernel(DevGrid g, con
         double dm = rho[base + i];
         if (e0) dm -= e0[i];
 #pragma unroll
-        for (int s = 0; s < ND_MAX; ++s)
-          if (s < dr.n) dm += dr.p[s][base + i];
+        for (int s = 0; s < ND; ++s) dm += dr.p[s][base + i];
         m += dm * wk[i];
       }
     }
@@ -761,17 +759,26 @@ rossbi_status indirect_moments(rossbi_grid* g, void* const* state) {
   const double* w = g->d_ind + L.w;
   double* part = g->d_ind + L.part;
   const float* wf = reinterpret_cast<const float*>(g->d_ind + L.wf);
-  if (d.precision == ROSSBI_FP32_PERT) {
-    DustRho<float> dr{};
-    for (int b = 5; b < g->nf; b += 4) dr.p[dr.n++] = (const float*)state[b + 3];
-    indirect_moments_kernel<float><<<IND_BLOCKS, IND_NT, 0, g->stream>>>(g->dg, (const float*)state[RHO], dr, 0, w,
-                                                                         wf, part);
-  } else {
-    DustRho<double> dr{};
-    for (int b = 5; b < g->nf; b += 4) dr.p[dr.n++] = (const double*)state[b + 3];
-    indirect_moments_kernel<double><<<IND_BLOCKS, IND_NT, 0, g->stream>>>(
-        g->dg, (const double*)state[RHO], dr, d.precision == ROSSBI_FP64, w, wf, part);
-  }
+  // one instantiation per dust-species count
+  auto launch = [&](auto tag, auto nd) {
+    using T = decltype(tag);
+    constexpr int ND = decltype(nd)::value;
+    DustRho<T> dr{};
+    for (int b = 5; b < g->nf; b += 4) dr.p[dr.n++] = (const T*)state[b + 3];
+    indirect_moments_kernel<T, ND><<<IND_BLOCKS, IND_NT, 0, g->stream>>>(
+        g->dg, (const T*)state[RHO], dr, d.precision == ROSSBI_FP64, w, wf, part);
+  };
+  auto by_species = [&](auto tag) {
+    switch ((g->nf - 5) / 4) {
+      case 0: launch(tag, std::integral_constant<int, 0>{}); break;
+      case 1: launch(tag, std::integral_constant<int, 1>{}); break;
+      case 2: launch(tag, std::integral_constant<int, 2>{}); break;
+      case 3: launch(tag, std::integral_constant<int, 3>{}); break;
+      default: launch(tag, std::integral_constant<int, 4>{}); break;
+    }
+  };
+  if (d.precision == ROSSBI_FP32_PERT) by_species(float{});
+  else by_species(double{});
   CK(cudaGetLastError());
   indirect_reduce_kernel<<<1, RED_NT, 0, g->stream>>>(part, IND_BLOCKS, d.nth, g->dg.x_ind, g->d_ind + L.cs,
                                                       g->d_ind, g->d_ind + L.g,
