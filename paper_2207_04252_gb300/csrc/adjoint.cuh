@@ -213,8 +213,8 @@ __device__ __noinline__ int riemann_jac(double g, double rl, double ul, double p
   bool conv = false;
   double zl = 0.0, zr = 0.0;
   if (G75) {
-    const double k = pow(pl / pr, 1.0 / 7.0);
-    double z = pow(ps / pl, 1.0 / 7.0);
+    const double k = root7(pl / pr);
+    double z = root7(ps / pl);
     for (int it = 0; it < 100; ++it) {
       double fl, fdl, fr, fdr;
       pressure_fn_z(Lv, ps, z, fl, fdl);
@@ -793,9 +793,10 @@ __global__ void __launch_bounds__(L * NL, 1) adj_flux_kernel(const AdjFluxArgs a
         Um[f] = eq_face(f, c) + qm[f];
         Up[f] = eq_face(f, c + 1) + qp[f];
       }
-      fallback = !(Um[RHO] > 0.0 && Up[RHO] > 0.0 &&
-                   gas_pressure(gam, Um[MU], Um[MV], Um[MW], Um[EN], Um[RHO]) > 0.0 &&
-                   gas_pressure(gam, Up[MU], Up[MV], Up[MW], Up[EN], Up[RHO]) > 0.0);
+      double Wm[5], Wp[5];  // the forward's test, on the same converted states
+      gas_prim(gam, Um, Wm);
+      gas_prim(gam, Up, Wp);
+      fallback = !(Um[RHO] > 0.0 && Up[RHO] > 0.0 && Wm[EN] > 0.0 && Wp[EN] > 0.0);
     }
     if (fallback) {
 #pragma unroll

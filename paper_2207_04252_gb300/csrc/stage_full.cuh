@@ -222,10 +222,11 @@ __device__ __forceinline__ void sweep_full(const StageArgs& a, const double* sE,
           Um[f] = eq_face(f, gd) + qm[f];
           Up[f] = eq_face(f, gd + 1) + qp[f];
         }
+        double WL[5], WR[5], WP[5];
+        gas_prim(gam, Um, WR);  // right state of the lower face
+        gas_prim(gam, Up, WP);  // left state of the upper face, for the lane above
         if (shaped && do_recon) {
-          const bool ok = Um[RHO] > 0.0 && Up[RHO] > 0.0 &&
-                          gas_pressure(gam, Um[MU], Um[MV], Um[MW], Um[EN], Um[RHO]) > 0.0 &&
-                          gas_pressure(gam, Up[MU], Up[MV], Up[MW], Up[EN], Up[RHO]) > 0.0;
+          const bool ok = Um[RHO] > 0.0 && Up[RHO] > 0.0 && WR[EN] > 0.0 && WP[EN] > 0.0;
           if (!ok) {
 #pragma unroll
             for (int f = 0; f < 5; ++f) {
@@ -233,11 +234,10 @@ __device__ __forceinline__ void sweep_full(const StageArgs& a, const double* sE,
               Um[f] = eq_face(f, gd) + e;
               Up[f] = eq_face(f, gd + 1) + e;
             }
+            gas_prim(gam, Um, WR);
+            gas_prim(gam, Up, WP);
           }
         }
-        double WL[5], WR[5], WP[5];
-        gas_prim(gam, Um, WR);  // right state of the lower face
-        gas_prim(gam, Up, WP);  // left state of the upper face, for the lane above
 #pragma unroll
         for (int f = 0; f < 5; ++f) WL[f] = __shfl_up_sync(FULL, WP[f], 1, L);
         if (do_face) {
