@@ -215,22 +215,8 @@ __device__ __noinline__ int riemann_jac(double g, double rl, double ul, double p
   if (G75) {
     const double k = root7(pl / pr);
     double z = root7(ps / pl);
-    for (int it = 0; it < 100; ++it) {
-      double fl, fdl, fr, fdr;
-      pressure_fn_z(Lv, ps, z, fl, fdl);
-      pressure_fn_z(Rv, ps, z * k, fr, fdr);
-      double zn = z - (fl + fr + ur - ul) * z / (7.0 * ps * (fdl + fdr));
-      double z2 = zn * zn, z7 = z2 * z2 * z2 * zn;
-      double pn = pl * z7;
-      if (!(pn >= pfloor)) {
-        pn = pfloor;
-        zn = pow(pfloor / pl, 1.0 / 7.0);
-      }
-      const double change = 2.0 * fabs(pn - ps) / (pn + ps);
-      ps = pn;
-      z = zn;
-      if (change <= 1e-12) { conv = true; break; }
-    }
+    double fl, fdl, fr, fdr, step;
+    conv = newton_z_g75(Lv, Rv, ur - ul, pfloor, k, ps, z, fl, fdl, fr, fdr, step);  // the forward's iteration
     zl = z;
     zr = z * k;
   } else {

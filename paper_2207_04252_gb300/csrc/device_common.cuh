@@ -194,18 +194,68 @@ __device__ __forceinline__ int riemann_face(double g, double rl, double ul, doub
 // k = (p_L / p_R)^(1/7)), so a face takes two powers instead of two per
 // iteration; the iterates, the stopping test on p and the sampling are those
 // of riemann_face.
-__device__ __forceinline__ void pressure_fn_z(const RSide& K, double p, double z, double& f, double& fd) {
-  if (z <= 1.0) {  // rarefaction: f = 5 c (z - 1), df/dp = 1 / (rho c z^6)
-    const double z3 = z * z * z;
+// Side constants of the gamma = 7/5 pressure functions, formed once per face:
+// 1/(rho c), the shock coefficients A = 2/((gamma+1) rho) (as sqrt(A) and
+// 1/A) and B = (gamma-1)/(gamma+1) p_K.
+struct RSideZ {
+  double irc, sqA, iA, B;
+};
+__device__ __forceinline__ RSideZ side_z(const RSide& K) {
+  RSideZ s;
+  s.irc = 1.0 / (K.rho * K.c);
+  s.iA = 1.2 * K.rho;
+  s.sqA = rsqrt(s.iA);
+  s.B = K.p * (1.0 / 6.0);
+  return s;
+}
+
+// Pressure function of side K at p = p_K z^7 (iz = 1/z): rarefaction
+// f = 5 c (z - 1), df/dp = 1 / (rho c z^6); shock f = (p - p_K) q with
+// q = sqrt(A / (B + p)), df/dp = (1 - (p - p_K) / (2 (B + p))) q, where
+// (p - p_K)/(B + p) = (p - p_K) q^2 / A: no division.
+__device__ __forceinline__ void pressure_fn_z(const RSide& K, const RSideZ& S, double p, double z, double iz,
+                                              double& f, double& fd) {
+  if (z <= 1.0) {
+    const double i3 = iz * iz * iz;
     f = 5.0 * K.c * (z - 1.0);
-    fd = 1.0 / (K.rho * K.c * z3 * z3);
-  } else {         // shock: A = 2 / ((gamma + 1) rho), B = (gamma - 1) / (gamma + 1) p_K
-    const double A = 1.0 / (1.2 * K.rho);
-    const double B = K.p / 6.0;
-    const double q = sqrt(A / (B + p));
-    f = (p - K.p) * q;
-    fd = (1.0 - 0.5 * (p - K.p) / (B + p)) * q;
+    fd = S.irc * i3 * i3;
+  } else {
+    const double q = S.sqA * rsqrt(S.B + p);
+    const double dp = p - K.p;
+    f = dp * q;
+    fd = (1.0 - 0.5 * dp * q * q * S.iA) * q;
   }
+}
+
+// Newton on z_L = (p / p_L)^(1/7) (p = p_L z_L^7, z_R = z_L k with
+// k = (p_L / p_R)^(1/7)) from the start ps, z; on return ps, z are the last
+// iterate, f*, fd* the pressure functions at the one before and step the last
+// change of p.  The stopping test 2 |dp| <= 1e-12 (p_new + p_old) is that of
+// riemann_face without its division.
+__device__ __forceinline__ bool newton_z_g75(const RSide& L, const RSide& R, double du, double pfloor, double k,
+                                             double& ps, double& z, double& fl, double& fdl, double& fr,
+                                             double& fdr, double& step) {
+  const RSideZ SL = side_z(L), SR = side_z(R);
+  const double ik = 1.0 / k;
+  for (int it = 0; it < 100; ++it) {
+    const double iz = 1.0 / z;
+    pressure_fn_z(L, SL, ps, z, iz, fl, fdl);
+    pressure_fn_z(R, SR, ps, z * k, iz * ik, fr, fdr);
+    // Newton on z_L: dp/dz_L = 7 p / z_L
+    double zn = z - (fl + fr + du) * z / (7.0 * ps * (fdl + fdr));
+    double z2 = zn * zn, z7 = z2 * z2 * z2 * zn;
+    double pn = L.p * z7;
+    if (!(pn >= pfloor)) {
+      pn = pfloor;
+      zn = pow(pfloor / L.p, 1.0 / 7.0);
+    }
+    step = pn - ps;
+    const bool done = 2.0 * fabs(step) <= 1e-12 * (pn + ps);
+    ps = pn;
+    z = zn;
+    if (done) return true;
+  }
+  return false;
 }
 
 // y^(1/7).  Near 1 (|y - 1| <= 2^-10, the common case of smooth flow, where
@@ -258,25 +308,7 @@ __device__ __forceinline__ int riemann_face_g75(double rl, double ul, double pl,
   const double k = root7(pl / pr);
   double z = root7(ps / pl);
   double fl, fdl, fr, fdr, step = 0.0;
-  bool conv = false;
-  for (int it = 0; it < 100; ++it) {
-    pressure_fn_z(L, ps, z, fl, fdl);
-    pressure_fn_z(R, ps, z * k, fr, fdr);
-    // Newton on z_L: dp/dz_L = 7 p / z_L
-    double zn = z - (fl + fr + ur - ul) * z / (7.0 * ps * (fdl + fdr));
-    double z2 = zn * zn, z7 = z2 * z2 * z2 * zn;
-    double pn = pl * z7;
-    if (!(pn >= pfloor)) {
-      pn = pfloor;
-      zn = pow(pfloor / pl, 1.0 / 7.0);
-    }
-    const double change = 2.0 * fabs(pn - ps) / (pn + ps);
-    step = pn - ps;
-    ps = pn;
-    z = zn;
-    if (change <= 1e-12) { conv = true; break; }
-  }
-  if (!conv) status |= STATUS_RIEMANN;
+  if (!newton_z_g75(L, R, ur - ul, pfloor, k, ps, z, fl, fdl, fr, fdr, step)) status |= STATUS_RIEMANN;
   fl += fdl * step;  // f_K at the converged p*, one Newton step from the last evaluation
   fr += fdr * step;
   const double us = 0.5 * (ul + ur) + 0.5 * (fr - fl);
