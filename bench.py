@@ -383,7 +383,7 @@ def measure_explosion(R, W, syn, torch, steps=2, warmup=1):
     torch.cuda.empty_cache()
     return {"workload": w.name, "value": w.ncell / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
             "warmup": warmup, "dtype": "f64", "status": R.status_string(status),
-            "note": "one z cell: the 14x6x6 tile computes six z planes per cell"}
+            "note": "one z cell: the flat 14x30x1 tile (no z halo, no z sweep)"}
 
 
 def measure_adjoint(R, W, syn, torch, steps=4, warmup=3):
