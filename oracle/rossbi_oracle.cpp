@@ -30,7 +30,14 @@
 //      it depends continuously on the data.  If a reconstructed gas face state
 //      has rho<=0 or P<=0, all gas departures of that cell are used flat in
 //      that direction.
-//      Option (a departure from the paper, kept for comparison): the same
+//      Option 2 (a departure in one component): the same on the departures
+//      of rho, rho u, rho v, rho w and of the pressure P(E) - P(E0) instead
+//      of the energy; the face energy is P / (gamma - 1) + |m|^2 / 2 rho of
+//      the face pressure, momenta and density.  Without the energy, the face
+//      pressure is no longer a difference of reconstructed terms O(Mach^2)
+//      larger than itself: the epicycle oscillates as it should and the
+//      vortex's rounding-level drift stays at 1e-13.
+//      Option 1 (a departure from the paper, kept for comparison): the same
 //      parabola and limiter on the departures of the PRIMITIVE gas variables
 //      (rho, u, v, w, P) from the equilibrium primitives, the face state being
 //      the face equilibrium primitives plus the interpolated departure.  In a
@@ -153,7 +160,7 @@ enum { MU = 0, MV = 1, MW = 2, EN = 3, RHO = 4, DMU = 5, DMV = 6, DMW = 7, DRHO 
 enum { ST_NONPHYSICAL = 1, ST_RIEMANN = 2 };
 // Reconstruction of the gas (reading R2): conservative departures (Sect. 2.7
 // on App. B's E, the default) or primitive departures (option).
-enum { RECON_CONSERVATIVE = 0, RECON_PRIMITIVE = 1 };
+enum { RECON_CONSERVATIVE = 0, RECON_PRIMITIVE = 1, RECON_PRESSURE = 2 };
 // Dust species s occupies fields 5 + 4 s .. 8 + 4 s (rho_d u_d, rho_d v_d,
 // rho_d w_d, rho_d); species 0 is the single dust fluid above.
 static const int ND_MAX = 4, NFMAX = 5 + 4 * ND_MAX;
@@ -361,6 +368,32 @@ static typename Acc::value_type dev(const Oracle& o, const Acc& E, int f, int i,
   return e;
 }
 
+template <class T>
+static inline T pressure(double g, const T* U);
+
+// Pressure departure P(E) - P(E0) of cell (i, j, k) under the same ghost
+// rule as dev() (reading R2, option 2); without an equilibrium, P(E).
+template <class Acc>
+static typename Acc::value_type pdev(const Oracle& o, const Acc& E, int i, int j, int k) {
+  using T = typename Acc::value_type;
+  int c[3] = {i, j, k};
+  for (int ax = 0; ax < 3; ++ax) {
+    if (c[ax] >= 0 && c[ax] < o.n[ax]) continue;
+    const int bc = c[ax] < 0 ? o.d.bc_lo[ax] : o.d.bc_hi[ax];
+    if (bc == BC_EQUILIBRIUM) return T(0.0);
+    if (bc == BC_PERIODIC)
+      c[ax] = ((c[ax] % o.n[ax]) + o.n[ax]) % o.n[ax];
+    else
+      c[ax] = c[ax] < 0 ? 0 : o.n[ax] - 1;
+  }
+  const long lin = ((long)c[2] * o.n[1] + c[1]) * o.n[0] + c[0];
+  T U[5];
+  for (int f = 0; f < 5; ++f) U[f] = E.get(f, lin);
+  if (!o.has_eq) return pressure(o.d.gamma, U);
+  const double* U0 = E0C(o, c[0], c[2]);
+  return pressure(o.d.gamma, U) - pressure(o.d.gamma, U0);
+}
+
 // ---------------------------------------------------------------- reconstruction
 template <class T>
 static inline T minmod(T a, T b) {
@@ -465,14 +498,31 @@ static void recon(const Oracle& o, const Acc& E, int ax, const int cell[3], T qm
   double e0m[5], e0p[5];
   eq_face(o, ax, cell[0], cell[2], c, e0m);
   eq_face(o, ax, cell[0], cell[2], c + 1, e0p);
-  if (o.recon == RECON_CONSERVATIVE) {
+  if (o.recon == RECON_CONSERVATIVE || o.recon == RECON_PRESSURE) {
     T em[5], ec[5], ep[5];
     bool gas_shaped = false;
     for (int f = 0; f < 5; ++f) {
       em[f] = dev(o, E, f, cm[0], cm[1], cm[2]);
       ec[f] = dev(o, E, f, cell[0], cell[1], cell[2]);
       ep[f] = dev(o, E, f, cp[0], cp[1], cp[2]);
+      if (o.recon == RECON_PRESSURE && f == EN) continue;
       gas_shaped |= parabola(em[f], ec[f], ep[f], xm, x0, xp, fm, fp, qm[f], qp[f]);
+    }
+    if (o.recon == RECON_PRESSURE) {
+      // option 2 of reading R2: the pressure departure is reconstructed in
+      // place of the energy one; the face energy follows from the face
+      // pressure, momenta and density
+      T pqm, pqp;
+      gas_shaped |= parabola(pdev(o, E, cm[0], cm[1], cm[2]), pdev(o, E, cell[0], cell[1], cell[2]),
+                             pdev(o, E, cp[0], cp[1], cp[2]), xm, x0, xp, fm, fp, pqm, pqp);
+      auto energy = [&](const double* e0f, T* q, T pq) {
+        T U[5];
+        for (int f = 0; f < 5; ++f) U[f] = e0f[f] + q[f];
+        const T P = (o.has_eq ? pressure(o.d.gamma, e0f) : 0.0) + pq;
+        q[EN] = P / (o.d.gamma - 1.0) + 0.5 * (U[MU] * U[MU] + U[MV] * U[MV] + U[MW] * U[MW]) / U[RHO] - e0f[EN];
+      };
+      energy(e0m, qm, pqm);
+      energy(e0p, qp, pqp);
     }
     if (gas_shaped) {  // positivity of both gas face states
       T Um[5], Up[5];
@@ -1326,7 +1376,7 @@ void orc_set_species_stokes(void* h, const double* f, int n) {
 // Gas reconstruction of reading R2: 0 = conservative departures (Sect. 2.7
 // on App. B's E; the default), 1 = primitive departures.
 int orc_set_recon(void* h, int mode) {
-  if (mode != RECON_CONSERVATIVE && mode != RECON_PRIMITIVE) return 1;
+  if (mode != RECON_CONSERVATIVE && mode != RECON_PRIMITIVE && mode != RECON_PRESSURE) return 1;
   ((Oracle*)h)->recon = mode;
   return 0;
 }

@@ -10,5 +10,5 @@ from .workloads import (  # noqa: F401
     Workload, SOD, DISC_NOISE, VORTEX, ADJOINT, THROUGHPUT, EXPLOSION, RWI, ALL, by_name, scaled,
     GEOM_BOX, GEOM_CYL, BC_PERIODIC, BC_OUTFLOW, BC_EQUILIBRIUM,
     F_MU, F_MV, F_MW, F_EN, F_RHO, F_DMU, F_DMV, F_DMW, F_DRHO,
-    RECON_CONSERVATIVE, RECON_PRIMITIVE,
+    RECON_CONSERVATIVE, RECON_PRIMITIVE, RECON_PRESSURE,
 )

@@ -26,7 +26,7 @@ BC_PERIODIC, BC_OUTFLOW, BC_EQUILIBRIUM = 0, 1, 2
 F_MU, F_MV, F_MW, F_EN, F_RHO, F_DMU, F_DMV, F_DMW, F_DRHO = range(9)
 # Gas reconstruction: the paper's component-wise parabola on the conservative
 # departures (Sect. 2.7 on App. B's E), or the primitive-departure option.
-RECON_CONSERVATIVE, RECON_PRIMITIVE = 0, 1
+RECON_CONSERVATIVE, RECON_PRIMITIVE, RECON_PRESSURE = 0, 1, 2
 
 H_ASPECT = 0.05
 DISC_PARAMS = (1.0, -0.5, H_ASPECT * H_ASPECT / 2.0, -1.0)  # sigma0, beta_sigma, T0, beta_T

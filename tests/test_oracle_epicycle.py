@@ -9,7 +9,9 @@ radially oscillates at the epicyclic frequency kappa, kappa^2 = (2 Omega / r)
 d(r^2 Omega)/dr = Omega_K^2 for Keplerian rotation, raised by the pressure
 term c_s^2 k^2 (~4 % for this width: kappa^2 + c_s^2 / 0.2^2).  The pin: the
 period of u_r at r0 over one oscillation gives 0.97 <= omega / Omega_K(r0)
-<= 1.06, and the amplitude does not grow.
+<= 1.06, and the amplitude does not grow, with the primitive-departure
+option and with option 2 (the pressure departure in place of the energy
+one).
 
 With the paper's conservative-departure reconstruction the same run does
 not oscillate: at this frame Mach number (~12 near r = 0.7) the component-
@@ -23,6 +25,7 @@ from dataclasses import replace
 import math
 
 import numpy as np
+import pytest
 
 import oracle
 import synthetic as syn
@@ -57,8 +60,9 @@ def _run(recon, t_end):
     return np.array(ts), np.array(us), np.array(umax), u0.max()
 
 
-def test_epicycle_frequency_primitive_option():
-    t, u, umax, a0 = _run(syn.RECON_PRIMITIVE, 7.5)
+@pytest.mark.parametrize("recon", [syn.RECON_PRIMITIVE, syn.RECON_PRESSURE], ids=["primitive", "pressure"])
+def test_epicycle_frequency(recon):
+    t, u, umax, a0 = _run(recon, 7.5)
     zc = t[1:][np.diff(np.sign(u)) != 0]  # zero crossings of u_r at r0
     assert len(zc) >= 2, zc
     omega = math.pi / (zc[1] - zc[0])     # half a period between consecutive crossings
