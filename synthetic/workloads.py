@@ -139,16 +139,20 @@ THROUGHPUT = _disc("bifluid_two_vortices_512x1024x128", 512, 1024, 128, 50, ic="
 # Delta_r))^2), at the equilibrium temperature (P scaled alike) with the
 # azimuthal velocity in radial balance with the bump's pressure gradient, and
 # the seed v_r = eps v_theta0 sin(m theta) G with eps = 1e-4 and mode m.  The
-# paper takes the setup of a cited work without printing delta and Delta_r:
-# delta = 0.25 and Delta_r = 0.05 r0 (= H(r0)) here.  The bump is resolved by
-# a narrower annulus, r in [0.6, 1.6] (128 log-spaced cells: 6.5 per Delta_r),
-# and a thinner disc, z in +-2 H(r0); gas only, in that annulus's equal-Mach
-# frame.  The modes' growth is measured, not pinned.
+# paper takes the setup of a cited work without printing delta and Delta_r.
+# In this disc (h = 0.05, T ~ 1/r, adiabatic perturbations with gamma = 7/5)
+# the linearised equations give no mode growing faster than 1e-3 Omega(r0)
+# for a bump as wide as H(r0) = 0.05 (delta up to 3); delta = 0.5 and
+# Delta_r = 0.025 r0 (= H(r0) / 2) give growth rates 0.06 to 0.14 Omega(r0)
+# for m = 2 ... 6 (0.111 for m = 4) and keep kappa^2 > 0.33 Omega^2
+# (delta = 1 at this width is Rayleigh-marginal).  The annulus r in
+# [0.6, 1.6] has 256 log-spaced cells (6.5 per Delta_r); z in +-2 H(r0);
+# gas only, in the annulus's equal-Mach frame.
 RWI = Workload(
-    name="rwi_m4_128x256x16", geometry=GEOM_CYL, nr=128, nth=256, nz=16,
+    name="rwi_m4_256x256x16", geometry=GEOM_CYL, nr=256, nth=256, nz=16,
     x0=(0.6, 0.0, -2.0 * H_ASPECT), x1=(1.6, 2.0 * math.pi, 2.0 * H_ASPECT),
     bc_lo=(BC_EQUILIBRIUM, BC_PERIODIC, BC_EQUILIBRIUM), bc_hi=(BC_EQUILIBRIUM, BC_PERIODIC, BC_EQUILIBRIUM),
-    disc=DISC_PARAMS, ic="rwi", steps=4000, rwi_mode=4, rwi_delta=0.25, rwi_width=0.05, rwi_eps=1e-4,
+    disc=DISC_PARAMS, ic="rwi", steps=4000, rwi_mode=4, rwi_delta=0.5, rwi_width=0.025, rwi_eps=1e-4,
     omega_frame=equal_mach_frame(0.6, 1.6))
 
 # Cylindrical explosion (Sect. 4.1; Toro ch. 17): a 2-D Riemann problem on the
