@@ -6,7 +6,8 @@ seed v_r = eps v_theta0 sin(m theta) G.
 
 Parity: the RWI disc against the oracle over 100 steps at 32x48x32, all three
 forms (FP64 and the FP64 perturbation form <= 1e-12, FP32 <= 1e-5; the oracle
-drifts from a 1e-15 input perturbation by 4e-14 over these 100 steps).
+drifts from a 1e-15 input perturbation by 2.3e-14 over these 100 steps, 2e-9
+element-wise).
 
 Growth: the paper measures the instability by the growth rates of the modes.
 In 2-D (one z cell at the midplane) the mode-m amplitude of v_r near r0 is
@@ -21,9 +22,10 @@ high-Mach instability, see the long runs, sets in before the window).
 Long runs: the mode-m amplitude of v_r on the midplane ring at r0 every 500
 steps, in the FP32 form on the 256x256x16 workload.  The primitive-departure
 option runs 30 000 steps (t = 40) and the seed must have grown; the paper's
-conservative reconstruction runs 5 000 (in this frame it turns non-physical
-after 7 000 to 12 500 steps, depending on the seeded mode: the waves reach the
-inner annulus, frame Mach 12 to 15) and must stay physical.
+conservative reconstruction runs 5 000 (t = 6.7) and must stay physical
+(longer runs on this annulus have turned non-physical at t = 19 to 34: the
+waves launched by the seed reach the inner annulus, at frame Mach 12 to 15,
+where the component-wise limiter on conservative departures is unstable).
 """
 from dataclasses import replace
 import math
