@@ -17,7 +17,8 @@ equations, tests/rwi_linear.py: 0.111 Omega(r0) for m = 4) within 10 %, with
 the rate steady across the window: the primitive-departure option in the
 FP32 and FP64 forms on the workload's annulus, and the paper's conservative
 reconstruction on the narrower annulus r in [0.75, 1.35] (on [0.6, 1.6] its
-high-Mach instability, see the long runs, sets in before the window).
+high-Mach instability, see the long runs, sets in before the window).  Modes
+m = 2, 3, 5, 6 are held to 0.85 to 1.05 of their linear rates.
 
 Long runs: the mode-m amplitude of v_r on the midplane ring at r0 every 500
 steps, in the FP32 form on the 256x256x16 workload.  The primitive-departure
@@ -156,6 +157,24 @@ def test_rwi_growth_rate_matches_linear_theory(lib, form, recon, narrow):
     assert lin > 0.1
     assert abs(rate / lin - 1.0) <= 0.1, (rate, lin)
     assert abs(early / late - 1.0) <= 0.1, (early, late)
+
+
+@pytest.mark.parametrize("m", [2, 3, 5, 6])
+def test_rwi_growth_rates_of_other_modes(lib, m):
+    """Modes m = 2, 3, 5, 6 of the same 2-D disc (FP32 form, primitive
+    option): the fitted rate between 0.85 and 1.05 of the linear one (the
+    coarser azimuthal resolution of the higher modes costs them most: m = 6
+    has 43 cells per wavelength at r0)."""
+    R, W = lib
+    w = replace(_two_d(syn.RWI, 256, 256, syn.RECON_PRIMITIVE), rwi_mode=m)
+    o = oracle.Oracle(w)
+    lin = rwi_growth_rate(lambda x: o.eq_prim(x, 0.0), m, w.rwi_r0, w.x0[0], w.x1[0], n=300)
+    t_end = 50.0
+    hist, status = _growth_history(R, W, w, R.ROSSBI_FP32_PERT, t_end, (1.25 * w.x0[0], 0.84 * w.x1[0], 1.0))
+    rate = _fit_rate(hist, 0.5 * t_end, t_end)
+    print(f"m = {m}: linear {lin:.4f}, fitted {rate:.4f}, ratio {rate / lin:.3f}")
+    assert status == 0
+    assert 0.85 <= rate / lin <= 1.05, (m, rate, lin)
 
 
 def _long_run(R, W, w, steps, every=500):
