@@ -46,9 +46,12 @@ def test_tlm_zero_direction_gives_zero_tangent():
     assert not t.any()
 
 
-def test_tlm_disc_random_direction():
-    """Gas-only disc, every field of every cell perturbed at once."""
-    w = syn.scaled(syn.DISC_NOISE, 12, 10, 32)
+@pytest.mark.parametrize("recon", [syn.RECON_CONSERVATIVE, syn.RECON_PRESSURE], ids=["conservative", "pressure"])
+def test_tlm_disc_random_direction(recon):
+    """Gas-only disc, every field of every cell perturbed at once (the paper's
+    reconstruction and option 2, whose pressure departure and face energy
+    carry their own tangents)."""
+    w = replace(syn.scaled(syn.DISC_NOISE, 12, 10, 32), recon=recon)
     o = oracle.Oracle(w)
     rng = np.random.default_rng(1)
     E = _jitter(oracle.initial_state(o), w.gamma, rng, 1e-3)
