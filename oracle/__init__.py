@@ -86,6 +86,7 @@ def lib():
         L.orc_sources.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]
         L.orc_set_species_stokes.argtypes = [ctypes.c_void_p, _D, ctypes.c_int]
         L.orc_set_recon.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.orc_set_dust_recon.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.orc_set_vertical_damping.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]
         L.orc_damping_rate.restype = ctypes.c_double
         L.orc_damping_rate.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
@@ -183,6 +184,13 @@ class Oracle:
         """X_ref of the indirect-gravity term (Sect. 2.10); 0 switches it off."""
         self.x_ind = float(x_ref)
         lib().orc_set_indirect(self.h, self.x_ind)
+
+    def set_dust_recon(self, mode):
+        """Dust reconstruction (reading R5): 0 = the parabola on rho_d and the
+        velocity (the default), 1 = the velocity flat where rho_d is at an
+        extremum."""
+        if lib().orc_set_dust_recon(self.h, int(mode)):
+            raise ValueError(f"unknown dust reconstruction mode {mode}")
 
     def set_damping(self, r_ein, r_eout, period_factor=1.0):
         """Wave-killing zones r < r_ein and r > r_eout (reading R17); a
