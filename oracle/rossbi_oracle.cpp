@@ -165,7 +165,9 @@ enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_EQUILIBRIUM = 2 };
 enum { MU = 0, MV = 1, MW = 2, EN = 3, RHO = 4, DMU = 5, DMV = 6, DMW = 7, DRHO = 8 };
 enum { ST_NONPHYSICAL = 1, ST_RIEMANN = 2 };
 // Reconstruction of the gas (reading R2): conservative departures (Sect. 2.7
-// on App. B's E, the default) or primitive departures (option).
+// on App. B's E, the default), primitive departures (option 1), or the
+// conservative ones with the pressure departure in place of the energy one
+// (option 2).
 enum { RECON_CONSERVATIVE = 0, RECON_PRIMITIVE = 1, RECON_PRESSURE = 2 };
 // Dust reconstruction (reading R5): the parabola on rho_d and each velocity
 // component (the default, as the kernels have it), or option 1, the same with
