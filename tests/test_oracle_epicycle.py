@@ -20,6 +20,13 @@ places, the face pressure (a difference of terms O(Mach^2) larger than
 itself) takes spurious jumps, and u_r grows ~100-fold within one orbit near
 r = 0.72.  Without the limiter, or with the primitive-departure option, it
 oscillates as above.  That run is reported here, not pinned.
+
+Where the instability sets in: on the narrow annulus r in [0.9, 1.1] with a
+seed of width 0.03, the frame rate sets the largest frame Mach number of the
+annulus.  Over one orbit the conservative reading keeps |u_r| at its seed up
+to Mach 7.5 (Omega_f = 0.8) and grows it about 200-fold from Mach 9.6
+(Omega_f = 0.7) on; the two options stay at their seed up to Mach 15.7
+(Omega_f = 0.4).  Pinned at Mach 3.7, 7.5 and 11.6.
 """
 from dataclasses import replace
 import math
@@ -75,3 +82,40 @@ def test_epicycle_conservative_reconstruction_report():
     t, u, umax, a0 = _run(syn.RECON_CONSERVATIVE, 2.5)
     print("conservative reconstruction, max |u_r| / seed at t =",
           [(f"{t[k]:.2f}", f"{umax[k] / a0:.1f}") for k in range(0, len(t), max(1, len(t) // 8))])
+
+
+def _narrow_growth(recon, omega_frame, t_end=6.3):
+    """Largest |u_r| over one orbit on r in [0.9, 1.1], divided by the seed's."""
+    w = replace(syn.RWI, nr=64, nth=4, nz=1, x0=(0.9, 0.0, -0.5 * H), x1=(1.1, 2.0 * math.pi, 0.5 * H),
+                rwi_delta=0.0, recon=recon, omega_frame=omega_frame,
+                bc_lo=(syn.BC_EQUILIBRIUM, syn.BC_PERIODIC, syn.BC_PERIODIC),
+                bc_hi=(syn.BC_EQUILIBRIUM, syn.BC_PERIODIC, syn.BC_PERIODIC))
+    o = oracle.Oracle(w)
+    E0 = o.equilibrium_state()
+    r, _ = o.coords(0)
+    u0 = 1e-4 * np.exp(-0.5 * ((r - 1.0) / 0.03) ** 2)
+    E = E0.copy()
+    E[0] = E0[4] * u0[None, None, :]
+    E[3] = E0[3] + 0.5 * E0[4] * u0[None, None, :] ** 2
+    t, growth = 0.0, 1.0
+    while t < t_end:
+        dt = o.cfl_dt(E)
+        E = o.step(E, dt)
+        t += dt
+        if o.take_status():
+            return math.inf
+        growth = max(growth, float(np.abs(E[0, 0, 0] / E[4, 0, 0]).max() / u0.max()))
+    return growth
+
+
+@pytest.mark.parametrize("omega_frame,stable", [(1.0, True), (0.8, True), (0.6, False)],
+                         ids=["mach_3.7", "mach_7.5", "mach_11.6"])
+def test_conservative_reading_stability_threshold(omega_frame, stable):
+    g_cons = _narrow_growth(syn.RECON_CONSERVATIVE, omega_frame)
+    g_pres = _narrow_growth(syn.RECON_PRESSURE, omega_frame)
+    print(f"Omega_f = {omega_frame}: max |u_r| / seed, conservative {g_cons:.2f}, option 2 {g_pres:.2f}")
+    assert g_pres <= 1.2
+    if stable:
+        assert g_cons <= 1.2
+    else:
+        assert g_cons >= 10.0
