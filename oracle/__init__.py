@@ -187,8 +187,8 @@ class Oracle:
 
     def set_dust_recon(self, mode):
         """Dust reconstruction (reading R5): 0 = the parabola on rho_d and the
-        velocity (the default), 1 = the velocity flat where rho_d is at an
-        extremum."""
+        velocity (the default), 1 = the velocity flat in a cell where rho_d is
+        a local maximum and the flow converges along the axis."""
         if lib().orc_set_dust_recon(self.h, int(mode)):
             raise ValueError(f"unknown dust reconstruction mode {mode}")
 

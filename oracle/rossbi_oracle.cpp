@@ -57,12 +57,16 @@
 //      dynamics (Bouchut, Jin & Li 2003): rho_L max(u_L,0)(1,u_L,...) +
 //      rho_R min(u_R,0)(1,u_R,...), which carries delta shocks by
 //      accumulating mass.  Option 1 (oracle only): the velocity is used flat
-//      in a cell where rho_d is at an extremum.  With the velocity parabola a
-//      delta shock's spike takes at its faces the interpolated velocity of
-//      the converging streams, which points back into the spike, and the
-//      spike falls behind the delta-shock speed of the pressureless Riemann
-//      problem (by 20 cells of 400 at t = 0.3 in the delta-shock pin); with
-//      option 1 it moves at that speed to within a cell.
+//      in a cell where rho_d is a local maximum along the axis and the
+//      velocity component along it decreases across the cell (a converging
+//      flow piling up mass: a delta shock's spike).  With the velocity
+//      parabola such a spike takes at its faces the interpolated velocity of
+//      the converging streams, which points back into it, and it falls
+//      behind the delta-shock speed of the pressureless Riemann problem (by
+//      20 cells of 400 at t = 0.3 in the delta-shock pin); with option 1 it
+//      moves at that speed to within a cell.  Flattening at every extremum
+//      instead stalls the outflow of a density minimum in a diverging flow
+//      and does not converge on a smooth one.
 //  R6  rotating frame of angular speed Omega_f: Coriolis 2 Omega_f rho v e_r -
 //      2 Omega_f rho u e_theta and centrifugal rho Omega_f^2 r e_r; the stored
 //      azimuthal velocity is frame-relative.
@@ -171,8 +175,9 @@ enum { ST_NONPHYSICAL = 1, ST_RIEMANN = 2 };
 enum { RECON_CONSERVATIVE = 0, RECON_PRIMITIVE = 1, RECON_PRESSURE = 2 };
 // Dust reconstruction (reading R5): the parabola on rho_d and each velocity
 // component (the default, as the kernels have it), or option 1, the same with
-// the velocity used flat in a cell where rho_d is at an extremum.
-enum { DUST_RECON_PARABOLA = 0, DUST_RECON_FLAT_AT_EXTREMA = 1 };
+// the velocity used flat in a cell where rho_d is a local maximum and the
+// flow converges along the axis.
+enum { DUST_RECON_PARABOLA = 0, DUST_RECON_FLAT_AT_SPIKES = 1 };
 // Dust species s occupies fields 5 + 4 s .. 8 + 4 s (rho_d u_d, rho_d v_d,
 // rho_d w_d, rho_d); species 0 is the single dust fluid above.
 static const int ND_MAX = 4, NFMAX = 5 + 4 * ND_MAX;
@@ -589,10 +594,11 @@ static void recon(const Oracle& o, const Acc& E, int ax, const int cell[3], T qm
       pp[q] = pp[3] > 0.0 ? dev(o, E, b + q, cp[0], cp[1], cp[2]) / pp[3] : T(0.0);
     }
     for (int q = 0; q < 4; ++q) parabola(pm[q], p0[q], pp[q], xm, x0, xp, fm, fp, qmw[q], qpw[q]);
-    // option 1: where rho_d is at an extremum (a delta shock's spike is one)
-    // the cell's own velocity is carried to both faces, so that the spike's
-    // mass leaves it at the spike's speed instead of the interpolated one
-    if (o.dust_recon == DUST_RECON_FLAT_AT_EXTREMA && !((p0[3] - pm[3]) * (pp[3] - p0[3]) > 0.0))
+    // option 1: where rho_d is a local maximum and the flow converges along
+    // the axis (a delta shock's spike) the cell's own velocity is carried to
+    // both faces, so that the spike's mass leaves it at the spike's speed
+    // instead of the interpolated one
+    if (o.dust_recon == DUST_RECON_FLAT_AT_SPIKES && p0[3] > pm[3] && p0[3] > pp[3] && pm[ax] > pp[ax])
       for (int q = 0; q < 3; ++q) qmw[q] = qpw[q] = p0[q];
     qm[b + 3] = qmw[3];
     qp[b + 3] = qpw[3];
@@ -1401,9 +1407,10 @@ int orc_set_recon(void* h, int mode) {
 }
 
 // Dust reconstruction of reading R5: 0 = the parabola on rho_d and the
-// velocity (the default), 1 = the velocity flat where rho_d is at an extremum.
+// velocity (the default), 1 = the velocity flat at a converging density
+// maximum.
 int orc_set_dust_recon(void* h, int mode) {
-  if (mode != DUST_RECON_PARABOLA && mode != DUST_RECON_FLAT_AT_EXTREMA) return 1;
+  if (mode != DUST_RECON_PARABOLA && mode != DUST_RECON_FLAT_AT_SPIKES) return 1;
   ((Oracle*)h)->dust_recon = mode;
   return 0;
 }
