@@ -80,7 +80,7 @@ def test_box_conservation(n_dust, stokes):
             assert abs(tot1 - tot0) <= 1e-14 * (scale[syn.F_MU + c] + scale[syn.F_DMU + c]) * 12
 
 
-def _sod_profile(nr, axis=0, mirror=False):
+def _sod_profile(nr, axis=0, mirror=False, recon=syn.RECON_CONSERVATIVE):
     n = [4, 4, 4]
     n[axis] = nr
     L = [4.0 / nr] * 3
@@ -89,7 +89,7 @@ def _sod_profile(nr, axis=0, mirror=False):
     bc_hi = [syn.BC_PERIODIC] * 3
     bc_lo[axis] = bc_hi[axis] = syn.BC_OUTFLOW
     w = syn.Workload(name="sod", geometry=syn.GEOM_BOX, nr=n[0], nth=n[1], nz=n[2], x0=(0, 0, 0), x1=tuple(L),
-                     bc_lo=tuple(bc_lo), bc_hi=tuple(bc_hi), ic="none", steps=0, omega_frame=0.0)
+                     bc_lo=tuple(bc_lo), bc_hi=tuple(bc_hi), ic="none", steps=0, omega_frame=0.0, recon=recon)
     o = oracle.Oracle(w)
     xc, _ = o.coords(axis)
     left = xc < 0.5
@@ -113,12 +113,15 @@ def _sod_profile(nr, axis=0, mirror=False):
     return xc, rho_line, m_line
 
 
-def test_sod_converges_to_exact():
+@pytest.mark.parametrize("recon", [syn.RECON_CONSERVATIVE, syn.RECON_PRIMITIVE, syn.RECON_PRESSURE],
+                         ids=["conservative", "primitive", "pressure"])
+def test_sod_converges_to_exact(recon):
     errs = []
     for nr in (128, 256):
-        xc, rho, _ = _sod_profile(nr)
+        xc, rho, _ = _sod_profile(nr, recon=recon)
         exact = np.array([oracle.riemann(1.4, (1, 0, 1), (0.125, 0, 0.1), S=(x - 0.5) / 0.2)[0][0] for x in xc])
         errs.append(np.abs(rho - exact).mean())
+    print("Sod L1 density errors at 128 and 256 cells", [f"{e:.2e}" for e in errs])
     assert errs[1] < 0.75 * errs[0]
     assert errs[1] < 0.01
 
