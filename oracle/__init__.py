@@ -87,6 +87,7 @@ def lib():
         L.orc_set_species_stokes.argtypes = [ctypes.c_void_p, _D, ctypes.c_int]
         L.orc_set_recon.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.orc_set_dust_recon.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.orc_set_drag_scheme.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.orc_set_vertical_damping.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]
         L.orc_damping_rate.restype = ctypes.c_double
         L.orc_damping_rate.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
@@ -138,6 +139,7 @@ class Oracle:
         self.shape = (self.nf, w.nz, w.nth, w.nr)
         self.status = 0
         self.x_ind = 0.0
+        self.drag_scheme = 0
         if lib().orc_set_recon(self.h, int(w.recon)):
             raise ValueError(f"unknown reconstruction mode {w.recon}")
         if w.drag_kappa:
@@ -191,6 +193,15 @@ class Oracle:
         a local maximum and the flow converges along the axis."""
         if lib().orc_set_dust_recon(self.h, int(mode)):
             raise ValueError(f"unknown dust reconstruction mode {mode}")
+
+    def set_drag_scheme(self, mode):
+        """Drag integration (reading R7): 0 = backward Euler in closed form
+        after each RK2 stage (the default), 1 = Strang splitting, half a step
+        of trapezoidal drag before and after the RK2 step of the other terms.
+        Single stages and sampled steps follow the default only."""
+        if lib().orc_set_drag_scheme(self.h, int(mode)):
+            raise ValueError(f"unknown drag scheme {mode}")
+        self.drag_scheme = int(mode)
 
     def set_damping(self, r_ein, r_eout, period_factor=1.0):
         """Wave-killing zones r < r_ein and r > r_eout (reading R17); a
@@ -247,6 +258,8 @@ class Oracle:
         return G
 
     def stage(self, Ein, Ebase, tau):
+        if self.drag_scheme:
+            raise ValueError("single stages follow the default drag integration")
         Ein = np.ascontiguousarray(Ein, dtype=np.float64)
         Ebase = np.ascontiguousarray(Ebase, dtype=np.float64)
         out = np.zeros_like(Ein)
@@ -271,6 +284,8 @@ class Oracle:
     def step_sampled(self, E, dt, cells):
         if self.x_ind != 0.0:
             raise ValueError("sampled steps need the whole stage state when indirect gravity is on")
+        if self.drag_scheme:
+            raise ValueError("sampled steps follow the default drag integration")
         E = np.ascontiguousarray(E, dtype=np.float64)
         cells = np.ascontiguousarray(cells, dtype=np.int64)
         out = np.zeros((len(cells), self.nf))

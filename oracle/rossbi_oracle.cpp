@@ -73,7 +73,11 @@
 //  R7  semi-implicit drag: after the explicit stage update, a closed-form
 //      backward-Euler relaxation of the gas-dust relative velocity over the
 //      stage length, conserving total momentum; the gas energy changes by the
-//      work of the drag on the gas (no frictional heating).
+//      work of the drag on the gas (no frictional heating).  This couples gas
+//      and dust at first order in time (backward Euler, and the drag split
+//      from the transport after each stage).  Option 1 (oracle only): Strang
+//      splitting, half a step of trapezoidal drag before and after the RK2
+//      step of the other terms, second order (the dusty-wave pin).
 //  R8  equilibrium exponent uses c_iso^2 = P/rho (App. A writes c_s^2).
 //  R9  Newton on p* stops when the relative change is <= 1e-12 (the error
 //      left after that step is far below round-off); PVRS start, floored at
@@ -178,6 +182,11 @@ enum { RECON_CONSERVATIVE = 0, RECON_PRIMITIVE = 1, RECON_PRESSURE = 2 };
 // the velocity used flat in a cell where rho_d is a local maximum and the
 // flow converges along the axis.
 enum { DUST_RECON_PARABOLA = 0, DUST_RECON_FLAT_AT_SPIKES = 1 };
+// Drag integration (reading R7): backward Euler in closed form after each
+// RK2 stage (the default, as the kernels have it), or option 1, Strang
+// splitting: half a step of trapezoidal (Crank-Nicolson) drag before and after
+// an RK2 step of the other terms.
+enum { DRAG_IN_STAGES = 0, DRAG_STRANG_TRAPEZOIDAL = 1 };
 // Dust species s occupies fields 5 + 4 s .. 8 + 4 s (rho_d u_d, rho_d v_d,
 // rho_d w_d, rho_d); species 0 is the single dust fluid above.
 static const int ND_MAX = 4, NFMAX = 5 + 4 * ND_MAX;
@@ -214,6 +223,7 @@ struct Oracle {
   int nd = 0;              // dust species
   int recon = RECON_CONSERVATIVE;  // gas reconstruction (reading R2)
   int dust_recon = DUST_RECON_PARABOLA;  // dust reconstruction (reading R5)
+  int drag_scheme = DRAG_IN_STAGES;      // drag integration (reading R7)
   double st_factor[ND_MAX] = {1.0, 1.0, 1.0, 1.0};  // St_k = St x st_factor[k] (reading R20)
   int status = 0;
   long newton_iters = 0, riemann_calls = 0;
@@ -1022,7 +1032,7 @@ static T stopping_time(const Oracle& o, int i, const T* U, const DustParamsT<T>&
 // solved in closed form, v_k' - v_g' = (v_k - v_g') / (1 + a_k); the gas
 // energy gains the work of the drag on the gas in both.
 template <class T>
-static void drag(const Oracle& o, int i, T* U, double tau, const DustParamsT<T>& dp) {
+static void drag(const Oracle& o, int i, T* U, double tau, const DustParamsT<T>& dp, double theta = 1.0) {
   if (o.nd == 0) return;
   const T rg = U[RHO];
   if (o.nd > 1) {
@@ -1033,19 +1043,22 @@ static void drag(const Oracle& o, int i, T* U, double tau, const DustParamsT<T>&
       const int b = 5 + 4 * sp;
       a[sp] = T(0.0);
       if (!(U[b + 3] > 0.0)) continue;
-      a[sp] = tau / stopping_time(o, i, U, dp, sp);
+      a[sp] = theta * tau / stopping_time(o, i, U, dp, sp);
       const T w = a[sp] / (1.0 + a[sp]);
       den += U[b + 3] * w;
       for (int c = 0; c < 3; ++c) num[c] += U[b + c] * w;  // rho_k v_k a_k / (1 + a_k)
     }
+    // backward Euler over theta tau; the theta-method's step is then
+    // v' = (v_BE - (1 - theta) v) / theta (trapezoidal for theta = 1/2)
     T dE = T(0.0);
     for (int c = 0; c < 3; ++c) {
       const T vg_ex = U[MU + c] / rg;
-      const T vg = num[c] / den;
+      const T vg = (num[c] / den - (1.0 - theta) * vg_ex) / theta;
       for (int sp = 0; sp < o.nd; ++sp) {
         const int b = 5 + 4 * sp;
         if (!(U[b + 3] > 0.0)) continue;
-        U[b + c] = U[b + 3] * ((U[b + c] / U[b + 3] + a[sp] * vg) / (1.0 + a[sp]));
+        const T vk = U[b + c] / U[b + 3];
+        U[b + c] = U[b + 3] * (((vk + a[sp] * (num[c] / den)) / (1.0 + a[sp]) - (1.0 - theta) * vk) / theta);
       }
       U[MU + c] = rg * vg;
       dE += 0.5 * rg * (vg * vg - vg_ex * vg_ex);
@@ -1063,7 +1076,7 @@ static void drag(const Oracle& o, int i, T* U, double tau, const DustParamsT<T>&
   for (int c = 0; c < 3; ++c) {
     const T vg_ex = U[MU + c] / rg;
     const T vd_ex = U[DMU + c] / rd;
-    const T X = mu * (vd_ex - vg_ex) * (kk / (1.0 + kk));
+    const T X = mu * (vd_ex - vg_ex) * (kk / (1.0 + theta * kk));  // theta-method; 1 = backward Euler
     U[MU + c] += X;
     U[DMU + c] -= X;
     dE += 0.5 * X * (U[MU + c] / rg + vg_ex);
@@ -1084,7 +1097,18 @@ static void stage_cell(Oracle& o, const Acc& Ein, const T* Ebase, long lin, doub
     for (int f = 0; f < o.nf; ++f) G[f] -= o.r0[(size_t)f * o.ncell + lin];  // Sect. 2.8 balanced scheme
   const double V = metric(o, i).V;
   for (int f = 0; f < o.nf; ++f) out[f] = Ebase[(size_t)f * o.ncell + lin] + tau * G[f] / V;
-  drag(o, i, out, tau, dp);
+  if (o.drag_scheme == DRAG_IN_STAGES) drag(o, i, out, tau, dp);
+}
+
+// Option 1 of reading R7: half a step of trapezoidal drag on every cell.
+template <class T>
+static void half_drag_all(const Oracle& o, T* E, double dt, const DustParamsT<T>& dp) {
+  T U[NFMAX];
+  for (long lin = 0; lin < o.ncell; ++lin) {
+    for (int f = 0; f < o.nf; ++f) U[f] = E[(size_t)f * o.ncell + lin];
+    drag(o, (int)(lin % o.n[0]), U, 0.5 * dt, dp, 0.5);
+    for (int f = 0; f < o.nf; ++f) E[(size_t)f * o.ncell + lin] = U[f];
+  }
 }
 
 template <class T>
@@ -1275,8 +1299,10 @@ int orc_step(void* h, double* E, double dt, double stokes, int law) {
   Oracle& o = *(Oracle*)h;
   const DustParams dp{stokes, law};
   std::vector<double> Es((size_t)o.nf * o.ncell), En((size_t)o.nf * o.ncell);
+  if (o.drag_scheme == DRAG_STRANG_TRAPEZOIDAL) half_drag_all(o, E, dt, dp);
   stage_all(o, E, E, Es.data(), 0.5 * dt, dp);
   stage_all(o, Es.data(), E, En.data(), dt, dp);
+  if (o.drag_scheme == DRAG_STRANG_TRAPEZOIDAL) half_drag_all(o, En.data(), dt, dp);
   std::memcpy(E, En.data(), sizeof(double) * En.size());
   const int st = o.status;
   o.status = 0;
@@ -1293,8 +1319,10 @@ int orc_step_tlm(void* h, double* E, double* dE, double dt, double stokes, doubl
   const size_t n = (size_t)o.nf * o.ncell;
   std::vector<Dual> X(n), Es(n), En(n);
   for (size_t q = 0; q < n; ++q) X[q] = Dual(E[q], dE[q]);
+  if (o.drag_scheme == DRAG_STRANG_TRAPEZOIDAL) half_drag_all(o, X.data(), dt, dp);
   stage_all(o, X.data(), X.data(), Es.data(), 0.5 * dt, dp);
   stage_all(o, Es.data(), X.data(), En.data(), dt, dp);
+  if (o.drag_scheme == DRAG_STRANG_TRAPEZOIDAL) half_drag_all(o, En.data(), dt, dp);
   for (size_t q = 0; q < n; ++q) {
     E[q] = En[q].v;
     dE[q] = En[q].d;
@@ -1310,6 +1338,7 @@ int orc_step_sampled(void* h, const double* E, double dt, double stokes, int law
                      double* out) {
   Oracle& o = *(Oracle*)h;
   if (o.x_ind != 0.0) return -1;  // the indirect term needs the whole of E*
+  if (o.drag_scheme != DRAG_IN_STAGES) return -1;  // sampled steps follow the default drag
   const DustParams dp{stokes, law};
   LazyStageAcc S{&o, E, 0.5 * dt, dp, {}};
   for (long s = 0; s < ncells; ++s) stage_cell(o, S, E, cells[s], dt, dp, out + (size_t)s * o.nf);
@@ -1412,6 +1441,14 @@ int orc_set_recon(void* h, int mode) {
 int orc_set_dust_recon(void* h, int mode) {
   if (mode != DUST_RECON_PARABOLA && mode != DUST_RECON_FLAT_AT_SPIKES) return 1;
   ((Oracle*)h)->dust_recon = mode;
+  return 0;
+}
+
+// Drag integration of reading R7: 0 = backward Euler after each RK2 stage
+// (the default), 1 = Strang splitting with trapezoidal half steps.
+int orc_set_drag_scheme(void* h, int mode) {
+  if (mode != DRAG_IN_STAGES && mode != DRAG_STRANG_TRAPEZOIDAL) return 1;
+  ((Oracle*)h)->drag_scheme = mode;
   return 0;
 }
 

@@ -1,0 +1,142 @@
+"""Gas-dust coupling (Sect. 2.9; reading R7) against the dusty acoustic wave.
+
+A linear sound wave in a gas carrying a pressureless dust fluid that it drags
+with a fixed stopping time t_s (dust-to-gas ratio eps, the dust relaxing at
+-(u_d - u_g) / t_s and the gas at -eps (u_g - u_d) / t_s) has, for
+perturbations proportional to exp(i (k x - omega t)), u_d = u_g / (1 - i omega
+t_s) and the dispersion relation
+
+    omega^2 (1 + eps / (1 - i omega t_s)) = c^2 k^2,
+
+a cubic in omega (c^2 = gamma P / rho_g: the drag heating is second order).
+Its right-moving, least-damped root is an exact damped travelling wave of the
+linearised equations; the test starts it (amplitude 1e-6 on the periodic
+unit interval, eps = 1, t_s = 0.1, 1, 0.01) and compares the gas and dust
+densities after t = 1.
+
+Pins: with drag option 1 (Strang splitting, half a step of trapezoidal drag
+before and after the RK2 step of the other terms) the errors fall at second
+order for every t_s (measured 2.0 to 2.7 from 32 to 256 cells); the default
+integration of R7 (backward Euler after each RK2 stage, as the kernels have
+it) converges too, but at first order (0.94 to 1.22 where the drag is not
+stiff), its error at 256 cells 5 to 50 times option 1's: the backward-Euler
+relaxation is first order in dt, and applied after a stage it also splits
+the drag from the transport at first order.  Option 1's several-species path
+(the backward-Euler system solved over tau / 2, then v' = 2 v_BE - v) gives
+two half-density twins the one-species result.
+"""
+from dataclasses import replace
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as syn
+
+F_DMU, F_DRHO = 5, 8
+
+
+def _omega(k, c2, eps, ts):
+    """Least-damped right-moving root of -i ts w^3 + (1 + eps) w^2 + i c2 k^2 ts w - c2 k^2 = 0."""
+    roots = np.roots([-1j * ts, 1.0 + eps, 1j * c2 * k * k * ts, -c2 * k * k])
+    om = max((r for r in roots if r.real > 1e-9), key=lambda r: r.imag)
+    assert abs(om * om * (1.0 + eps / (1.0 - 1j * om * ts)) - c2 * k * k) < 1e-9 * c2 * k * k
+    return om
+
+
+def _run(n, ts, scheme, eps=1.0, amp=1e-6, t_end=1.0, species=1):
+    w = replace(syn.SOD, name="dusty_wave", nr=n, nth=1, nz=1, x1=(1.0, 1.0 / n, 1.0 / n),
+                bc_lo=(syn.BC_PERIODIC,) * 3, bc_hi=(syn.BC_PERIODIC,) * 3, n_dust=species, stokes=ts,
+                drag_law=0, dust_stokes_factors=(1.0,) * species if species > 1 else ())
+    o = oracle.Oracle(w)
+    o.set_drag_scheme(scheme)
+    _, xf = o.coords(0)
+    dx = xf[1] - xf[0]
+    g, k = w.gamma, 2.0 * math.pi
+    rg0, rd0, P0 = 1.0, eps, 1.0
+    c2 = g * P0 / rg0
+    om = _omega(k, c2, eps, ts)
+    ug = 1.0
+    ud = ug / (1.0 - 1j * om * ts)
+    rg, rd = rg0 * k * ug / om, rd0 * k * ud / om
+    avg = (np.exp(1j * k * xf[1:]) - np.exp(1j * k * xf[:-1])) / (1j * k * dx)
+
+    def wave(t, a):
+        return (a * amp * avg * np.exp(-1j * om * t)).real
+
+    E = np.zeros(o.shape)
+    E[syn.F_RHO, 0, 0] = rg0 + wave(0.0, rg)
+    E[syn.F_MU, 0, 0] = wave(0.0, rg0 * ug)
+    E[syn.F_EN, 0, 0] = (P0 + wave(0.0, c2 * rg)) / (g - 1.0)
+    for s in range(species):
+        E[F_DRHO + 4 * s, 0, 0] = (rd0 + wave(0.0, rd)) / species
+        E[F_DMU + 4 * s, 0, 0] = wave(0.0, rd0 * ud) / species
+    t = 0.0
+    while t < t_end - 1e-14:
+        dt = min(o.cfl_dt(E), t_end - t)
+        E = o.step(E, dt)
+        t += dt
+    assert o.take_status() == 0
+    dg, dd = wave(t_end, rg), wave(t_end, rd)
+    rho_d = sum(E[F_DRHO + 4 * s, 0, 0] for s in range(species))
+    err_g = np.abs(E[syn.F_RHO, 0, 0] - rg0 - dg).mean() / np.abs(dg).mean()
+    err_d = np.abs(rho_d - rd0 - dd).mean() / np.abs(dd).mean()
+    return err_g, err_d, E
+
+
+@pytest.mark.parametrize("ts", [0.1, 1.0, 0.01])
+def test_dusty_wave_option_1_second_order(ts):
+    res = [_run(n, ts, 1)[:2] for n in (32, 64, 128, 256)]
+    eg = [e for e, _ in res]
+    ed = [e for _, e in res]
+    og = [math.log2(eg[i] / eg[i + 1]) for i in range(3)]
+    od = [math.log2(ed[i] / ed[i + 1]) for i in range(3)]
+    print(f"t_s = {ts}: gas {[f'{e:.2e}' for e in eg]} orders {[f'{p:.2f}' for p in og]}; "
+          f"dust {[f'{e:.2e}' for e in ed]} orders {[f'{p:.2f}' for p in od]}")
+    assert all(p >= 1.9 for p in og), og
+    assert all(p >= 1.8 for p in od), od
+    assert eg[-1] < 5e-4 and ed[-1] < 1e-3
+
+
+@pytest.mark.parametrize("ts", [0.1, 1.0])
+def test_dusty_wave_default_first_order(ts):
+    eg = [_run(n, ts, 0)[0] for n in (32, 64, 128, 256)]
+    og = [math.log2(eg[i] / eg[i + 1]) for i in range(3)]
+    e1 = _run(256, ts, 1)[0]
+    print(f"t_s = {ts}: default {[f'{e:.2e}' for e in eg]} orders {[f'{p:.2f}' for p in og]}; option 1 at 256: {e1:.2e}")
+    assert all(0.8 <= p <= 1.4 for p in og), og      # converges, at first order
+    assert eg[-1] > 5.0 * e1
+
+
+def test_option_1_several_species_twins():
+    _, _, one = _run(64, 0.1, 1)
+    _, _, two = _run(64, 0.1, 1, species=2)
+    np.testing.assert_allclose(two[:5], one[:5], rtol=1e-12, atol=1e-18)
+    np.testing.assert_allclose(two[F_DRHO] + two[F_DRHO + 4], one[F_DRHO], rtol=1e-12, atol=1e-18)
+    np.testing.assert_allclose(two[F_DMU] + two[F_DMU + 4], one[F_DMU], rtol=1e-10, atol=1e-18)
+
+
+def test_option_1_tangent_linear_step():
+    """The tangent-linear step carries option 1's half drag steps: against
+    central differences of the value step, in the direction of the wave's
+    own departure from the uniform state (the limited parabolas are
+    positively homogeneous, so no limiter branch changes along it)."""
+    w = replace(syn.SOD, name="dusty_wave", nr=32, nth=1, nz=1, x1=(1.0, 1.0 / 32, 1.0 / 32),
+                bc_lo=(syn.BC_PERIODIC,) * 3, bc_hi=(syn.BC_PERIODIC,) * 3, n_dust=1, stokes=0.1, drag_law=0)
+    _, _, E = _run(32, 0.1, 1, t_end=0.05)
+    base = np.zeros_like(E)
+    base[syn.F_RHO], base[syn.F_EN], base[F_DRHO] = 1.0, 1.0 / (w.gamma - 1.0), 1.0
+    d = E - base
+    o = oracle.Oracle(w)
+    o.set_drag_scheme(1)
+    dt = o.cfl_dt(E)
+    E1, t = o.step_tlm(E, d, dt)
+    assert np.array_equal(E1, o.step(E, dt))
+    h = 1e-2
+    fd = (o.step(E + h * d, dt) - o.step(E - h * d, dt)) / (2.0 * h)
+    scale = np.abs(fd).max(axis=(1, 2, 3))
+    live = scale > 0.0
+    err = np.abs(t - fd).max(axis=(1, 2, 3))
+    print("relative tangent error per field", err[live] / scale[live])
+    assert np.all(err[live] <= 1e-6 * scale[live])
