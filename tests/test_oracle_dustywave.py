@@ -23,7 +23,9 @@ stiff), its error at 256 cells 5 to 50 times option 1's: the backward-Euler
 relaxation is first order in dt, and applied after a stage it also splits
 the drag from the transport at first order.  Option 1's several-species path
 (the backward-Euler system solved over tau / 2, then v' = 2 v_BE - v) gives
-two half-density twins the one-species result.
+two half-density twins the one-species result, and with two species of
+different stopping times (0.1 and 1) it meets the several-species dispersion
+relation at second order too.
 """
 from dataclasses import replace
 import math
@@ -140,3 +142,71 @@ def test_option_1_tangent_linear_step():
     err = np.abs(t - fd).max(axis=(1, 2, 3))
     print("relative tangent error per field", err[live] / scale[live])
     assert np.all(err[live] <= 1e-6 * scale[live])
+
+
+def _omega_species(k, c2, eps, ts):
+    """Least-damped right-moving root of omega^2 (1 + sum_k eps_k / (1 - i omega t_k)) = c^2 k^2."""
+    P = np.poly1d([1.0 + 0j])
+    for t in ts:
+        P = P * np.poly1d([-1j * t, 1.0])
+    S = np.poly1d([0j])
+    for i, e in enumerate(eps):
+        Q = np.poly1d([e + 0j])
+        for j, t2 in enumerate(ts):
+            if j != i:
+                Q = Q * np.poly1d([-1j * t2, 1.0])
+        S = S + Q
+    poly = np.poly1d([1.0, 0.0, 0.0]) * (P + S) - c2 * k * k * P
+    om = max((r for r in poly.roots if r.real > 1e-9), key=lambda r: r.imag)
+    lhs = om * om * (1.0 + sum(e / (1.0 - 1j * om * t) for e, t in zip(eps, ts)))
+    assert abs(lhs - c2 * k * k) < 1e-9 * c2 * k * k
+    return om
+
+
+def _run_species(n, scheme, ts=(0.1, 1.0), eps=(0.5, 0.5), amp=1e-6, t_end=1.0):
+    w = replace(syn.SOD, name="dusty_wave_species", nr=n, nth=1, nz=1, x1=(1.0, 1.0 / n, 1.0 / n),
+                bc_lo=(syn.BC_PERIODIC,) * 3, bc_hi=(syn.BC_PERIODIC,) * 3, n_dust=len(ts), stokes=ts[0],
+                drag_law=0, dust_stokes_factors=tuple(t / ts[0] for t in ts))
+    o = oracle.Oracle(w)
+    o.set_drag_scheme(scheme)
+    _, xf = o.coords(0)
+    dx = xf[1] - xf[0]
+    g, k = w.gamma, 2.0 * math.pi
+    c2 = g
+    om = _omega_species(k, c2, eps, ts)
+    avg = (np.exp(1j * k * xf[1:]) - np.exp(1j * k * xf[:-1])) / (1j * k * dx)
+
+    def wave(t, a):
+        return (a * amp * avg * np.exp(-1j * om * t)).real
+
+    rg = k / om
+    E = np.zeros(o.shape)
+    E[syn.F_RHO, 0, 0] = 1.0 + wave(0.0, rg)
+    E[syn.F_MU, 0, 0] = wave(0.0, 1.0)
+    E[syn.F_EN, 0, 0] = (1.0 + wave(0.0, c2 * rg)) / (g - 1.0)
+    uds = [1.0 / (1.0 - 1j * om * t) for t in ts]
+    for s, (e, ud) in enumerate(zip(eps, uds)):
+        E[F_DRHO + 4 * s, 0, 0] = e + wave(0.0, e * k * ud / om)
+        E[F_DMU + 4 * s, 0, 0] = wave(0.0, e * ud)
+    t = 0.0
+    while t < t_end - 1e-14:
+        dt = min(o.cfl_dt(E), t_end - t)
+        E = o.step(E, dt)
+        t += dt
+    assert o.take_status() == 0
+    errs = [np.abs(E[syn.F_RHO, 0, 0] - 1.0 - wave(t_end, rg)).mean() / np.abs(wave(t_end, rg)).mean()]
+    for s, (e, ud) in enumerate(zip(eps, uds)):
+        dd = wave(t_end, e * k * ud / om)
+        errs.append(np.abs(E[F_DRHO + 4 * s, 0, 0] - e - dd).mean() / np.abs(dd).mean())
+    return errs
+
+
+def test_dusty_wave_two_species_option_1_second_order():
+    """Two species (t_s = 0.1 and 1, eps = 0.5 each): the several-species
+    dispersion relation omega^2 (1 + sum eps_k / (1 - i omega t_k)) = c^2 k^2;
+    gas and both dust densities converge at second order with option 1."""
+    res = np.array([_run_species(n, 1) for n in (32, 64, 128, 256)])
+    orders = np.log2(res[:-1] / res[1:])
+    print("errors (gas, species 0, species 1):", res[-1], "orders", orders.round(2).tolist())
+    assert np.all(orders >= 1.8), orders
+    assert np.all(res[-1] < 1e-3)
