@@ -18,8 +18,8 @@ Pins: with drag option 1 (Strang splitting, half a step of trapezoidal drag
 before and after the RK2 step of the other terms) the errors fall at second
 order for every t_s (measured 2.0 to 2.7 from 32 to 256 cells); the default
 integration of R7 (backward Euler after each RK2 stage, as the kernels have
-it) converges too, but at first order (0.94 to 1.22 where the drag is not
-stiff), its error at 256 cells 5 to 50 times option 1's: the backward-Euler
+it) converges too, but at first order (0.94 to 1.22 for t_s = 0.1 and 1),
+its error at 256 cells 14 and 49 times option 1's there: the backward-Euler
 relaxation is first order in dt, and applied after a stage it also splits
 the drag from the transport at first order.  Option 1's several-species path
 (the backward-Euler system solved over tau / 2, then v' = 2 v_BE - v) gives
