@@ -27,10 +27,11 @@ Smooth flow, the other side of the trade: dust at rest density 1 with
 u = 0.1 sin(2 pi x), periodic, converges at x = 1/2 and diverges at x = 0;
 until the characteristics cross (t = 1 / (0.2 pi) = 1.59) the solution is
 smooth, x = x0 + u0(x0) t, rho = 1 / (1 + u0'(x0) t), u = u0(x0).  At t = 1
-the density error falls with the mesh in both options (L1 orders 1.6 to 1.8
-from 64 to 512 cells; the limiter clips the sharpening maximum).  Flattening
-the velocity at every density extremum instead, minima included, stalls the
-outflow of the diverging minimum and does not converge (1e-2 at every mesh).
+the density error falls with the mesh in both options (L1 orders 1.6 to 1.7
+for the parabola, 1.4 to 2.1 for option 1, from 64 to 512 cells; the limiter
+clips the sharpening maximum).  Flattening the velocity at every density
+extremum instead, minima included, stalls the outflow of the diverging
+minimum and does not converge (6e-3 to 1.3e-2 at every mesh).
 """
 from dataclasses import replace
 import math
