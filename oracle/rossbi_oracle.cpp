@@ -138,11 +138,14 @@
 // Parity unpinned (readings checked only for their properties and for
 // self-consistency, since the paper gives no formula or value to test them
 // against): the exact MinMod rule of R2 (pinned: exact on quadratics, flat at
-// extrema, no new extrema, Lipschitz), the dust flux of R5 (pinned: its case
-// table and conservation), the drag integrator of R7 (pinned: its closed form
-// and the exponential limit), the vortex initial condition (a recipe of the
-// workloads), and the wave-killing profile and constants of R17 (pinned: its
-// structure).
+// extrema, no new extrema, Lipschitz; second-order convergence on smooth
+// waves), the dust flux of R5 (pinned: its case table, conservation, and the
+// delta-shock and smooth-compression solutions of pressureless gas), the drag
+// integrator of R7 (pinned: its closed form, the exponential limit, and its
+// first-order convergence to the dusty acoustic wave), the vortex initial
+// condition (a recipe of the workloads; its velocity is pinned against the
+// recipe's stream function), and the wave-killing profile and constants of
+// R17 (pinned: its structure).
 //
 // Tangent-linear mode (the paper has none; it pins the GPU adjoint).  The
 // numeric core is written for a scalar type T and also instantiated with a
