@@ -14,6 +14,7 @@ import math
 from dataclasses import replace
 
 import numpy as np
+import pytest
 
 import oracle
 import synthetic as syn
@@ -63,11 +64,16 @@ def test_dust_settles_at_terminal_velocity():
     assert settling_error(w, E, o.coords(2)[0], o.coords(0)[0]) <= 1e-2
 
 
-def test_dust_drifts_at_the_nsh_rate():
-    w = drift_workload()
+@pytest.mark.parametrize("stokes,steps", [(0.01, 400), (0.1, 400), (1.0, 2400)],
+                         ids=["st_0.01", "st_0.1", "st_1"])
+def test_dust_drifts_at_the_nsh_rate(stokes, steps):
+    """Across the drift's maximum at St = 1 (the rate goes as St / (1 + St^2));
+    each run covers several stopping times: 400 steps are ~1.8 time units,
+    2400 ~10.6 (measured errors 0.74 %, 0.29 %, 0.52 %)."""
+    w = replace(drift_workload(), stokes=stokes)
     o = oracle.Oracle(w)
     E = oracle.initial_state(o)
-    for _ in range(400):  # ~1.8 time units: a few stopping times and a quarter orbit
+    for _ in range(steps):
         E = o.step(E, o.cfl_dt(E))
     assert o.take_status() == 0
     rc = o.coords(0)[0]
